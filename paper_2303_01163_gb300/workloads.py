@@ -1,0 +1,167 @@
+"""Seeded synthetic inputs for the advection-diffusion problems ASDSM solves.
+
+This module only draws problem data (coefficients, source term s, boundary
+data g) on the uniform grid; it holds none of the method's arithmetic.  Both
+the CPU oracle and the CUDA path consume what it returns, so it imports
+neither of them.
+
+Grid convention (shared by every caller): a d-dimensional array with ``N``
+points per axis including the boundary, point ``x_i = i / (N - 1)``, axis
+order (z, y, x) so that x is the fastest-varying index (the vector ordering
+of Section 2.2 of the paper).
+
+Workload families (the paper's experiments use manufactured solutions only,
+Section 4; there is no dataset):
+
+* ``manufactured_sine_2d`` - u = sin(pi x) sin(pi y) with s derived from
+  eq. (1.1) and g = u on the boundary (the smooth setting of Example 1, with
+  the sine product instead of sin(pi x + pi y)).
+* ``random_fourier_2d`` - alpha_i log-uniform in [1e-2, 1], beta_i uniform
+  in [-10, 10], s a sum of 16 random sine modes, zero Dirichlet data.
+* ``manufactured_sine_3d`` / ``random_fourier_3d`` - the 3D analogues.
+* ``polynomial_2d`` - u = p(x) q(y) with quadratic p, q: central differences
+  are exact for it on every uniform mesh, which pins the whole initial guess.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Problem:
+    """One Dirichlet problem for eq. (1.1) sampled on a uniform grid."""
+
+    d: int
+    N: int
+    alpha: tuple
+    beta: tuple
+    s: np.ndarray          # source term on the full grid (boundary entries unused)
+    g: np.ndarray          # full grid: boundary entries carry the Dirichlet data, interior 0
+    u_exact: np.ndarray | None = None   # continuous solution sampled on the grid, if known
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def unknowns(self) -> int:
+        return (self.N - 2) ** self.d
+
+
+def _axes(N: int, d: int):
+    x = np.linspace(0.0, 1.0, N)
+    return np.meshgrid(*([x] * d), indexing="ij")  # returns (z, y, x) order for d=3 when reversed
+
+
+def _grid2(N):
+    x = np.linspace(0.0, 1.0, N)
+    Y, X = np.meshgrid(x, x, indexing="ij")   # [y, x]
+    return X, Y
+
+
+def _grid3(N):
+    x = np.linspace(0.0, 1.0, N)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")   # [z, y, x]
+    return X, Y, Z
+
+
+def _boundary_only(u: np.ndarray) -> np.ndarray:
+    g = np.zeros_like(u)
+    sl = [slice(1, -1)] * u.ndim
+    g[...] = u
+    g[tuple(sl)] = 0.0
+    return g
+
+
+def manufactured_sine_2d(N: int, alpha=(1.0, 1.0), beta=(1.0, 1.0)) -> Problem:
+    X, Y = _grid2(N)
+    ax, ay = alpha
+    bx, by = beta
+    pi = np.pi
+    u = np.sin(pi * X) * np.sin(pi * Y)
+    s = ((ax + ay) * pi**2 * np.sin(pi * X) * np.sin(pi * Y)
+         + bx * pi * np.cos(pi * X) * np.sin(pi * Y)
+         + by * pi * np.sin(pi * X) * np.cos(pi * Y))
+    return Problem(2, N, tuple(alpha), tuple(beta), s, _boundary_only(u), u,
+                   name=f"sine2d_N{N}")
+
+
+def manufactured_shifted_sine_2d(N: int, alpha=(1.0, 1.0), beta=(1.0, 1.0), k: float = 1.0) -> Problem:
+    """u = sin(k pi x + k pi y): Example 1 of Section 4 (k=1 smooth, k=4 oscillatory)."""
+    X, Y = _grid2(N)
+    ax, ay = alpha
+    bx, by = beta
+    w = k * np.pi
+    u = np.sin(w * X + w * Y)
+    s = (ax + ay) * w**2 * u + (bx + by) * w * np.cos(w * X + w * Y)
+    return Problem(2, N, tuple(alpha), tuple(beta), s, _boundary_only(u), u,
+                   name=f"shiftsine2d_k{k}_N{N}")
+
+
+def polynomial_2d(N: int, alpha=(1.0, 1.0), beta=(1.0, 1.0),
+                  p=(0.3, -1.2, 2.0), q=(1.1, 0.7, -1.5)) -> Problem:
+    """u = p(x) q(y), p and q quadratics (coefficients low to high order)."""
+    X, Y = _grid2(N)
+    ax, ay = alpha
+    bx, by = beta
+    P = p[0] + p[1] * X + p[2] * X**2
+    Px = p[1] + 2 * p[2] * X
+    Pxx = 2 * p[2] + 0 * X
+    Q = q[0] + q[1] * Y + q[2] * Y**2
+    Qy = q[1] + 2 * q[2] * Y
+    Qyy = 2 * q[2] + 0 * Y
+    u = P * Q
+    s = -ax * Pxx * Q - ay * P * Qyy + bx * Px * Q + by * P * Qy
+    return Problem(2, N, tuple(alpha), tuple(beta), s, _boundary_only(u), u,
+                   name=f"poly2d_N{N}")
+
+
+def random_coefficients(rng: np.random.Generator, d: int, beta_max: float):
+    alpha = tuple(float(a) for a in 10.0 ** rng.uniform(-2.0, 0.0, d))
+    beta = tuple(float(b) for b in rng.uniform(-beta_max, beta_max, d))
+    return alpha, beta
+
+
+def random_fourier_2d(N: int, seed: int, modes: int = 16, kmax: int = 32,
+                      beta_max: float = 10.0) -> Problem:
+    """alpha_i log-uniform in [1e-2,1], beta_i ~ U(-beta_max, beta_max),
+    s = sum_m a_m sin(k_m pi x) sin(l_m pi y), a_m ~ N(0,1), k_m,l_m ~ U{1..kmax}, g = 0."""
+    rng = np.random.default_rng(seed)
+    alpha, beta = random_coefficients(rng, 2, beta_max)
+    a = rng.normal(size=modes)
+    k = rng.integers(1, kmax + 1, modes)
+    l = rng.integers(1, kmax + 1, modes)
+    x = np.linspace(0.0, 1.0, N)
+    sx = np.sin(np.pi * np.outer(k, x))      # [m, x]
+    sy = np.sin(np.pi * np.outer(l, x))      # [m, y]
+    s = np.einsum("m,my,mx->yx", a, sy, sx)
+    g = np.zeros((N, N))
+    return Problem(2, N, alpha, beta, s, g, None, name=f"fourier2d_N{N}_seed{seed}",
+                   meta={"a": a, "k": k, "l": l, "seed": seed})
+
+
+def manufactured_sine_3d(N: int, alpha=(1.0, 1.0, 1.0), beta=(1.0, 1.0, 1.0)) -> Problem:
+    X, Y, Z = _grid3(N)
+    ax, ay, az = alpha
+    bx, by, bz = beta
+    pi = np.pi
+    sx, sy, sz = np.sin(pi * X), np.sin(pi * Y), np.sin(pi * Z)
+    cx, cy, cz = np.cos(pi * X), np.cos(pi * Y), np.cos(pi * Z)
+    u = sx * sy * sz
+    s = (ax + ay + az) * pi**2 * u + pi * (bx * cx * sy * sz + by * sx * cy * sz + bz * sx * sy * cz)
+    return Problem(3, N, tuple(alpha), tuple(beta), s, _boundary_only(u), u, name=f"sine3d_N{N}")
+
+
+def random_sine_3d(N: int, seed: int, beta_max: float = 5.0) -> Problem:
+    """Random alpha_i log-uniform in [1e-2,1], beta_i ~ U(-beta_max, beta_max), u = prod sin(pi x_i)."""
+    rng = np.random.default_rng(seed)
+    alpha, beta = random_coefficients(rng, 3, beta_max)
+    p = manufactured_sine_3d(N, alpha, beta)
+    p.name = f"randsine3d_N{N}_seed{seed}"
+    p.meta["seed"] = seed
+    return p
+
+
+def batch_sizes(count: int, seed: int, choices=(129, 257, 513, 1025, 2049)):
+    rng = np.random.default_rng(seed)
+    return [int(c) for c in rng.choice(np.asarray(choices), size=count)]
