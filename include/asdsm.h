@@ -1,0 +1,163 @@
+/*
+ * asdsm.h - C ABI of the GB300 (sm_103a) implementation of the Anisotropic
+ * Submeshes Domain Splitting Method (ASDSM) of K. Trotti, "A domain splitting
+ * strategy for solving PDEs" (arXiv 2303.01163).
+ *
+ * The library solves the steady advection-diffusion equation (eq. 1.1)
+ *     sum_i ( -alpha_i d^2u/dx_i^2 + beta_i du/dx_i ) = s   on the unit square,
+ *     u = g                                              on its boundary,
+ * discretised by second-order centred finite differences on a uniform grid
+ * (Section 2.3), by iterating Algorithm 4 (ASDSM) of Section 3.2 on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid arrays are dense FP64, x fastest (the vector ordering of Section 2.2):
+ * element (i, j) of an N x N grid (point x = i/(N-1), y = j/(N-1)) is at
+ * offset j*N + i.  Arrays cover the whole grid INCLUDING the boundary ring.
+ * All array arguments are DEVICE pointers owned by the caller (for example
+ * PyTorch tensors); the library never frees them.  Work is enqueued on the
+ * CUDA stream given to asdsm_setup.  Functions that report results to the
+ * host (asdsm_solve, asdsm_residual, asdsm_initial_guess) synchronise that
+ * stream before returning; the others return once the work is enqueued.
+ *
+ * Sizes: N - 1 must be a power of two (N = 2^p + 1, p >= 2) and mc (coarse
+ * intervals per axis, the N_c + 1 of eq. 2.1) a power of two with
+ * 2 <= mc <= (N - 1)/4, so every line, submesh and hole system has
+ * 2^q - 1 unknowns per axis.  Other sizes return ASDSM_ERR_INVALID.
+ *
+ * Errors: every int-returning function returns ASDSM_OK (0) or a negative
+ * code (see asdsm_strerror).  The library never aborts or traps; after an
+ * error the handle stays valid and may be destroyed or reused.
+ */
+#ifndef ASDSM_H
+#define ASDSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define ASDSM_OK                 0
+#define ASDSM_ERR_INVALID       -1   /* bad argument: sizes violate eq. 2.1 / powers of two, alpha <= 0, null pointer */
+#define ASDSM_ERR_CUDA          -2   /* a CUDA runtime call failed (message in asdsm_last_error) */
+#define ASDSM_ERR_OOM           -3   /* device allocation failed */
+#define ASDSM_ERR_NAN           -4   /* a NaN/Inf appeared in the residual (bad input data) */
+#define ASDSM_NOT_CONVERGED     -5   /* max_sweeps reached above tol; u holds the last iterate */
+#define ASDSM_STAGNATED         -6   /* residual stopped decreasing (Remark after Alg. 4); u holds the last iterate */
+#define ASDSM_ERR_RANGE         -7   /* mixed path: the fixed-point accumulator would overflow */
+
+/* ---- precision modes ---------------------------------------------------- */
+#define ASDSM_FP64   0   /* every step in FP64 (the plain method) */
+#define ASDSM_MIXED  1   /* submesh solves, merge, fill and directions in FP32; residual and
+                            accumulation exact to FP64 level (64-bit fixed-point u, FP32-pair
+                            arithmetic for the residual) */
+
+/* Problem description: one instance of eq. (1.1) on the unit square (d = 2). */
+typedef struct {
+    int32_t d;          /* space dimension; 2 */
+    int32_t n;          /* grid points per axis including the boundary (N) */
+    int32_t mc;         /* coarse intervals per axis (N_c + 1 in eq. 2.1) */
+    int32_t pad_;
+    double  alpha[3];   /* diffusion per axis, > 0 (x, y[, z]) */
+    double  beta[3];    /* advection per axis (x, y[, z]) */
+} asdsm_desc;
+
+/* Iteration options (Algorithm 4 and the readings listed in the design doc). */
+typedef struct {
+    double   tol;               /* stop when ||b - A u||_2 / ||b||_2 <= tol */
+    int32_t  max_sweeps;        /* sweeps of Algorithm 4 (hole corrections count as sweeps) */
+    int32_t  precision;         /* ASDSM_FP64 or ASDSM_MIXED */
+    int32_t  accel_m;           /* 1: the paper's step 6 (s_hat >= 0); m > 1: restarted GCR(m) with the
+                                   Algorithm-1 correction as flexible preconditioner */
+    int32_t  skip_initial_guess;/* 1: start from the interior of u as given (resume); 0: Algorithm 1 */
+    uint64_t seed;              /* SplitMix64 seed of the random choice of Algorithm 2 step 3 */
+    double   hole_fix_ratio;    /* re-fill holes when ||r_holes|| > ratio*||r|| ... */
+    double   hole_fix_growth;   /* ... and > growth * (hole residual after the last fill) */
+    int32_t  stagnation_window; /* stagnated if ||r_k|| > (1 - stagnation_factor) ||r_{k-window}|| */
+    int32_t  pad_;
+    double   stagnation_factor;
+} asdsm_opts;
+
+/* Per-solve statistics. */
+typedef struct {
+    int32_t sweeps;        /* sweeps performed (including hole corrections) */
+    int32_t status;        /* ASDSM_OK, ASDSM_NOT_CONVERGED, ASDSM_STAGNATED, ... */
+    int32_t hole_fixes;    /* hole-residual corrections performed */
+    int32_t fixed_shift;   /* mixed path: u = U * 2^-fixed_shift; 0 on the FP64 path */
+    double  rel_res;       /* final ||b - A u|| / ||b|| */
+    double  rel_res0;      /* relative residual of the initial iterate */
+    double  setup_ms;      /* right-hand sides + initial guess, GPU time */
+    double  solve_ms;      /* whole call, GPU time */
+} asdsm_stats;
+
+typedef struct asdsm_handle asdsm_handle;
+
+/* Fill *opts with the defaults: tol 1e-10, max_sweeps 500, ASDSM_MIXED,
+ * accel_m 8, seed 0, hole_fix_ratio 0.25, hole_fix_growth 4, stagnation
+ * window 10 with factor 1e-3, skip_initial_guess 0. */
+void asdsm_default_opts(asdsm_opts* opts);
+
+/* Create a solver for one problem (eq. 1.1 with desc's sizes and
+ * coefficients).  Precomputes, in FP64 on the host, the block cyclic
+ * reduction factors of every submesh operator of eq. (2.4) (A_fc, A_cf, A_cc
+ * and the hole blocks A_(ij) of Remark 2.4) and the spline operator of
+ * Algorithm 2, uploads them, and allocates all device work space.
+ * stream: a cudaStream_t (NULL = legacy default stream).  The handle keeps
+ * the stream; opts are copied.  Returns ASDSM_ERR_INVALID for sizes that
+ * violate eq. (2.1) or the power-of-two rule, ASDSM_ERR_OOM if allocation
+ * fails.  *out is NULL on error. */
+int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, asdsm_handle** out);
+
+/* Replace the iteration options of an existing handle (e.g. precision). */
+int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts);
+
+/* Algorithm 4 (ASDSM).  s: device N*N source term (boundary entries unused).
+ * u: device N*N; its boundary ring carries the Dirichlet data g on input and
+ * is never written; its interior is overwritten by the solution (or used as
+ * the first iterate when opts.skip_initial_guess is set).  stats may be NULL.
+ * Returns ASDSM_OK when tol was reached, ASDSM_NOT_CONVERGED or
+ * ASDSM_STAGNATED otherwise (u then holds the last iterate), or an error. */
+int asdsm_solve(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats);
+
+/* Algorithm 1 with b_cc given (the initial guess u^(0)).  Same s/u contract
+ * as asdsm_solve; writes the interior of u. */
+int asdsm_initial_guess(asdsm_handle* h, const double* s, double* u);
+
+/* Fine residual of Algorithm 4 step 3: r = b_ff - A_ff u over the interior,
+ * b_ff being s plus the Dirichlet lifting of u's boundary ring.  s, u:
+ * device N*N.  r: device N*N or NULL; when given, its interior receives r and
+ * its boundary ring zeros.  rel_norm (host, may be NULL) receives
+ * ||r||_2/||b_ff||_2.  Always computed in FP64. */
+int asdsm_residual(asdsm_handle* h, const double* s, const double* u, double* r, double* rel_norm);
+
+/* Direct solve of one family of the linear systems of eq. (2.4) by the
+ * library's block cyclic reduction, in the handle's precision (for checking
+ * a single step against a reference).  mesh:
+ *   0 = A_fc on Omega^{h,H}: in/out hold N_c*N_f values, layout [line j][x]
+ *   1 = A_cf on Omega^{H,h}: layout [y][column i]
+ *   2 = A_cc on Omega^{H,H}: layout [y][x]
+ *   3 = the holes (P A P^T of Algorithm 3): in/out are N*N grids; only hole
+ *       points are read and written (others are left untouched in out).
+ * in/out: device FP64 arrays; they may not alias. */
+int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out);
+
+/* Relative residual after each completed sweep of the last asdsm_solve
+ * (entry 0: initial iterate).  Copies min(cap, sweeps+1) values to the host
+ * array hist and returns that count (or a negative error). */
+int asdsm_history(asdsm_handle* h, double* hist, int cap);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+void asdsm_destroy(asdsm_handle* h);
+
+/* Static description of a status code. */
+const char* asdsm_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* asdsm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASDSM_H */

@@ -59,10 +59,11 @@ R15 Refinement to tight tolerances: with accel_m > 1 the correction e of
 R18 Hole residual.  In exact arithmetic the residual vanishes in the holes
     (Prop. 3.1).  When rounding has made its hole part exceed both
     hole_fix_ratio * ||r|| and hole_fix_growth times its value just after
-    the last Filler, the sweep is replaced by Algorithm 3 applied to the
-    current iterate: its step 1 then gives c = -P A u, so step 2 solves the
-    hole systems with the hole part of the current residual and zeroes it
-    (down to rounding).  The GCR cycle restarts afterwards.
+    the last such correction (zero before the first one), the sweep is
+    replaced by Algorithm 3 applied to the current iterate: its step 1 then
+    gives c = -P A u, so step 2 solves the hole systems with the hole part of
+    the current residual and zeroes it (down to rounding).  The GCR cycle
+    restarts afterwards.
 """
 from __future__ import annotations
 
@@ -319,7 +320,7 @@ def asdsm(disc: Discretisation2D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
     nb = np.linalg.norm(b_ff)
     hist, steps, bits, kinds, iterates = [], [], [], [], []
     Z, Q = [], []                    # GCR cycle: directions and their A-images on the skeleton
-    hole_ref = None                  # hole residual norm right after the last Filler
+    hole_ref = 0.0                   # hole residual norm right after the last correction (R18)
     status = "max_sweeps"
     k = 0                                                         # step 2
     while True:
@@ -338,8 +339,6 @@ def asdsm(disc: Discretisation2D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
             status = "stagnated"
             break
         hole_norm = np.linalg.norm(disc.P_ff_holes @ r)
-        if hole_ref is None:
-            hole_ref = hole_norm
         if hole_norm > hole_fix_ratio * np.linalg.norm(r) and hole_norm > hole_fix_growth * hole_ref:
             u = disc.filler(u, b_ff)                              # R18
             hole_ref = np.linalg.norm(disc.P_ff_holes @ disc.residual(b_ff, u))

@@ -1,0 +1,217 @@
+"""Python binding of the C ABI in include/asdsm.h (argument marshalling only).
+
+Every step of ASDSM runs in libasdsm.so on the GPU; this module only passes
+device pointers of PyTorch tensors, the current CUDA stream and plain
+structs.  It raises if the library is missing: there is no CPU fallback.
+
+    import torch
+    from paper_2303_01163_gb300 import asdsm
+    solver = asdsm.Solver(N=1025, mc=64, alpha=(1, 1), beta=(1, 1))
+    u = torch.zeros(N, N, dtype=torch.float64, device="cuda")   # ring = g
+    stats = solver.solve(s, u)                                  # s: (N, N) float64 on the GPU
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libasdsm.so")
+
+OK = 0
+ERR_INVALID = -1
+ERR_CUDA = -2
+ERR_OOM = -3
+ERR_NAN = -4
+NOT_CONVERGED = -5
+STAGNATED = -6
+ERR_RANGE = -7
+
+FP64 = 0
+MIXED = 1
+
+MESH_FC, MESH_CF, MESH_CC, MESH_HOLES = 0, 1, 2, 3
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("n", ctypes.c_int32), ("mc", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("alpha", ctypes.c_double * 3), ("beta", ctypes.c_double * 3)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("accel_m", ctypes.c_int32), ("skip_initial_guess", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("hole_fix_ratio", ctypes.c_double), ("hole_fix_growth", ctypes.c_double),
+                ("stagnation_window", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("stagnation_factor", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("status", ctypes.c_int32), ("hole_fixes", ctypes.c_int32),
+                ("fixed_shift", ctypes.c_int32), ("rel_res", ctypes.c_double), ("rel_res0", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load libasdsm.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libasdsm.so not built ({_LIB_PATH}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.c_void_p
+    lib.asdsm_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.asdsm_default_opts.restype = None
+    lib.asdsm_setup.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(Opts), P, ctypes.POINTER(P)]
+    lib.asdsm_setup.restype = ctypes.c_int
+    lib.asdsm_set_opts.argtypes = [P, ctypes.POINTER(Opts)]
+    lib.asdsm_set_opts.restype = ctypes.c_int
+    lib.asdsm_solve.argtypes = [P, P, P, ctypes.POINTER(Stats)]
+    lib.asdsm_solve.restype = ctypes.c_int
+    lib.asdsm_initial_guess.argtypes = [P, P, P]
+    lib.asdsm_initial_guess.restype = ctypes.c_int
+    lib.asdsm_residual.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_double)]
+    lib.asdsm_residual.restype = ctypes.c_int
+    lib.asdsm_submesh_solve.argtypes = [P, ctypes.c_int, P, P]
+    lib.asdsm_submesh_solve.restype = ctypes.c_int
+    lib.asdsm_history.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    lib.asdsm_history.restype = ctypes.c_int
+    lib.asdsm_destroy.argtypes = [P]
+    lib.asdsm_destroy.restype = None
+    lib.asdsm_strerror.argtypes = [ctypes.c_int]
+    lib.asdsm_strerror.restype = ctypes.c_char_p
+    lib.asdsm_last_error.argtypes = []
+    lib.asdsm_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class AsdsmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        lib = load()
+        msg = lib.asdsm_strerror(code).decode()
+        extra = lib.asdsm_last_error().decode()
+        super().__init__(f"{what}: {msg} ({code})" + (f": {extra}" if extra else ""))
+        self.code = code
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    load().asdsm_default_opts(ctypes.byref(o))
+    return o
+
+
+def _ptr(t, dtype_name="float64"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected torch.{dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class SolveResult:
+    status: int
+    stats: dict
+    history: list
+
+
+class Solver:
+    """One problem of eq. (1.1) on an N x N grid (the handle of asdsm_setup)."""
+
+    def __init__(self, N: int, mc: int, alpha, beta, *, precision: int = MIXED, tol: float = 1e-10,
+                 max_sweeps: int = 500, accel_m: int = 8, seed: int = 0, stream=None, **opt_overrides):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.N, self.mc = int(N), int(mc)
+        d = Desc()
+        d.d = 2
+        d.n = self.N
+        d.mc = self.mc
+        for q in range(2):
+            d.alpha[q] = float(alpha[q])
+            d.beta[q] = float(beta[q])
+        o = default_opts()
+        o.tol, o.max_sweeps, o.precision, o.accel_m, o.seed = tol, max_sweeps, precision, accel_m, seed
+        for k, v in opt_overrides.items():
+            setattr(o, k, v)
+        self.opts = o
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        rc = lib.asdsm_setup(ctypes.byref(d), ctypes.byref(o), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_setup")
+        self._h = h
+
+    def set_opts(self, **kw):
+        for k, v in kw.items():
+            setattr(self.opts, k, v)
+        rc = self._lib.asdsm_set_opts(self._h, ctypes.byref(self.opts))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_set_opts")
+
+    def solve(self, s, u, check: bool = True) -> SolveResult:
+        st = Stats()
+        rc = self._lib.asdsm_solve(self._h, _ptr(s), _ptr(u), ctypes.byref(st))
+        if rc not in (OK, NOT_CONVERGED, STAGNATED) and check:
+            raise AsdsmError(rc, "asdsm_solve")
+        return SolveResult(rc, st.as_dict(), self.history())
+
+    def initial_guess(self, s, u):
+        rc = self._lib.asdsm_initial_guess(self._h, _ptr(s), _ptr(u))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_initial_guess")
+
+    def residual(self, s, u, r=None) -> float:
+        rel = ctypes.c_double()
+        rc = self._lib.asdsm_residual(self._h, _ptr(s), _ptr(u), _ptr(r) if r is not None else None, ctypes.byref(rel))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_residual")
+        return rel.value
+
+    def submesh_solve(self, mesh: int, inp, out):
+        rc = self._lib.asdsm_submesh_solve(self._h, int(mesh), _ptr(inp), _ptr(out))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_submesh_solve")
+
+    def history(self) -> list:
+        cap = 100000
+        buf = (ctypes.c_double * cap)()
+        n = self._lib.asdsm_history(self._h, buf, cap)
+        if n < 0:
+            raise AsdsmError(n, "asdsm_history")
+        return [buf[i] for i in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.asdsm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

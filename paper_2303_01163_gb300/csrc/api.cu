@@ -1,0 +1,785 @@
+// C ABI of the ASDSM library (include/asdsm.h) and the host orchestration of
+// Algorithm 4 on one GPU stream.
+//
+// Per sweep (all on the handle's stream):
+//   residual kernel  : step 7 of the previous sweep fused with step 3
+//                      (u += sum_j delta_j z_j ; r = b - A u ; r on the skeleton
+//                      gathered for steps 4.1/4.2 and the least squares)
+//   bcr_solve        : steps 1.1/1.2 of Algorithm 1 (both families in one batch)
+//   multi_dot        : norms of step 2 of Algorithm 1
+//   merge_knots/write: Algorithm 2 (random choice, spline correction, merge)
+//   fill_holes       : Algorithm 3 with 0 b
+//   skeleton_apply   : A e on the skeleton rows (step 6 least squares)
+//   multi_dot        : the least-squares / GCR(m) inner products
+// The host reads two small reductions per sweep (the residual norms and the
+// least-squares inner products) and keeps the m x m GCR bookkeeping.
+#include "asdsm.h"
+#include "asdsm_internal.h"
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstring>
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+using namespace asdsm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr int kMaxM = 16;
+
+struct DevBcr {
+    void* Pt = nullptr; void* Qt = nullptr; void* Bt = nullptr;
+    int R = 0, C = 0, L = 0;
+};
+
+uint64_t splitmix64_out(uint64_t state) {
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+// Coin of Algorithm 2 step 3 at sweep k: top bit of SplitMix64 output k.
+int choice_bit(uint64_t seed, int k) {
+    const uint64_t state = seed + (uint64_t)(k + 1) * 0x9E3779B97F4A7C15ULL;
+    return (int)(splitmix64_out(state) >> 63);
+}
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+struct asdsm_handle {
+    asdsm_desc desc{};
+    asdsm_opts opts{};
+    cudaStream_t st = nullptr;
+    int num_sms = 152;
+    Geometry g{};
+    Stencil sten{};
+    double alpha[2]{}, beta[2]{};
+    // Factors: [0] = FP64, [1] = FP32.
+    DevBcr fc[2], cf[2], cc[2], hole[2];
+    void* Sm[2] = {nullptr, nullptr};
+    // Work buffers, per precision (allocated on first use).
+    struct Work {
+        bool ready = false;
+        void* Xfc = nullptr; void* Xcf = nullptr; void* Yfc = nullptr; void* Ycf = nullptr;
+        void* Xcc = nullptr; void* Ycc = nullptr;
+        void* E1 = nullptr; void* E2 = nullptr; void* M1 = nullptr; void* M2 = nullptr;
+        void* z[kMaxM] = {};
+        int nz = 0;
+        void* rskel = nullptr; void* q = nullptr;
+        void* qp[kMaxM] = {};
+        void* rfull = nullptr;   // full-grid residual for hole corrections
+    } w[2];
+    double* u_work = nullptr;       // FP64 ping-pong partner of the caller's u
+    long long* U[2] = {nullptr, nullptr};
+    float* s_hi = nullptr; float* s_lo = nullptr;
+    double* partials = nullptr;     // reduction scratch
+    int partials_cap = 0;
+    double* dsmall = nullptr;       // small device results (norms, dots)
+    int* dflag = nullptr;
+    double* hsmall = nullptr;       // pinned host mirror of dsmall
+    std::vector<double> hist;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+};
+
+namespace {
+
+int set_cuda_error(cudaError_t e) {
+    g_last_error = cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? ASDSM_ERR_OOM : ASDSM_ERR_CUDA;
+}
+
+#define CK(...)                                         \
+    do {                                                \
+        cudaError_t e__ = (__VA_ARGS__);                \
+        if (e__ != cudaSuccess) return set_cuda_error(e__); \
+    } while (0)
+
+template <typename T>
+int upload_bcr(const BcrFactors& f, DevBcr* d) {
+    const size_t n = f.Pt.size();
+    std::vector<T> tmp(n);
+    void** dst[3] = {&d->Pt, &d->Qt, &d->Bt};
+    const std::vector<double>* src[3] = {&f.Pt, &f.Qt, &f.Bt};
+    for (int q = 0; q < 3; ++q) {
+        CK(cudaMalloc(dst[q], n * sizeof(T)));
+        for (size_t e = 0; e < n; ++e) tmp[e] = (T)(*src[q])[e];
+        CK(cudaMemcpy(*dst[q], tmp.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    d->R = f.R; d->C = f.C; d->L = f.L;
+    return ASDSM_OK;
+}
+
+template <typename T>
+int upload_vec(const std::vector<double>& v, void** d) {
+    std::vector<T> tmp(v.begin(), v.end());
+    CK(cudaMalloc(d, std::max<size_t>(1, tmp.size()) * sizeof(T)));
+    if (!tmp.empty()) CK(cudaMemcpy(*d, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ASDSM_OK;
+}
+
+template <typename T>
+BcrSys<T> sys_of(const DevBcr& d, void* X, void* Y, int nsys = 1) {
+    BcrSys<T> s{};
+    s.X = (T*)X; s.Y = (T*)Y;
+    s.Pt = (const T*)d.Pt; s.Qt = (const T*)d.Qt; s.Bt = (const T*)d.Bt;
+    s.R = d.R; s.C = d.C; s.L = d.L; s.nsys = nsys;
+    s.stride = (long long)d.R * d.C;
+    return s;
+}
+
+template <typename T>
+int ensure_work(asdsm_handle* h, int pi) {
+    auto& w = h->w[pi];
+    const Geometry& g = h->g;
+    const int m = std::max(1, std::min(h->opts.accel_m, kMaxM));
+    if (!w.ready) {
+        const size_t aniso = (size_t)g.Nf * g.Nc * sizeof(T);
+        const size_t coarse = (size_t)g.Nc * g.Nc * sizeof(T);
+        CK(cudaMalloc(&w.Xfc, aniso)); CK(cudaMalloc(&w.Xcf, aniso));
+        CK(cudaMalloc(&w.Yfc, aniso)); CK(cudaMalloc(&w.Ycf, aniso));
+        CK(cudaMalloc(&w.Xcc, coarse)); CK(cudaMalloc(&w.Ycc, coarse));
+        CK(cudaMalloc(&w.E1, coarse)); CK(cudaMalloc(&w.E2, coarse));
+        const size_t mom = (size_t)g.Nc * (g.mc + 1) * sizeof(T);
+        CK(cudaMalloc(&w.M1, mom)); CK(cudaMalloc(&w.M2, mom));
+        CK(cudaMalloc(&w.rskel, (size_t)g.skel * sizeof(T)));
+        CK(cudaMalloc(&w.q, (size_t)g.skel * sizeof(T)));
+        CK(cudaMalloc(&w.rfull, (size_t)g.N * g.N * sizeof(T)));
+        CK(cudaMemsetAsync(w.rfull, 0, (size_t)g.N * g.N * sizeof(T), h->st));
+        w.ready = true;
+    }
+    while (w.nz < m) {
+        const size_t grid = (size_t)g.N * g.N * sizeof(T);
+        CK(cudaMalloc(&w.z[w.nz], grid));
+        CK(cudaMemsetAsync(w.z[w.nz], 0, grid, h->st));      // ring stays zero for ever
+        CK(cudaMalloc(&w.qp[w.nz], (size_t)g.skel * sizeof(T)));
+        ++w.nz;
+    }
+    return ASDSM_OK;
+}
+
+int ensure_partials(asdsm_handle* h, int n) {
+    if (n <= h->partials_cap) return ASDSM_OK;
+    if (h->partials) cudaFree(h->partials);
+    CK(cudaMalloc(&h->partials, (size_t)n * sizeof(double)));
+    h->partials_cap = n;
+    return ASDSM_OK;
+}
+
+// Copy `count` doubles of dsmall to the host and wait.
+int read_small(asdsm_handle* h, int count) {
+    CK(cudaMemcpyAsync(h->hsmall, h->dsmall, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return ASDSM_OK;
+}
+
+// ||b_ff||^2 via the FP64 residual of the zero-interior grid (r = b there).
+int bnorm2(asdsm_handle* h, const double* s, const double* u, double* out) {
+    const Geometry& g = h->g;
+    CK(ring_from<double>(u, h->u_work, g, 1, h->st));
+    int nb = 0;
+    const int need = 2 * residual_grid_blocks(g);
+    if (int rc = ensure_partials(h, need)) return rc;
+    ResidOut o{};
+    o.partials = h->partials;
+    UpdateTerms up{};
+    CK(residual_fp64(s, h->u_work, h->u_work, up, g, h->sten, o, &nb, h->st));
+    CK(reduce_partials(h->partials, nb, 2, h->dsmall, h->st));
+    if (int rc = read_small(h, 2)) return rc;
+    *out = h->hsmall[0];
+    return ASDSM_OK;
+}
+
+// Mixed-path residual coefficients (FP32 pairs of the stencil parts times 2^-S).
+MixedCoefs mixed_coefs(const asdsm_handle* h, int S) {
+    const double hh = 1.0 / h->g.M;
+    const double sc = std::ldexp(1.0, -S);
+    const double v[4] = {h->alpha[0] / (hh * hh) * sc, h->alpha[1] / (hh * hh) * sc,
+                         h->beta[0] / (2 * hh) * sc, h->beta[1] / (2 * hh) * sc};
+    MixedCoefs k{};
+    float* dst[4] = {k.kxx, k.kyy, k.kx, k.ky};
+    for (int q = 0; q < 4; ++q) {
+        const float hi = (float)v[q];
+        dst[q][0] = hi;
+        dst[q][1] = (float)(v[q] - (double)hi);
+    }
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 (initial guess) into the direction slot z[0] (T), ring = g.
+// ---------------------------------------------------------------------------
+template <typename T>
+int initial_guess_to_z(asdsm_handle* h, const double* s, const double* u) {
+    const int pi = sizeof(T) == 8 ? 0 : 1;
+    auto& w = h->w[pi];
+    const Geometry& g = h->g;
+    cudaStream_t st = h->st;
+    CK(build_submesh_rhs<T>(s, u, g, h->alpha, h->beta, (T*)w.Xfc, (T*)w.Xcf, (T*)w.Xcc, st));
+    BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
+    CK(bcr_solve<T>(sys, 2, st));                                       // steps 1.1, 1.2
+    BcrSys<T> scc = sys_of<T>(h->cc[pi], w.Xcc, w.Ycc);
+    CK(bcr_solve<T>(&scc, 1, st));                                      // step 1.3
+    T* z = (T*)w.z[0];
+    CK(ring_from<T>(u, z, g, 0, st));
+    MergeArgs<T> ma{};
+    ma.Yfc = (T*)w.Yfc; ma.Ycf = (T*)w.Ycf; ma.Ycc = (T*)w.Ycc;
+    ma.norms2 = nullptr; ma.re_mode = 1; ma.choice = 0;
+    ma.Sm = (const T*)h->Sm[pi];
+    ma.E1 = (T*)w.E1; ma.E2 = (T*)w.E2; ma.M1 = (T*)w.M1; ma.M2 = (T*)w.M2;
+    ma.z = z; ma.g = g;
+    CK(merge_knots<T>(ma, st));                                         // Algorithm 2 steps 1-4
+    CK(merge_write<T>(ma, st));                                         // steps 5-6
+    FillArgs<T> fa{};
+    fa.mode = FILL_WITH_SOURCE;
+    fa.z = z; fa.out = z;
+    if (sizeof(T) == 8) fa.src_d = s; else fa.src_hi = h->s_hi;
+    fa.Pt = (const T*)h->hole[pi].Pt; fa.Qt = (const T*)h->hole[pi].Qt; fa.Bt = (const T*)h->hole[pi].Bt;
+    fa.L = h->hole[pi].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+    CK(fill_holes<T>(fa, h->num_sms, st));                              // Algorithm 3 with b_ff
+    // Restore the ring of z to zero for later use as a direction slot is done by the caller.
+    return ASDSM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 4.
+// ---------------------------------------------------------------------------
+template <typename T>
+int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) {
+    const bool mixed = sizeof(T) == 4;
+    const int pi = mixed ? 1 : 0;
+    if (int rc = ensure_work<T>(h, pi)) return rc;
+    auto& w = h->w[pi];
+    const Geometry& g = h->g;
+    cudaStream_t st = h->st;
+    const asdsm_opts& op = h->opts;
+    const int m = std::max(1, std::min(op.accel_m, kMaxM));
+    const long long NN = (long long)g.N * g.N;
+    if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), 4096))) return rc;
+    h->hist.clear();
+    asdsm_stats stt{};
+    CK(cudaEventRecord(h->ev0, st));
+
+    double b2 = 0.0;
+    if (int rc = bnorm2(h, s, u, &b2)) return rc;
+    const double bnorm = std::sqrt(b2);
+    if (!std::isfinite(bnorm)) return ASDSM_ERR_NAN;
+
+    // Iterate storage.  FP64: ping-pong between the caller's u and u_work (ring = g in both).
+    // Mixed: U[0]/U[1] (64-bit fixed point, u = U 2^-S).
+    double* ucur = u;
+    double* unxt = h->u_work;
+    int Ucur = 0;
+    int S = 0;
+    double scale = 1.0;
+    if (mixed) {
+        CK(split_source(s, h->s_hi, h->s_lo, NN, st));
+    }
+    CK(ring_from<double>(u, h->u_work, g, 0, st));
+
+    // Step 1: initial guess (or resume from u).
+    if (!op.skip_initial_guess) {
+        if (int rc = initial_guess_to_z<T>(h, s, u)) return rc;
+        if (!mixed) {
+            CK(copy_interior<double, double>((const double*)w.z[0], u, g, st));
+        }
+    } else if (mixed) {
+        CK(convert_array<double, float>(u, (float*)w.z[0], NN, st));
+    }
+    if (mixed) {
+        // Fixed-point scale from max |u| (interior and ring), with 2^4 headroom.
+        int nb = 0;
+        CK(maxabs<float>((const float*)w.z[0], NN, h->partials, &nb, st));
+        CK(cudaMemcpyAsync(h->hsmall, h->partials, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double mx = 0.0;
+        for (int q = 0; q < nb; ++q) mx = std::max(mx, h->hsmall[q]);
+        if (!std::isfinite(mx)) return ASDSM_ERR_NAN;
+        if (mx <= 0.0) mx = 1.0;
+        int e2 = 0;
+        std::frexp(mx, &e2);               // mx < 2^e2
+        S = 58 - e2;                        // |U| < 2^58: 2^5 headroom below the 2^63 range and the 2^60 check
+        scale = std::ldexp(1.0, S);
+        const float* zsrc = op.skip_initial_guess ? nullptr : (const float*)w.z[0];
+        CK(to_fixed(zsrc, u, h->U[0], scale, g, st));
+        CK(to_fixed(zsrc, u, h->U[1], scale, g, st));   // ring of the partner
+    }
+    // Direction slots need a zero ring again (slot 0 carried g).
+    CK(ring_from<T>(nullptr, (T*)w.z[0], g, 0, st));
+    CK(cudaEventRecord(h->ev1, st));
+    const MixedCoefs mk = mixed ? mixed_coefs(h, S) : MixedCoefs{};
+
+    // GCR bookkeeping (host, FP64).
+    double Tm[kMaxM][kMaxM] = {};
+    int kc = 0;                  // directions in the current cycle
+    UpdateTerms pend{};          // step 7 of the previous sweep, applied by the next residual kernel
+    double hole_ref = 0.0;       // hole residual right after the last correction (0 before the first)
+    bool hole_ref_pending = false;
+    const bool trace = std::getenv("ASDSM_TRACE") != nullptr;
+    int status = ASDSM_NOT_CONVERGED;
+    int k = 0;
+    int hole_fixes = 0;
+    double rel0 = 0.0, rel = 0.0;
+    std::vector<double> rhist;
+    for (;;) {
+        // ---- step 3: residual (with the pending step-7 update fused) ----
+        ResidOut o{};
+        o.rfc = w.Xfc; o.rcf = w.Xcf; o.rskel = w.rskel; o.rfull = nullptr; o.partials = h->partials;
+        int nb = 0;
+        if (!mixed) {
+            double* dst = pend.count > 0 ? unxt : ucur;
+            CK(residual_fp64(s, ucur, dst, pend, g, h->sten, o, &nb, st));
+            if (pend.count > 0) std::swap(ucur, unxt);
+        } else {
+            UpdateTerms ps = pend;
+            for (int q = 0; q < ps.count; ++q) ps.coef[q] *= scale;
+            CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), st));
+            CK(residual_mixed(h->s_hi, h->s_lo, h->U[Ucur], h->U[1 - Ucur], ps, scale, g, mk, o, &nb, h->dflag, st));
+            if (pend.count > 0) Ucur = 1 - Ucur;
+        }
+        pend.count = 0;
+        CK(reduce_partials(h->partials, nb, 2, h->dsmall, st));
+        if (mixed) CK(cudaMemcpyAsync(h->dsmall + 2, h->dflag, sizeof(int), cudaMemcpyDeviceToDevice, st));
+        if (int rc = read_small(h, 3)) return rc;
+        const double r2 = h->hsmall[0], rh2 = h->hsmall[1];
+        if (mixed) {
+            int ovf = 0;
+            std::memcpy(&ovf, &h->hsmall[2], sizeof(int));
+            if (ovf) { status = ASDSM_ERR_RANGE; break; }
+        }
+        const double rnorm = std::sqrt(r2), hnorm = std::sqrt(rh2);
+        rel = bnorm > 0 ? rnorm / bnorm : rnorm;
+        if (!std::isfinite(rel)) { status = ASDSM_ERR_NAN; break; }
+        rhist.push_back(rel);
+        if (k == 0) rel0 = rel;
+        if (rel <= op.tol) { status = ASDSM_OK; break; }
+        if (k >= op.max_sweeps) { status = ASDSM_NOT_CONVERGED; break; }
+        const int win = op.stagnation_window;
+        if (win > 0 && (int)rhist.size() > win &&
+            rhist.back() > (1.0 - op.stagnation_factor) * rhist[rhist.size() - 1 - win]) {
+            status = ASDSM_STAGNATED;
+            break;
+        }
+        if (hole_ref_pending) { hole_ref = hnorm; hole_ref_pending = false; }
+        if (trace)
+            std::fprintf(stderr, "asdsm: k=%d rel=%.6e hole_rel=%.6e kc=%d\n", k, rel, bnorm > 0 ? hnorm / bnorm : hnorm, kc);
+        if (hnorm > op.hole_fix_ratio * rnorm && hnorm > op.hole_fix_growth * hole_ref) {
+            // Rounding has left a residual in the holes: Algorithm 3 on the current iterate.
+            o.rfc = nullptr; o.rcf = nullptr; o.rskel = nullptr; o.rfull = w.rfull;
+            UpdateTerms none{};
+            FillArgs<T> fa{};
+            fa.mode = FILL_RESIDUAL_TO_U;
+            if (!mixed) {
+                CK(residual_fp64(s, ucur, ucur, none, g, h->sten, o, &nb, st));
+                fa.src_d = (const double*)w.rfull;
+                fa.u_d = ucur;
+            } else {
+                CK(residual_mixed(h->s_hi, h->s_lo, h->U[Ucur], h->U[Ucur], none, scale, g, mk, o, &nb, h->dflag, st));
+                fa.src_hi = (const float*)w.rfull;
+                fa.U = h->U[Ucur];
+                fa.fixed_scale = scale;
+            }
+            fa.Pt = (const T*)h->hole[pi].Pt; fa.Qt = (const T*)h->hole[pi].Qt; fa.Bt = (const T*)h->hole[pi].Bt;
+            fa.L = h->hole[pi].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+            CK(fill_holes<T>(fa, h->num_sms, st));
+            ++hole_fixes;
+            kc = 0;
+            hole_ref_pending = true;         // re-read from the next residual
+            ++k;
+            continue;
+        }
+        // ---- steps 4-5: the error guess of Algorithm 1 without b_cc ----
+        const int bit = choice_bit(op.seed, k);
+        BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
+        CK(bcr_solve<T>(sys, 2, st));
+        {
+            const T* av[2] = {(const T*)w.Yfc, (const T*)w.Ycf};
+            int nb2 = 0;
+            // Two separate dots over the same length.
+            CK(multi_dot<T>(av, av, 2, (long long)g.Nf * g.Nc, h->partials, &nb2, st));
+            CK(reduce_partials(h->partials, nb2, 2, h->dsmall + 200, st));
+        }
+        T* z = (T*)w.z[kc];
+        MergeArgs<T> ma{};
+        ma.Yfc = (T*)w.Yfc; ma.Ycf = (T*)w.Ycf; ma.Ycc = nullptr;
+        ma.norms2 = h->dsmall + 200; ma.re_mode = 0; ma.choice = bit;
+        ma.Sm = (const T*)h->Sm[pi];
+        ma.E1 = (T*)w.E1; ma.E2 = (T*)w.E2; ma.M1 = (T*)w.M1; ma.M2 = (T*)w.M2;
+        ma.z = z; ma.g = g;
+        CK(merge_knots<T>(ma, st));
+        CK(merge_write<T>(ma, st));
+        FillArgs<T> fa{};
+        fa.mode = FILL_HOMOGENEOUS;
+        fa.z = z; fa.out = z;
+        fa.Pt = (const T*)h->hole[pi].Pt; fa.Qt = (const T*)h->hole[pi].Qt; fa.Bt = (const T*)h->hole[pi].Bt;
+        fa.L = h->hole[pi].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+        CK(fill_holes<T>(fa, h->num_sms, st));
+        // ---- step 6: least squares on the skeleton rows ----
+        CK(skeleton_apply<T>(z, g, h->sten, (T*)w.q, st));
+        const T* da[2 + 2 * kMaxM];
+        const T* db[2 + 2 * kMaxM];
+        int nd = 0;
+        da[nd] = (const T*)w.q; db[nd] = (const T*)w.q; ++nd;          // <q,q>
+        da[nd] = (const T*)w.q; db[nd] = (const T*)w.rskel; ++nd;      // <q,r>
+        for (int j = 0; j < kc; ++j) {
+            da[nd] = (const T*)w.q; db[nd] = (const T*)w.qp[j]; ++nd;     // <q, q'_j>
+            da[nd] = (const T*)w.rskel; db[nd] = (const T*)w.qp[j]; ++nd; // <r, q'_j>
+        }
+        int nb3 = 0;
+        CK(multi_dot<T>(da, db, nd, g.skel, h->partials, &nb3, st));
+        CK(reduce_partials(h->partials, nb3, nd, h->dsmall, st));
+        if (int rc = read_small(h, nd)) return rc;
+        const double qq = h->hsmall[0], qr = h->hsmall[1];
+        if (m == 1) {
+            // Paper's step 6: s_hat = argmin_{s >= 0} ||r - s A e||.
+            const double shat = qq > 0 ? std::max(0.0, qr / qq) : 0.0;
+            pend.count = 1;
+            pend.z[0] = z;
+            pend.coef[0] = shat;
+        } else {
+            // GCR(m): orthogonalise A e against the cycle's previous directions.
+            double beta_[kMaxM] = {}, rq[kMaxM] = {};
+            double nu2 = qq;
+            for (int j = 0; j < kc; ++j) {
+                beta_[j] = h->hsmall[2 + 2 * j];
+                rq[j] = h->hsmall[3 + 2 * j];
+                nu2 -= beta_[j] * beta_[j];
+            }
+            if (!(nu2 > 1e-24 * qq) || !(qq > 0)) {
+                kc = 0;                       // dependent direction: restart the cycle
+                ++k;
+                continue;
+            }
+            const double nu = std::sqrt(nu2);
+            double alpha_ = qr;
+            for (int j = 0; j < kc; ++j) alpha_ -= beta_[j] * rq[j];
+            alpha_ /= nu;
+            // Column kc of T: z'_kc = sum_i T[i][kc] z_i.
+            for (int i = 0; i <= kc; ++i) Tm[i][kc] = 0.0;
+            Tm[kc][kc] = 1.0 / nu;
+            for (int j = 0; j < kc; ++j)
+                for (int i = 0; i <= j; ++i) Tm[i][kc] -= beta_[j] * Tm[i][j] / nu;
+            pend.count = kc + 1;
+            for (int i = 0; i <= kc; ++i) {
+                pend.z[i] = w.z[i];
+                pend.coef[i] = alpha_ * Tm[i][kc];
+            }
+            const T* qps[kMaxM];
+            for (int j = 0; j < kc; ++j) qps[j] = (const T*)w.qp[j];
+            CK(combine_skeleton<T>((const T*)w.q, qps, beta_, kc, 1.0 / nu, g.skel, (T*)w.qp[kc], st));
+            ++kc;
+            if (kc >= m) kc = 0;
+        }
+        ++k;
+    }
+    // Final iterate to the caller's buffer.
+    if (!mixed) {
+        if (ucur != u) CK(copy_interior<double, double>(ucur, u, g, st));
+    } else if (status != ASDSM_ERR_RANGE) {
+        CK(from_fixed(h->U[Ucur], std::ldexp(1.0, -S), u, g, st));
+    }
+    CK(cudaEventRecord(h->ev2, st));
+    CK(cudaEventSynchronize(h->ev2));
+    float ms_setup = 0.f, ms_all = 0.f;
+    cudaEventElapsedTime(&ms_setup, h->ev0, h->ev1);
+    cudaEventElapsedTime(&ms_all, h->ev0, h->ev2);
+    h->hist = rhist;
+    stt.sweeps = k;
+    stt.status = status;
+    stt.hole_fixes = hole_fixes;
+    stt.fixed_shift = mixed ? S : 0;
+    stt.rel_res = rel;
+    stt.rel_res0 = rel0;
+    stt.setup_ms = ms_setup;
+    stt.solve_ms = ms_all;
+    if (stats) *stats = stt;
+    return status;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void asdsm_default_opts(asdsm_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-10;
+    o->max_sweeps = 500;
+    o->precision = ASDSM_MIXED;
+    o->accel_m = 8;
+    o->skip_initial_guess = 0;
+    o->seed = 0;
+    o->hole_fix_ratio = 0.25;
+    o->hole_fix_growth = 4.0;
+    o->stagnation_window = 10;
+    o->stagnation_factor = 1e-3;
+}
+
+const char* asdsm_strerror(int code) {
+    switch (code) {
+        case ASDSM_OK: return "ok";
+        case ASDSM_ERR_INVALID: return "invalid argument (sizes must satisfy eq. 2.1 with N-1 and mc powers of two, 2 <= mc, (N-1)/mc in [2, 32]; alpha > 0)";
+        case ASDSM_ERR_CUDA: return "CUDA runtime error";
+        case ASDSM_ERR_OOM: return "device allocation failed";
+        case ASDSM_ERR_NAN: return "NaN or Inf in the residual";
+        case ASDSM_NOT_CONVERGED: return "max_sweeps reached above tol";
+        case ASDSM_STAGNATED: return "residual stagnated";
+        case ASDSM_ERR_RANGE: return "fixed-point accumulator range exceeded";
+        default: return "unknown status";
+    }
+}
+
+const char* asdsm_last_error(void) { return g_last_error.c_str(); }
+
+int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, asdsm_handle** out) {
+    if (!out) return ASDSM_ERR_INVALID;
+    *out = nullptr;
+    if (!desc) return ASDSM_ERR_INVALID;
+    if (desc->d != 2) return ASDSM_ERR_INVALID;
+    const long long N = desc->n, mc = desc->mc;
+    if (N < 5 || !is_pow2(N - 1) || mc < 2 || !is_pow2(mc) || (N - 1) % mc != 0) return ASDSM_ERR_INVALID;
+    const long long n = (N - 1) / mc;
+    if (n < 2 || n > 32) return ASDSM_ERR_INVALID;
+    if (!(desc->alpha[0] > 0) || !(desc->alpha[1] > 0)) return ASDSM_ERR_INVALID;
+    for (int q = 0; q < 2; ++q)
+        if (!std::isfinite(desc->alpha[q]) || !std::isfinite(desc->beta[q])) return ASDSM_ERR_INVALID;
+
+    asdsm_handle* h = new asdsm_handle();
+    h->desc = *desc;
+    if (opts) h->opts = *opts; else asdsm_default_opts(&h->opts);
+    if (h->opts.accel_m < 1 || h->opts.accel_m > kMaxM) { delete h; return ASDSM_ERR_INVALID; }
+    h->st = (cudaStream_t)stream;
+    auto fail = [&](int rc) { asdsm_destroy(h); return rc; };
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(set_cuda_error(e));
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    Geometry& g = h->g;
+    g.N = (int)N; g.M = (int)(N - 1); g.Nf = (int)(N - 2); g.mc = (int)mc; g.Nc = (int)(mc - 1); g.n = (int)n;
+    g.skel = (long long)g.Nc * g.Nf + (long long)g.Nc * (g.Nf - g.Nc);
+    for (int q = 0; q < 2; ++q) { h->alpha[q] = desc->alpha[q]; h->beta[q] = desc->beta[q]; }
+    const double ax = h->alpha[0], ay = h->alpha[1], bx = h->beta[0], by = h->beta[1];
+    const double hh = 1.0 / g.M, HH = 1.0 / g.mc;
+    // Section 2.3 stencil of A_ff.
+    h->sten.cc = 2 * ax / (hh * hh) + 2 * ay / (hh * hh);
+    h->sten.cw = -ax / (hh * hh) - bx / (2 * hh);
+    h->sten.ce = -ax / (hh * hh) + bx / (2 * hh);
+    h->sten.cs = -ay / (hh * hh) - by / (2 * hh);
+    h->sten.cn = -ay / (hh * hh) + by / (2 * hh);
+    // Block cyclic reduction factors (eq. 2.4 systems; rows = the fine axis of each family).
+    auto row = [](double a, double b, double sp, double* lo, double* d, double* up) {
+        *lo = -a / (sp * sp) - b / (2 * sp);
+        *d = 2 * a / (sp * sp);
+        *up = -a / (sp * sp) + b / (2 * sp);
+    };
+    double xl_h, xd_h, xu_h, yl_h, yd_h, yu_h, xl_H, xd_H, xu_H, yl_H, yd_H, yu_H;
+    row(ax, bx, hh, &xl_h, &xd_h, &xu_h);
+    row(ay, by, hh, &yl_h, &yd_h, &yu_h);
+    row(ax, bx, HH, &xl_H, &xd_H, &xu_H);
+    row(ay, by, HH, &yl_H, &yd_H, &yu_H);
+    BcrFactors ffc, fcf, fcc, fho;
+    // A_fc: rows x (fine), columns the coarse lines in y.
+    if (!make_bcr(g.Nf, xl_h, xd_h, xu_h, g.Nc, yl_H, yd_H, yu_H, &ffc)) return fail(ASDSM_ERR_INVALID);
+    // A_cf: rows y (fine), columns the coarse lines in x.
+    if (!make_bcr(g.Nf, yl_h, yd_h, yu_h, g.Nc, xl_H, xd_H, xu_H, &fcf)) return fail(ASDSM_ERR_INVALID);
+    // A_cc: rows y (coarse), columns x (coarse).
+    if (!make_bcr(g.Nc, yl_H, yd_H, yu_H, g.Nc, xl_H, xd_H, xu_H, &fcc)) return fail(ASDSM_ERR_INVALID);
+    // Hole blocks A_(ij): rows y, columns x, both fine.
+    if (!make_bcr(g.n - 1, yl_h, yd_h, yu_h, g.n - 1, xl_h, xd_h, xu_h, &fho)) return fail(ASDSM_ERR_INVALID);
+    int rc;
+    if ((rc = upload_bcr<double>(ffc, &h->fc[0])) || (rc = upload_bcr<float>(ffc, &h->fc[1])) ||
+        (rc = upload_bcr<double>(fcf, &h->cf[0])) || (rc = upload_bcr<float>(fcf, &h->cf[1])) ||
+        (rc = upload_bcr<double>(fcc, &h->cc[0])) || (rc = upload_bcr<float>(fcc, &h->cc[1])) ||
+        (rc = upload_bcr<double>(fho, &h->hole[0])) || (rc = upload_bcr<float>(fho, &h->hole[1])))
+        return fail(rc);
+    const std::vector<double> Sm = spline_moment_operator(g.mc);
+    if ((rc = upload_vec<double>(Sm, &h->Sm[0])) || (rc = upload_vec<float>(Sm, &h->Sm[1]))) return fail(rc);
+    if (fill_smem_bytes<double>(g.n, h->hole[0].L) > 227 * 1024) return fail(ASDSM_ERR_INVALID);
+    const size_t NN = (size_t)g.N * g.N;
+    if ((e = cudaMalloc(&h->u_work, NN * sizeof(double))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMalloc(&h->U[0], NN * sizeof(long long))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMalloc(&h->U[1], NN * sizeof(long long))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMalloc(&h->s_hi, NN * sizeof(float))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMalloc(&h->s_lo, NN * sizeof(float))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMalloc(&h->dsmall, 256 * sizeof(double))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMalloc(&h->dflag, sizeof(int))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMallocHost(&h->hsmall, 4096 * sizeof(double))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaEventCreate(&h->ev2)) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), 4096)))) return fail(rc);
+    *out = h;
+    return ASDSM_OK;
+}
+
+int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts) {
+    if (!h || !opts) return ASDSM_ERR_INVALID;
+    if (opts->accel_m < 1 || opts->accel_m > kMaxM) return ASDSM_ERR_INVALID;
+    if (opts->precision != ASDSM_FP64 && opts->precision != ASDSM_MIXED) return ASDSM_ERR_INVALID;
+    h->opts = *opts;
+    return ASDSM_OK;
+}
+
+int asdsm_solve(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) {
+    if (!h || !s || !u) return ASDSM_ERR_INVALID;
+    if (h->opts.precision == ASDSM_FP64) return solve_impl<double>(h, s, u, stats);
+    if (h->opts.precision == ASDSM_MIXED) return solve_impl<float>(h, s, u, stats);
+    return ASDSM_ERR_INVALID;
+}
+
+int asdsm_initial_guess(asdsm_handle* h, const double* s, double* u) {
+    if (!h || !s || !u) return ASDSM_ERR_INVALID;
+    int rc;
+    if (h->opts.precision == ASDSM_FP64) {
+        if ((rc = ensure_work<double>(h, 0))) return rc;
+        if ((rc = initial_guess_to_z<double>(h, s, u))) return rc;
+        CK(copy_interior<double, double>((const double*)h->w[0].z[0], u, h->g, h->st));
+        CK(ring_from<double>(nullptr, (double*)h->w[0].z[0], h->g, 0, h->st));
+    } else {
+        CK(split_source(s, h->s_hi, h->s_lo, (long long)h->g.N * h->g.N, h->st));
+        if ((rc = ensure_work<float>(h, 1))) return rc;
+        if ((rc = initial_guess_to_z<float>(h, s, u))) return rc;
+        CK(copy_interior<float, double>((const float*)h->w[1].z[0], u, h->g, h->st));
+        CK(ring_from<float>(nullptr, (float*)h->w[1].z[0], h->g, 0, h->st));
+    }
+    CK(cudaStreamSynchronize(h->st));
+    return ASDSM_OK;
+}
+
+int asdsm_residual(asdsm_handle* h, const double* s, const double* u, double* r, double* rel_norm) {
+    if (!h || !s || !u) return ASDSM_ERR_INVALID;
+    const Geometry& g = h->g;
+    double b2 = 0.0;
+    int rc;
+    if ((rc = bnorm2(h, s, u, &b2))) return rc;
+    ResidOut o{};
+    o.partials = h->partials;
+    o.rfull = r;
+    UpdateTerms up{};
+    int nb = 0;
+    if (r) CK(ring_from<double>(nullptr, r, g, 0, h->st));
+    CK(residual_fp64(s, u, const_cast<double*>(u), up, g, h->sten, o, &nb, h->st));
+    CK(reduce_partials(h->partials, nb, 2, h->dsmall, h->st));
+    if ((rc = read_small(h, 2))) return rc;
+    if (rel_norm) *rel_norm = b2 > 0 ? std::sqrt(h->hsmall[0] / b2) : std::sqrt(h->hsmall[0]);
+    return ASDSM_OK;
+}
+
+int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out) {
+    if (!h || !in || !out || in == out) return ASDSM_ERR_INVALID;
+    const Geometry& g = h->g;
+    const bool fp64 = h->opts.precision == ASDSM_FP64;
+    const int pi = fp64 ? 0 : 1;
+    int rc;
+    if ((rc = fp64 ? ensure_work<double>(h, 0) : ensure_work<float>(h, 1))) return rc;
+    auto& w = h->w[pi];
+    cudaStream_t st = h->st;
+    if (mesh >= 0 && mesh <= 2) {
+        const DevBcr& d = mesh == 0 ? h->fc[pi] : (mesh == 1 ? h->cf[pi] : h->cc[pi]);
+        void* X = mesh == 2 ? w.Xcc : w.Xfc;
+        void* Y = mesh == 2 ? w.Ycc : w.Yfc;
+        const long long n = (long long)d.R * d.C;
+        // Layouts: fc in/out are [line][x] on the API, [x][line] inside.
+        if (fp64) {
+            BcrSys<double> s = sys_of<double>(d, X, Y);
+            if (mesh == 0) {
+                std::vector<double> hin(n), hx(n);
+                CK(cudaMemcpy(hin.data(), in, n * sizeof(double), cudaMemcpyDeviceToHost));
+                for (int l = 0; l < g.Nc; ++l)
+                    for (int x = 0; x < g.Nf; ++x) hx[(size_t)x * g.Nc + l] = hin[(size_t)l * g.Nf + x];
+                CK(cudaMemcpy(X, hx.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+            } else {
+                CK(cudaMemcpyAsync(X, in, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+            CK(bcr_solve<double>(&s, 1, st));
+            if (mesh == 0) {
+                std::vector<double> hy(n), hout(n);
+                CK(cudaMemcpy(hy.data(), Y, n * sizeof(double), cudaMemcpyDeviceToHost));
+                for (int l = 0; l < g.Nc; ++l)
+                    for (int x = 0; x < g.Nf; ++x) hout[(size_t)l * g.Nf + x] = hy[(size_t)x * g.Nc + l];
+                CK(cudaMemcpy(out, hout.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+            } else {
+                CK(cudaMemcpyAsync(out, Y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+        } else {
+            BcrSys<float> s = sys_of<float>(d, X, Y);
+            std::vector<double> hin(n), hx(n);
+            CK(cudaMemcpy(hin.data(), in, n * sizeof(double), cudaMemcpyDeviceToHost));
+            if (mesh == 0) {
+                for (int l = 0; l < g.Nc; ++l)
+                    for (int x = 0; x < g.Nf; ++x) hx[(size_t)x * g.Nc + l] = hin[(size_t)l * g.Nf + x];
+            } else {
+                hx = hin;
+            }
+            std::vector<float> hf(hx.begin(), hx.end());
+            CK(cudaMemcpy(X, hf.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+            CK(bcr_solve<float>(&s, 1, st));
+            CK(cudaMemcpy(hf.data(), Y, n * sizeof(float), cudaMemcpyDeviceToHost));
+            std::vector<double> hout(n);
+            if (mesh == 0) {
+                for (int l = 0; l < g.Nc; ++l)
+                    for (int x = 0; x < g.Nf; ++x) hout[(size_t)l * g.Nf + x] = hf[(size_t)x * g.Nc + l];
+            } else {
+                for (long long q = 0; q < n; ++q) hout[q] = hf[q];
+            }
+            CK(cudaMemcpy(out, hout.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        }
+    } else if (mesh == 3) {
+        if (fp64) {
+            FillArgs<double> fa{};
+            fa.mode = FILL_ARRAY; fa.src_d = in; fa.out_d = out;
+            fa.Pt = (const double*)h->hole[0].Pt; fa.Qt = (const double*)h->hole[0].Qt; fa.Bt = (const double*)h->hole[0].Bt;
+            fa.L = h->hole[0].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+            CK(fill_holes<double>(fa, h->num_sms, st));
+        } else {
+            FillArgs<float> fa{};
+            fa.mode = FILL_ARRAY; fa.src_d = in; fa.out_d = out;
+            fa.Pt = (const float*)h->hole[1].Pt; fa.Qt = (const float*)h->hole[1].Qt; fa.Bt = (const float*)h->hole[1].Bt;
+            fa.L = h->hole[1].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+            CK(fill_holes<float>(fa, h->num_sms, st));
+        }
+    } else {
+        return ASDSM_ERR_INVALID;
+    }
+    CK(cudaStreamSynchronize(st));
+    return ASDSM_OK;
+}
+
+int asdsm_history(asdsm_handle* h, double* hist, int cap) {
+    if (!h || (!hist && cap > 0)) return ASDSM_ERR_INVALID;
+    const int n = std::min<int>(cap, (int)h->hist.size());
+    for (int q = 0; q < n; ++q) hist[q] = h->hist[q];
+    return n;
+}
+
+void asdsm_destroy(asdsm_handle* h) {
+    if (!h) return;
+    auto fr = [](void* p) { if (p) cudaFree(p); };
+    for (int p = 0; p < 2; ++p) {
+        DevBcr* ds[4] = {&h->fc[p], &h->cf[p], &h->cc[p], &h->hole[p]};
+        for (auto* d : ds) { fr(d->Pt); fr(d->Qt); fr(d->Bt); }
+        fr(h->Sm[p]);
+        auto& w = h->w[p];
+        void* bufs[] = {w.Xfc, w.Xcf, w.Yfc, w.Ycf, w.Xcc, w.Ycc, w.E1, w.E2, w.M1, w.M2, w.rskel, w.q, w.rfull};
+        for (void* b : bufs) fr(b);
+        for (int q = 0; q < w.nz; ++q) { fr(w.z[q]); fr(w.qp[q]); }
+    }
+    fr(h->u_work); fr(h->U[0]); fr(h->U[1]); fr(h->s_hi); fr(h->s_lo);
+    fr(h->partials); fr(h->dsmall); fr(h->dflag);
+    if (h->hsmall) cudaFreeHost(h->hsmall);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->ev2) cudaEventDestroy(h->ev2);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// Internal declarations shared by the translation units of the ASDSM library.
+// Not part of the public ABI (see include/asdsm.h).
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include <string>
+#include <cuda_runtime.h>
+
+namespace asdsm {
+
+// ---------------------------------------------------------------------------
+// Host FP64 precomputation (host_math.cu)
+// ---------------------------------------------------------------------------
+
+// Block cyclic reduction factors of the block tridiagonal Toeplitz system
+//     a x_{i-1} + (d I + T) x_i + c x_{i+1} = f_i,   i = 1..R,  x_0 = x_{R+1} = 0,
+// with R = 2^L - 1 rows and T the C x C tridiagonal Toeplitz matrix
+// tridiag(tl, td, tu) (T[k][k-1] = tl, T[k][k+1] = tu).  At level l the
+// surviving rows satisfy A_l x_{i-s} + B_l x_i + C_l x_{i+s} = f_i^(l)
+// (s = 2^l); the factors kept per level are P_l = A_l B_l^{-1},
+// Q_l = C_l B_l^{-1} and B_l^{-1}, each stored transposed ([k][c] = M[c][k]).
+struct BcrFactors {
+    int R = 0, C = 0, L = 0;
+    std::vector<double> Pt, Qt, Bt;   // [L][C][C]
+};
+bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, double tu, BcrFactors* out);
+
+// Moments of the not-a-knot cubic spline on the uniform knots 0, H, .., 1
+// (mc intervals) through values (0, y_1, .., y_{mc-1}, 0): M = Sm y with
+// Sm of shape (mc+1) x (mc-1), row-major.
+std::vector<double> spline_moment_operator(int mc);
+
+// ---------------------------------------------------------------------------
+// Device-side descriptors
+// ---------------------------------------------------------------------------
+template <typename T>
+struct BcrSys {
+    T* X;              // right-hand sides, [nsys][R][C]; overwritten by the forward reduction
+    T* Y;              // solutions, [nsys][R][C]
+    const T* Pt;       // [L][C][C]
+    const T* Qt;
+    const T* Bt;
+    int R, C, L;
+    int nsys;          // systems sharing these factors
+    long long stride;  // elements between consecutive systems
+};
+
+// Stencil coefficients of A_ff (5-point, Section 2.3): A u = cc u_c + cw u_w + ce u_e + cs u_s + cn u_n.
+struct Stencil {
+    double cc, cw, ce, cs, cn;
+};
+
+struct Geometry {
+    int N;      // grid points per axis incl. boundary
+    int M;      // N - 1 fine intervals
+    int Nf;     // N - 2 interior points per axis
+    int mc;     // coarse intervals
+    int Nc;     // mc - 1 coarse lines per axis
+    int n;      // M / mc
+    long long skel;   // compact skeleton length: Nc*Nf + Nc*(Nf - Nc)
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (kernels_*.cu).  All enqueue on `st`; none synchronise.
+// ---------------------------------------------------------------------------
+// Block cyclic reduction of up to 2 factor groups (e.g. the fc and cf families).
+template <typename T>
+cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st);
+
+// Mode of the hole solve of Algorithm 3.
+enum FillMode : int {
+    FILL_WITH_SOURCE = 0,   // rhs = s - A_hs z  (inhomogeneous Filler of the initial guess; z carries g on its ring)
+    FILL_HOMOGENEOUS = 1,   // rhs = - A_hs z     (Filler with 0 b of Algorithm 4 step 5)
+    FILL_RESIDUAL_TO_U = 2, // rhs = r (holes);  u_holes += solution   (hole-residual correction)
+    FILL_ARRAY = 3          // rhs = given array (holes), no skeleton term; write solution to out
+};
+
+// Fused Algorithm 3 over all holes: each CTA keeps the hole BCR factors in
+// shared memory and solves holes one after another.
+template <typename T>
+struct FillArgs {
+    int mode;
+    const T* z;               // full grid, skeleton values (and g on the ring for FILL_WITH_SOURCE)
+    T* out;                   // full grid, receives hole values (modes 0, 1, 3)
+    const double* src_d;      // FP64 source grid (mode 0, FP64 path) / rhs grid (mode 3)
+    const float* src_hi;      // FP32 source (mode 0, mixed path) / residual grid (mode 2)
+    double* out_d;            // mode 3: FP64 output grid (hole points written)
+    double* u_d;              // mode 2, FP64 path: u += v on holes
+    long long* U;             // mode 2, mixed path: U += round(v * scale)
+    double fixed_scale;       // 2^S for mode 2 mixed
+    const T* Pt; const T* Qt; const T* Bt;
+    int L, n;                 // hole systems are (n-1) x (n-1)
+    Geometry g;
+    Stencil sten;
+};
+template <typename T>
+cudaError_t fill_holes(const FillArgs<T>& a, int num_sms, cudaStream_t st);
+template <typename T>
+size_t fill_smem_bytes(int n, int L);
+
+// Right-hand sides of eq. (2.4) on the submeshes (Dirichlet lifting from u's ring).
+template <typename T>
+cudaError_t build_submesh_rhs(const double* s, const double* u, const Geometry& g,
+                              const double alpha[2], const double beta[2],
+                              T* bfc, T* bcf, T* bcc, cudaStream_t st);
+
+// Residual kernels -----------------------------------------------------------
+struct ResidOut {
+    void* rfc;          // T [Nf][Nc]  (BCR layout of Omega^{h,H})
+    void* rcf;          // T [Nf][Nc]  (BCR layout of Omega^{H,h})
+    void* rskel;        // T [skel]    (compact skeleton)
+    void* rfull;        // float or double full grid (optional)
+    double* partials;   // [nblocks][2]: sum r^2, sum r^2 over holes
+};
+struct UpdateTerms {
+    const void* z[16];  // directions (T full grid)
+    double coef[16];    // u += sum coef_j z_j
+    int count;
+};
+// FP64 path: u_out = u_in + sum coef z (interior), r = s - A u_out.
+cudaError_t residual_fp64(const double* s, const double* u_in, double* u_out, const UpdateTerms& up,
+                          const Geometry& g, const Stencil& st_, ResidOut out, int* nblocks, cudaStream_t st);
+// Mixed path: U_out = U_in + round(2^S sum coef z), r = s - A U_out 2^-S in FP32-pair arithmetic.
+struct MixedCoefs {
+    float kxx[2], kyy[2], kx[2], ky[2];   // (hi, lo) of alpha_x/h^2 2^-S, alpha_y/h^2 2^-S, beta_x/(2h) 2^-S, beta_y/(2h) 2^-S
+};
+cudaError_t residual_mixed(const float* s_hi, const float* s_lo, const long long* U_in, long long* U_out,
+                           const UpdateTerms& up, double scale, const Geometry& g, const MixedCoefs& k,
+                           ResidOut out, int* nblocks, int* overflow_flag, cudaStream_t st);
+int residual_grid_blocks(const Geometry& g);
+
+// Reductions ----------------------------------------------------------------
+// out[j] = sum over blocks of partials[b][j]  (fixed order, 1 CTA), j < ncols
+cudaError_t reduce_partials(const double* partials, int nblocks, int ncols, double* out, cudaStream_t st);
+// Multi-dot: out partials for dots <a_i, b_i>, i < ndots over length n vectors.
+template <typename T>
+cudaError_t multi_dot(const T* const* a, const T* const* b, int ndots, long long n,
+                      double* partials, int* nblocks, cudaStream_t st);
+
+// Merge (Algorithm 2) --------------------------------------------------------
+template <typename T>
+struct MergeArgs {
+    const T* Yfc;  const T* Ycf;  const T* Ycc;  // solutions; Ycc used when re_mode
+    const double* norms2;     // [2]: ||Yfc||^2, ||Ycf||^2 (normalisation of Algorithm 1 step 2)
+    int re_mode;              // 1: Richardson (u_cc given), 0: random choice
+    int choice;               // 0 or 1 (Algorithm 2 step 3)
+    const T* Sm;              // (mc+1) x Nc spline moment operator
+    T* E1; T* E2;             // [Nc][Nc] knot errors (fc lines: E1[l][k]; cf columns: E2[l][k])
+    T* M1; T* M2;             // moments: M1[l][mc+1], M2[k][mc+1]
+    T* z;                     // full grid output (skeleton written)
+    Geometry g;
+};
+template <typename T> cudaError_t merge_knots(const MergeArgs<T>& a, cudaStream_t st);
+template <typename T> cudaError_t merge_write(const MergeArgs<T>& a, cudaStream_t st);
+
+// q = (A z) on the compact skeleton.
+template <typename T>
+cudaError_t skeleton_apply(const T* z, const Geometry& g, const Stencil& s, T* q, cudaStream_t st);
+// qp = (q - sum beta_j Qp_j) * inv_nu   (Qp, beta: host arrays, k <= 16)
+template <typename T>
+cudaError_t combine_skeleton(const T* q, const T* const* Qp, const double* beta, int k, double inv_nu,
+                             long long n, T* out, cudaStream_t st);
+
+// Grid utilities -------------------------------------------------------------
+template <typename T>
+cudaError_t fill_value(T* p, long long n, T v, cudaStream_t st);
+// dst interior = src interior (converted), ring untouched
+template <typename Ts, typename Td>
+cudaError_t copy_interior(const Ts* src, Td* dst, const Geometry& g, cudaStream_t st);
+// z (T full grid) = 0 interior, ring = g from u
+template <typename T>
+cudaError_t ring_from(const double* u, T* z, const Geometry& g, int zero_interior, cudaStream_t st);
+// max |v| over a full grid (double partials per block)
+template <typename T>
+cudaError_t maxabs(const T* v, long long n, double* partials, int* nblocks, cudaStream_t st);
+// z == nullptr: convert u_ring_src everywhere (resume from an FP64 iterate)
+cudaError_t to_fixed(const float* z, const double* u_ring_src, long long* U, double scale, const Geometry& g, cudaStream_t st);
+cudaError_t from_fixed(const long long* U, double inv_scale, double* u, const Geometry& g, cudaStream_t st);
+cudaError_t split_source(const double* s, float* hi, float* lo, long long n, cudaStream_t st);
+// compact skeleton <-> BCR layouts, for checking: convert FP64 in -> T
+template <typename Ts, typename Td>
+cudaError_t convert_array(const Ts* in, Td* out, long long n, cudaStream_t st);
+
+}  // namespace asdsm

@@ -1,0 +1,164 @@
+// Host-side FP64 precomputation for the ASDSM library.
+//
+// * Block cyclic reduction (BCR) factors of the separable constant-coefficient
+//   operators of eq. (2.4): every submesh system of Section 2.3 (A_fc, A_cf,
+//   A_cc) and every hole block A_(ij) of Remark 2.4 is
+//       (T_row (x) I + I (x) T_col) x = f
+//   with T_row, T_col tridiagonal Toeplitz.  Ordered row by row it is block
+//   tridiagonal with blocks a I, (d I + T_col), c I.  With R = 2^L - 1 rows,
+//   cyclic reduction keeps the Toeplitz structure at every level, so one set
+//   of C x C factors per level serves every row (and every hole).
+// * The moment operator of the not-a-knot cubic spline used by "Spline" in
+//   Algorithm 2 (knot values zero at both ends).
+#include "asdsm_internal.h"
+#include <cmath>
+#include <algorithm>
+
+namespace asdsm {
+
+namespace {
+
+// C = A B, all n x n row-major.
+void matmul(const double* A, const double* B, double* C, int n) {
+    std::fill(C, C + (size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double* a = A + (size_t)i * n;
+        double* c = C + (size_t)i * n;
+        for (int k = 0; k < n; ++k) {
+            const double aik = a[k];
+            if (aik == 0.0) continue;
+            const double* b = B + (size_t)k * n;
+            for (int j = 0; j < n; ++j) c[j] += aik * b[j];
+        }
+    }
+}
+
+// In-place inverse of an n x n row-major matrix by Gauss-Jordan elimination
+// with partial pivoting.  Returns false when a pivot vanishes.
+bool invert(std::vector<double>& A, int n) {
+    std::vector<double> I((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        double best = std::fabs(A[(size_t)col * n + col]);
+        for (int r = col + 1; r < n; ++r) {
+            double v = std::fabs(A[(size_t)r * n + col]);
+            if (v > best) { best = v; piv = r; }
+        }
+        if (!(best > 0.0) || !std::isfinite(best)) return false;
+        if (piv != col) {
+            for (int j = 0; j < n; ++j) {
+                std::swap(A[(size_t)col * n + j], A[(size_t)piv * n + j]);
+                std::swap(I[(size_t)col * n + j], I[(size_t)piv * n + j]);
+            }
+        }
+        const double inv = 1.0 / A[(size_t)col * n + col];
+        for (int j = 0; j < n; ++j) {
+            A[(size_t)col * n + j] *= inv;
+            I[(size_t)col * n + j] *= inv;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const double f = A[(size_t)r * n + col];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                A[(size_t)r * n + j] -= f * A[(size_t)col * n + j];
+                I[(size_t)r * n + j] -= f * I[(size_t)col * n + j];
+            }
+        }
+    }
+    A.swap(I);
+    return true;
+}
+
+void transpose_into(const double* M, double* out, int n) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) out[(size_t)j * n + i] = M[(size_t)i * n + j];
+}
+
+}  // namespace
+
+bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, double tu, BcrFactors* out) {
+    int L = 0;
+    while (((1 << L) - 1) < R) ++L;
+    if (((1 << L) - 1) != R || C < 1) return false;
+    const size_t n2 = (size_t)C * C;
+    out->R = R; out->C = C; out->L = L;
+    out->Pt.assign((size_t)L * n2, 0.0);
+    out->Qt.assign((size_t)L * n2, 0.0);
+    out->Bt.assign((size_t)L * n2, 0.0);
+    // Level 0: A_0 = a I, C_0 = c I, B_0 = d I + T.
+    std::vector<double> A(n2, 0.0), Cm(n2, 0.0), B(n2, 0.0);
+    for (int k = 0; k < C; ++k) {
+        A[(size_t)k * C + k] = a;
+        Cm[(size_t)k * C + k] = c;
+        B[(size_t)k * C + k] = d + td;
+        if (k > 0) B[(size_t)k * C + k - 1] = tl;
+        if (k + 1 < C) B[(size_t)k * C + k + 1] = tu;
+    }
+    std::vector<double> Binv, P(n2), Q(n2), t1(n2), t2(n2);
+    for (int l = 0; l < L; ++l) {
+        Binv = B;
+        if (!invert(Binv, C)) return false;
+        matmul(A.data(), Binv.data(), P.data(), C);     // P_l = A_l B_l^{-1}
+        matmul(Cm.data(), Binv.data(), Q.data(), C);    // Q_l = C_l B_l^{-1}
+        transpose_into(P.data(), out->Pt.data() + (size_t)l * n2, C);
+        transpose_into(Q.data(), out->Qt.data() + (size_t)l * n2, C);
+        transpose_into(Binv.data(), out->Bt.data() + (size_t)l * n2, C);
+        if (l + 1 == L) break;
+        // B_{l+1} = B_l - P_l C_l - Q_l A_l ; A_{l+1} = -P_l A_l ; C_{l+1} = -Q_l C_l
+        matmul(P.data(), Cm.data(), t1.data(), C);
+        matmul(Q.data(), A.data(), t2.data(), C);
+        for (size_t e = 0; e < n2; ++e) B[e] = B[e] - t1[e] - t2[e];
+        matmul(P.data(), A.data(), t1.data(), C);
+        matmul(Q.data(), Cm.data(), t2.data(), C);
+        for (size_t e = 0; e < n2; ++e) { A[e] = -t1[e]; Cm[e] = -t2[e]; }
+    }
+    for (double v : out->Pt) if (!std::isfinite(v)) return false;
+    for (double v : out->Bt) if (!std::isfinite(v)) return false;
+    return true;
+}
+
+std::vector<double> spline_moment_operator(int mc) {
+    // Unknowns M_0..M_mc (second derivatives at the knots), H = 1/mc.
+    // Interior knots k = 1..mc-1:  M_{k-1} + 4 M_k + M_{k+1} = 6 (y_{k+1} - 2 y_k + y_{k-1}) / H^2.
+    // Not-a-knot (third derivative continuous at x_1 and x_{mc-1}):
+    //   M_0 - 2 M_1 + M_2 = 0,   M_{mc-2} - 2 M_{mc-1} + M_mc = 0.
+    // Three knots (mc = 2): the interpolant is the parabola, M_0 = M_1 = M_2.
+    const int K = mc + 1, Nc = mc - 1;
+    const double H = 1.0 / mc;
+    std::vector<double> Sm((size_t)K * Nc, 0.0);
+    if (mc == 2) {
+        for (int r = 0; r < 3; ++r) Sm[(size_t)r * 1 + 0] = -2.0 / (H * H);
+        return Sm;
+    }
+    std::vector<double> Km((size_t)K * K, 0.0);
+    Km[0 * K + 0] = 1.0; Km[0 * K + 1] = -2.0; Km[0 * K + 2] = 1.0;
+    for (int k = 1; k < mc; ++k) {
+        Km[(size_t)k * K + k - 1] = 1.0;
+        Km[(size_t)k * K + k] = 4.0;
+        Km[(size_t)k * K + k + 1] = 1.0;
+    }
+    Km[(size_t)mc * K + mc - 2] = 1.0; Km[(size_t)mc * K + mc - 1] = -2.0; Km[(size_t)mc * K + mc] = 1.0;
+    std::vector<double> Kinv = Km;
+    invert(Kinv, K);
+    // rhs for a unit value at interior knot q (1..mc-1): row k gets 6/H^2 * (second difference of e_q at k).
+    for (int q = 1; q < mc; ++q) {
+        std::vector<double> rhs(K, 0.0);
+        for (int k = 1; k < mc; ++k) {
+            double v = 0.0;
+            if (k + 1 == q) v += 1.0;
+            if (k == q) v -= 2.0;
+            if (k - 1 == q) v += 1.0;
+            rhs[k] = 6.0 * v / (H * H);
+        }
+        for (int r = 0; r < K; ++r) {
+            double acc = 0.0;
+            for (int k = 0; k < K; ++k) acc += Kinv[(size_t)r * K + k] * rhs[k];
+            Sm[(size_t)r * Nc + (q - 1)] = acc;
+        }
+    }
+    return Sm;
+}
+
+}  // namespace asdsm

@@ -1,0 +1,79 @@
+"""CPU checks of the C ABI boundary: the library builds, loads and exports every
+entry point declared in include/*.h.  No compute call is made here."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(asdsm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_01163_gb300 import asdsm
+    return asdsm.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("asdsm_setup", "asdsm_solve", "asdsm_residual", "asdsm_destroy", "asdsm_initial_guess",
+                     "asdsm_submesh_solve", "asdsm_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_structs_match_the_header_layout(lib):
+    from paper_2303_01163_gb300 import asdsm
+    assert ctypes.sizeof(asdsm.Desc) == 4 * 4 + 6 * 8
+    assert ctypes.sizeof(asdsm.Opts) == 8 + 4 * 4 + 8 + 8 + 8 + 4 + 4 + 8
+    assert ctypes.sizeof(asdsm.Stats) == 4 * 4 + 4 * 8
+
+
+def test_strerror_and_defaults_need_no_gpu(lib):
+    from paper_2303_01163_gb300 import asdsm
+    assert lib.asdsm_strerror(0) == b"ok"
+    assert b"invalid" in lib.asdsm_strerror(-1)
+    o = asdsm.default_opts()
+    assert o.tol == 1e-10 and o.accel_m == 8 and o.precision == asdsm.MIXED
+
+
+def test_null_arguments_are_rejected_without_touching_the_gpu(lib):
+    from paper_2303_01163_gb300 import asdsm
+    h = ctypes.c_void_p()
+    assert lib.asdsm_setup(None, None, None, ctypes.byref(h)) == asdsm.ERR_INVALID
+    d = asdsm.Desc()
+    d.d, d.n, d.mc = 2, 66, 8              # N-1 = 65 is not a power of two
+    d.alpha[0] = d.alpha[1] = 1.0
+    assert lib.asdsm_setup(ctypes.byref(d), None, None, ctypes.byref(h)) == asdsm.ERR_INVALID
+    d.n, d.mc = 65, 3                      # mc not a power of two
+    assert lib.asdsm_setup(ctypes.byref(d), None, None, ctypes.byref(h)) == asdsm.ERR_INVALID
+    d.mc = 8
+    d.alpha[0] = 0.0                       # alpha must be positive
+    assert lib.asdsm_setup(ctypes.byref(d), None, None, ctypes.byref(h)) == asdsm.ERR_INVALID
+    assert lib.asdsm_solve(None, None, None, None) == asdsm.ERR_INVALID
+    lib.asdsm_destroy(None)
+
+
+def test_product_package_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2303_01163_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
+        src = open(path).read()
+        assert "oracle" not in re.findall(r"^\s*(?:from|import)\s+(\w+)", src, flags=re.M), path
