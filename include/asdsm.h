@@ -22,8 +22,9 @@
  *
  * Sizes: N - 1 must be a power of two (N = 2^p + 1, p >= 2) and mc (coarse
  * intervals per axis, the N_c + 1 of eq. 2.1) a power of two with
- * 2 <= mc <= (N - 1)/4, so every line, submesh and hole system has
- * 2^q - 1 unknowns per axis.  Other sizes return ASDSM_ERR_INVALID.
+ * 2 <= (N - 1)/mc <= 32, so every line, submesh and hole system has
+ * 2^q - 1 unknowns per axis and a hole's factors fit in shared memory.
+ * Other sizes return ASDSM_ERR_INVALID.
  *
  * Errors: every int-returning function returns ASDSM_OK (0) or a negative
  * code (see asdsm_strerror).  The library never aborts or traps; after an
@@ -90,7 +91,22 @@ typedef struct {
     double  rel_res0;      /* relative residual of the initial iterate */
     double  setup_ms;      /* right-hand sides + initial guess, GPU time */
     double  solve_ms;      /* whole call, GPU time */
+    int64_t launches;      /* kernels this call launched */
 } asdsm_stats;
+
+/* Per-kernel-family timing of the last asdsm_solve calls (enabled with
+ * asdsm_profile).  ms is the sum of CUDA-event durations on the handle's
+ * stream around the family's launches; bytes and flops are the ALGORITHMIC
+ * traffic and arithmetic of those launches (the minimum the method needs:
+ * each grid value read or written once), counted by the library. */
+typedef struct {
+    char    name[24];
+    int64_t launches;
+    int64_t calls;         /* timed groups (one group may hold several launches) */
+    double  ms;
+    double  bytes;
+    double  flops;
+} asdsm_kprof;
 
 typedef struct asdsm_handle asdsm_handle;
 
@@ -147,6 +163,17 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
  * (entry 0: initial iterate).  Copies min(cap, sweeps+1) values to the host
  * array hist and returns that count (or a negative error). */
 int asdsm_history(asdsm_handle* h, double* hist, int cap);
+
+/* Turn per-kernel-family CUDA-event timing on (1) or off (0) and clear the
+ * accumulated counters.  Timing adds two event records per kernel group. */
+int asdsm_profile(asdsm_handle* h, int enable);
+
+/* Copy up to cap family records (see asdsm_kprof) to the host array out;
+ * returns the number of families or a negative error. */
+int asdsm_profile_read(asdsm_handle* h, asdsm_kprof* out, int cap);
+
+/* Kernels launched by this library in this process so far. */
+int64_t asdsm_launch_count(void);
 
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void asdsm_destroy(asdsm_handle* h);

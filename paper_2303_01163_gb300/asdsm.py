@@ -49,10 +49,15 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("status", ctypes.c_int32), ("hole_fixes", ctypes.c_int32),
                 ("fixed_shift", ctypes.c_int32), ("rel_res", ctypes.c_double), ("rel_res0", ctypes.c_double),
-                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KProf(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("calls", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 _lib = None
@@ -87,6 +92,12 @@ def load() -> ctypes.CDLL:
     lib.asdsm_submesh_solve.restype = ctypes.c_int
     lib.asdsm_history.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.asdsm_history.restype = ctypes.c_int
+    lib.asdsm_profile.argtypes = [P, ctypes.c_int]
+    lib.asdsm_profile.restype = ctypes.c_int
+    lib.asdsm_profile_read.argtypes = [P, ctypes.POINTER(KProf), ctypes.c_int]
+    lib.asdsm_profile_read.restype = ctypes.c_int
+    lib.asdsm_launch_count.argtypes = []
+    lib.asdsm_launch_count.restype = ctypes.c_int64
     lib.asdsm_destroy.argtypes = [P]
     lib.asdsm_destroy.restype = None
     lib.asdsm_strerror.argtypes = [ctypes.c_int]
@@ -190,6 +201,19 @@ class Solver:
         rc = self._lib.asdsm_submesh_solve(self._h, int(mesh), _ptr(inp), _ptr(out))
         if rc != OK:
             raise AsdsmError(rc, "asdsm_submesh_solve")
+
+    def profile(self, enable: bool = True):
+        rc = self._lib.asdsm_profile(self._h, 1 if enable else 0)
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_profile")
+
+    def profile_read(self) -> dict:
+        buf = (KProf * 16)()
+        n = self._lib.asdsm_profile_read(self._h, buf, 16)
+        if n < 0:
+            raise AsdsmError(n, "asdsm_profile_read")
+        return {buf[i].name.decode(): {"launches": buf[i].launches, "calls": buf[i].calls, "ms": buf[i].ms,
+                                       "bytes": buf[i].bytes, "flops": buf[i].flops} for i in range(n)}
 
     def history(self) -> list:
         cap = 100000

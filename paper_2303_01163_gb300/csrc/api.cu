@@ -86,6 +86,13 @@ struct asdsm_handle {
     double* hsmall = nullptr;       // pinned host mirror of dsmall
     std::vector<double> hist;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    // Per-kernel-family profiling (asdsm_profile).
+    bool prof = false;
+    asdsm_kprof pc[8] = {};
+    struct PendingEv { int a, b, cat; long long launches; double bytes, flops; };
+    std::vector<cudaEvent_t> evpool;
+    int evnext = 0;
+    std::vector<PendingEv> pend_ev;
 };
 
 namespace {
@@ -179,6 +186,67 @@ int read_small(asdsm_handle* h, int count) {
     return ASDSM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Profiling: event pairs around kernel groups, resolved after the solve syncs.
+// ---------------------------------------------------------------------------
+enum ProfCat { PC_RESID = 0, PC_BCR, PC_FILL, PC_MERGE, PC_LSQ, PC_NORM, PC_OTHER, PC_COUNT };
+const char* kProfNames[PC_COUNT] = {"residual", "bcr_aniso", "fill_holes", "merge", "least_squares", "norms", "other"};
+
+struct ProfMark { int ev = -1; long long l0 = 0; };
+
+ProfMark prof_begin(asdsm_handle* h) {
+    ProfMark m;
+    m.l0 = launch_count();
+    if (!h->prof) return m;
+    if (h->evnext + 2 > (int)h->evpool.size()) {
+        for (int q = 0; q < 64; ++q) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return m;
+            h->evpool.push_back(e);
+        }
+    }
+    m.ev = h->evnext;
+    h->evnext += 2;
+    cudaEventRecord(h->evpool[m.ev], h->st);
+    return m;
+}
+
+void prof_end(asdsm_handle* h, const ProfMark& m, int cat, double bytes, double flops) {
+    if (!h->prof || m.ev < 0) return;
+    cudaEventRecord(h->evpool[m.ev + 1], h->st);
+    h->pend_ev.push_back({m.ev, m.ev + 1, cat, launch_count() - m.l0, bytes, flops});
+}
+
+// After a stream synchronisation: fold the recorded pairs into the counters.
+void prof_resolve(asdsm_handle* h) {
+    for (const auto& p : h->pend_ev) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->evpool[p.a], h->evpool[p.b]) != cudaSuccess) continue;
+        asdsm_kprof& c = h->pc[p.cat];
+        c.ms += ms;
+        c.calls += 1;
+        c.launches += p.launches;
+        c.bytes += p.bytes;
+        c.flops += p.flops;
+    }
+    h->pend_ev.clear();
+    h->evnext = 0;
+}
+
+// Multiply-adds of block cyclic reduction for R = 2^L - 1 rows of C unknowns
+// (forward: two C x C products per reduced row; backward: B^{-1} f plus one
+// product per existing neighbour).
+double bcr_macs(int R, int C, int L) {
+    const double c2 = (double)C * C;
+    double macs = 0.0;
+    for (int l = 0; l + 1 < L; ++l) macs += (double)(((R + 1) >> (l + 1)) - 1) * 2.0 * c2;
+    for (int l = 0; l < L; ++l) {
+        const double rb = (double)((R + 1) >> (l + 1));
+        macs += rb * c2 + 2.0 * (rb - 1.0) * c2;
+    }
+    return macs;
+}
+
 // ||b_ff||^2 via the FP64 residual of the zero-interior grid (r = b there).
 int bnorm2(asdsm_handle* h, const double* s, const double* u, double* out) {
     const Geometry& g = h->g;
@@ -263,7 +331,12 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
     const long long NN = (long long)g.N * g.N;
     if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), 4096))) return rc;
     h->hist.clear();
+    h->pend_ev.clear();
+    h->evnext = 0;
     asdsm_stats stt{};
+    const long long launches0 = launch_count();
+    const double NF2 = (double)g.Nf * g.Nf;
+    const double ES = (double)sizeof(T);
     CK(cudaEventRecord(h->ev0, st));
 
     double b2 = 0.0;
@@ -332,16 +405,25 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         ResidOut o{};
         o.rfc = w.Xfc; o.rcf = w.Xcf; o.rskel = w.rskel; o.rfull = nullptr; o.partials = h->partials;
         int nb = 0;
-        if (!mixed) {
-            double* dst = pend.count > 0 ? unxt : ucur;
-            CK(residual_fp64(s, ucur, dst, pend, g, h->sten, o, &nb, st));
-            if (pend.count > 0) std::swap(ucur, unxt);
-        } else {
-            UpdateTerms ps = pend;
-            for (int q = 0; q < ps.count; ++q) ps.coef[q] *= scale;
-            CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), st));
-            CK(residual_mixed(h->s_hi, h->s_lo, h->U[Ucur], h->U[1 - Ucur], ps, scale, g, mk, o, &nb, h->dflag, st));
-            if (pend.count > 0) Ucur = 1 - Ucur;
+        {
+            // Algorithmic bytes: read u and s, read each pending direction, write u when updated,
+            // write the skeleton gathers (fc, cf, compact).
+            const double ub = mixed ? 8.0 : 8.0;
+            const double bytes = NF2 * (ub + 8.0 + ES * pend.count + (pend.count > 0 ? ub : 0.0))
+                               + ES * (2.0 * g.Nc * g.Nf + (double)g.skel);
+            if (mixed) CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), st));
+            const ProfMark pm = prof_begin(h);
+            if (!mixed) {
+                double* dst = pend.count > 0 ? unxt : ucur;
+                CK(residual_fp64(s, ucur, dst, pend, g, h->sten, o, &nb, st));
+                if (pend.count > 0) std::swap(ucur, unxt);
+            } else {
+                UpdateTerms ps = pend;
+                for (int q = 0; q < ps.count; ++q) ps.coef[q] *= scale;
+                CK(residual_mixed(h->s_hi, h->s_lo, h->U[Ucur], h->U[1 - Ucur], ps, scale, g, mk, o, &nb, h->dflag, st));
+                if (pend.count > 0) Ucur = 1 - Ucur;
+            }
+            prof_end(h, pm, PC_RESID, bytes, 0.0);
         }
         pend.count = 0;
         CK(reduce_partials(h->partials, nb, 2, h->dsmall, st));
@@ -397,13 +479,21 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         // ---- steps 4-5: the error guess of Algorithm 1 without b_cc ----
         const int bit = choice_bit(op.seed, k);
         BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
-        CK(bcr_solve<T>(sys, 2, st));
         {
+            const ProfMark pm = prof_begin(h);
+            CK(bcr_solve<T>(sys, 2, st));
+            const double flops = 2.0 * 2.0 * bcr_macs(g.Nf, g.Nc, h->fc[pi].L);
+            const double bytes = ES * (4.0 * g.Nf * g.Nc) + ES * 2.0 * 3.0 * h->fc[pi].L * (double)g.Nc * g.Nc;
+            prof_end(h, pm, PC_BCR, bytes, flops);
+        }
+        {
+            const ProfMark pm = prof_begin(h);
             const T* av[2] = {(const T*)w.Yfc, (const T*)w.Ycf};
             int nb2 = 0;
             // Two separate dots over the same length.
             CK(multi_dot<T>(av, av, 2, (long long)g.Nf * g.Nc, h->partials, &nb2, st));
             CK(reduce_partials(h->partials, nb2, 2, h->dsmall + 200, st));
+            prof_end(h, pm, PC_NORM, ES * 2.0 * g.Nf * g.Nc, 4.0 * g.Nf * g.Nc);
         }
         T* z = (T*)w.z[kc];
         MergeArgs<T> ma{};
@@ -412,15 +502,27 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         ma.Sm = (const T*)h->Sm[pi];
         ma.E1 = (T*)w.E1; ma.E2 = (T*)w.E2; ma.M1 = (T*)w.M1; ma.M2 = (T*)w.M2;
         ma.z = z; ma.g = g;
-        CK(merge_knots<T>(ma, st));
-        CK(merge_write<T>(ma, st));
+        {
+            const ProfMark pm = prof_begin(h);
+            CK(merge_knots<T>(ma, st));
+            CK(merge_write<T>(ma, st));
+            prof_end(h, pm, PC_MERGE, ES * 4.0 * g.Nf * g.Nc, 0.0);
+        }
         FillArgs<T> fa{};
         fa.mode = FILL_HOMOGENEOUS;
         fa.z = z; fa.out = z;
         fa.Pt = (const T*)h->hole[pi].Pt; fa.Qt = (const T*)h->hole[pi].Qt; fa.Bt = (const T*)h->hole[pi].Bt;
         fa.L = h->hole[pi].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
-        CK(fill_holes<T>(fa, h->num_sms, st));
+        {
+            const ProfMark pm = prof_begin(h);
+            CK(fill_holes<T>(fa, h->num_sms, st));
+            const double holes = (double)g.mc * g.mc;
+            const double flops = 2.0 * holes * bcr_macs(g.n - 1, g.n - 1, h->hole[pi].L);
+            const double bytes = ES * (holes * (g.n - 1.0) * (g.n - 1.0) + holes * 4.0 * (g.n - 1.0));
+            prof_end(h, pm, PC_FILL, bytes, flops);
+        }
         // ---- step 6: least squares on the skeleton rows ----
+        const ProfMark pm_lsq = prof_begin(h);
         CK(skeleton_apply<T>(z, g, h->sten, (T*)w.q, st));
         const T* da[2 + 2 * kMaxM];
         const T* db[2 + 2 * kMaxM];
@@ -434,6 +536,7 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         int nb3 = 0;
         CK(multi_dot<T>(da, db, nd, g.skel, h->partials, &nb3, st));
         CK(reduce_partials(h->partials, nb3, nd, h->dsmall, st));
+        prof_end(h, pm_lsq, PC_LSQ, ES * (double)g.skel * (6.0 + 2.0 * nd), 2.0 * (double)g.skel * nd);
         if (int rc = read_small(h, nd)) return rc;
         const double qq = h->hsmall[0], qr = h->hsmall[1];
         if (m == 1) {
@@ -490,6 +593,8 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
     cudaEventElapsedTime(&ms_setup, h->ev0, h->ev1);
     cudaEventElapsedTime(&ms_all, h->ev0, h->ev2);
     h->hist = rhist;
+    prof_resolve(h);
+    stt.launches = launch_count() - launches0;
     stt.sweeps = k;
     stt.status = status;
     stt.hole_fixes = hole_fixes;
@@ -617,6 +722,7 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaEventCreate(&h->ev2)) != cudaSuccess) return fail(set_cuda_error(e));
     if ((rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), 4096)))) return fail(rc);
+    asdsm_profile(h, 0);
     *out = h;
     return ASDSM_OK;
 }
@@ -761,8 +867,28 @@ int asdsm_history(asdsm_handle* h, double* hist, int cap) {
     return n;
 }
 
+int asdsm_profile(asdsm_handle* h, int enable) {
+    if (!h) return ASDSM_ERR_INVALID;
+    h->prof = enable != 0;
+    std::memset(h->pc, 0, sizeof(h->pc));
+    for (int c = 0; c < PC_COUNT; ++c) std::snprintf(h->pc[c].name, sizeof(h->pc[c].name), "%s", kProfNames[c]);
+    h->pend_ev.clear();
+    h->evnext = 0;
+    return ASDSM_OK;
+}
+
+int asdsm_profile_read(asdsm_handle* h, asdsm_kprof* out, int cap) {
+    if (!h || (!out && cap > 0)) return ASDSM_ERR_INVALID;
+    const int n = std::min<int>(cap, PC_COUNT);
+    for (int c = 0; c < n; ++c) out[c] = h->pc[c];
+    return n;
+}
+
+int64_t asdsm_launch_count(void) { return launch_count(); }
+
 void asdsm_destroy(asdsm_handle* h) {
     if (!h) return;
+    for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
     auto fr = [](void* p) { if (p) cudaFree(p); };
     for (int p = 0; p < 2; ++p) {
         DevBcr* ds[4] = {&h->fc[p], &h->cf[p], &h->cc[p], &h->hole[p]};

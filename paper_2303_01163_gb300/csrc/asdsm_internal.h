@@ -61,6 +61,10 @@ struct Geometry {
     long long skel;   // compact skeleton length: Nc*Nf + Nc*(Nf - Nc)
 };
 
+// Process-wide count of kernel launches made by the library.
+void note_launch(long long n = 1);
+long long launch_count();
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (kernels_*.cu).  All enqueue on `st`; none synchronise.
 // ---------------------------------------------------------------------------

@@ -4,8 +4,13 @@
 // operator for the step-6 least squares, reductions and conversions.
 #include "asdsm_internal.h"
 #include <cuda_runtime.h>
+#include <atomic>
 
 namespace asdsm {
+
+static std::atomic<long long> g_launches{0};
+void note_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -534,6 +539,7 @@ cudaError_t residual_fp64(const double* s, const double* u_in, double* u_out, co
     dim3 grid((g.Nf + RX - 1) / RX, (g.Nf + RY - 1) / RY);
     *nblocks = grid.x * grid.y;
     residual_fp64_kernel<<<grid, RTHREADS, 0, st>>>(s, u_in, u_out, up, g, c, out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -543,6 +549,7 @@ cudaError_t residual_mixed(const float* s_hi, const float* s_lo, const long long
     dim3 grid((g.Nf + RX - 1) / RX, (g.Nf + RY - 1) / RY);
     *nblocks = grid.x * grid.y;
     residual_mixed_kernel<<<grid, RTHREADS, 0, st>>>(s_hi, s_lo, U_in, U_out, up, g, k, out, overflow_flag);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -552,11 +559,13 @@ cudaError_t build_submesh_rhs(const double* s, const double* u, const Geometry& 
                               T* bfc, T* bcf, T* bcc, cudaStream_t st) {
     const long long total = 2LL * g.Nf * g.Nc + (long long)g.Nc * g.Nc;
     submesh_rhs_kernel<T><<<grid_for(total), 256, 0, st>>>(s, u, g, alpha[0], alpha[1], beta[0], beta[1], bfc, bcf, bcc);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t reduce_partials(const double* partials, int nblocks, int ncols, double* out, cudaStream_t st) {
     reduce_partials_kernel<<<1, 1024, 0, st>>>(partials, nblocks, ncols, out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -569,6 +578,7 @@ cudaError_t multi_dot(const T* const* a, const T* const* b, int ndots, long long
     unsigned grid = grid_for(n, DOT_THREADS, 152LL * 2);
     *nblocks = (int)grid;
     multi_dot_kernel<T><<<grid, DOT_THREADS, 0, st>>>(d, ndots, n, partials);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -576,18 +586,21 @@ template <typename T>
 cudaError_t merge_knots(const MergeArgs<T>& a, cudaStream_t st) {
     const size_t smem = sizeof(T) * (size_t)a.g.Nc;
     merge_knots_kernel<T><<<2 * a.g.Nc, 128, smem, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t merge_write(const MergeArgs<T>& a, cudaStream_t st) {
     merge_write_kernel<T><<<grid_for(2LL * a.g.Nf * a.g.Nc), 256, 0, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t skeleton_apply(const T* z, const Geometry& g, const Stencil& s, T* q, cudaStream_t st) {
     skeleton_apply_kernel<T><<<grid_for(g.skel), 256, 0, st>>>(z, g, s, q);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -598,24 +611,28 @@ cudaError_t combine_skeleton(const T* q, const T* const* Qp, const double* beta,
     CombineArgs<T> c{};
     for (int j = 0; j < k; ++j) { c.Qp[j] = Qp[j]; c.beta[j] = beta[j]; }
     combine_kernel<T><<<grid_for(n), 256, 0, st>>>(q, c, k, inv_nu, n, out);
+    note_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t fill_value(T* p, long long n, T v, cudaStream_t st) {
     fill_value_kernel<T><<<grid_for(n), 256, 0, st>>>(p, n, v);
+    note_launch();
     return cudaGetLastError();
 }
 
 template <typename Ts, typename Td>
 cudaError_t copy_interior(const Ts* src, Td* dst, const Geometry& g, cudaStream_t st) {
     copy_interior_kernel<Ts, Td><<<grid_for((long long)g.Nf * g.Nf), 256, 0, st>>>(src, dst, g);
+    note_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t ring_from(const double* u, T* z, const Geometry& g, int zero_interior, cudaStream_t st) {
     ring_from_kernel<T><<<grid_for((long long)g.N * g.N), 256, 0, st>>>(u, z, g, zero_interior);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -624,27 +641,32 @@ cudaError_t maxabs(const T* v, long long n, double* partials, int* nblocks, cuda
     unsigned grid = grid_for(n, 256, 152LL * 2);
     *nblocks = (int)grid;
     maxabs_kernel<T><<<grid, 256, 0, st>>>(v, n, partials);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t to_fixed(const float* z, const double* u_ring_src, long long* U, double scale, const Geometry& g, cudaStream_t st) {
     to_fixed_kernel<<<grid_for((long long)g.N * g.N), 256, 0, st>>>(z, u_ring_src, U, scale, g);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t from_fixed(const long long* U, double inv_scale, double* u, const Geometry& g, cudaStream_t st) {
     from_fixed_kernel<<<grid_for((long long)g.Nf * g.Nf), 256, 0, st>>>(U, inv_scale, u, g);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t split_source(const double* s, float* hi, float* lo, long long n, cudaStream_t st) {
     split_kernel<<<grid_for(n), 256, 0, st>>>(s, hi, lo, n);
+    note_launch();
     return cudaGetLastError();
 }
 
 template <typename Ts, typename Td>
 cudaError_t convert_array(const Ts* in, Td* out, long long n, cudaStream_t st) {
     convert_kernel<Ts, Td><<<grid_for(n), 256, 0, st>>>(in, out, n);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -113,6 +113,7 @@ cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, cudaSt
     dim3 block(TC, TR);
     BcrSys<T> g1 = ngroups > 1 ? groups[1] : groups[0];
     bcr_level_kernel<T, kBackward><<<grid, block, 0, st>>>(groups[0], g1, ngroups, level);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -287,6 +288,7 @@ cudaError_t fill_holes(const FillArgs<T>& a, int num_sms, cudaStream_t st) {
     long long grid = (long long)num_sms * per_sm;
     if (grid > nholes) grid = nholes;
     fill_holes_kernel<T><<<(unsigned)grid, FILL_THREADS, smem, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
