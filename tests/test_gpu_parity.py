@@ -231,7 +231,10 @@ def test_advection_dominated_tiny_grid_matches_oracle_iterates(lib):
         u = _dev(p.g)
         sv.solve(_dev(p.s), u)
     assert _relerr(orc.interior(u.cpu().numpy()), uo) <= 1e-10
-    # NaN in the source is reported, not trapped
+
+
+def test_nan_source_is_reported_not_trapped(lib):
+    import torch
     with lib.Solver(17, 4, (1, 1), (1, 1), precision=lib.MIXED) as sv:
         s = torch.zeros(17, 17, dtype=torch.float64, device="cuda")
         s[5, 5] = float("nan")
