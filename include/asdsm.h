@@ -175,6 +175,31 @@ int asdsm_profile_read(asdsm_handle* h, asdsm_kprof* out, int cap);
 /* Kernels launched by this library in this process so far. */
 int64_t asdsm_launch_count(void);
 
+/* Fine residual and relative residual norm WITHOUT ANY DEVICE ALLOCATION.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc when they need the residual - code being recorded into a CUDA
+ * graph (allocation is not a capturable operation), services whose device
+ * memory is reserved up front by their own pool, loops where an allocation
+ * would stall the device.  It needs no handle.
+ * desc: only d (= 2), n (N, 3 <= N <= 8193), alpha and beta are read.
+ * s, u: device N*N FP64 arrays as for asdsm_residual (u's ring = g).
+ * r: device N*N or NULL; its interior receives r = b_ff - A_ff u (the ring is
+ * not written).  rel_norm: host pointer or NULL; receives ||r||/||b_ff||
+ * (the call then synchronises `stream`).  stream: cudaStream_t or NULL.
+ * Scratch: statically allocated device arrays of about 1 MiB held by every
+ * GPU that loads the library until the process exits.  The first call on a
+ * device looks up their device address (cudaGetSymbolAddress) with that
+ * device current, so make that first call before any stream capture.  All
+ * calls share the scratch; each call rewrites every slot it reads, so nothing
+ * carries over, but calls that overlap on the GPU race.  Grids larger than
+ * 8193 points per axis return ASDSM_ERR_INVALID (message in
+ * asdsm_noalloc_last_error). */
+int asdsm_residual_noalloc(const asdsm_desc* desc, const double* s, const double* u, double* r,
+                           double* rel_norm, void* stream);
+
+/* Text of the last error of asdsm_residual_noalloc on this thread ("" if none). */
+const char* asdsm_noalloc_last_error(void);
+
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void asdsm_destroy(asdsm_handle* h);
 

@@ -98,6 +98,10 @@ def load() -> ctypes.CDLL:
     lib.asdsm_profile_read.restype = ctypes.c_int
     lib.asdsm_launch_count.argtypes = []
     lib.asdsm_launch_count.restype = ctypes.c_int64
+    lib.asdsm_residual_noalloc.argtypes = [ctypes.POINTER(Desc), P, P, P, ctypes.POINTER(ctypes.c_double), P]
+    lib.asdsm_residual_noalloc.restype = ctypes.c_int
+    lib.asdsm_noalloc_last_error.argtypes = []
+    lib.asdsm_noalloc_last_error.restype = ctypes.c_char_p
     lib.asdsm_destroy.argtypes = [P]
     lib.asdsm_destroy.restype = None
     lib.asdsm_strerror.argtypes = [ctypes.c_int]
@@ -132,6 +136,26 @@ def _ptr(t, dtype_name="float64"):
     if not t.is_contiguous():
         raise TypeError("expected a contiguous tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def residual_noalloc(N: int, alpha, beta, s, u, r=None, stream=None) -> float:
+    """asdsm_residual_noalloc: residual and ||r||/||b|| with no device allocation."""
+    import torch
+    lib = load()
+    d = Desc()
+    d.d, d.n = 2, int(N)
+    for q in range(2):
+        d.alpha[q] = float(alpha[q])
+        d.beta[q] = float(beta[q])
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    rel = ctypes.c_double()
+    rc = lib.asdsm_residual_noalloc(ctypes.byref(d), _ptr(s), _ptr(u), _ptr(r) if r is not None else None,
+                                    ctypes.byref(rel), ctypes.c_void_p(stream.cuda_stream))
+    if rc != OK:
+        raise RuntimeError(f"asdsm_residual_noalloc: {lib.asdsm_strerror(rc).decode()} ({rc}): "
+                           f"{lib.asdsm_noalloc_last_error().decode()}")
+    return rel.value
 
 
 @dataclass

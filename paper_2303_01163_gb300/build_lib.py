@@ -1,6 +1,6 @@
 """Builds the in-tree CUDA library libasdsm.so for sm_103a with nvcc.
 
-Four translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``paper_2303_01163_gb300/_lib/libasdsm.so``.  A rebuild happens only when a
 source or header is newer than the library.
 """
@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libasdsm.so")
 
-SOURCES = ["host_math.cu", "kernels_solve.cu", "kernels_grid.cu", "api.cu"]
+SOURCES = ["host_math.cu", "kernels_solve.cu", "kernels_grid.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
