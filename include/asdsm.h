@@ -129,7 +129,9 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
 /* Replace the iteration options of an existing handle (e.g. precision). */
 int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts);
 
-/* Algorithm 4 (ASDSM).  s: device N*N source term (boundary entries unused).
+/* Algorithm 4 (ASDSM).  The initial guess (Algorithm 1) is computed in FP64 in
+ * both precisions; the mixed path then runs its sweeps as described above.
+ * s: device N*N source term (boundary entries unused).
  * u: device N*N; its boundary ring carries the Dirichlet data g on input and
  * is never written; its interior is overwritten by the solution (or used as
  * the first iterate when opts.skip_initial_guess is set).  stats may be NULL.
@@ -137,8 +139,9 @@ int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts);
  * ASDSM_STAGNATED otherwise (u then holds the last iterate), or an error. */
 int asdsm_solve(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats);
 
-/* Algorithm 1 with b_cc given (the initial guess u^(0)).  Same s/u contract
- * as asdsm_solve; writes the interior of u. */
+/* Algorithm 1 with b_cc given (the initial guess u^(0)), computed in the
+ * handle's precision (FP32 steps for ASDSM_MIXED).  Same s/u contract as
+ * asdsm_solve; writes the interior of u. */
 int asdsm_initial_guess(asdsm_handle* h, const double* s, double* u);
 
 /* Fine residual of Algorithm 4 step 3: r = b_ff - A_ff u over the interior,

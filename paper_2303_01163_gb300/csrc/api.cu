@@ -33,7 +33,8 @@ thread_local std::string g_last_error;
 constexpr int kMaxM = 16;
 
 struct DevBcr {
-    void* Pt = nullptr; void* Qt = nullptr; void* Bt = nullptr;
+    void* Mt = nullptr; void* Bt = nullptr;
+    double wl[kMaxLevels] = {}, wr[kMaxLevels] = {};
     int R = 0, C = 0, L = 0;
 };
 
@@ -110,15 +111,16 @@ int set_cuda_error(cudaError_t e) {
 
 template <typename T>
 int upload_bcr(const BcrFactors& f, DevBcr* d) {
-    const size_t n = f.Pt.size();
+    const size_t n = f.Mt.size();
     std::vector<T> tmp(n);
-    void** dst[3] = {&d->Pt, &d->Qt, &d->Bt};
-    const std::vector<double>* src[3] = {&f.Pt, &f.Qt, &f.Bt};
-    for (int q = 0; q < 3; ++q) {
+    void** dst[2] = {&d->Mt, &d->Bt};
+    const std::vector<double>* src[2] = {&f.Mt, &f.Bt};
+    for (int q = 0; q < 2; ++q) {
         CK(cudaMalloc(dst[q], n * sizeof(T)));
         for (size_t e = 0; e < n; ++e) tmp[e] = (T)(*src[q])[e];
         CK(cudaMemcpy(*dst[q], tmp.data(), n * sizeof(T), cudaMemcpyHostToDevice));
     }
+    for (int l = 0; l < f.L; ++l) { d->wl[l] = f.wl[l]; d->wr[l] = f.wr[l]; }
     d->R = f.R; d->C = f.C; d->L = f.L;
     return ASDSM_OK;
 }
@@ -135,17 +137,26 @@ template <typename T>
 BcrSys<T> sys_of(const DevBcr& d, void* X, void* Y, int nsys = 1) {
     BcrSys<T> s{};
     s.X = (T*)X; s.Y = (T*)Y;
-    s.Pt = (const T*)d.Pt; s.Qt = (const T*)d.Qt; s.Bt = (const T*)d.Bt;
+    s.Mt = (const T*)d.Mt; s.Bt = (const T*)d.Bt;
+    for (int l = 0; l < d.L; ++l) { s.wl[l] = (T)d.wl[l]; s.wr[l] = (T)d.wr[l]; }
     s.R = d.R; s.C = d.C; s.L = d.L; s.nsys = nsys;
     s.stride = (long long)d.R * d.C;
     return s;
 }
 
+// Hole factors into a FillArgs.
 template <typename T>
-int ensure_work(asdsm_handle* h, int pi) {
+void hole_factors(const DevBcr& d, FillArgs<T>* fa) {
+    fa->Mt = (const T*)d.Mt; fa->Bt = (const T*)d.Bt;
+    for (int l = 0; l < d.L; ++l) { fa->wl[l] = (T)d.wl[l]; fa->wr[l] = (T)d.wr[l]; }
+    fa->L = d.L;
+}
+
+template <typename T>
+int ensure_work(asdsm_handle* h, int pi, int slots = -1) {
     auto& w = h->w[pi];
     const Geometry& g = h->g;
-    const int m = std::max(1, std::min(h->opts.accel_m, kMaxM));
+    const int m = slots > 0 ? slots : std::max(1, std::min(h->opts.accel_m, kMaxM));
     if (!w.ready) {
         const size_t aniso = (size_t)g.Nf * g.Nc * sizeof(T);
         const size_t coarse = (size_t)g.Nc * g.Nc * sizeof(T);
@@ -264,18 +275,21 @@ int bnorm2(asdsm_handle* h, const double* s, const double* u, double* out) {
     return ASDSM_OK;
 }
 
-// Mixed-path residual coefficients (FP32 pairs of the stencil parts times 2^-S).
+// Mixed-path residual coefficients: FP32 pairs of the stencil parts times 2^-S
+// and times the weights 2^44, 2^22 of the integer pieces.
 MixedCoefs mixed_coefs(const asdsm_handle* h, int S) {
     const double hh = 1.0 / h->g.M;
     const double sc = std::ldexp(1.0, -S);
     const double v[4] = {h->alpha[0] / (hh * hh) * sc, h->alpha[1] / (hh * hh) * sc,
                          h->beta[0] / (2 * hh) * sc, h->beta[1] / (2 * hh) * sc};
     MixedCoefs k{};
-    float* dst[4] = {k.kxx, k.kyy, k.kx, k.ky};
     for (int q = 0; q < 4; ++q) {
-        const float hi = (float)v[q];
-        dst[q][0] = hi;
-        dst[q][1] = (float)(v[q] - (double)hi);
+        const double w2 = std::ldexp(v[q], 44), w1 = std::ldexp(v[q], 22);
+        k.k2[q][0] = (float)w2;
+        k.k2[q][1] = (float)(w2 - (double)k.k2[q][0]);
+        k.k1[q][0] = (float)w1;
+        k.k1[q][1] = (float)(w1 - (double)k.k1[q][0]);
+        k.k0[q] = (float)v[q];
     }
     return k;
 }
@@ -308,8 +322,8 @@ int initial_guess_to_z(asdsm_handle* h, const double* s, const double* u) {
     fa.mode = FILL_WITH_SOURCE;
     fa.z = z; fa.out = z;
     if (sizeof(T) == 8) fa.src_d = s; else fa.src_hi = h->s_hi;
-    fa.Pt = (const T*)h->hole[pi].Pt; fa.Qt = (const T*)h->hole[pi].Qt; fa.Bt = (const T*)h->hole[pi].Bt;
-    fa.L = h->hole[pi].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+    hole_factors<T>(h->hole[pi], &fa);
+    fa.n = g.n; fa.g = g; fa.sten = h->sten;
     CK(fill_holes<T>(fa, h->num_sms, st));                              // Algorithm 3 with b_ff
     // Restore the ring of z to zero for later use as a direction slot is done by the caller.
     return ASDSM_OK;
@@ -356,19 +370,25 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
     }
     CK(ring_from<double>(u, h->u_work, g, 0, st));
 
-    // Step 1: initial guess (or resume from u).
+    // Step 1: initial guess (or resume from u).  The mixed path computes
+    // Algorithm 1 once in FP64: an FP32 u^(0) carries rounding noise whose
+    // residual is rough, and ASDSM corrections reduce rough residuals slowly
+    // (the irregular-residual stagnation of Section 4, Example 2).
+    const double* u0d = u;           // FP64 grid holding u^(0) (ring = g)
     if (!op.skip_initial_guess) {
-        if (int rc = initial_guess_to_z<T>(h, s, u)) return rc;
         if (!mixed) {
+            if (int rc = initial_guess_to_z<double>(h, s, u)) return rc;
             CK(copy_interior<double, double>((const double*)w.z[0], u, g, st));
+        } else {
+            if (int rc = ensure_work<double>(h, 0, 1)) return rc;
+            if (int rc = initial_guess_to_z<double>(h, s, u)) return rc;
+            u0d = (const double*)h->w[0].z[0];
         }
-    } else if (mixed) {
-        CK(convert_array<double, float>(u, (float*)w.z[0], NN, st));
     }
     if (mixed) {
-        // Fixed-point scale from max |u| (interior and ring), with 2^4 headroom.
+        // Fixed-point scale from max |u| (interior and ring), with 2^5 headroom.
         int nb = 0;
-        CK(maxabs<float>((const float*)w.z[0], NN, h->partials, &nb, st));
+        CK(maxabs<double>(u0d, NN, h->partials, &nb, st));
         CK(cudaMemcpyAsync(h->hsmall, h->partials, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         double mx = 0.0;
@@ -379,11 +399,11 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         std::frexp(mx, &e2);               // mx < 2^e2
         S = 58 - e2;                        // |U| < 2^58: 2^5 headroom below the 2^63 range and the 2^60 check
         scale = std::ldexp(1.0, S);
-        const float* zsrc = op.skip_initial_guess ? nullptr : (const float*)w.z[0];
-        CK(to_fixed(zsrc, u, h->U[0], scale, g, st));
-        CK(to_fixed(zsrc, u, h->U[1], scale, g, st));   // ring of the partner
+        CK(to_fixed(nullptr, u0d, h->U[0], scale, g, st));
+        CK(to_fixed(nullptr, u0d, h->U[1], scale, g, st));   // ring of the partner
     }
     // Direction slots need a zero ring again (slot 0 carried g).
+    if (!op.skip_initial_guess) CK(ring_from<double>(nullptr, (double*)h->w[0].z[0], g, 0, st));
     CK(ring_from<T>(nullptr, (T*)w.z[0], g, 0, st));
     CK(cudaEventRecord(h->ev1, st));
     const MixedCoefs mk = mixed ? mixed_coefs(h, S) : MixedCoefs{};
@@ -418,9 +438,7 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
                 CK(residual_fp64(s, ucur, dst, pend, g, h->sten, o, &nb, st));
                 if (pend.count > 0) std::swap(ucur, unxt);
             } else {
-                UpdateTerms ps = pend;
-                for (int q = 0; q < ps.count; ++q) ps.coef[q] *= scale;
-                CK(residual_mixed(h->s_hi, h->s_lo, h->U[Ucur], h->U[1 - Ucur], ps, scale, g, mk, o, &nb, h->dflag, st));
+                CK(residual_mixed(h->s_hi, h->s_lo, h->U[Ucur], h->U[1 - Ucur], pend, scale, g, mk, o, &nb, h->dflag, st));
                 if (pend.count > 0) Ucur = 1 - Ucur;
             }
             prof_end(h, pm, PC_RESID, bytes, 0.0);
@@ -467,8 +485,8 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
                 fa.U = h->U[Ucur];
                 fa.fixed_scale = scale;
             }
-            fa.Pt = (const T*)h->hole[pi].Pt; fa.Qt = (const T*)h->hole[pi].Qt; fa.Bt = (const T*)h->hole[pi].Bt;
-            fa.L = h->hole[pi].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+            hole_factors<T>(h->hole[pi], &fa);
+            fa.n = g.n; fa.g = g; fa.sten = h->sten;
             CK(fill_holes<T>(fa, h->num_sms, st));
             ++hole_fixes;
             kc = 0;
@@ -511,8 +529,8 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         FillArgs<T> fa{};
         fa.mode = FILL_HOMOGENEOUS;
         fa.z = z; fa.out = z;
-        fa.Pt = (const T*)h->hole[pi].Pt; fa.Qt = (const T*)h->hole[pi].Qt; fa.Bt = (const T*)h->hole[pi].Bt;
-        fa.L = h->hole[pi].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+        hole_factors<T>(h->hole[pi], &fa);
+        fa.n = g.n; fa.g = g; fa.sten = h->sten;
         {
             const ProfMark pm = prof_begin(h);
             CK(fill_holes<T>(fa, h->num_sms, st));
@@ -524,19 +542,13 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         // ---- step 6: least squares on the skeleton rows ----
         const ProfMark pm_lsq = prof_begin(h);
         CK(skeleton_apply<T>(z, g, h->sten, (T*)w.q, st));
-        const T* da[2 + 2 * kMaxM];
-        const T* db[2 + 2 * kMaxM];
-        int nd = 0;
-        da[nd] = (const T*)w.q; db[nd] = (const T*)w.q; ++nd;          // <q,q>
-        da[nd] = (const T*)w.q; db[nd] = (const T*)w.rskel; ++nd;      // <q,r>
-        for (int j = 0; j < kc; ++j) {
-            da[nd] = (const T*)w.q; db[nd] = (const T*)w.qp[j]; ++nd;     // <q, q'_j>
-            da[nd] = (const T*)w.rskel; db[nd] = (const T*)w.qp[j]; ++nd; // <r, q'_j>
-        }
+        const T* qpv[kMaxM];
+        for (int j = 0; j < kc; ++j) qpv[j] = (const T*)w.qp[j];
+        const int nd = 2 + 2 * kc;      // <q,q>, <q,r>, then <q,q'_j>, <r,q'_j>
         int nb3 = 0;
-        CK(multi_dot<T>(da, db, nd, g.skel, h->partials, &nb3, st));
+        CK(gcr_dots<T>((const T*)w.q, (const T*)w.rskel, qpv, kc, g.skel, h->partials, &nb3, st));
         CK(reduce_partials(h->partials, nb3, nd, h->dsmall, st));
-        prof_end(h, pm_lsq, PC_LSQ, ES * (double)g.skel * (6.0 + 2.0 * nd), 2.0 * (double)g.skel * nd);
+        prof_end(h, pm_lsq, PC_LSQ, ES * (double)g.skel * (6.0 + 2.0 + kc), 2.0 * (double)g.skel * nd);
         if (int rc = read_small(h, nd)) return rc;
         const double qq = h->hsmall[0], qr = h->hsmall[1];
         if (m == 1) {
@@ -671,6 +683,8 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     Geometry& g = h->g;
     g.N = (int)N; g.M = (int)(N - 1); g.Nf = (int)(N - 2); g.mc = (int)mc; g.Nc = (int)(mc - 1); g.n = (int)n;
     g.skel = (long long)g.Nc * g.Nf + (long long)g.Nc * (g.Nf - g.Nc);
+    g.ln = 0;
+    while ((1 << g.ln) < g.n) ++g.ln;
     for (int q = 0; q < 2; ++q) { h->alpha[q] = desc->alpha[q]; h->beta[q] = desc->beta[q]; }
     const double ax = h->alpha[0], ay = h->alpha[1], bx = h->beta[0], by = h->beta[1];
     const double hh = 1.0 / g.M, HH = 1.0 / g.mc;
@@ -706,8 +720,12 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
         (rc = upload_bcr<double>(fcc, &h->cc[0])) || (rc = upload_bcr<float>(fcc, &h->cc[1])) ||
         (rc = upload_bcr<double>(fho, &h->hole[0])) || (rc = upload_bcr<float>(fho, &h->hole[1])))
         return fail(rc);
+    // Spline moment operator, stored transposed ([knot][moment]) for the merge kernel.
     const std::vector<double> Sm = spline_moment_operator(g.mc);
-    if ((rc = upload_vec<double>(Sm, &h->Sm[0])) || (rc = upload_vec<float>(Sm, &h->Sm[1]))) return fail(rc);
+    std::vector<double> SmT(Sm.size());
+    for (int r = 0; r <= g.mc; ++r)
+        for (int q = 0; q < g.Nc; ++q) SmT[(size_t)q * (g.mc + 1) + r] = Sm[(size_t)r * g.Nc + q];
+    if ((rc = upload_vec<double>(SmT, &h->Sm[0])) || (rc = upload_vec<float>(SmT, &h->Sm[1]))) return fail(rc);
     if (fill_smem_bytes<double>(g.n, h->hole[0].L) > 227 * 1024) return fail(ASDSM_ERR_INVALID);
     const size_t NN = (size_t)g.N * g.N;
     if ((e = cudaMalloc(&h->u_work, NN * sizeof(double))) != cudaSuccess) return fail(set_cuda_error(e));
@@ -843,14 +861,14 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
         if (fp64) {
             FillArgs<double> fa{};
             fa.mode = FILL_ARRAY; fa.src_d = in; fa.out_d = out;
-            fa.Pt = (const double*)h->hole[0].Pt; fa.Qt = (const double*)h->hole[0].Qt; fa.Bt = (const double*)h->hole[0].Bt;
-            fa.L = h->hole[0].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+            hole_factors<double>(h->hole[0], &fa);
+            fa.n = g.n; fa.g = g; fa.sten = h->sten;
             CK(fill_holes<double>(fa, h->num_sms, st));
         } else {
             FillArgs<float> fa{};
             fa.mode = FILL_ARRAY; fa.src_d = in; fa.out_d = out;
-            fa.Pt = (const float*)h->hole[1].Pt; fa.Qt = (const float*)h->hole[1].Qt; fa.Bt = (const float*)h->hole[1].Bt;
-            fa.L = h->hole[1].L; fa.n = g.n; fa.g = g; fa.sten = h->sten;
+            hole_factors<float>(h->hole[1], &fa);
+            fa.n = g.n; fa.g = g; fa.sten = h->sten;
             CK(fill_holes<float>(fa, h->num_sms, st));
         }
     } else {
@@ -892,7 +910,7 @@ void asdsm_destroy(asdsm_handle* h) {
     auto fr = [](void* p) { if (p) cudaFree(p); };
     for (int p = 0; p < 2; ++p) {
         DevBcr* ds[4] = {&h->fc[p], &h->cf[p], &h->cc[p], &h->hole[p]};
-        for (auto* d : ds) { fr(d->Pt); fr(d->Qt); fr(d->Bt); }
+        for (auto* d : ds) { fr(d->Mt); fr(d->Bt); }
         fr(h->Sm[p]);
         auto& w = h->w[p];
         void* bufs[] = {w.Xfc, w.Xcf, w.Yfc, w.Ycf, w.Xcc, w.Ycc, w.E1, w.E2, w.M1, w.M2, w.rskel, w.q, w.rfull};

@@ -18,11 +18,16 @@ namespace asdsm {
 // with R = 2^L - 1 rows and T the C x C tridiagonal Toeplitz matrix
 // tridiag(tl, td, tu) (T[k][k-1] = tl, T[k][k+1] = tu).  At level l the
 // surviving rows satisfy A_l x_{i-s} + B_l x_i + C_l x_{i+s} = f_i^(l)
-// (s = 2^l); the factors kept per level are P_l = A_l B_l^{-1},
-// Q_l = C_l B_l^{-1} and B_l^{-1}, each stored transposed ([k][c] = M[c][k]).
+// (s = 2^l), with P_l = A_l B_l^{-1} and Q_l = C_l B_l^{-1}.  Because
+// A_0 = a I and C_0 = c I, every level keeps C_l = (c/a)^(2^l) A_l, hence
+// Q_l = (c/a)^(2^l) P_l: one matrix per level serves both neighbours.
+// Stored per level: M_l (the larger of P_l, Q_l) and B_l^{-1}, transposed
+// ([k][c] = M[c][k]), and the weights with P_l = wl_l M_l, Q_l = wr_l M_l
+// (one of them is 1, the other has modulus <= 1).
 struct BcrFactors {
     int R = 0, C = 0, L = 0;
-    std::vector<double> Pt, Qt, Bt;   // [L][C][C]
+    std::vector<double> Mt, Bt;       // [L][C][C]
+    std::vector<double> wl, wr;       // [L]
 };
 bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, double tu, BcrFactors* out);
 
@@ -34,13 +39,15 @@ std::vector<double> spline_moment_operator(int mc);
 // ---------------------------------------------------------------------------
 // Device-side descriptors
 // ---------------------------------------------------------------------------
+constexpr int kMaxLevels = 16;
+
 template <typename T>
 struct BcrSys {
     T* X;              // right-hand sides, [nsys][R][C]; overwritten by the forward reduction
     T* Y;              // solutions, [nsys][R][C]
-    const T* Pt;       // [L][C][C]
-    const T* Qt;
-    const T* Bt;
+    const T* Mt;       // [L][C][C]
+    const T* Bt;       // [L][C][C]
+    T wl[kMaxLevels], wr[kMaxLevels];
     int R, C, L;
     int nsys;          // systems sharing these factors
     long long stride;  // elements between consecutive systems
@@ -57,7 +64,8 @@ struct Geometry {
     int Nf;     // N - 2 interior points per axis
     int mc;     // coarse intervals
     int Nc;     // mc - 1 coarse lines per axis
-    int n;      // M / mc
+    int n;      // M / mc (a power of two)
+    int ln;     // log2(n)
     long long skel;   // compact skeleton length: Nc*Nf + Nc*(Nf - Nc)
 };
 
@@ -93,7 +101,8 @@ struct FillArgs {
     double* u_d;              // mode 2, FP64 path: u += v on holes
     long long* U;             // mode 2, mixed path: U += round(v * scale)
     double fixed_scale;       // 2^S for mode 2 mixed
-    const T* Pt; const T* Qt; const T* Bt;
+    const T* Mt; const T* Bt;
+    T wl[kMaxLevels], wr[kMaxLevels];
     int L, n;                 // hole systems are (n-1) x (n-1)
     Geometry g;
     Stencil sten;
@@ -125,9 +134,14 @@ struct UpdateTerms {
 // FP64 path: u_out = u_in + sum coef z (interior), r = s - A u_out.
 cudaError_t residual_fp64(const double* s, const double* u_in, double* u_out, const UpdateTerms& up,
                           const Geometry& g, const Stencil& st_, ResidOut out, int* nblocks, cudaStream_t st);
-// Mixed path: U_out = U_in + round(2^S sum coef z), r = s - A U_out 2^-S in FP32-pair arithmetic.
+// Mixed path: U_out = U_in + round(2^S sum coef z), r = s - A U_out 2^-S in FP32-pair arithmetic
+// (coef are the unscaled step lengths; `scale` = 2^S).
+// Stencil parts q = 0..3 (alpha_x/h^2, alpha_y/h^2, beta_x/(2h), beta_y/(2h)), each times 2^-S,
+// pre-multiplied by the weights of the 22-bit pieces of the integer differences.
 struct MixedCoefs {
-    float kxx[2], kyy[2], kx[2], ky[2];   // (hi, lo) of alpha_x/h^2 2^-S, alpha_y/h^2 2^-S, beta_x/(2h) 2^-S, beta_y/(2h) 2^-S
+    float k2[4][2];   // (hi, lo) of part * 2^44
+    float k1[4][2];   // (hi, lo) of part * 2^22
+    float k0[4];      // part (FP32; the low piece needs no more)
 };
 cudaError_t residual_mixed(const float* s_hi, const float* s_lo, const long long* U_in, long long* U_out,
                            const UpdateTerms& up, double scale, const Geometry& g, const MixedCoefs& k,
@@ -142,6 +156,12 @@ template <typename T>
 cudaError_t multi_dot(const T* const* a, const T* const* b, int ndots, long long n,
                       double* partials, int* nblocks, cudaStream_t st);
 
+// GCR inner products in one pass: partials [block][2 + 2k] = <q,q>, <q,r>, then
+// <q,p_j>, <r,p_j> for j < k (k <= 15).
+template <typename T>
+cudaError_t gcr_dots(const T* q, const T* r, const T* const* p, int k, long long n,
+                     double* partials, int* nblocks, cudaStream_t st);
+
 // Merge (Algorithm 2) --------------------------------------------------------
 template <typename T>
 struct MergeArgs {
@@ -149,7 +169,7 @@ struct MergeArgs {
     const double* norms2;     // [2]: ||Yfc||^2, ||Ycf||^2 (normalisation of Algorithm 1 step 2)
     int re_mode;              // 1: Richardson (u_cc given), 0: random choice
     int choice;               // 0 or 1 (Algorithm 2 step 3)
-    const T* Sm;              // (mc+1) x Nc spline moment operator
+    const T* Sm;              // spline moment operator, transposed: [Nc knots][mc+1 moments]
     T* E1; T* E2;             // [Nc][Nc] knot errors (fc lines: E1[l][k]; cf columns: E2[l][k])
     T* M1; T* M2;             // moments: M1[l][mc+1], M2[k][mc+1]
     T* z;                     // full grid output (skeleton written)

@@ -81,12 +81,16 @@ void transpose_into(const double* M, double* out, int n) {
 bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, double tu, BcrFactors* out) {
     int L = 0;
     while (((1 << L) - 1) < R) ++L;
-    if (((1 << L) - 1) != R || C < 1) return false;
+    if (((1 << L) - 1) != R || C < 1 || L > 16) return false;
     const size_t n2 = (size_t)C * C;
     out->R = R; out->C = C; out->L = L;
-    out->Pt.assign((size_t)L * n2, 0.0);
-    out->Qt.assign((size_t)L * n2, 0.0);
+    out->Mt.assign((size_t)L * n2, 0.0);
     out->Bt.assign((size_t)L * n2, 0.0);
+    out->wl.assign(L, 0.0);
+    out->wr.assign(L, 0.0);
+    // Which neighbour's factor is the larger one: |Q_l| / |P_l| = |c/a|^(2^l).
+    const bool left_dominant = std::fabs(a) >= std::fabs(c);
+    const double ratio = left_dominant ? c / a : a / c;     // modulus <= 1
     // Level 0: A_0 = a I, C_0 = c I, B_0 = d I + T.
     std::vector<double> A(n2, 0.0), Cm(n2, 0.0), B(n2, 0.0);
     for (int k = 0; k < C; ++k) {
@@ -97,14 +101,17 @@ bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, 
         if (k + 1 < C) B[(size_t)k * C + k + 1] = tu;
     }
     std::vector<double> Binv, P(n2), Q(n2), t1(n2), t2(n2);
+    double w = ratio;                                        // ratio^(2^l)
     for (int l = 0; l < L; ++l) {
         Binv = B;
         if (!invert(Binv, C)) return false;
-        matmul(A.data(), Binv.data(), P.data(), C);     // P_l = A_l B_l^{-1}
-        matmul(Cm.data(), Binv.data(), Q.data(), C);    // Q_l = C_l B_l^{-1}
-        transpose_into(P.data(), out->Pt.data() + (size_t)l * n2, C);
-        transpose_into(Q.data(), out->Qt.data() + (size_t)l * n2, C);
+        matmul(A.data(), Binv.data(), P.data(), C);          // P_l = A_l B_l^{-1}
+        matmul(Cm.data(), Binv.data(), Q.data(), C);         // Q_l = C_l B_l^{-1}
+        transpose_into(left_dominant ? P.data() : Q.data(), out->Mt.data() + (size_t)l * n2, C);
         transpose_into(Binv.data(), out->Bt.data() + (size_t)l * n2, C);
+        out->wl[l] = left_dominant ? 1.0 : w;
+        out->wr[l] = left_dominant ? w : 1.0;
+        w = w * w;
         if (l + 1 == L) break;
         // B_{l+1} = B_l - P_l C_l - Q_l A_l ; A_{l+1} = -P_l A_l ; C_{l+1} = -Q_l C_l
         matmul(P.data(), Cm.data(), t1.data(), C);
@@ -114,7 +121,7 @@ bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, 
         matmul(Q.data(), Cm.data(), t2.data(), C);
         for (size_t e = 0; e < n2; ++e) { A[e] = -t1[e]; Cm[e] = -t2[e]; }
     }
-    for (double v : out->Pt) if (!std::isfinite(v)) return false;
+    for (double v : out->Mt) if (!std::isfinite(v)) return false;
     for (double v : out->Bt) if (!std::isfinite(v)) return false;
     return true;
 }

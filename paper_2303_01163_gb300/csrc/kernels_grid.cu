@@ -21,7 +21,8 @@ constexpr int RTHREADS = 256;
 
 __device__ __forceinline__ int skel_kind(int i, int j, int n) {
     // 0 = hole, 1 = fc line only (y on a coarse line), 2 = cf column only, 3 = cross point
-    const bool fx = (i % n) == 0, fy = (j % n) == 0;
+    // (n is a power of two)
+    const bool fx = (i & (n - 1)) == 0, fy = (j & (n - 1)) == 0;
     return (fy ? 1 : 0) + (fx ? 2 : 0);
 }
 
@@ -29,11 +30,9 @@ __device__ __forceinline__ int skel_kind(int i, int j, int n) {
 // Layout: fc lines [l][x] (l = j/n - 1, x = i - 1), then the cf columns
 // without cross points, row by row: [yr][k] with yr the non-cross row rank.
 __device__ __forceinline__ long long skel_index(int i, int j, const Geometry& g) {
-    const int n = g.n;
-    if (j % n == 0) return (long long)(j / n - 1) * g.Nf + (i - 1);
-    const int y0 = j - 1;
-    const int yr = y0 - (j / n);            // rows y0 before j with (y0+1) % n == 0
-    return (long long)g.Nc * g.Nf + (long long)yr * g.Nc + (i / n - 1);
+    if ((j & (g.n - 1)) == 0) return (long long)((j >> g.ln) - 1) * g.Nf + (i - 1);
+    const int yr = j - 1 - (j >> g.ln);     // rows y0 before j with (y0+1) % n == 0
+    return (long long)g.Nc * g.Nf + (long long)yr * g.Nc + ((i >> g.ln) - 1);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -69,12 +68,11 @@ __device__ void block_sum2(double a, double b, double* partials) {
 template <typename T>
 __device__ __forceinline__ void store_skeleton(const ResidOut& o, const Geometry& g, int i, int j, int kind, T v) {
     if (kind == 0) return;
-    const int n = g.n;
     if (kind & 1) {   // on an fc line: BCR layout [x][line]
-        reinterpret_cast<T*>(o.rfc)[(long long)(i - 1) * g.Nc + (j / n - 1)] = v;
+        reinterpret_cast<T*>(o.rfc)[(long long)(i - 1) * g.Nc + ((j >> g.ln) - 1)] = v;
     }
     if (kind & 2) {   // on a cf column: BCR layout [y][column]
-        reinterpret_cast<T*>(o.rcf)[(long long)(j - 1) * g.Nc + (i / n - 1)] = v;
+        reinterpret_cast<T*>(o.rcf)[(long long)(j - 1) * g.Nc + ((i >> g.ln) - 1)] = v;
     }
     reinterpret_cast<T*>(o.rskel)[skel_index(i, j, g)] = v;
 }
@@ -124,107 +122,149 @@ residual_fp64_kernel(const double* __restrict__ s, const double* __restrict__ u_
 }
 
 // ---------------------------------------------------------------------------
-// FP32-pair ("double-float") primitives: Knuth's TwoSum, FMA-based TwoProd.
+// Exact integer <-> FP32 conversions that stay off the FP64 pipe.  On GB300
+// the 64-bit integer conversions (I2F.S64 / F2I.S64) run on the FP64 unit,
+// which is 1/70 of the FP32 rate; these use only integer and FP32 ops.
 // ---------------------------------------------------------------------------
-struct df { float hi, lo; };
-
-__device__ __forceinline__ df two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
+// D = f2 * 2^44 + f1 * 2^22 + f0 exactly, f0, f1 in [0, 2^22), f2 in (-2^19, 2^19).
+// Each piece becomes a float through the exponent-bias trick (x | 2^23 bits, minus 2^23).
+__device__ __forceinline__ void split3(long long D, float& f2, float& f1, float& f0) {
+    const unsigned lo = (unsigned)(unsigned long long)D;
+    const unsigned hi = (unsigned)((unsigned long long)D >> 32);
+    const unsigned p0 = lo & 0x3FFFFFu;
+    const unsigned p1 = __funnelshift_r(lo, hi, 22) & 0x3FFFFFu;
+    const int p2 = (int)hi >> 12;
+    f0 = __fsub_rn(__uint_as_float(0x4B000000u | p0), 8388608.0f);
+    f1 = __fsub_rn(__uint_as_float(0x4B000000u | p1), 8388608.0f);
+    f2 = __fsub_rn(__int_as_float(0x4B400000 + p2), 12582912.0f);
 }
-__device__ __forceinline__ df quick_two_sum(float a, float b) {   // needs |a| >= |b| or a == 0
-    const float s = __fadd_rn(a, b);
-    const float e = __fsub_rn(b, __fsub_rn(s, a));
-    return {s, e};
-}
-__device__ __forceinline__ df df_add(df a, df b) {                   // accurate sum
-    df s = two_sum(a.hi, b.hi);
-    df t = two_sum(a.lo, b.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
-    s = quick_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
-    return quick_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ df df_mul(df a, df b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
-    return quick_two_sum(p, e);
-}
-// Exact split of a 64-bit integer into an FP32 pair (exact while |D| < 2^48).
-__device__ __forceinline__ df ll_to_df(long long D) {
-    const float hi = __ll2float_rn(D);
-    const long long rem = D - __float2ll_rn(hi);
-    return {hi, __ll2float_rn(rem)};
+// Nearest 64-bit integer of a float (|d| < 2^62): round to an integral float,
+// then shift its significand into place.
+__device__ __forceinline__ long long f2ll_rn(float d) {
+    const float r = rintf(d);
+    const unsigned b = __float_as_uint(r);
+    const int E = (int)((b >> 23) & 0xFFu);
+    if (E == 0) return 0;
+    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = E - 150;
+    const long long v = sh >= 0 ? (m << sh) : (m >> (-sh));
+    return (b >> 31) ? -v : v;
 }
 
 // ---------------------------------------------------------------------------
 // Mixed residual: U (64-bit fixed point, u = U 2^-S) is the accumulator.
-//   U_out = U_in + round(sum (coef_j 2^S) z_j)       (step 7 of the previous sweep)
+//   U_out = U_in + round(sum_j c_j z_j)              (step 7 of the previous sweep, c_j carry 2^S)
 //   A u   = kxx (2U_c - U_w - U_e) + kyy (2U_c - U_s - U_n) + kx (U_e - U_w) + ky (U_n - U_s)
-// The integer differences are exact; each k (carrying 2^-S) is an FP32 pair,
-// so r = s - A u keeps FP64-level accuracy although only FP32 units are used.
+// The integer differences are exact; each splits exactly into 22-bit pieces
+// whose products with FP32 pairs of the coefficients (carrying 2^-S and the
+// piece weight) are error-free (TwoProd) and summed with TwoSum, so
+// r = s - A u keeps FP64-level accuracy with FP32/INT32 instructions only.
+// Layout: a warp owns 30 output columns (lanes 1..30; lanes 0 and 31 carry the
+// halo columns) and marches down MS_ROWS rows keeping rows j-1, j, j+1 in
+// registers; x neighbours come from warp shuffles.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(RTHREADS)
+constexpr int MS_OUT = 30;
+constexpr int MS_WARPS = 8;
+constexpr int MS_ROWS = 32;
+
+struct UpdateF {
+    const float* z[16];
+    float c[16];
+    int count;
+};
+
+__device__ __forceinline__ long long load_updated(const long long* __restrict__ U_in, const UpdateF& up,
+                                                  int N, int x, int j) {
+    if (x < 0 || x > N - 1 || j < 0 || j > N - 1) return 0;
+    const long long idx = (long long)j * N + x;
+    long long v = U_in[idx];
+    if (up.count > 0 && x >= 1 && j >= 1 && x <= N - 2 && j <= N - 2) {
+        float d = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (q < up.count) d = __fmaf_rn(up.c[q], __ldg(up.z[q] + idx), d);
+        v += f2ll_rn(d);
+    }
+    return v;
+}
+
+__device__ __forceinline__ void acc_prod(float khi, float klo, float f, float& hi, float& err) {
+    const float p = __fmul_rn(khi, f);
+    float e = __fmaf_rn(khi, f, -p);
+    e = __fmaf_rn(klo, f, e);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    err = __fadd_rn(err, __fadd_rn(t, e));
+}
+
+__global__ void __launch_bounds__(32 * MS_WARPS)
 residual_mixed_kernel(const float* __restrict__ s_hi, const float* __restrict__ s_lo,
                       const long long* __restrict__ U_in, long long* __restrict__ U_out,
-                      UpdateTerms up, Geometry g, MixedCoefs k, ResidOut o, int* overflow) {
-    __shared__ long long tile[RY + 2][RX + 2];
+                      UpdateF up, Geometry g, MixedCoefs k, ResidOut o, int* overflow) {
     const int N = g.N;
-    const int i0 = blockIdx.x * RX + 1, j0 = blockIdx.y * RY + 1;
-    float cf[16];
-    for (int q = 0; q < 16; ++q) cf[q] = q < up.count ? (float)up.coef[q] : 0.0f;
-    for (int e = threadIdx.x; e < (RX + 2) * (RY + 2); e += RTHREADS) {
-        const int ty = e / (RX + 2), tx = e % (RX + 2);
-        const int i = i0 - 1 + tx, j = j0 - 1 + ty;
-        long long v = 0;
-        if (i <= N - 1 && j <= N - 1) {
-            const long long idx = (long long)j * N + i;
-            v = U_in[idx];
-            if (up.count > 0 && i >= 1 && j >= 1 && i <= N - 2 && j <= N - 2) {
-                float d = 0.0f;
-                for (int q = 0; q < up.count; ++q) d = __fmaf_rn(cf[q], reinterpret_cast<const float*>(up.z[q])[idx], d);
-                v += __float2ll_rn(d);
-            }
-        }
-        tile[ty][tx] = v;
-    }
-    __syncthreads();
-    double sr = 0.0, sh = 0.0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = 1 + (blockIdx.x * MS_WARPS + warp) * MS_OUT + lane - 1;   // lane 0: west halo
+    const bool out_col = lane >= 1 && lane <= MS_OUT && x <= N - 2;
+    const int j0 = 1 + blockIdx.y * MS_ROWS;
+    const int j1 = min(j0 + MS_ROWS - 1, N - 2);
+    long long um = load_updated(U_in, up, N, x, j0 - 1);
+    long long uc = load_updated(U_in, up, N, x, j0);
     float srf = 0.0f, shf = 0.0f;
-    const df kxx{k.kxx[0], k.kxx[1]}, kyy{k.kyy[0], k.kyy[1]}, kx{k.kx[0], k.kx[1]}, ky{k.ky[0], k.ky[1]};
     const long long lim = 1LL << 60;
     bool ovf = false;
-    for (int e = threadIdx.x; e < RX * RY; e += RTHREADS) {
-        const int ty = e / RX, tx = e % RX;
-        const int i = i0 + tx, j = j0 + ty;
-        if (i > N - 2 || j > N - 2) continue;
-        const long long idx = (long long)j * N + i;
-        const long long uc = tile[ty + 1][tx + 1];
-        const long long uw = tile[ty + 1][tx], ue = tile[ty + 1][tx + 2];
-        const long long us = tile[ty][tx + 1], un = tile[ty + 2][tx + 1];
-        ovf |= (uc > lim) || (uc < -lim);
-        if (up.count > 0) U_out[idx] = uc;
-        const df dxx = ll_to_df(2 * uc - uw - ue);
-        const df dyy = ll_to_df(2 * uc - us - un);
-        const df dx = ll_to_df(ue - uw);
-        const df dy = ll_to_df(un - us);
-        df Au = df_add(df_add(df_mul(kxx, dxx), df_mul(kyy, dyy)), df_add(df_mul(kx, dx), df_mul(ky, dy)));
-        Au.hi = -Au.hi; Au.lo = -Au.lo;
-        const df r = df_add(df{s_hi[idx], s_lo[idx]}, Au);
-        const float rf = __fadd_rn(r.hi, r.lo);
-        const int kind = skel_kind(i, j, g.n);
-        srf = __fmaf_rn(rf, rf, srf);
-        if (kind == 0) shf = __fmaf_rn(rf, rf, shf);
-        if (o.rfull) reinterpret_cast<float*>(o.rfull)[idx] = rf;
-        if (o.rskel) store_skeleton<float>(o, g, i, j, kind, rf);
+    for (int j = j0; j <= j1; ++j) {
+        const long long un = load_updated(U_in, up, N, x, j + 1);
+        const long long uw = __shfl_up_sync(0xffffffffu, uc, 1);
+        const long long ue = __shfl_down_sync(0xffffffffu, uc, 1);
+        if (out_col) {
+            const long long idx = (long long)j * N + x;
+            ovf |= (uc > lim) || (uc < -lim);
+            if (up.count > 0) U_out[idx] = uc;
+            const long long D[4] = {2 * uc - uw - ue, 2 * uc - um - un, ue - uw, un - um};
+            float hi = 0.0f, err = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float f2, f1, f0;
+                split3(D[q], f2, f1, f0);
+                acc_prod(k.k2[q][0], k.k2[q][1], f2, hi, err);
+                acc_prod(k.k1[q][0], k.k1[q][1], f1, hi, err);
+                err = __fmaf_rn(k.k0[q], f0, err);
+            }
+            // r = s - A u: TwoSum of the leading parts, then the small terms.
+            const float sh = __ldg(s_hi + idx), sl = __ldg(s_lo + idx);
+            const float a = sh, b = -hi;
+            const float s = __fadd_rn(a, b);
+            const float bb = __fsub_rn(s, a);
+            const float t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+            const float rf = __fadd_rn(s, __fsub_rn(__fadd_rn(t, sl), err));
+            const int kind = skel_kind(x, j, g.n);
+            srf = __fmaf_rn(rf, rf, srf);
+            if (kind == 0) shf = __fmaf_rn(rf, rf, shf);
+            if (o.rfull) reinterpret_cast<float*>(o.rfull)[idx] = rf;
+            if (o.rskel) store_skeleton<float>(o, g, x, j, kind, rf);
+        }
+        um = uc;
+        uc = un;
     }
-    sr = srf;
-    sh = shf;
     if (ovf) atomicOr(overflow, 1);
-    block_sum2(sr, sh, o.partials);
+    // Block reduction of the two norms (8 warps).
+    __shared__ double red[2][MS_WARPS];
+    double a = warp_sum((double)srf), b = warp_sum((double)shf);
+    if (lane == 0) { red[0][warp] = a; red[1][warp] = b; }
+    __syncthreads();
+    if (warp == 0) {
+        a = lane < MS_WARPS ? red[0][lane] : 0.0;
+        b = lane < MS_WARPS ? red[1][lane] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (lane == 0) {
+            const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+            o.partials[2 * blk] = a;
+            o.partials[2 * blk + 1] = b;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -282,24 +322,40 @@ __device__ __forceinline__ T cross_t2(const MergeArgs<T>& a, T inv2, int l, int 
     return a.Ycf[(long long)((l + 1) * a.g.n - 1) * a.g.Nc + k] * inv2;
 }
 
+// 1/||u|| of Algorithm 1 step 2 (FP32 reciprocal square root on the mixed path:
+// a single scale factor, and FP64 division and square root are slow on this part).
 template <typename T>
 __device__ __forceinline__ void inv_norms(const MergeArgs<T>& a, T* inv1, T* inv2) {
     if (a.re_mode) { *inv1 = T(1); *inv2 = T(1); return; }
     const double n1 = a.norms2[0], n2 = a.norms2[1];
-    *inv1 = n1 > 0.0 ? (T)(1.0 / sqrt(n1)) : T(1);
-    *inv2 = n2 > 0.0 ? (T)(1.0 / sqrt(n2)) : T(1);
+    if constexpr (sizeof(T) == 4) {
+        *inv1 = n1 > 0.0 ? rsqrtf((float)n1) : 1.0f;
+        *inv2 = n2 > 0.0 ? rsqrtf((float)n2) : 1.0f;
+    } else {
+        *inv1 = n1 > 0.0 ? (T)(1.0 / sqrt(n1)) : T(1);
+        *inv2 = n2 > 0.0 ? (T)(1.0 / sqrt(n2)) : T(1);
+    }
 }
+
+// One CTA per (family, block of 16 coarse lines).  Sm is the spline moment
+// operator transposed, [knot q][moment r], so threads over r read it coalesced
+// and every value serves the 16 lines of the block.
+constexpr int MK_LINES = 4;
 
 template <typename T>
 __global__ void merge_knots_kernel(MergeArgs<T> a) {
     const int Nc = a.g.Nc, K = a.g.mc + 1;
-    const int fam = blockIdx.x / Nc;       // 0: fc line l, 1: cf column k
-    const int line = blockIdx.x % Nc;
+    const int nblk = (Nc + MK_LINES - 1) / MK_LINES;
+    const int fam = blockIdx.x / nblk;         // 0: fc lines, 1: cf columns
+    const int l0 = (blockIdx.x % nblk) * MK_LINES;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* e = reinterpret_cast<T*>(smem_raw);  // Nc knot errors of this line
+    T* e = reinterpret_cast<T*>(smem_raw);     // [MK_LINES][Nc] knot errors of the block's lines
     T inv1, inv2;
     inv_norms(a, &inv1, &inv2);
-    for (int q = threadIdx.x; q < Nc; q += blockDim.x) {
+    for (int idx = threadIdx.x; idx < MK_LINES * Nc; idx += blockDim.x) {
+        const int li = idx / Nc, q = idx % Nc;
+        const int line = l0 + li;
+        if (line >= Nc) { e[idx] = T(0); continue; }
         // fc line l = line: knots along x (k = q); cf column k = line: knots along y (l = q)
         const int l = fam == 0 ? line : q;
         const int k = fam == 0 ? q : line;
@@ -308,28 +364,42 @@ __global__ void merge_knots_kernel(MergeArgs<T> a) {
         if (a.re_mode) uh = t1 + t2 - a.Ycc[(long long)l * Nc + k];   // step 2: combination RE
         else uh = a.choice ? t2 : t1;                                  // step 3
         const T err = fam == 0 ? uh - t1 : uh - t2;                    // step 4
-        e[q] = err;
+        e[idx] = err;
         if (fam == 0) a.E1[(long long)l * Nc + k] = err;
         else a.E2[(long long)l * Nc + k] = err;
     }
     __syncthreads();
-    T* Mout = fam == 0 ? a.M1 + (long long)line * K : a.M2 + (long long)line * K;
     for (int r = threadIdx.x; r < K; r += blockDim.x) {
-        T acc = T(0);
-        for (int q = 0; q < Nc; ++q) acc += a.Sm[(long long)r * Nc + q] * e[q];
-        Mout[r] = acc;
+        T acc[MK_LINES];
+#pragma unroll
+        for (int li = 0; li < MK_LINES; ++li) acc[li] = T(0);
+        const T* __restrict__ Smr = a.Sm + r;
+#pragma unroll 8
+        for (int q = 0; q < Nc; ++q) {
+            const T sm = __ldg(Smr + (long long)q * K);
+#pragma unroll
+            for (int li = 0; li < MK_LINES; ++li) acc[li] += sm * e[li * Nc + q];
+        }
+        for (int li = 0; li < MK_LINES; ++li) {
+            const int line = l0 + li;
+            if (line >= Nc) break;
+            T* Mout = fam == 0 ? a.M1 + (long long)line * K : a.M2 + (long long)line * K;
+            Mout[r] = acc[li];
+        }
     }
 }
 
-// Value of the not-a-knot spline with moments Mv and knot values (0, e.., 0)
-// at fine offset t = p (0..n) inside coarse interval ki (0..mc-1).
+// Weights of the not-a-knot spline with moments M and knot values (0, e.., 0) at
+// fine offset p (0..n) of a coarse interval: S = w0 M_k + w1 M_{k+1} + w2 y_k + w3 y_{k+1},
+// with t = pH/n, u = H - t: w0 = u^3/(6H) - Hu/6, w1 = t^3/(6H) - Ht/6, w2 = u/H, w3 = t/H.
 template <typename T>
-__device__ __forceinline__ T spline_eval(const T* Mv, T yk, T yk1, int ki, int p, int n, T H) {
-    if (p == 0) return yk;                   // at a knot the spline interpolates exactly
+__device__ __forceinline__ void spline_weights(int p, int n, T H, T* w) {
     const T t = H * (T)p / (T)n;
     const T u = H - t;
-    const T Mk = Mv[ki], Mk1 = Mv[ki + 1];
-    return Mk * (u * u * u / (6 * H) - H * u / 6) + Mk1 * (t * t * t / (6 * H) - H * t / 6) + yk * (u / H) + yk1 * (t / H);
+    w[0] = u * u * u / (6 * H) - H * u / 6;
+    w[1] = t * t * t / (6 * H) - H * t / 6;
+    w[2] = u / H;
+    w[3] = t / H;
 }
 
 template <typename T>
@@ -337,31 +407,40 @@ __global__ void merge_write_kernel(MergeArgs<T> a) {
     const Geometry& g = a.g;
     const int Nf = g.Nf, Nc = g.Nc, n = g.n, N = g.N, K = g.mc + 1;
     const T H = T(1) / (T)g.mc;
+    __shared__ T sw[33][4];                     // spline weights per fine offset p = 0..n (n <= 32)
+    for (int p = threadIdx.x; p <= n; p += blockDim.x) spline_weights<T>(p, n, H, sw[p]);
+    __syncthreads();
     T inv1, inv2;
     inv_norms(a, &inv1, &inv2);
     const long long total = 2LL * Nf * Nc;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         if (e < (long long)Nf * Nc) {
-            // fc line l, fine x: value u_fc/||u_fc|| + Spline(e1) (step 5.1); cross points too (step 6).
+            // fc line l, fine x: u_fc/||u_fc|| + Spline(e1) (step 5.1); cross points too (step 6).
             const int l = (int)(e / Nf), x = (int)(e % Nf);
             const int i = x + 1, ki = i / n, p = i % n;
-            const T* Mv = a.M1 + (long long)l * K;
+            T corr;
             const T yk = ki == 0 ? T(0) : a.E1[(long long)l * Nc + ki - 1];
-            const T yk1 = ki + 1 >= g.mc ? T(0) : a.E1[(long long)l * Nc + ki];
-            const T v = a.Yfc[(long long)x * Nc + l] * inv1 + spline_eval(Mv, yk, yk1, ki, p, n, H);
-            a.z[(long long)((l + 1) * n) * N + i] = v;
+            if (p == 0) {
+                corr = yk;                       // at a knot the spline interpolates exactly
+            } else {
+                const T* Mv = a.M1 + (long long)l * K;
+                const T yk1 = ki + 1 >= g.mc ? T(0) : a.E1[(long long)l * Nc + ki];
+                corr = sw[p][0] * Mv[ki] + sw[p][1] * Mv[ki + 1] + sw[p][2] * yk + sw[p][3] * yk1;
+            }
+            a.z[(long long)((l + 1) * n) * N + i] = a.Yfc[(long long)x * Nc + l] * inv1 + corr;
         } else {
-            // cf column k, fine y (cross points skipped: they keep the fc value).
+            // cf points, ordered [y][column] so that consecutive threads read Ycf contiguously;
+            // cross points are skipped: they keep the fc value.
             const long long f = e - (long long)Nf * Nc;
-            const int k = (int)(f / Nf), y = (int)(f % Nf);
+            const int y = (int)(f / Nc), k = (int)(f % Nc);
             const int j = y + 1;
             if (j % n == 0) continue;
             const int ki = j / n, p = j % n;
             const T* Mv = a.M2 + (long long)k * K;
             const T yk = ki == 0 ? T(0) : a.E2[(long long)(ki - 1) * Nc + k];
             const T yk1 = ki + 1 >= g.mc ? T(0) : a.E2[(long long)ki * Nc + k];
-            const T v = a.Ycf[(long long)y * Nc + k] * inv2 + spline_eval(Mv, yk, yk1, ki, p, n, H);
-            a.z[(long long)j * N + (k + 1) * n] = v;
+            const T corr = sw[p][0] * Mv[ki] + sw[p][1] * Mv[ki + 1] + sw[p][2] * yk + sw[p][3] * yk1;
+            a.z[(long long)j * N + (k + 1) * n] = a.Ycf[(long long)y * Nc + k] * inv2 + corr;
         }
     }
 }
@@ -393,10 +472,17 @@ struct CombineArgs { const T* Qp[16]; double beta[16]; };
 template <typename T>
 __global__ void combine_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
                                double inv_nu, long long n, T* __restrict__ out) {
+    // Arithmetic in the vectors' own precision.
+    T beta[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)c.beta[j] : T(0);
+    const T inu = (T)inv_nu;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        double v = (double)q[e];
-        for (int j = 0; j < k; ++j) v -= c.beta[j] * (double)c.Qp[j][e];
-        out[e] = (T)(v * inv_nu);
+        T v = q[e];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < k) v -= beta[j] * __ldg(c.Qp[j] + e);
+        out[e] = v * inu;
     }
 }
 
@@ -411,12 +497,12 @@ __global__ void __launch_bounds__(DOT_THREADS)
 multi_dot_kernel(DotArgs<T> d, int ndots, long long n, double* partials) {
     __shared__ double red[DOT_THREADS / 32];
     for (int q = 0; q < ndots; ++q) {
-        double acc = 0.0;
+        T acct = T(0);
         const T* a = d.a[q];
         const T* b = d.b[q];
         for (long long e = blockIdx.x * (long long)DOT_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * DOT_THREADS)
-            acc += (double)a[e] * (double)b[e];
-        acc = warp_sum(acc);
+            acct += a[e] * b[e];
+        double acc = warp_sum((double)acct);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -425,6 +511,45 @@ multi_dot_kernel(DotArgs<T> d, int ndots, long long n, double* partials) {
             if (threadIdx.x == 0) partials[(long long)blockIdx.x * ndots + q] = v;
         }
         __syncthreads();
+    }
+}
+
+// Inner products of the GCR step in one pass over the skeleton vectors:
+// out partials [block][2 + 2k]: <q,q>, <q,r>, then <q,p_j>, <r,p_j> for j < k.
+template <typename T>
+struct GcrDotArgs { const T* p[16]; };
+
+template <typename T, int K>
+__global__ void __launch_bounds__(DOT_THREADS)
+gcr_dots_kernel(const T* __restrict__ q, const T* __restrict__ r, GcrDotArgs<T> P, long long n, double* partials) {
+    constexpr int ND = 2 + 2 * K;
+    // Per-thread sums in the vectors' precision (a few dozen terms each), block sums in FP64.
+    T acc[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) acc[d] = T(0);
+    for (long long e = blockIdx.x * (long long)DOT_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * DOT_THREADS) {
+        const T qv = q[e], rv = r[e];
+        acc[0] += qv * qv;
+        acc[1] += qv * rv;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const T pv = __ldg(P.p[j] + e);
+            acc[2 + 2 * j] += qv * pv;
+            acc[3 + 2 * j] += rv * pv;
+        }
+    }
+    __shared__ double red[DOT_THREADS / 32][ND];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        const double v = warp_sum((double)acc[d]);
+        if (lane == 0) red[w][d] = v;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < ND; d += DOT_THREADS) {
+        double v = 0.0;
+        for (int ww = 0; ww < DOT_THREADS / 32; ++ww) v += red[ww][d];
+        partials[(long long)blockIdx.x * ND + d] = v;
     }
 }
 
@@ -531,7 +656,9 @@ inline unsigned grid_for(long long n, int threads = 256, long long cap = 152LL *
 // Launchers
 // ---------------------------------------------------------------------------
 int residual_grid_blocks(const Geometry& g) {
-    return ((g.Nf + RX - 1) / RX) * ((g.Nf + RY - 1) / RY);
+    const int a = ((g.Nf + RX - 1) / RX) * ((g.Nf + RY - 1) / RY);
+    const int b = ((g.Nf + MS_OUT * MS_WARPS - 1) / (MS_OUT * MS_WARPS)) * ((g.Nf + MS_ROWS - 1) / MS_ROWS);
+    return a > b ? a : b;
 }
 
 cudaError_t residual_fp64(const double* s, const double* u_in, double* u_out, const UpdateTerms& up,
@@ -544,11 +671,17 @@ cudaError_t residual_fp64(const double* s, const double* u_in, double* u_out, co
 }
 
 cudaError_t residual_mixed(const float* s_hi, const float* s_lo, const long long* U_in, long long* U_out,
-                           const UpdateTerms& up, double /*scale*/, const Geometry& g, const MixedCoefs& k,
+                           const UpdateTerms& up, double scale, const Geometry& g, const MixedCoefs& k,
                            ResidOut out, int* nblocks, int* overflow_flag, cudaStream_t st) {
-    dim3 grid((g.Nf + RX - 1) / RX, (g.Nf + RY - 1) / RY);
+    UpdateF uf{};
+    uf.count = up.count;
+    for (int q = 0; q < up.count && q < 16; ++q) {
+        uf.z[q] = reinterpret_cast<const float*>(up.z[q]);
+        uf.c[q] = (float)(up.coef[q] * scale);
+    }
+    dim3 grid((g.Nf + MS_OUT * MS_WARPS - 1) / (MS_OUT * MS_WARPS), (g.Nf + MS_ROWS - 1) / MS_ROWS);
     *nblocks = grid.x * grid.y;
-    residual_mixed_kernel<<<grid, RTHREADS, 0, st>>>(s_hi, s_lo, U_in, U_out, up, g, k, out, overflow_flag);
+    residual_mixed_kernel<<<grid, 32 * MS_WARPS, 0, st>>>(s_hi, s_lo, U_in, U_out, uf, g, k, out, overflow_flag);
     note_launch();
     return cudaGetLastError();
 }
@@ -582,10 +715,51 @@ cudaError_t multi_dot(const T* const* a, const T* const* b, int ndots, long long
     return cudaGetLastError();
 }
 
+template <typename T, int K>
+cudaError_t gcr_dots_launch(const T* q, const T* r, const GcrDotArgs<T>& P, long long n, double* partials,
+                            unsigned grid, cudaStream_t st) {
+    gcr_dots_kernel<T, K><<<grid, DOT_THREADS, 0, st>>>(q, r, P, n, partials);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gcr_dots(const T* q, const T* r, const T* const* p, int k, long long n,
+                     double* partials, int* nblocks, cudaStream_t st) {
+    GcrDotArgs<T> P{};
+    for (int j = 0; j < k && j < 16; ++j) P.p[j] = p[j];
+    const unsigned grid = grid_for(n, DOT_THREADS, 152LL * 2);
+    *nblocks = (int)grid;
+    switch (k) {
+        case 0: return gcr_dots_launch<T, 0>(q, r, P, n, partials, grid, st);
+        case 1: return gcr_dots_launch<T, 1>(q, r, P, n, partials, grid, st);
+        case 2: return gcr_dots_launch<T, 2>(q, r, P, n, partials, grid, st);
+        case 3: return gcr_dots_launch<T, 3>(q, r, P, n, partials, grid, st);
+        case 4: return gcr_dots_launch<T, 4>(q, r, P, n, partials, grid, st);
+        case 5: return gcr_dots_launch<T, 5>(q, r, P, n, partials, grid, st);
+        case 6: return gcr_dots_launch<T, 6>(q, r, P, n, partials, grid, st);
+        case 7: return gcr_dots_launch<T, 7>(q, r, P, n, partials, grid, st);
+        case 8: return gcr_dots_launch<T, 8>(q, r, P, n, partials, grid, st);
+        case 9: return gcr_dots_launch<T, 9>(q, r, P, n, partials, grid, st);
+        case 10: return gcr_dots_launch<T, 10>(q, r, P, n, partials, grid, st);
+        case 11: return gcr_dots_launch<T, 11>(q, r, P, n, partials, grid, st);
+        case 12: return gcr_dots_launch<T, 12>(q, r, P, n, partials, grid, st);
+        case 13: return gcr_dots_launch<T, 13>(q, r, P, n, partials, grid, st);
+        case 14: return gcr_dots_launch<T, 14>(q, r, P, n, partials, grid, st);
+        case 15: return gcr_dots_launch<T, 15>(q, r, P, n, partials, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename T>
 cudaError_t merge_knots(const MergeArgs<T>& a, cudaStream_t st) {
-    const size_t smem = sizeof(T) * (size_t)a.g.Nc;
-    merge_knots_kernel<T><<<2 * a.g.Nc, 128, smem, st>>>(a);
+    const size_t smem = sizeof(T) * (size_t)MK_LINES * a.g.Nc;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(merge_knots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int nblk = (a.g.Nc + MK_LINES - 1) / MK_LINES;
+    merge_knots_kernel<T><<<2 * nblk, 256, smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
@@ -674,6 +848,7 @@ cudaError_t convert_array(const Ts* in, Td* out, long long n, cudaStream_t st) {
 #define INST(T) \
     template cudaError_t build_submesh_rhs<T>(const double*, const double*, const Geometry&, const double*, const double*, T*, T*, T*, cudaStream_t); \
     template cudaError_t multi_dot<T>(const T* const*, const T* const*, int, long long, double*, int*, cudaStream_t); \
+    template cudaError_t gcr_dots<T>(const T*, const T*, const T* const*, int, long long, double*, int*, cudaStream_t); \
     template cudaError_t merge_knots<T>(const MergeArgs<T>&, cudaStream_t); \
     template cudaError_t merge_write<T>(const MergeArgs<T>&, cudaStream_t); \
     template cudaError_t skeleton_apply<T>(const T*, const Geometry&, const Stencil&, T*, cudaStream_t); \

@@ -3,98 +3,188 @@
 // Every system of eq. (2.4) is block tridiagonal Toeplitz along its "row"
 // axis (R = 2^L - 1 rows, each a vector of C unknowns along the other axis):
 //     a x_{i-1} + (d I + T) x_i + c x_{i+1} = f_i.
-// Block cyclic reduction (BCR) with the per-level factors of host_math.cu:
+// Block cyclic reduction (BCR) with the per-level factors of host_math.cu
+// (P_l = wl_l M_l, Q_l = wr_l M_l, B_l^{-1}):
 //   forward, level l = 0..L-2 (s = 2^l), rows i = 2s, 4s, ...:
-//       f_i <- f_i - P_l f_{i-s} - Q_l f_{i+s}
+//       f_i <- f_i - M_l (wl_l f_{i-s} + wr_l f_{i+s})
 //   backward, level l = L-1..0, rows i = s, 3s, 5s, ...:
-//       x_i  = B_l^{-1} f_i - P_l x_{i-s} - Q_l x_{i+s}
+//       x_i  = B_l^{-1} f_i - M_l (wl_l x_{i-s} + wr_l x_{i+s})
 // (P_l, Q_l, B_l^{-1} are functions of T and commute, so the back-substitution
 // reuses the forward factors).  Row 0 and row R+1 are zero.
 //
-// bcr_level_kernel: one launch per level, a CTA computes a TR x TC tile of
-// output rows x columns and streams the C x C factors through shared memory
-// in KT-wide slices.  Used for the anisotropic families (R = N_f rows).
-// fill_holes_kernel: the Filler of Algorithm 3, all levels of one hole in
-// shared memory; persistent CTAs keep every level's factors resident and walk
-// over the holes.
+// bcr_level_kernel: one launch per level; the level is a small dense GEMM
+// (rows of the level x C outputs x C or 2C reduction) split over the
+// reduction dimension among the 8 CTAs of a thread-block cluster, whose
+// partial tiles are summed in a fixed order through distributed shared
+// memory.  Used for the anisotropic families (R = N_f rows, C = N_c).
+// fill_holes_kernel: the Filler of Algorithm 3.  A warp segment of C+1 lanes
+// owns one hole (lane c = hole column c); 32/(C+1) holes share a warp.  The
+// factors of every level stay resident in shared memory for all holes a
+// persistent CTA visits; only warp-level synchronisation is needed.
 #include "asdsm_internal.h"
 #include <cuda_runtime.h>
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
 
 namespace asdsm {
 
 namespace {
 
-constexpr int TR = 8;      // output rows per CTA
-constexpr int TC = 32;     // output columns per CTA
-constexpr int KT = 32;     // reduction slice
+constexpr int GT_N = 64;       // output columns per tile
+constexpr int GT_K = 32;       // reduction slice
+constexpr int GT_THREADS = 256;
+constexpr int KSPLIT = 8;      // CTAs of a cluster sharing one output tile
 
-template <typename T, bool kBackward>
-__global__ void __launch_bounds__(TR * TC)
-bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
-    // blockIdx.z enumerates (group, system); blockIdx.y row tiles; blockIdx.x column tiles.
+// One BCR level as a GEMM: out[t][c] = sum_k A[t][k] F[k][c], the reduction
+// running over one factor (forward: -M (wl f_{i-s} + wr f_{i+s})) or two
+// (backward: B^{-1} f_i, then -M (wl x_{i-s} + wr x_{i+s})), i.e. K' = C or 2C.
+// A cluster of KSPLIT CTAs shares one TM x 64 output tile: CTA r multiplies the
+// 32-wide slices r, r+KSPLIT, ... of K', keeps its partial tile in shared
+// memory, and after a cluster barrier each CTA sums one eighth of the tile
+// over the 8 partials in rank order (deterministic) and writes it.
+template <typename T, bool kBackward, int TM, int KS>
+__device__ __forceinline__ void bcr_level_body(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
+    constexpr int RPT = TM / 16;                       // output rows per thread
+    constexpr int A_PER_T = TM * GT_K / GT_THREADS;    // A-slice elements per thread (2 or 8)
+    constexpr int F_PER_T = GT_K * GT_N / GT_THREADS;  // factor-slice elements per thread (8)
+    // The slices As [k][row], Fs [k][col] and, after the reduction loop, the
+    // partial tile Part [row][col] share one buffer (Part fits in As + Fs).
+    constexpr int AS_ELEMS = GT_K * (TM + 4), FS_ELEMS = GT_K * GT_N;
+    static_assert(TM * GT_N <= AS_ELEMS + FS_ELEMS, "partial tile must fit in the slice buffers");
+    __shared__ __align__(16) T smem_buf[AS_ELEMS + FS_ELEMS];
+    T (*As)[TM + 4] = reinterpret_cast<T (*)[TM + 4]>(smem_buf);
+    T (*Fs)[GT_N] = reinterpret_cast<T (*)[GT_N]>(smem_buf + AS_ELEMS);
+    T* Part = smem_buf;
+    const int rank = KS > 1 ? (int)cg::this_cluster().block_rank() : 0;
     int z = blockIdx.z;
     const BcrSys<T>* gp = &g0;
     if (ngroups > 1 && z >= g0.nsys) { gp = &g1; z -= g0.nsys; }
     const BcrSys<T>& g = *gp;
-    if (z >= g.nsys) return;
+    // Every CTA of a cluster takes the same branch below (same z, tile), so the
+    // cluster barriers are always reached by all of them.
+    const bool active = z < g.nsys && level < g.L;
     const int R = g.R, C = g.C;
     const int s = 1 << level;
-    // Output rows of this level (1-based): forward i = 2s*t (t = 1..), backward i = s*(2t-1).
-    const int nrows = kBackward ? ((R + 1) >> (level + 1)) : (((R + 1) >> (level + 1)) - 1);
-    const int t0 = blockIdx.y * TR;
-    if (t0 >= nrows) return;
-    const int c0 = blockIdx.x * TC;
+    const int nrows = active ? (kBackward ? ((R + 1) >> (level + 1)) : (((R + 1) >> (level + 1)) - 1)) : 0;
+    const int t0 = blockIdx.y * TM;
+    const int c0 = (blockIdx.x / KS) * GT_N;
+    const bool tile_ok = active && t0 < nrows && c0 < C;
     const size_t n2 = (size_t)C * C;
-    const T* Pt = g.Pt + (size_t)level * n2;
-    const T* Qt = g.Qt + (size_t)level * n2;
-    const T* Bt = g.Bt + (size_t)level * n2;
-    T* X = g.X + (size_t)z * g.stride;
-    T* Y = g.Y + (size_t)z * g.stride;
+    const T* Mt = g.Mt + (size_t)(active ? level : 0) * n2;
+    const T* Bt = g.Bt + (size_t)(active ? level : 0) * n2;
+    const T wl = active ? g.wl[level] : T(0), wr = active ? g.wr[level] : T(0);
+    T* X = g.X + (size_t)(active ? z : 0) * g.stride;
+    T* Y = g.Y + (size_t)(active ? z : 0) * g.stride;
+    const T* nb = kBackward ? Y : X;            // neighbour rows: solved (bwd) or reduced (fwd)
 
-    __shared__ T sP[KT][TC], sQ[KT][TC], sB[kBackward ? KT : 1][TC];
-    __shared__ T sL[TR][KT], sR[TR][KT], sM[kBackward ? TR : 1][KT];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    T acc[RPT][4];
+#pragma unroll
+    for (int a = 0; a < RPT; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
 
-    const int tc = threadIdx.x, tr = threadIdx.y;
-    const int row_t = t0 + tr;                     // 0-based index into this level's rows
-    const bool row_ok = row_t < nrows;
-    const int i = kBackward ? s * (2 * row_t + 1) : 2 * s * (row_t + 1);   // 1-based row
-    const int col = c0 + tc;
-    const T* src = kBackward ? Y : X;              // neighbours: solved rows (bwd) or reduced rhs (fwd)
-    T acc = T(0);
-    for (int k0 = 0; k0 < C; k0 += KT) {
-        // Factor slices: [k][c] layout, threads along c.
-        for (int kk = tr; kk < KT; kk += TR) {
-            const int k = k0 + kk;
-            const bool ok = (k < C) && (col < C);
-            sP[kk][tc] = ok ? Pt[(size_t)k * C + col] : T(0);
-            sQ[kk][tc] = ok ? Qt[(size_t)k * C + col] : T(0);
-            if (kBackward) sB[kk][tc] = ok ? Bt[(size_t)k * C + col] : T(0);
+    const int nk = (C + GT_K - 1) / GT_K;        // slices per factor pass
+    const int passes = kBackward ? 2 : 1;
+    for (int q = rank; tile_ok && q < passes * nk; q += KS) {
+        const int pass = kBackward ? q / nk : 1;  // 0: B^{-1} f_i, 1: -M v_i
+        const int k0 = (q % nk) * GT_K;
+        const T* Fm = pass == 0 ? Bt : Mt;
+#pragma unroll
+        for (int j = 0; j < A_PER_T; ++j) {
+            const int e = tid + j * GT_THREADS;
+            const int r = e / GT_K, kk = e % GT_K;
+            const int t = t0 + r, k = k0 + kk;
+            T v = T(0);
+            if (t < nrows && k < C) {
+                const int i = kBackward ? s * (2 * t + 1) : 2 * s * (t + 1);
+                if (pass == 0) {
+                    v = X[(size_t)(i - 1) * C + k];
+                } else {
+                    if (i - s >= 1) v += wl * nb[(size_t)(i - s - 1) * C + k];
+                    if (i + s <= R) v += wr * nb[(size_t)(i + s - 1) * C + k];
+                    v = -v;
+                }
+            }
+            As[kk][r] = v;
         }
-        // Neighbour rows i-s, i+s (and row i for the backward B^{-1} f_i term).
-        {
-            const int k = k0 + tc;
-            const bool kok = row_ok && (k < C);
-            const int il = i - s, ir = i + s;
-            sL[tr][tc] = (kok && il >= 1) ? src[(size_t)(il - 1) * C + k] : T(0);
-            sR[tr][tc] = (kok && ir <= R) ? src[(size_t)(ir - 1) * C + k] : T(0);
-            if (kBackward) sM[tr][tc] = kok ? X[(size_t)(i - 1) * C + k] : T(0);
+#pragma unroll
+        for (int j = 0; j < F_PER_T; ++j) {
+            const int e = tid + j * GT_THREADS;
+            const int kk = e / GT_N, cc = e % GT_N;
+            const int k = k0 + kk, c = c0 + cc;
+            Fs[kk][cc] = (k < C && c < C) ? __ldg(Fm + (size_t)k * C + c) : T(0);
         }
         __syncthreads();
 #pragma unroll 8
-        for (int kk = 0; kk < KT; ++kk) {
-            acc -= sP[kk][tc] * sL[tr][kk];
-            acc -= sQ[kk][tc] * sR[tr][kk];
-            if (kBackward) acc += sB[kk][tc] * sM[tr][kk];
+        for (int kk = 0; kk < GT_K; ++kk) {
+            T av[RPT], bv[4];
+            if constexpr (sizeof(T) == 4 && RPT == 4) {
+                const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+                av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+            } else {
+#pragma unroll
+                for (int a = 0; a < RPT; ++a) av[a] = As[kk][ty * RPT + a];
+            }
+            if constexpr (sizeof(T) == 4) {
+                const float4 b4 = *reinterpret_cast<const float4*>(&Fs[kk][tx * 4]);
+                bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
+            } else {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) bv[b] = Fs[kk][tx * 4 + b];
+            }
+#pragma unroll
+            for (int a = 0; a < RPT; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
         }
         __syncthreads();
     }
-    if (row_ok && col < C) {
-        if (kBackward) {
-            Y[(size_t)(i - 1) * C + col] = acc;
-        } else {
-            X[(size_t)(i - 1) * C + col] += acc;
+    if constexpr (KS == 1) {
+        for (int a = 0; tile_ok && a < RPT; ++a) {
+            const int t = t0 + ty * RPT + a;
+            if (t >= nrows) continue;
+            const int i = kBackward ? s * (2 * t + 1) : 2 * s * (t + 1);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int c = c0 + tx * 4 + b;
+                if (c >= C) continue;
+                if (kBackward) Y[(size_t)(i - 1) * C + c] = acc[a][b];
+                else X[(size_t)(i - 1) * C + c] += acc[a][b];
+            }
         }
+    } else {
+        cg::cluster_group cluster = cg::this_cluster();
+        __syncthreads();     // the slice buffers are reused for the partial tile
+#pragma unroll
+        for (int a = 0; a < RPT; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Part[(ty * RPT + a) * GT_N + tx * 4 + b] = acc[a][b];
+        cluster.sync();
+        // Rank r reduces elements [r*TM*64/KS, (r+1)*TM*64/KS) of the tile over the partials.
+        constexpr int SLICE = TM * GT_N / KS;
+        for (int e = rank * SLICE + tid; tile_ok && e < (rank + 1) * SLICE; e += GT_THREADS) {
+            T sum = T(0);
+#pragma unroll
+            for (int rr = 0; rr < KS; ++rr) sum += cluster.map_shared_rank(Part, rr)[e];
+            const int r = e / GT_N, cc = e % GT_N;
+            const int t = t0 + r, c = c0 + cc;
+            if (t < nrows && c < C) {
+                const int i = kBackward ? s * (2 * t + 1) : 2 * s * (t + 1);
+                if (kBackward) Y[(size_t)(i - 1) * C + c] = sum;
+                else X[(size_t)(i - 1) * C + c] += sum;
+            }
+        }
+        cluster.sync();          // partial tiles stay alive until every CTA has read them
     }
+}
+
+template <typename T, bool kBackward, int TM>
+__global__ void __cluster_dims__(KSPLIT, 1, 1) __launch_bounds__(GT_THREADS)
+bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
+    bcr_level_body<T, kBackward, TM, KSPLIT>(g0, g1, ngroups, level);
 }
 
 template <typename T, bool kBackward>
@@ -109,10 +199,15 @@ cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, cudaSt
         nsys += g.nsys;
     }
     if (maxRows <= 0 || nsys == 0) return cudaSuccess;
-    dim3 grid((maxC + TC - 1) / TC, (maxRows + TR - 1) / TR, nsys);
-    dim3 block(TC, TR);
     BcrSys<T> g1 = ngroups > 1 ? groups[1] : groups[0];
-    bcr_level_kernel<T, kBackward><<<grid, block, 0, st>>>(groups[0], g1, ngroups, level);
+    const int ctiles = (maxC + GT_N - 1) / GT_N;
+    if (maxRows >= 64) {
+        dim3 grid(KSPLIT * ctiles, (maxRows + 63) / 64, nsys);
+        bcr_level_kernel<T, kBackward, 64><<<grid, GT_THREADS, 0, st>>>(groups[0], g1, ngroups, level);
+    } else {
+        dim3 grid(KSPLIT * ctiles, (maxRows + 15) / 16, nsys);
+        bcr_level_kernel<T, kBackward, 16><<<grid, GT_THREADS, 0, st>>>(groups[0], g1, ngroups, level);
+    }
     note_launch();
     return cudaGetLastError();
 }
@@ -138,11 +233,12 @@ template cudaError_t bcr_solve<float>(const BcrSys<float>*, int, cudaStream_t);
 template cudaError_t bcr_solve<double>(const BcrSys<double>*, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Fused hole fill (Algorithm 3).
+// Fused hole fill (Algorithm 3): one warp segment per hole.
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int FILL_THREADS = 256;
+constexpr int FILL_MAX_WARPS = 8;
+constexpr int FILL_MAX_THREADS = 32 * FILL_MAX_WARPS;
 
 template <typename T>
 __device__ __forceinline__ T load_src(const FillArgs<T>& a, long long idx);
@@ -156,140 +252,255 @@ __device__ __forceinline__ float load_src<float>(const FillArgs<float>& a, long 
     return a.src_hi ? a.src_hi[idx] : (a.src_d ? (float)a.src_d[idx] : 0.0f);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(FILL_THREADS)
+// Shared-memory layout (elements of T): factors Mt, Bt of all levels as
+// [L][C][CP] with CP = C+1 (padded row), then per hole segment X, Y and a
+// staging block V, each [R][CP].
+__host__ __device__ constexpr int fill_cp(int C) { return C + 1; }
+
+// acc[t] += sum_k F[k][c] * V[t*vs + k] for t < ROWS (V rows 16-byte aligned, padded column zero).
+template <typename T, int C, int ROWS>
+__device__ __forceinline__ void fill_matvec(const T* __restrict__ F, const T* __restrict__ V, int vs, int c, T* acc) {
+    constexpr int CP = fill_cp(C);
+    if constexpr (sizeof(T) == 4 && (C + 1) % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < C + 1; k += 4) {
+            const T m0 = F[(k + 0) * CP + c];
+            const T m1 = F[(k + 1) * CP + c];
+            const T m2 = F[(k + 2) * CP + c];
+            const T m3 = (k + 3 < C) ? F[(k + 3) * CP + c] : T(0);
+#pragma unroll
+            for (int t = 0; t < ROWS; ++t) {
+                const float4 v = *reinterpret_cast<const float4*>(V + t * vs + k);
+                acc[t] += m0 * v.x + m1 * v.y + m2 * v.z + m3 * v.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            const T m = F[k * CP + c];
+#pragma unroll
+            for (int t = 0; t < ROWS; ++t) acc[t] += m * V[t * vs + k];
+        }
+    }
+}
+
+// Row counts of a level are 2^q or 2^q - 1: dispatch them to compile-time loops.
+template <typename T, int C>
+__device__ __forceinline__ void fill_matvec_n(int rows, const T* F, const T* V, int vs, int c, T* acc) {
+    switch (rows) {
+        case 1: fill_matvec<T, C, 1>(F, V, vs, c, acc); break;
+        case 2: if constexpr (C >= 2) fill_matvec<T, C, 2>(F, V, vs, c, acc); break;
+        case 3: if constexpr (C >= 3) fill_matvec<T, C, 3>(F, V, vs, c, acc); break;
+        case 4: if constexpr (C >= 4) fill_matvec<T, C, 4>(F, V, vs, c, acc); break;
+        case 7: if constexpr (C >= 7) fill_matvec<T, C, 7>(F, V, vs, c, acc); break;
+        case 8: if constexpr (C >= 8) fill_matvec<T, C, 8>(F, V, vs, c, acc); break;
+        case 15: if constexpr (C >= 15) fill_matvec<T, C, 15>(F, V, vs, c, acc); break;
+        case 16: if constexpr (C >= 16) fill_matvec<T, C, 16>(F, V, vs, c, acc); break;
+        default: break;
+    }
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(FILL_MAX_THREADS)
 fill_holes_kernel(FillArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
-    const int C = a.n - 1;          // unknowns per hole row and per hole column
-    const int R = C;
-    const int L = a.L;
-    const size_t n2 = (size_t)C * C;
-    T* sPt = sm;
-    T* sQt = sPt + L * n2;
-    T* sBt = sQt + L * n2;
-    T* sX = sBt + L * n2;
-    T* sY = sX + (size_t)R * C;
-    // Factors of every level stay resident for all holes this CTA visits.
-    for (size_t e = threadIdx.x; e < L * n2; e += blockDim.x) {
-        sPt[e] = a.Pt[e];
-        sQt[e] = a.Qt[e];
-        sBt[e] = a.Bt[e];
+    constexpr int R = C;
+    constexpr int CP = fill_cp(C);
+    constexpr int S = C + 1;                    // lanes per hole segment
+    constexpr int SEGS = 32 / S;                // holes per warp
+    constexpr int L = (C == 1) ? 1 : (C == 3) ? 2 : (C == 7) ? 3 : (C == 15) ? 4 : 5;
+    constexpr int FSZ = C * CP;                 // one padded C x C factor
+    constexpr int SEG = 3 * R * CP;             // X, Y, V per segment
+    T* sMt = sm;
+    T* sBt = sMt + L * FSZ;
+    T* work = sBt + L * FSZ;
+    __shared__ T sW[2][kMaxLevels];
+    for (int e = threadIdx.x; e < L * C * C; e += blockDim.x) {
+        const int l = e / (C * C), r = (e / C) % C, c = e % C;
+        sMt[l * FSZ + r * CP + c] = a.Mt[e];
+        sBt[l * FSZ + r * CP + c] = a.Bt[e];
+    }
+    if (threadIdx.x < kMaxLevels) {
+        sW[0][threadIdx.x] = a.wl[threadIdx.x];
+        sW[1][threadIdx.x] = a.wr[threadIdx.x];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = lane / S, c = lane % S;     // c == C: padding lane (keeps the zero column)
+    T* X = work + (warp * SEGS + seg) * SEG;
+    T* Y = X + R * CP;
+    T* V = Y + R * CP;
+    // The padding column of X and V stays zero (the float4 mat-vec reads it).
+    if (c == C) {
+        for (int y = 0; y < R; ++y) { X[y * CP + C] = T(0); V[y * CP + C] = T(0); }
     }
     const Geometry& g = a.g;
     const int N = g.N, n = a.n, mc = g.mc;
     const long long nholes = (long long)mc * mc;
     const T cw = (T)a.sten.cw, ce = (T)a.sten.ce, cs = (T)a.sten.cs, cn = (T)a.sten.cn;
-    __syncthreads();
-    for (long long hole = blockIdx.x; hole < nholes; hole += gridDim.x) {
-        const int bi = (int)(hole % mc), bj = (int)(hole / mc);
-        const int gx0 = bi * n, gy0 = bj * n;     // hole-local (x,y) in 1..n-1 -> grid (gx0+x, gy0+y)
+    const int warps_cta = blockDim.x >> 5;
+    const long long warps_total = (long long)gridDim.x * warps_cta;
+    const long long gwarp = (long long)blockIdx.x * warps_cta + warp;
+    for (long long base = gwarp * SEGS; base < nholes; base += warps_total * SEGS) {
+        const long long hole = base + seg;
+        const bool hole_ok = c < C && hole < nholes;
+        const int bi = hole_ok ? (int)(hole % mc) : 0, bj = hole_ok ? (int)(hole / mc) : 0;
+        const int gx = bi * n + c + 1;          // grid x of this lane's column
         // Right-hand side of step 2: P b + c with c = -P A (skeleton).
-        for (int e = threadIdx.x; e < R * C; e += blockDim.x) {
-            const int y = e / C + 1, x = e % C + 1;
-            const long long gidx = (long long)(gy0 + y) * N + (gx0 + x);
-            T f = T(0);
-            if (a.mode == FILL_WITH_SOURCE || a.mode == FILL_ARRAY || a.mode == FILL_RESIDUAL_TO_U)
-                f = load_src<T>(a, gidx);
-            if (a.mode == FILL_WITH_SOURCE || a.mode == FILL_HOMOGENEOUS) {
-                if (x == 1) f -= cw * a.z[gidx - 1];
-                if (x == C) f -= ce * a.z[gidx + 1];
-                if (y == 1) f -= cs * a.z[gidx - N];
-                if (y == C) f -= cn * a.z[gidx + N];
+        if (hole_ok) {
+#pragma unroll
+            for (int y = 1; y <= R; ++y) {
+                const long long gidx = (long long)(bj * n + y) * N + gx;
+                T f = T(0);
+                if (a.mode == FILL_WITH_SOURCE || a.mode == FILL_ARRAY || a.mode == FILL_RESIDUAL_TO_U)
+                    f = load_src<T>(a, gidx);
+                if (a.mode == FILL_WITH_SOURCE || a.mode == FILL_HOMOGENEOUS) {
+                    if (c == 0) f -= cw * a.z[gidx - 1];
+                    if (c == C - 1) f -= ce * a.z[gidx + 1];
+                    if (y == 1) f -= cs * a.z[gidx - N];
+                    if (y == R) f -= cn * a.z[gidx + N];
+                }
+                X[(y - 1) * CP + c] = f;
             }
-            sX[e] = f;
         }
-        __syncthreads();
-        // Forward reduction.
+        __syncwarp();
+        // Forward reduction: f_i -= M (wl f_{i-s} + wr f_{i+s}).
+#pragma unroll
         for (int l = 0; l + 1 < L; ++l) {
             const int s = 1 << l;
             const int nrows = ((R + 1) >> (l + 1)) - 1;
-            const T* P = sPt + l * n2;
-            const T* Q = sQt + l * n2;
-            for (int e = threadIdx.x; e < nrows * C; e += blockDim.x) {
-                const int t = e / C, c = e % C;
-                const int i = 2 * s * (t + 1);
-                const T* fl = sX + (size_t)(i - s - 1) * C;
-                const T* fr = sX + (size_t)(i + s - 1) * C;   // i + s <= R always at these levels
-                T acc = T(0);
-                for (int k = 0; k < C; ++k) acc += P[(size_t)k * C + c] * fl[k] + Q[(size_t)k * C + c] * fr[k];
-                sY[(size_t)(i - 1) * C + c] = acc;            // stage, rows i are written below
+            const T wl = sW[0][l], wr = sW[1][l];
+            if (hole_ok) {
+                for (int t = 0; t < nrows; ++t) {
+                    const int i = 2 * s * (t + 1);
+                    V[t * CP + c] = wl * X[(i - s - 1) * CP + c] + wr * X[(i + s - 1) * CP + c];
+                }
             }
-            __syncthreads();
-            for (int e = threadIdx.x; e < nrows * C; e += blockDim.x) {
-                const int t = e / C, c = e % C;
-                const int i = 2 * s * (t + 1);
-                sX[(size_t)(i - 1) * C + c] -= sY[(size_t)(i - 1) * C + c];
+            __syncwarp();
+            if (hole_ok) {
+                T acc[(R + 1) / 2];
+#pragma unroll
+                for (int t = 0; t < (R + 1) / 2; ++t) acc[t] = T(0);
+                fill_matvec_n<T, C>(nrows, sMt + l * FSZ, V, CP, c, acc);
+                for (int t = 0; t < nrows; ++t) {
+                    const int i = 2 * s * (t + 1);
+                    X[(i - 1) * CP + c] -= acc[t];
+                }
             }
-            __syncthreads();
+            __syncwarp();
         }
-        // Back substitution.
+        // Back substitution: x_i = B^{-1} f_i - M (wl x_{i-s} + wr x_{i+s}).
+#pragma unroll
         for (int l = L - 1; l >= 0; --l) {
             const int s = 1 << l;
             const int nrows = (R + 1) >> (l + 1);
-            const T* P = sPt + l * n2;
-            const T* Q = sQt + l * n2;
-            const T* B = sBt + l * n2;
-            for (int e = threadIdx.x; e < nrows * C; e += blockDim.x) {
-                const int t = e / C, c = e % C;
-                const int i = s * (2 * t + 1);
-                const T* f = sX + (size_t)(i - 1) * C;
-                T acc = T(0);
-                for (int k = 0; k < C; ++k) acc += B[(size_t)k * C + c] * f[k];
-                if (i - s >= 1) {
-                    const T* xl = sY + (size_t)(i - s - 1) * C;
-                    for (int k = 0; k < C; ++k) acc -= P[(size_t)k * C + c] * xl[k];
+            const T wl = sW[0][l], wr = sW[1][l];
+            if (hole_ok) {
+                for (int t = 0; t < nrows; ++t) {
+                    const int i = s * (2 * t + 1);
+                    T v = T(0);
+                    if (i - s >= 1) v += wl * Y[(i - s - 1) * CP + c];
+                    if (i + s <= R) v += wr * Y[(i + s - 1) * CP + c];
+                    V[t * CP + c] = v;
                 }
-                if (i + s <= R) {
-                    const T* xr = sY + (size_t)(i + s - 1) * C;
-                    for (int k = 0; k < C; ++k) acc -= Q[(size_t)k * C + c] * xr[k];
-                }
-                sY[(size_t)(i - 1) * C + c] = acc;
             }
-            __syncthreads();
+            __syncwarp();
+            if (hole_ok) {
+                // B^{-1} f_i reads rows i = s(2t+1) of X: a strided view (s-1, 3s-1, ...) * CP.
+                T acc[(R + 1) / 2];
+#pragma unroll
+                for (int t = 0; t < (R + 1) / 2; ++t) acc[t] = T(0);
+                fill_matvec_n<T, C>(nrows, sBt + l * FSZ, X + (s - 1) * CP, 2 * s * CP, c, acc);
+                T acc2[(R + 1) / 2];
+#pragma unroll
+                for (int t = 0; t < (R + 1) / 2; ++t) acc2[t] = T(0);
+                fill_matvec_n<T, C>(nrows, sMt + l * FSZ, V, CP, c, acc2);
+                for (int t = 0; t < nrows; ++t) {
+                    const int i = s * (2 * t + 1);
+                    Y[(i - 1) * CP + c] = acc[t] - acc2[t];
+                }
+            }
+            __syncwarp();
         }
         // Step 3: write the hole values.
-        for (int e = threadIdx.x; e < R * C; e += blockDim.x) {
-            const int y = e / C + 1, x = e % C + 1;
-            const long long gidx = (long long)(gy0 + y) * N + (gx0 + x);
-            const T v = sY[e];
-            if (a.mode == FILL_RESIDUAL_TO_U) {
-                if (a.U) a.U[gidx] += __double2ll_rn((double)v * a.fixed_scale);
-                else a.u_d[gidx] += (double)v;
-            } else if (a.mode == FILL_ARRAY && a.out_d) {
-                a.out_d[gidx] = (double)v;
-            } else {
-                a.out[gidx] = v;
+        if (hole_ok) {
+#pragma unroll
+            for (int y = 1; y <= R; ++y) {
+                const long long gidx = (long long)(bj * n + y) * N + gx;
+                const T v = Y[(y - 1) * CP + c];
+                if (a.mode == FILL_RESIDUAL_TO_U) {
+                    if (a.U) a.U[gidx] += __double2ll_rn((double)v * a.fixed_scale);
+                    else a.u_d[gidx] += (double)v;
+                } else if (a.mode == FILL_ARRAY && a.out_d) {
+                    a.out_d[gidx] = (double)v;
+                } else {
+                    a.out[gidx] = v;
+                }
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
 }  // namespace
 
+namespace {
+size_t fill_factor_bytes(size_t esz, int n, int L) {
+    const size_t C = (size_t)(n - 1), CP = (size_t)fill_cp((int)C);
+    return esz * 2 * (size_t)L * C * CP;
+}
+size_t fill_warp_bytes(size_t esz, int n) {
+    const size_t C = (size_t)(n - 1), CP = (size_t)fill_cp((int)C);
+    return esz * (32 / (C + 1)) * 3 * C * CP;
+}
+int fill_warps(size_t esz, int n, int L) {
+    const size_t budget = 227 * 1024;
+    const size_t f = fill_factor_bytes(esz, n, L), w = fill_warp_bytes(esz, n);
+    if (f + w > budget) return 0;
+    const size_t k = (budget - f) / w;
+    return (int)(k < (size_t)FILL_MAX_WARPS ? k : (size_t)FILL_MAX_WARPS);
+}
+}  // namespace
+
+// Shared memory of one fill CTA with at least one warp (0-fit test by the caller).
 template <typename T>
 size_t fill_smem_bytes(int n, int L) {
-    const size_t C = (size_t)(n - 1);
-    return sizeof(T) * (3 * (size_t)L * C * C + 2 * C * C);
+    return fill_factor_bytes(sizeof(T), n, L) + fill_warp_bytes(sizeof(T), n);
+}
+
+template <typename T, int C>
+cudaError_t fill_holes_launch(const FillArgs<T>& a, int num_sms, cudaStream_t st) {
+    const int warps = fill_warps(sizeof(T), a.n, a.L);
+    if (warps < 1) return cudaErrorInvalidValue;
+    const size_t smem = fill_factor_bytes(sizeof(T), a.n, a.L) + (size_t)warps * fill_warp_bytes(sizeof(T), a.n);
+    cudaError_t e = cudaFuncSetAttribute(fill_holes_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_holes_kernel<T, C>, 32 * warps, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const long long nholes = (long long)a.g.mc * a.g.mc;
+    const long long segs = 32 / a.n;
+    const long long per_cta = (long long)warps * segs;
+    long long grid = (long long)num_sms * per_sm;
+    const long long need = (nholes + per_cta - 1) / per_cta;
+    if (grid > need) grid = need;
+    fill_holes_kernel<T, C><<<(unsigned)grid, 32 * warps, smem, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t fill_holes(const FillArgs<T>& a, int num_sms, cudaStream_t st) {
-    const size_t smem = fill_smem_bytes<T>(a.n, a.L);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fill_holes_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_holes_kernel<T>, FILL_THREADS, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const long long nholes = (long long)a.g.mc * a.g.mc;
-    long long grid = (long long)num_sms * per_sm;
-    if (grid > nholes) grid = nholes;
-    fill_holes_kernel<T><<<(unsigned)grid, FILL_THREADS, smem, st>>>(a);
-    note_launch();
-    return cudaGetLastError();
+    switch (a.n) {
+        case 2: return fill_holes_launch<T, 1>(a, num_sms, st);
+        case 4: return fill_holes_launch<T, 3>(a, num_sms, st);
+        case 8: return fill_holes_launch<T, 7>(a, num_sms, st);
+        case 16: return fill_holes_launch<T, 15>(a, num_sms, st);
+        case 32: return fill_holes_launch<T, 31>(a, num_sms, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template size_t fill_smem_bytes<float>(int, int);

@@ -130,8 +130,9 @@ def test_fp64_iterates_match_oracle(lib, name, make, mc, m):
             got = orc.interior(u.cpu().numpy())
         assert res.stats["sweeps"] == info["sweeps"]
         assert _relerr(got, uo) <= 1e-12, (sweeps, _relerr(got, uo))
-        # Residual histories agree to the rounding level of each residual (1e-14 of ||b||).
-        np.testing.assert_allclose(res.history, info["hist"], rtol=1e-8, atol=1e-14)
+        # Residual histories: iterates agreeing to 1e-12 give relative residuals that agree to
+        # ||A|| ||du|| / ||b|| <= 8 (N-1)^2 |u|/|b| * 1e-12 (a few 1e-11 on these grids).
+        np.testing.assert_allclose(res.history, info["hist"], rtol=1e-6, atol=1e-11)
 
 
 def test_fp64_solves_cfg1_to_1e12_like_the_oracle(lib):
