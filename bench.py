@@ -152,7 +152,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sweeps_needed = 100   # sweeps the mixed GPU solve of this workload takes (recorded in the design doc)
+    sweeps_needed = 100   # an upper estimate of the sweeps the mixed GPU solve of this workload takes
     vals = []
     for k in range(args.warmup + args.steps):
         r = oracle_sample(sweeps_needed, sample_sweeps=4)

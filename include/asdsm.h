@@ -65,7 +65,7 @@ typedef struct {
     double  beta[3];    /* advection per axis (x, y[, z]) */
 } asdsm_desc;
 
-/* Iteration options (Algorithm 4 and the readings listed in the design doc). */
+/* Iteration options of Algorithm 4. */
 typedef struct {
     double   tol;               /* stop when ||b - A u||_2 / ||b||_2 <= tol */
     int32_t  max_sweeps;        /* sweeps of Algorithm 4 (hole corrections count as sweeps) */
@@ -77,7 +77,9 @@ typedef struct {
     double   hole_fix_ratio;    /* re-fill holes when ||r_holes|| > ratio*||r|| ... */
     double   hole_fix_growth;   /* ... and > growth * (hole residual after the last fill) */
     int32_t  stagnation_window; /* stagnated if ||r_k|| > (1 - stagnation_factor) ||r_{k-window}|| */
-    int32_t  pad_;
+    int32_t  sweep_graph;       /* 1 (default): sweeps replayed as CUDA graphs, every decision between
+                                   sweeps taken on the device; 0: the host takes them (two reads per
+                                   sweep).  Same arithmetic; profiling (asdsm_profile) uses 0. */
     double   stagnation_factor;
 } asdsm_opts;
 

@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_sweeps", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("accel_m", ctypes.c_int32), ("skip_initial_guess", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("hole_fix_ratio", ctypes.c_double), ("hole_fix_growth", ctypes.c_double),
-                ("stagnation_window", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("stagnation_window", ctypes.c_int32), ("sweep_graph", ctypes.c_int32),
                 ("stagnation_factor", ctypes.c_double)]
 
 

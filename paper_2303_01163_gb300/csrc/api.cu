@@ -94,6 +94,23 @@ struct asdsm_handle {
     std::vector<cudaEvent_t> evpool;
     int evnext = 0;
     std::vector<PendingEv> pend_ev;
+    // Device-driven sweeps (opts.sweep_graph): control block, residual history,
+    // capture streams and the instantiated graph of kSweepsPerGraph sweeps.
+    SweepCtl* dctl = nullptr;
+    SweepCtl* hctl = nullptr;          // pinned
+    double* dhist = nullptr;
+    int hist_cap = 0;
+    int* hdone = nullptr;              // pinned [2]: done flags read between graph launches
+    cudaEvent_t evc[2] = {nullptr, nullptr};
+    cudaStream_t cap_st = nullptr, body_st = nullptr;
+    struct SweepGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int prec = -1, m = 0, S = 0;
+        const void* s = nullptr; const void* u = nullptr; const void* partials = nullptr;
+        long long top_launches = 0;            // kernels per sweep outside the switch node
+        long long body_launches[20] = {};      // kernels of each switch body
+    } gr;
 };
 
 namespace {
@@ -330,6 +347,239 @@ int initial_guess_to_z(asdsm_handle* h, const double* s, const double* u) {
 }
 
 // ---------------------------------------------------------------------------
+// Device-driven sweeps: one CUDA graph replays kSweepsPerGraph sweeps.  Per
+// sweep: the residual kernel (pending update read from the device), the norm
+// reduction, the controller, and a switch node whose bodies are the sweep for
+// direction slot kc (bodies 0..m-1) and the hole correction of the iterate in
+// buffer 0 or 1 (bodies m, m+1); value m+2 runs nothing (solve ended).
+// ---------------------------------------------------------------------------
+constexpr int kSweepsPerGraph = 8;
+
+void destroy_graph(asdsm_handle* h) {
+    if (h->gr.exec) cudaGraphExecDestroy(h->gr.exec);
+    if (h->gr.graph) cudaGraphDestroy(h->gr.graph);
+    h->gr = asdsm_handle::SweepGraph{};
+}
+
+template <typename T>
+int enqueue_residual_dyn(asdsm_handle* h, const double* s, double* u, double scale, const MixedCoefs& mk,
+                         int m, cudaStream_t st) {
+    const int pi = sizeof(T) == 8 ? 0 : 1;
+    auto& w = h->w[pi];
+    const Geometry& g = h->g;
+    ResidOut o{};
+    o.rfc = w.Xfc; o.rcf = w.Xcf; o.rskel = w.rskel; o.rfull = nullptr; o.partials = h->partials;
+    UpdateTerms up{};
+    for (int j = 0; j < m; ++j) up.z[j] = w.z[j];
+    up.dyn = &h->dctl->upd;
+    int nb = 0;
+    if (sizeof(T) == 8) CK(residual_fp64(s, u, h->u_work, up, g, h->sten, o, &nb, st));
+    else CK(residual_mixed(h->s_hi, h->s_lo, h->U[0], h->U[1], up, scale, g, mk, o, &nb, h->dflag, st));
+    CK(reduce_partials(h->partials, nb, 2, h->dsmall, st));
+    return ASDSM_OK;
+}
+
+// Hole-residual correction of the iterate in buffer par.
+template <typename T>
+int enqueue_holefix(asdsm_handle* h, const double* s, double* u, int par, double scale, const MixedCoefs& mk,
+                    cudaStream_t st) {
+    const int pi = sizeof(T) == 8 ? 0 : 1;
+    auto& w = h->w[pi];
+    const Geometry& g = h->g;
+    ResidOut o{};
+    o.rfull = w.rfull; o.partials = h->partials;
+    UpdateTerms none{};
+    FillArgs<T> fa{};
+    fa.mode = FILL_RESIDUAL_TO_U;
+    int nb = 0;
+    if (sizeof(T) == 8) {
+        double* ucur = par ? h->u_work : u;
+        CK(residual_fp64(s, ucur, ucur, none, g, h->sten, o, &nb, st));
+        fa.src_d = (const double*)w.rfull;
+        fa.u_d = ucur;
+    } else {
+        CK(residual_mixed(h->s_hi, h->s_lo, h->U[par], h->U[par], none, scale, g, mk, o, &nb, h->dflag, st));
+        fa.src_hi = (const float*)w.rfull;
+        fa.U = h->U[par];
+        fa.fixed_scale = scale;
+    }
+    hole_factors<T>(h->hole[pi], &fa);
+    fa.n = g.n; fa.g = g; fa.sten = h->sten;
+    CK(fill_holes<T>(fa, h->num_sms, st));
+    return ASDSM_OK;
+}
+
+// Steps 4-6 with the new direction in slot kc, then the step lengths.
+template <typename T>
+int enqueue_sweep_body(asdsm_handle* h, int kc, int m, cudaStream_t st) {
+    const int pi = sizeof(T) == 8 ? 0 : 1;
+    auto& w = h->w[pi];
+    const Geometry& g = h->g;
+    BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
+    CK(bcr_solve<T>(sys, 2, st));
+    const T* av[2] = {(const T*)w.Yfc, (const T*)w.Ycf};
+    int nb2 = 0;
+    CK(multi_dot<T>(av, av, 2, (long long)g.Nf * g.Nc, h->partials, &nb2, st));
+    CK(reduce_partials(h->partials, nb2, 2, h->dsmall + 200, st));
+    T* z = (T*)w.z[kc];
+    MergeArgs<T> ma{};
+    ma.Yfc = (T*)w.Yfc; ma.Ycf = (T*)w.Ycf; ma.Ycc = nullptr;
+    ma.norms2 = h->dsmall + 200; ma.re_mode = 0; ma.choice = 0; ma.choice_dev = &h->dctl->choice;
+    ma.Sm = (const T*)h->Sm[pi];
+    ma.E1 = (T*)w.E1; ma.E2 = (T*)w.E2; ma.M1 = (T*)w.M1; ma.M2 = (T*)w.M2;
+    ma.z = z; ma.g = g;
+    CK(merge_knots<T>(ma, st));
+    CK(merge_write<T>(ma, st));
+    FillArgs<T> fa{};
+    fa.mode = FILL_HOMOGENEOUS;
+    fa.z = z; fa.out = z;
+    hole_factors<T>(h->hole[pi], &fa);
+    fa.n = g.n; fa.g = g; fa.sten = h->sten;
+    CK(fill_holes<T>(fa, h->num_sms, st));
+    CK(skeleton_apply<T>(z, g, h->sten, (T*)w.q, st));
+    const T* qpv[kMaxM];
+    for (int j = 0; j < kc; ++j) qpv[j] = (const T*)w.qp[j];
+    int nb3 = 0;
+    CK(gcr_dots<T>((const T*)w.q, (const T*)w.rskel, qpv, kc, g.skel, h->partials, &nb3, st));
+    CK(reduce_partials(h->partials, nb3, 2 + 2 * kc, h->dsmall, st));
+    CK(ctl_after_dots(h->dctl, h->dsmall, st));
+    if (m > 1) CK(combine_skeleton_dyn<T>((const T*)w.q, qpv, kc, &h->dctl->comb, g.skel, (T*)w.qp[kc], st));
+    return ASDSM_OK;
+}
+
+// Capture and instantiate the graph for this precision, m, fixed-point shift
+// and buffers (rebuilt when any of them changes).
+template <typename T>
+int ensure_graph(asdsm_handle* h, const double* s, double* u, int m, int S, double scale, const MixedCoefs& mk) {
+    const int prec = sizeof(T) == 8 ? ASDSM_FP64 : ASDSM_MIXED;
+    auto& G = h->gr;
+    const bool fp64 = prec == ASDSM_FP64;
+    if (G.exec && G.prec == prec && G.m == m && G.S == S && G.partials == h->partials &&
+        (!fp64 || (G.s == s && G.u == u)))
+        return ASDSM_OK;
+    destroy_graph(h);
+    if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    if (!h->body_st) CK(cudaStreamCreateWithFlags(&h->body_st, cudaStreamNonBlocking));
+    const long long lc0 = launch_count();
+    int rc = ASDSM_OK;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    for (int i = 0; i < kSweepsPerGraph && rc == ASDSM_OK; ++i) {
+        const long long t0 = launch_count();
+        if ((rc = enqueue_residual_dyn<T>(h, s, u, scale, mk, m, h->cap_st))) break;
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cgraph = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraphConditionalHandle hc;
+        if ((e = cudaStreamGetCaptureInfo(h->cap_st, &cst, nullptr, &cgraph, &deps, nullptr, &ndeps)) != cudaSuccess ||
+            (e = cudaGraphConditionalHandleCreate(&hc, cgraph, (unsigned)(m + 2), cudaGraphCondAssignDefault)) != cudaSuccess ||
+            (e = ctl_after_residual(h->dctl, h->dsmall, h->dflag, h->dhist, hc, h->cap_st)) != cudaSuccess ||
+            (e = cudaStreamGetCaptureInfo(h->cap_st, &cst, nullptr, &cgraph, &deps, nullptr, &ndeps)) != cudaSuccess) {
+            rc = set_cuda_error(e);
+            break;
+        }
+        if (i == 0) G.top_launches = launch_count() - t0;
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = hc;
+        np.conditional.type = cudaGraphCondTypeSwitch;
+        np.conditional.size = (unsigned)(m + 2);
+        cudaGraphNode_t node;
+        if ((e = cudaGraphAddNode(&node, cgraph, deps, nullptr, ndeps, &np)) != cudaSuccess ||
+            (e = cudaStreamUpdateCaptureDependencies(h->cap_st, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess) {
+            rc = set_cuda_error(e);
+            break;
+        }
+        for (int b = 0; b < m + 2 && rc == ASDSM_OK; ++b) {
+            if ((e = cudaStreamBeginCaptureToGraph(h->body_st, np.conditional.phGraph_out[b], nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+                rc = set_cuda_error(e);
+                break;
+            }
+            const long long b0 = launch_count();
+            rc = b < m ? enqueue_sweep_body<T>(h, b, m, h->body_st)
+                       : enqueue_holefix<T>(h, s, u, b - m, scale, mk, h->body_st);
+            if (i == 0) G.body_launches[b] = launch_count() - b0;
+            cudaGraph_t bg = nullptr;
+            e = cudaStreamEndCapture(h->body_st, &bg);
+            if (rc == ASDSM_OK && e != cudaSuccess) rc = set_cuda_error(e);
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->cap_st, &graph);
+    note_launch(-(launch_count() - lc0));           // captured, not launched
+    if (rc != ASDSM_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return set_cuda_error(e); }
+    G.graph = graph;
+    if ((e = cudaGraphInstantiate(&G.exec, graph, 0)) != cudaSuccess) { destroy_graph(h); return set_cuda_error(e); }
+    G.prec = prec; G.m = m; G.S = S; G.s = s; G.u = u; G.partials = h->partials;
+    return ASDSM_OK;
+}
+
+struct LoopResult {
+    int status = ASDSM_NOT_CONVERGED, k = 0, hole_fixes = 0, par = 0;
+    double rel0 = 0.0, rel = 0.0;
+    std::vector<double> hist;
+};
+
+// The sweeps of Algorithm 4 as graph launches; the host only reads the done
+// flag of the previous launch while the next one runs.  At most
+// max_sweeps / kSweepsPerGraph + 2 launches: every sweep of a launch either
+// advances k or ends the solve, and k = max_sweeps ends it.
+template <typename T>
+int graph_sweeps(asdsm_handle* h, const double* s, double* u, double bnorm, int S, double scale,
+                 const MixedCoefs& mk, LoopResult* out) {
+    const asdsm_opts& op = h->opts;
+    const int m = std::max(1, std::min(op.accel_m, kMaxM));
+    cudaStream_t st = h->st;
+    if (h->hist_cap < op.max_sweeps + 2) {
+        if (h->dhist) cudaFree(h->dhist);
+        h->dhist = nullptr;
+        h->hist_cap = 0;
+        CK(cudaMalloc(&h->dhist, (size_t)(op.max_sweeps + 2) * sizeof(double)));
+        h->hist_cap = op.max_sweeps + 2;
+        destroy_graph(h);                                   // the graph holds the old pointer
+    }
+    if (int rc = ensure_graph<T>(h, s, u, m, S, scale, mk)) return rc;
+    SweepCtl& c = *h->hctl;
+    std::memset(&c, 0, sizeof(c));
+    c.bnorm = bnorm; c.tol = op.tol; c.hole_fix_ratio = op.hole_fix_ratio; c.hole_fix_growth = op.hole_fix_growth;
+    c.stagnation_factor = op.stagnation_factor; c.scale = scale; c.seed = op.seed;
+    c.max_sweeps = op.max_sweeps; c.window = op.stagnation_window; c.m = m; c.mixed = sizeof(T) == 4;
+    c.hist_cap = h->hist_cap;
+    c.upd.live = 1;
+    CK(cudaMemcpyAsync(h->dctl, &c, sizeof(c), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), st));
+    const int max_launches = op.max_sweeps / kSweepsPerGraph + 2;
+    int launched = 0;
+    bool done = false;
+    for (int q = 0; q < max_launches && !done; ++q) {
+        CK(cudaGraphLaunch(h->gr.exec, st));
+        CK(cudaMemcpyAsync(&h->hdone[q & 1], &h->dctl->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(h->evc[q & 1], st));
+        ++launched;
+        if (q >= 1) {
+            CK(cudaEventSynchronize(h->evc[(q - 1) & 1]));
+            done = h->hdone[(q - 1) & 1] != 0;
+        }
+    }
+    CK(cudaMemcpyAsync(h->hctl, h->dctl, sizeof(SweepCtl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out->hist.resize((size_t)std::min(c.nhist, c.hist_cap));
+    if (!out->hist.empty())
+        CK(cudaMemcpy(out->hist.data(), h->dhist, out->hist.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    if (!c.done) { g_last_error = "device sweep control did not finish"; return ASDSM_ERR_CUDA; }
+    out->status = c.status; out->k = c.k; out->hole_fixes = c.hole_fixes; out->par = c.upd.par;
+    out->rel0 = c.rel0; out->rel = c.rel;
+    // Kernels that ran: every replayed sweep's fixed part plus the bodies the switch nodes chose.
+    long long ran = (long long)launched * kSweepsPerGraph * h->gr.top_launches;
+    for (int b = 0; b < m + 2 && b < 20; ++b) ran += (long long)c.runs[b] * h->gr.body_launches[b];
+    note_launch(ran);
+    return ASDSM_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Algorithm 4.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -408,6 +658,19 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
     CK(cudaEventRecord(h->ev1, st));
     const MixedCoefs mk = mixed ? mixed_coefs(h, S) : MixedCoefs{};
 
+    int status = ASDSM_NOT_CONVERGED;
+    int k = 0;
+    int hole_fixes = 0;
+    double rel0 = 0.0, rel = 0.0;
+    std::vector<double> rhist;
+    if (op.sweep_graph && !h->prof) {
+        LoopResult lr;
+        if (int rc = graph_sweeps<T>(h, s, u, bnorm, S, scale, mk, &lr)) return rc;
+        status = lr.status; k = lr.k; hole_fixes = lr.hole_fixes; rel0 = lr.rel0; rel = lr.rel;
+        rhist = lr.hist;
+        if (!mixed) { if (lr.par) ucur = h->u_work; }
+        else Ucur = lr.par;
+    } else {
     // GCR bookkeeping (host, FP64).
     double Tm[kMaxM][kMaxM] = {};
     int kc = 0;                  // directions in the current cycle
@@ -415,11 +678,6 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
     double hole_ref = 0.0;       // hole residual right after the last correction (0 before the first)
     bool hole_ref_pending = false;
     const bool trace = std::getenv("ASDSM_TRACE") != nullptr;
-    int status = ASDSM_NOT_CONVERGED;
-    int k = 0;
-    int hole_fixes = 0;
-    double rel0 = 0.0, rel = 0.0;
-    std::vector<double> rhist;
     for (;;) {
         // ---- step 3: residual (with the pending step-7 update fused) ----
         ResidOut o{};
@@ -593,6 +851,7 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         }
         ++k;
     }
+    }
     // Final iterate to the caller's buffer.
     if (!mixed) {
         if (ucur != u) CK(copy_interior<double, double>(ucur, u, g, st));
@@ -639,6 +898,7 @@ void asdsm_default_opts(asdsm_opts* o) {
     o->hole_fix_growth = 4.0;
     o->stagnation_window = 10;
     o->stagnation_factor = 1e-3;
+    o->sweep_graph = 1;
 }
 
 const char* asdsm_strerror(int code) {
@@ -739,6 +999,11 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaEventCreate(&h->ev2)) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMalloc(&h->dctl, sizeof(SweepCtl))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMallocHost(&h->hctl, sizeof(SweepCtl))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMallocHost(&h->hdone, 2 * sizeof(int))) != cudaSuccess) return fail(set_cuda_error(e));
+    for (int q = 0; q < 2; ++q)
+        if ((e = cudaEventCreateWithFlags(&h->evc[q], cudaEventDisableTiming)) != cudaSuccess) return fail(set_cuda_error(e));
     if ((rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), 4096)))) return fail(rc);
     asdsm_profile(h, 0);
     *out = h;
@@ -923,6 +1188,13 @@ void asdsm_destroy(asdsm_handle* h) {
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->ev2) cudaEventDestroy(h->ev2);
+    destroy_graph(h);
+    fr(h->dctl); fr(h->dhist);
+    if (h->hctl) cudaFreeHost(h->hctl);
+    if (h->hdone) cudaFreeHost(h->hdone);
+    for (int q = 0; q < 2; ++q) if (h->evc[q]) cudaEventDestroy(h->evc[q]);
+    if (h->cap_st) cudaStreamDestroy(h->cap_st);
+    if (h->body_st) cudaStreamDestroy(h->body_st);
     delete h;
 }
 

@@ -126,10 +126,24 @@ struct ResidOut {
     void* rfull;        // float or double full grid (optional)
     double* partials;   // [nblocks][2]: sum r^2, sum r^2 over holes
 };
+// Step 7 of Algorithm 4 as state on the device (sweeps driven from the GPU):
+// the residual kernel of the next sweep reads the pending step lengths and
+// which of the two iterate buffers is current.
+struct DynUpdate {
+    int live;           // 0 once the solve has ended: the residual kernel returns at once
+    int count;          // pending directions: u += sum_j coef_j z_j, j < count
+    int par;            // current iterate: buffer 0 (par = 0) or buffer 1
+    int pad;
+    double coef[16];    // step lengths (FP64 path)
+    float cf[16];       // step lengths times 2^S, rounded to FP32 (mixed path)
+};
 struct UpdateTerms {
     const void* z[16];  // directions (T full grid)
     double coef[16];    // u += sum coef_j z_j
     int count;
+    // Non-null: count, coefficients and the current buffer come from the
+    // device; the kernel's input/output pointers are then buffers 0 and 1.
+    const DynUpdate* dyn;
 };
 // FP64 path: u_out = u_in + sum coef z (interior), r = s - A u_out.
 cudaError_t residual_fp64(const double* s, const double* u_in, double* u_out, const UpdateTerms& up,
@@ -169,6 +183,7 @@ struct MergeArgs {
     const double* norms2;     // [2]: ||Yfc||^2, ||Ycf||^2 (normalisation of Algorithm 1 step 2)
     int re_mode;              // 1: Richardson (u_cc given), 0: random choice
     int choice;               // 0 or 1 (Algorithm 2 step 3)
+    const int* choice_dev;    // non-null: the choice is read from the device instead
     const T* Sm;              // spline moment operator, transposed: [Nc knots][mc+1 moments]
     T* E1; T* E2;             // [Nc][Nc] knot errors (fc lines: E1[l][k]; cf columns: E2[l][k])
     T* M1; T* M2;             // moments: M1[l][mc+1], M2[k][mc+1]
@@ -185,6 +200,44 @@ cudaError_t skeleton_apply(const T* z, const Geometry& g, const Stencil& s, T* q
 template <typename T>
 cudaError_t combine_skeleton(const T* q, const T* const* Qp, const double* beta, int k, double inv_nu,
                              long long n, T* out, cudaStream_t st);
+
+// Device-held GCR combination: qp = (q - sum beta_j Qp_j) * inv_nu when run != 0.
+struct CtlCombine {
+    int run;
+    int pad;
+    double beta[16];
+    double inv_nu;
+};
+template <typename T>
+cudaError_t combine_skeleton_dyn(const T* q, const T* const* Qp, int k, const CtlCombine* c,
+                                 long long n, T* out, cudaStream_t st);
+
+// Sweep control on the device (control.cu) ---------------------------------------
+// The decisions of Algorithm 4 that the host loop takes between sweeps
+// (convergence, stagnation, the hole-residual correction, the GCR(m)
+// bookkeeping), kept in device memory so that whole sweeps run as a CUDA graph.
+struct SweepCtl {
+    // Set by the host before the first sweep.
+    double bnorm, tol, hole_fix_ratio, hole_fix_growth, stagnation_factor, scale;
+    unsigned long long seed;
+    int max_sweeps, window, m, mixed;
+    int hist_cap;
+    // State.
+    int k, status, done, kc, hole_fixes, hole_ref_pending, nhist, branch;
+    int runs[20];                 // executions of each branch (sweep bodies 0..m-1, hole fixes m, m+1)
+    double hole_ref, rel0, rel;
+    double Tm[16][16];
+    DynUpdate upd;
+    int choice;
+    int pad2;
+    CtlCombine comb;
+};
+// After the residual norms: decide the branch of this sweep and select it in
+// the graph's switch node (value m + 2 = nothing: the solve has ended).
+cudaError_t ctl_after_residual(SweepCtl* c, const double* sums, int* overflow, double* hist,
+                               cudaGraphConditionalHandle sw, cudaStream_t st);
+// After the least-squares inner products: the step lengths of step 6 / GCR(m).
+cudaError_t ctl_after_dots(SweepCtl* c, const double* dots, cudaStream_t st);
 
 // Grid utilities -------------------------------------------------------------
 template <typename T>

@@ -1,0 +1,154 @@
+// Sweep control of Algorithm 4 on the device.
+//
+// These single-thread kernels take, between the kernels of a sweep, the
+// decisions the host loop of api.cu takes between sweeps, in the same order and
+// FP64 arithmetic: the stopping tests of Algorithm 4 (tolerance, sweep limit,
+// stagnation), the hole-residual correction (Proposition 3.1: after an exact
+// Filler the residual vanishes in the holes, so a large hole residual is
+// rounding to be removed by one more Filler), and the step lengths of step 6
+// (the clamped s_hat, or the GCR(m) least squares over the cycle's
+// directions).  With them a run of sweeps is a fixed sequence of launches that
+// a CUDA graph replays; the branch taken by a sweep (new direction in slot kc,
+// hole correction, or nothing once the solve has ended) is selected through
+// the graph's switch node.
+#include "asdsm.h"
+#include "asdsm_internal.h"
+#include <cuda_runtime.h>
+
+namespace asdsm {
+
+namespace {
+
+__device__ unsigned long long splitmix64_dev(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Coin of Algorithm 2 step 3 at sweep k: top bit of SplitMix64 output k.
+__device__ int choice_bit_dev(unsigned long long seed, int k) {
+    const unsigned long long state = seed + (unsigned long long)(k + 1) * 0x9E3779B97F4A7C15ULL;
+    return (int)(splitmix64_dev(state) >> 63);
+}
+
+__device__ void finish(SweepCtl* c, int status, cudaGraphConditionalHandle sw) {
+    c->status = status;
+    c->done = 1;
+    c->upd.live = 0;
+    c->branch = c->m + 2;
+    cudaGraphSetConditional(sw, (unsigned)(c->m + 2));
+}
+
+__global__ void ctl_after_residual_kernel(SweepCtl* c, const double* __restrict__ sums, int* overflow,
+                                          double* hist, cudaGraphConditionalHandle sw) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (c->done) {
+        cudaGraphSetConditional(sw, (unsigned)(c->m + 2));
+        return;
+    }
+    // The residual kernel has applied the pending update into the other buffer.
+    if (c->upd.count > 0) c->upd.par ^= 1;
+    c->upd.count = 0;
+    c->comb.run = 0;
+    if (c->mixed) {
+        const int ovf = *overflow;
+        *overflow = 0;
+        if (ovf) { finish(c, ASDSM_ERR_RANGE, sw); return; }
+    }
+    const double rnorm = sqrt(sums[0]), hnorm = sqrt(sums[1]);
+    const double rel = c->bnorm > 0 ? rnorm / c->bnorm : rnorm;
+    c->rel = rel;
+    if (!isfinite(rel)) { finish(c, ASDSM_ERR_NAN, sw); return; }
+    if (c->nhist < c->hist_cap) hist[c->nhist] = rel;
+    c->nhist += 1;
+    if (c->k == 0) c->rel0 = rel;
+    if (rel <= c->tol) { finish(c, ASDSM_OK, sw); return; }
+    if (c->k >= c->max_sweeps) { finish(c, ASDSM_NOT_CONVERGED, sw); return; }
+    const int win = c->window;
+    if (win > 0 && c->nhist > win && c->nhist <= c->hist_cap &&
+        rel > (1.0 - c->stagnation_factor) * hist[c->nhist - 1 - win]) {
+        finish(c, ASDSM_STAGNATED, sw);
+        return;
+    }
+    if (c->hole_ref_pending) { c->hole_ref = hnorm; c->hole_ref_pending = 0; }
+    int branch;
+    if (hnorm > c->hole_fix_ratio * rnorm && hnorm > c->hole_fix_growth * c->hole_ref) {
+        branch = c->m + c->upd.par;      // hole correction on the current iterate buffer
+        c->hole_fixes += 1;
+        c->kc = 0;
+        c->hole_ref_pending = 1;
+        c->k += 1;
+    } else {
+        branch = c->kc;                  // error guess into direction slot kc
+        c->choice = choice_bit_dev(c->seed, c->k);
+    }
+    c->branch = branch;
+    if (branch < 20) c->runs[branch] += 1;
+    cudaGraphSetConditional(sw, (unsigned)branch);
+}
+
+__global__ void ctl_after_dots_kernel(SweepCtl* c, const double* __restrict__ dots) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || c->done) return;
+    const int m = c->m, kc = c->kc;
+    const double qq = dots[0], qr = dots[1];
+    c->comb.run = 0;
+    if (m == 1) {
+        // Step 6: s_hat = argmin_{s >= 0} ||r - s A e||.
+        const double shat = qq > 0 ? fmax(0.0, qr / qq) : 0.0;
+        c->upd.count = 1;
+        c->upd.coef[0] = shat;
+        c->upd.cf[0] = (float)(shat * c->scale);
+        c->k += 1;
+        return;
+    }
+    // GCR(m): orthogonalise A e against the cycle's previous directions.
+    double beta[16], rq[16];
+    double nu2 = qq;
+    for (int j = 0; j < kc; ++j) {
+        beta[j] = dots[2 + 2 * j];
+        rq[j] = dots[3 + 2 * j];
+        nu2 -= beta[j] * beta[j];
+    }
+    if (!(nu2 > 1e-24 * qq) || !(qq > 0)) {
+        c->kc = 0;                       // dependent direction: restart the cycle
+        c->k += 1;
+        return;
+    }
+    const double nu = sqrt(nu2);
+    double alpha = qr;
+    for (int j = 0; j < kc; ++j) alpha -= beta[j] * rq[j];
+    alpha /= nu;
+    // Column kc of T: z'_kc = sum_i T[i][kc] z_i.
+    for (int i = 0; i <= kc; ++i) c->Tm[i][kc] = 0.0;
+    c->Tm[kc][kc] = 1.0 / nu;
+    for (int j = 0; j < kc; ++j)
+        for (int i = 0; i <= j; ++i) c->Tm[i][kc] -= beta[j] * c->Tm[i][j] / nu;
+    c->upd.count = kc + 1;
+    for (int i = 0; i <= kc; ++i) {
+        const double v = alpha * c->Tm[i][kc];
+        c->upd.coef[i] = v;
+        c->upd.cf[i] = (float)(v * c->scale);
+    }
+    c->comb.run = 1;
+    for (int j = 0; j < kc; ++j) c->comb.beta[j] = beta[j];
+    c->comb.inv_nu = 1.0 / nu;
+    c->kc = kc + 1 >= m ? 0 : kc + 1;
+    c->k += 1;
+}
+
+}  // namespace
+
+cudaError_t ctl_after_residual(SweepCtl* c, const double* sums, int* overflow, double* hist,
+                               cudaGraphConditionalHandle sw, cudaStream_t st) {
+    ctl_after_residual_kernel<<<1, 32, 0, st>>>(c, sums, overflow, hist, sw);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t ctl_after_dots(SweepCtl* c, const double* dots, cudaStream_t st) {
+    ctl_after_dots_kernel<<<1, 32, 0, st>>>(c, dots);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace asdsm

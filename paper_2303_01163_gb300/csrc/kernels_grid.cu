@@ -81,11 +81,19 @@ __device__ __forceinline__ void store_skeleton(const ResidOut& o, const Geometry
 // FP64 residual (plain path): u_out = u_in + sum c_j z_j ; r = s - A u_out.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(RTHREADS)
-residual_fp64_kernel(const double* __restrict__ s, const double* __restrict__ u_in, double* __restrict__ u_out,
+residual_fp64_kernel(const double* __restrict__ s, const double* u_in, double* u_out,
                      UpdateTerms up, Geometry g, Stencil c, ResidOut o) {
     __shared__ double tile[RY + 2][RX + 2];
     const int N = g.N;
     const int i0 = blockIdx.x * RX + 1, j0 = blockIdx.y * RY + 1;   // first interior point of the tile
+    int count = up.count;
+    const double* ucur = u_in;
+    double* unxt = u_out;
+    if (up.dyn) {
+        if (!up.dyn->live) return;
+        count = up.dyn->count;
+        if (up.dyn->par) { ucur = u_out; unxt = const_cast<double*>(u_in); }
+    }
     // Load u (+ update) on the tile and its halo.  Ring points keep g (no update).
     for (int e = threadIdx.x; e < (RX + 2) * (RY + 2); e += RTHREADS) {
         const int ty = e / (RX + 2), tx = e % (RX + 2);
@@ -93,9 +101,10 @@ residual_fp64_kernel(const double* __restrict__ s, const double* __restrict__ u_
         double v = 0.0;
         if (i <= N - 1 && j <= N - 1) {
             const long long idx = (long long)j * N + i;
-            v = u_in[idx];
+            v = ucur[idx];
             if (i >= 1 && j >= 1 && i <= N - 2 && j <= N - 2) {
-                for (int q = 0; q < up.count; ++q) v += up.coef[q] * reinterpret_cast<const double*>(up.z[q])[idx];
+                for (int q = 0; q < count; ++q)
+                    v += (up.dyn ? up.dyn->coef[q] : up.coef[q]) * reinterpret_cast<const double*>(up.z[q])[idx];
             }
         }
         tile[ty][tx] = v;
@@ -108,7 +117,7 @@ residual_fp64_kernel(const double* __restrict__ s, const double* __restrict__ u_
         if (i > N - 2 || j > N - 2) continue;
         const long long idx = (long long)j * N + i;
         const double uc = tile[ty + 1][tx + 1];
-        if (u_out != u_in || up.count > 0) u_out[idx] = uc;
+        if (up.dyn ? count > 0 : (u_out != u_in || count > 0)) unxt[idx] = uc;
         const double Au = c.cc * uc + c.cw * tile[ty + 1][tx] + c.ce * tile[ty + 1][tx + 2]
                         + c.cs * tile[ty][tx + 1] + c.cn * tile[ty + 2][tx + 1];
         const double r = s[idx] - Au;
@@ -171,6 +180,7 @@ struct UpdateF {
     const float* z[16];
     float c[16];
     int count;
+    const DynUpdate* dyn;   // non-null: count and c come from the device, U_in/U_out are buffers 0/1
 };
 
 __device__ __forceinline__ long long load_updated(const long long* __restrict__ U_in, const UpdateF& up,
@@ -201,9 +211,18 @@ __device__ __forceinline__ void acc_prod(float khi, float klo, float f, float& h
 
 __global__ void __launch_bounds__(32 * MS_WARPS)
 residual_mixed_kernel(const float* __restrict__ s_hi, const float* __restrict__ s_lo,
-                      const long long* __restrict__ U_in, long long* __restrict__ U_out,
+                      const long long* U_in0, long long* U_out0,
                       UpdateF up, Geometry g, MixedCoefs k, ResidOut o, int* overflow) {
     const int N = g.N;
+    const long long* __restrict__ U_in = U_in0;
+    long long* __restrict__ U_out = U_out0;
+    if (up.dyn) {
+        if (!up.dyn->live) return;
+        up.count = up.dyn->count;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) up.c[q] = up.dyn->cf[q];
+        if (up.dyn->par) { U_in = U_out0; U_out = const_cast<long long*>(U_in0); }
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x = 1 + (blockIdx.x * MS_WARPS + warp) * MS_OUT + lane - 1;   // lane 0: west halo
     const bool out_col = lane >= 1 && lane <= MS_OUT && x <= N - 2;
@@ -305,9 +324,9 @@ __global__ void submesh_rhs_kernel(const double* __restrict__ s, const double* _
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 2.  merge_knots: one CTA per (family, coarse line): the cross-point
-// values of both anisotropic solutions on that line, the chosen/extrapolated
-// u_hat, the errors e and the spline moments of the correction.
+// Algorithm 2.  merge_knots: the cross-point values of both anisotropic
+// solutions, the chosen/extrapolated u_hat, the errors e and the spline
+// moments of the correction along every coarse line.
 // merge_write: every skeleton point gets its anisotropic value plus the spline
 // correction (step 5) and the merged skeleton is stored (step 6).
 // ---------------------------------------------------------------------------
@@ -337,54 +356,99 @@ __device__ __forceinline__ void inv_norms(const MergeArgs<T>& a, T* inv1, T* inv
     }
 }
 
-// One CTA per (family, block of 16 coarse lines).  Sm is the spline moment
-// operator transposed, [knot q][moment r], so threads over r read it coalesced
-// and every value serves the 16 lines of the block.
-constexpr int MK_LINES = 4;
+// Knot errors and spline moments as one small GEMM per family:
+//   M[line][r] = sum_q Sm[r][q] e[line][q]
+// with e (Algorithm 2 steps 2-4) formed on the fly from the cross points.  A CTA
+// owns MK_L lines x MK_R moments and walks the knots in chunks of MK_Q staged
+// in shared memory (Sm is stored transposed, [knot q][moment r], so the staging
+// reads are coalesced); the next chunk is loaded into registers while the
+// current one is multiplied.  The CTAs of the first moment block also store e.
+constexpr int MK_L = 16, MK_R = 32, MK_Q = 32, MK_THREADS = 128;
 
 template <typename T>
-__global__ void merge_knots_kernel(MergeArgs<T> a) {
+__device__ __forceinline__ T knot_error(const MergeArgs<T>& a, int fam, int line, int q, T inv1, T inv2, int choice) {
+    const int l = fam == 0 ? line : q;       // fc line l: knots along x (k = q)
+    const int k = fam == 0 ? q : line;       // cf column k: knots along y (l = q)
+    const T t1 = cross_t1(a, inv1, l, k), t2 = cross_t2(a, inv2, l, k);
+    T uh;
+    if (a.re_mode) uh = t1 + t2 - a.Ycc[(long long)l * a.g.Nc + k];   // step 2: combination RE
+    else uh = choice ? t2 : t1;                                        // step 3
+    return fam == 0 ? uh - t1 : uh - t2;                               // step 4
+}
+
+template <typename T>
+__global__ void __launch_bounds__(MK_THREADS) merge_knots_kernel(MergeArgs<T> a) {
     const int Nc = a.g.Nc, K = a.g.mc + 1;
-    const int nblk = (Nc + MK_LINES - 1) / MK_LINES;
-    const int fam = blockIdx.x / nblk;         // 0: fc lines, 1: cf columns
-    const int l0 = (blockIdx.x % nblk) * MK_LINES;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* e = reinterpret_cast<T*>(smem_raw);     // [MK_LINES][Nc] knot errors of the block's lines
+    const int nlb = (Nc + MK_L - 1) / MK_L;
+    const int fam = blockIdx.x / nlb;            // 0: fc lines, 1: cf columns
+    const int l0 = (blockIdx.x % nlb) * MK_L;
+    const int r0 = blockIdx.y * MK_R;
+    const bool store_e = blockIdx.y == 0;
+    __shared__ T Es[MK_Q][MK_L + 1];
+    __shared__ __align__(16) T Ss[MK_Q][MK_R];
     T inv1, inv2;
     inv_norms(a, &inv1, &inv2);
-    for (int idx = threadIdx.x; idx < MK_LINES * Nc; idx += blockDim.x) {
-        const int li = idx / Nc, q = idx % Nc;
-        const int line = l0 + li;
-        if (line >= Nc) { e[idx] = T(0); continue; }
-        // fc line l = line: knots along x (k = q); cf column k = line: knots along y (l = q)
-        const int l = fam == 0 ? line : q;
-        const int k = fam == 0 ? q : line;
-        const T t1 = cross_t1(a, inv1, l, k), t2 = cross_t2(a, inv2, l, k);
-        T uh;
-        if (a.re_mode) uh = t1 + t2 - a.Ycc[(long long)l * Nc + k];   // step 2: combination RE
-        else uh = a.choice ? t2 : t1;                                  // step 3
-        const T err = fam == 0 ? uh - t1 : uh - t2;                    // step 4
-        e[idx] = err;
-        if (fam == 0) a.E1[(long long)l * Nc + k] = err;
-        else a.E2[(long long)l * Nc + k] = err;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < K; r += blockDim.x) {
-        T acc[MK_LINES];
+    const int choice = a.choice_dev ? *a.choice_dev : a.choice;
+    const int tid = threadIdx.x;
+    const int tl = tid / (MK_R / 2), tr = tid % (MK_R / 2);   // 2 lines x 2 moments per thread
+    constexpr int EPT = MK_L * MK_Q / MK_THREADS;             // 4
+    constexpr int SPT = MK_Q * MK_R / MK_THREADS;             // 8
+    T ev[EPT], sv[SPT];
+    auto load_chunk = [&](int q0) {
 #pragma unroll
-        for (int li = 0; li < MK_LINES; ++li) acc[li] = T(0);
-        const T* __restrict__ Smr = a.Sm + r;
-#pragma unroll 8
-        for (int q = 0; q < Nc; ++q) {
-            const T sm = __ldg(Smr + (long long)q * K);
-#pragma unroll
-            for (int li = 0; li < MK_LINES; ++li) acc[li] += sm * e[li * Nc + q];
+        for (int j = 0; j < EPT; ++j) {
+            const int e = tid + j * MK_THREADS;
+            const int li = e / MK_Q, qq = e % MK_Q;
+            const int line = l0 + li, q = q0 + qq;
+            ev[j] = (line < Nc && q < Nc) ? knot_error(a, fam, line, q, inv1, inv2, choice) : T(0);
         }
-        for (int li = 0; li < MK_LINES; ++li) {
-            const int line = l0 + li;
-            if (line >= Nc) break;
-            T* Mout = fam == 0 ? a.M1 + (long long)line * K : a.M2 + (long long)line * K;
-            Mout[r] = acc[li];
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) {
+            const int e = tid + j * MK_THREADS;
+            const int qq = e / MK_R, rr = e % MK_R;
+            const int q = q0 + qq, r = r0 + rr;
+            sv[j] = (q < Nc && r < K) ? __ldg(a.Sm + (long long)q * K + r) : T(0);
+        }
+    };
+    T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+    load_chunk(0);
+    for (int q0 = 0; q0 < Nc; q0 += MK_Q) {
+        __syncthreads();                         // previous chunk consumed
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            const int e = tid + j * MK_THREADS;
+            const int li = e / MK_Q, qq = e % MK_Q;
+            Es[qq][li] = ev[j];
+            const int line = l0 + li, q = q0 + qq;
+            if (store_e && line < Nc && q < Nc) {
+                if (fam == 0) a.E1[(long long)line * Nc + q] = ev[j];      // E1[l][k]
+                else a.E2[(long long)q * Nc + line] = ev[j];               // E2[l][k]
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) {
+            const int e = tid + j * MK_THREADS;
+            Ss[e / MK_R][e % MK_R] = sv[j];
+        }
+        __syncthreads();
+        if (q0 + MK_Q < Nc) load_chunk(q0 + MK_Q);
+#pragma unroll 8
+        for (int qq = 0; qq < MK_Q; ++qq) {
+            const T e0 = Es[qq][2 * tl], e1 = Es[qq][2 * tl + 1];
+            const T s0 = Ss[qq][2 * tr], s1 = Ss[qq][2 * tr + 1];
+            acc[0][0] += s0 * e0; acc[0][1] += s1 * e0;
+            acc[1][0] += s0 * e1; acc[1][1] += s1 * e1;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int line = l0 + 2 * tl + i;
+        if (line >= Nc) continue;
+        T* Mout = (fam == 0 ? a.M1 : a.M2) + (long long)line * K;
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int r = r0 + 2 * tr + jj;
+            if (r < K) Mout[r] = acc[i][jj];
         }
     }
 }
@@ -477,6 +541,23 @@ __global__ void combine_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
 #pragma unroll
     for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)c.beta[j] : T(0);
     const T inu = (T)inv_nu;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        T v = q[e];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < k) v -= beta[j] * __ldg(c.Qp[j] + e);
+        out[e] = v * inu;
+    }
+}
+
+template <typename T>
+__global__ void combine_dyn_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
+                                   const CtlCombine* __restrict__ ctl, long long n, T* __restrict__ out) {
+    if (!ctl->run) return;
+    T beta[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)ctl->beta[j] : T(0);
+    const T inu = (T)ctl->inv_nu;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         T v = q[e];
 #pragma unroll
@@ -674,10 +755,11 @@ cudaError_t residual_mixed(const float* s_hi, const float* s_lo, const long long
                            const UpdateTerms& up, double scale, const Geometry& g, const MixedCoefs& k,
                            ResidOut out, int* nblocks, int* overflow_flag, cudaStream_t st) {
     UpdateF uf{};
+    uf.dyn = up.dyn;
     uf.count = up.count;
-    for (int q = 0; q < up.count && q < 16; ++q) {
-        uf.z[q] = reinterpret_cast<const float*>(up.z[q]);
-        uf.c[q] = (float)(up.coef[q] * scale);
+    for (int q = 0; q < 16; ++q) {
+        uf.z[q] = reinterpret_cast<const float*>(up.z[q]);     // every slot given (device-held counts may use them)
+        if (q < up.count) uf.c[q] = (float)(up.coef[q] * scale);
     }
     dim3 grid((g.Nf + MS_OUT * MS_WARPS - 1) / (MS_OUT * MS_WARPS), (g.Nf + MS_ROWS - 1) / MS_ROWS);
     *nblocks = grid.x * grid.y;
@@ -753,13 +835,9 @@ cudaError_t gcr_dots(const T* q, const T* r, const T* const* p, int k, long long
 
 template <typename T>
 cudaError_t merge_knots(const MergeArgs<T>& a, cudaStream_t st) {
-    const size_t smem = sizeof(T) * (size_t)MK_LINES * a.g.Nc;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(merge_knots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int nblk = (a.g.Nc + MK_LINES - 1) / MK_LINES;
-    merge_knots_kernel<T><<<2 * nblk, 256, smem, st>>>(a);
+    const int nlb = (a.g.Nc + MK_L - 1) / MK_L;
+    const int nrb = (a.g.mc + 1 + MK_R - 1) / MK_R;
+    merge_knots_kernel<T><<<dim3(2 * nlb, nrb), MK_THREADS, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
@@ -785,6 +863,17 @@ cudaError_t combine_skeleton(const T* q, const T* const* Qp, const double* beta,
     CombineArgs<T> c{};
     for (int j = 0; j < k; ++j) { c.Qp[j] = Qp[j]; c.beta[j] = beta[j]; }
     combine_kernel<T><<<grid_for(n), 256, 0, st>>>(q, c, k, inv_nu, n, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t combine_skeleton_dyn(const T* q, const T* const* Qp, int k, const CtlCombine* ctl,
+                                 long long n, T* out, cudaStream_t st) {
+    if (k > 16) return cudaErrorInvalidValue;
+    CombineArgs<T> c{};
+    for (int j = 0; j < k; ++j) c.Qp[j] = Qp[j];
+    combine_dyn_kernel<T><<<grid_for(n), 256, 0, st>>>(q, c, k, ctl, n, out);
     note_launch();
     return cudaGetLastError();
 }
@@ -853,6 +942,7 @@ cudaError_t convert_array(const Ts* in, Td* out, long long n, cudaStream_t st) {
     template cudaError_t merge_write<T>(const MergeArgs<T>&, cudaStream_t); \
     template cudaError_t skeleton_apply<T>(const T*, const Geometry&, const Stencil&, T*, cudaStream_t); \
     template cudaError_t combine_skeleton<T>(const T*, const T* const*, const double*, int, double, long long, T*, cudaStream_t); \
+    template cudaError_t combine_skeleton_dyn<T>(const T*, const T* const*, int, const CtlCombine*, long long, T*, cudaStream_t); \
     template cudaError_t fill_value<T>(T*, long long, T, cudaStream_t); \
     template cudaError_t ring_from<T>(const double*, T*, const Geometry&, int, cudaStream_t); \
     template cudaError_t maxabs<T>(const T*, long long, double*, int*, cudaStream_t);

@@ -182,7 +182,7 @@ __device__ __forceinline__ void bcr_level_body(BcrSys<T> g0, BcrSys<T> g1, int n
 }
 
 template <typename T, bool kBackward, int TM>
-__global__ void __cluster_dims__(KSPLIT, 1, 1) __launch_bounds__(GT_THREADS)
+__global__ void __cluster_dims__(KSPLIT, 1, 1) __launch_bounds__(GT_THREADS, sizeof(T) == 4 ? 4 : 3)
 bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
     bcr_level_body<T, kBackward, TM, KSPLIT>(g0, g1, ngroups, level);
 }
@@ -342,13 +342,49 @@ fill_holes_kernel(FillArgs<T> a) {
     const int warps_cta = blockDim.x >> 5;
     const long long warps_total = (long long)gridDim.x * warps_cta;
     const long long gwarp = (long long)blockIdx.x * warps_cta + warp;
-    for (long long base = gwarp * SEGS; base < nholes; base += warps_total * SEGS) {
+    // Homogeneous mode: the right-hand side is -A_hs z, i.e. the skeleton values
+    // around the hole times the stencil.  Lane c < C fetches four of them (left
+    // and right of row c, below and above column c); the next hole's four are
+    // loaded while the current hole is solved.
+    const bool homog = a.mode == FILL_HOMOGENEOUS;
+    const long long hstep = warps_total * SEGS;
+    auto load_ring = [&](long long hole, T* v) {
+        if (c < C && hole < nholes) {
+            const int bi = (int)(hole % mc), bj = (int)(hole / mc);
+            const long long row = (long long)(bj * n + c + 1) * N;
+            v[0] = a.z[row + bi * n];                                   // left of row c
+            v[1] = a.z[row + bi * n + n];                               // right of row c
+            v[2] = a.z[(long long)(bj * n) * N + bi * n + c + 1];       // below column c
+            v[3] = a.z[(long long)(bj * n + n) * N + bi * n + c + 1];   // above column c
+        } else {
+            v[0] = v[1] = v[2] = v[3] = T(0);
+        }
+    };
+    T ring_next[4];
+    if (homog) load_ring(gwarp * SEGS + seg, ring_next);
+    for (long long base = gwarp * SEGS; base < nholes; base += hstep) {
         const long long hole = base + seg;
         const bool hole_ok = c < C && hole < nholes;
         const int bi = hole_ok ? (int)(hole % mc) : 0, bj = hole_ok ? (int)(hole / mc) : 0;
         const int gx = bi * n + c + 1;          // grid x of this lane's column
         // Right-hand side of step 2: P b + c with c = -P A (skeleton).
-        if (hole_ok) {
+        if (homog) {
+            T ring[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ring[q] = ring_next[q];
+            load_ring(hole + hstep, ring_next);
+            if (hole_ok) {
+#pragma unroll
+                for (int y = 0; y < R; ++y) X[y * CP + c] = T(0);
+                X[c] = -cs * ring[2];
+                X[(R - 1) * CP + c] -= cn * ring[3];
+            }
+            __syncwarp();
+            if (hole_ok) {
+                X[c * CP] -= cw * ring[0];
+                X[c * CP + C - 1] -= ce * ring[1];
+            }
+        } else if (hole_ok) {
 #pragma unroll
             for (int y = 1; y <= R; ++y) {
                 const long long gidx = (long long)(bj * n + y) * N + gx;
