@@ -183,16 +183,28 @@ struct UpdateF {
     const DynUpdate* dyn;   // non-null: count and c come from the device, U_in/U_out are buffers 0/1
 };
 
+// Balanced two-digit split of a difference with |D| < 2^43:
+// D = f1 2^22 + f0 exactly, f0, f1 integers in [-2^21, 2^21].
+__device__ __forceinline__ void split2(long long D, float& f1, float& f0) {
+    const unsigned lo = (unsigned)(unsigned long long)D;
+    const int d0 = ((int)(lo << 10)) >> 10;                 // low 22 bits, sign-extended
+    const unsigned long long R = (unsigned long long)(D - (long long)d0);   // low 22 bits zero
+    const int d1 = (int)__funnelshift_r((unsigned)R, (unsigned)(R >> 32), 22);
+    f0 = __fsub_rn(__int_as_float(0x4B400000 + d0), 12582912.0f);
+    f1 = __fsub_rn(__int_as_float(0x4B400000 + d1), 12582912.0f);
+}
+
+// U of row j at column x with the pending update applied (interior only).
+template <int CNT>
 __device__ __forceinline__ long long load_updated(const long long* __restrict__ U_in, const UpdateF& up,
-                                                  int N, int x, int j) {
-    if (x < 0 || x > N - 1 || j < 0 || j > N - 1) return 0;
+                                                  int N, int x, int j, bool xin, bool xint) {
+    if (!xin) return 0;
     const long long idx = (long long)j * N + x;
     long long v = U_in[idx];
-    if (up.count > 0 && x >= 1 && j >= 1 && x <= N - 2 && j <= N - 2) {
+    if (CNT > 0 && xint && j >= 1 && j <= N - 2) {
         float d = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-            if (q < up.count) d = __fmaf_rn(up.c[q], __ldg(up.z[q] + idx), d);
+        for (int q = 0; q < CNT; ++q) d = __fmaf_rn(up.c[q], __ldg(up.z[q] + idx), d);
         v += f2ll_rn(d);
     }
     return v;
@@ -209,40 +221,32 @@ __device__ __forceinline__ void acc_prod(float khi, float klo, float f, float& h
     err = __fadd_rn(err, __fadd_rn(t, e));
 }
 
-__global__ void __launch_bounds__(32 * MS_WARPS)
-residual_mixed_kernel(const float* __restrict__ s_hi, const float* __restrict__ s_lo,
-                      const long long* U_in0, long long* U_out0,
-                      UpdateF up, Geometry g, MixedCoefs k, ResidOut o, int* overflow) {
+// The row march of one warp with CNT pending directions (a compile-time count,
+// so the update loop has no per-point control flow).
+template <int CNT>
+__device__ __forceinline__ void resid_rows(const float* __restrict__ s_hi, const float* __restrict__ s_lo,
+                                           const long long* __restrict__ U_in, long long* __restrict__ U_out,
+                                           const UpdateF& up, const Geometry& g, const MixedCoefs& k,
+                                           const ResidOut& o, int x, int j0, int j1, bool out_col,
+                                           float& srf, float& shf, bool& ovf) {
     const int N = g.N;
-    const long long* __restrict__ U_in = U_in0;
-    long long* __restrict__ U_out = U_out0;
-    if (up.dyn) {
-        if (!up.dyn->live) return;
-        up.count = up.dyn->count;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) up.c[q] = up.dyn->cf[q];
-        if (up.dyn->par) { U_in = U_out0; U_out = const_cast<long long*>(U_in0); }
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x = 1 + (blockIdx.x * MS_WARPS + warp) * MS_OUT + lane - 1;   // lane 0: west halo
-    const bool out_col = lane >= 1 && lane <= MS_OUT && x <= N - 2;
-    const int j0 = 1 + blockIdx.y * MS_ROWS;
-    const int j1 = min(j0 + MS_ROWS - 1, N - 2);
-    long long um = load_updated(U_in, up, N, x, j0 - 1);
-    long long uc = load_updated(U_in, up, N, x, j0);
-    float srf = 0.0f, shf = 0.0f;
+    const bool xin = x >= 0 && x <= N - 1, xint = x >= 1 && x <= N - 2;
+    long long um = load_updated<CNT>(U_in, up, N, x, j0 - 1, xin, xint);
+    long long uc = load_updated<CNT>(U_in, up, N, x, j0, xin, xint);
     const long long lim = 1LL << 60;
-    bool ovf = false;
     for (int j = j0; j <= j1; ++j) {
-        const long long un = load_updated(U_in, up, N, x, j + 1);
+        const long long un = load_updated<CNT>(U_in, up, N, x, j + 1, xin, xint);
         const long long uw = __shfl_up_sync(0xffffffffu, uc, 1);
         const long long ue = __shfl_down_sync(0xffffffffu, uc, 1);
-        if (out_col) {
-            const long long idx = (long long)j * N + x;
-            ovf |= (uc > lim) || (uc < -lim);
-            if (up.count > 0) U_out[idx] = uc;
-            const long long D[4] = {2 * uc - uw - ue, 2 * uc - um - un, ue - uw, un - um};
-            float hi = 0.0f, err = 0.0f;
+        const long long idx = (long long)j * N + x;
+        const long long D[4] = {2 * uc - uw - ue, 2 * uc - um - un, ue - uw, un - um};
+        // Differences below 2^43 in modulus (the usual case: u is smooth on the
+        // fine scale) need two 22-bit digits; otherwise the warp takes three.
+        bool wide = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wide |= (unsigned long long)(D[q] + (1LL << 43)) >= (1ULL << 44);
+        float hi = 0.0f, err = 0.0f;
+        if (__any_sync(0xffffffffu, out_col && wide)) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float f2, f1, f0;
@@ -251,6 +255,18 @@ residual_mixed_kernel(const float* __restrict__ s_hi, const float* __restrict__ 
                 acc_prod(k.k1[q][0], k.k1[q][1], f1, hi, err);
                 err = __fmaf_rn(k.k0[q], f0, err);
             }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float f1, f0;
+                split2(D[q], f1, f0);
+                acc_prod(k.k1[q][0], k.k1[q][1], f1, hi, err);
+                err = __fmaf_rn(k.k0[q], f0, err);
+            }
+        }
+        if (out_col) {
+            ovf |= (uc > lim) || (uc < -lim);
+            if (CNT > 0) U_out[idx] = uc;
             // r = s - A u: TwoSum of the leading parts, then the small terms.
             const float sh = __ldg(s_hi + idx), sl = __ldg(s_lo + idx);
             const float a = sh, b = -hi;
@@ -266,6 +282,37 @@ residual_mixed_kernel(const float* __restrict__ s_hi, const float* __restrict__ 
         }
         um = uc;
         uc = un;
+    }
+}
+
+__global__ void __launch_bounds__(32 * MS_WARPS)
+residual_mixed_kernel(const float* __restrict__ s_hi, const float* __restrict__ s_lo,
+                      const long long* U_in0, long long* U_out0,
+                      UpdateF up, Geometry g, MixedCoefs k, ResidOut o, int* overflow) {
+    const int N = g.N;
+    const long long* U_in = U_in0;
+    long long* U_out = U_out0;
+    if (up.dyn) {
+        if (!up.dyn->live) return;
+        up.count = up.dyn->count;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) up.c[q] = up.dyn->cf[q];
+        if (up.dyn->par) { U_in = U_out0; U_out = const_cast<long long*>(U_in0); }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = 1 + (blockIdx.x * MS_WARPS + warp) * MS_OUT + lane - 1;   // lane 0: west halo
+    const bool out_col = lane >= 1 && lane <= MS_OUT && x <= N - 2;
+    const int j0 = 1 + blockIdx.y * MS_ROWS;
+    const int j1 = min(j0 + MS_ROWS - 1, N - 2);
+    float srf = 0.0f, shf = 0.0f;
+    bool ovf = false;
+    switch (up.count) {
+#define RESID_CASE(C) case C: resid_rows<C>(s_hi, s_lo, U_in, U_out, up, g, k, o, x, j0, j1, out_col, srf, shf, ovf); break;
+        RESID_CASE(0) RESID_CASE(1) RESID_CASE(2) RESID_CASE(3) RESID_CASE(4) RESID_CASE(5) RESID_CASE(6)
+        RESID_CASE(7) RESID_CASE(8) RESID_CASE(9) RESID_CASE(10) RESID_CASE(11) RESID_CASE(12)
+        RESID_CASE(13) RESID_CASE(14) RESID_CASE(15) RESID_CASE(16)
+#undef RESID_CASE
+        default: break;
     }
     if (ovf) atomicOr(overflow, 1);
     // Block reduction of the two norms (8 warps).
