@@ -76,9 +76,16 @@ long long launch_count();
 // ---------------------------------------------------------------------------
 // Kernel launchers (kernels_*.cu).  All enqueue on `st`; none synchronise.
 // ---------------------------------------------------------------------------
+// Launch shape of every BCR level: cfg[dir][level] = (TM << 8) | KS with TM
+// in {16, 64} output rows per CTA and KS in {1, 2, 4, 8} CTAs per cluster
+// splitting the reduction; 0 (or no table) = the built-in choice.
+struct BcrTune {
+    int cfg[2][kMaxLevels];    // [0] forward, [1] backward
+    int num_sms;
+};
 // Block cyclic reduction of up to 2 factor groups (e.g. the fc and cf families).
 template <typename T>
-cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st);
+cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st, const BcrTune* tune = nullptr);
 
 // Mode of the hole solve of Algorithm 3.
 enum FillMode : int {

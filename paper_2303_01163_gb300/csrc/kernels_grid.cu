@@ -194,20 +194,32 @@ __device__ __forceinline__ void split2(long long D, float& f1, float& f0) {
     f1 = __fsub_rn(__int_as_float(0x4B400000 + d1), 12582912.0f);
 }
 
-// U of row j at column x with the pending update applied (interior only).
+// Raw loads of row j at column x (U and the pending directions), issued one
+// row ahead of their use; finish_row applies the update (interior only: the
+// direction values are zero elsewhere).
 template <int CNT>
-__device__ __forceinline__ long long load_updated(const long long* __restrict__ U_in, const UpdateF& up,
-                                                  int N, int x, int j, bool xin, bool xint) {
-    if (!xin) return 0;
+struct RowLoads {
+    long long U;
+    float z[CNT > 0 ? CNT : 1];
+};
+
+template <int CNT>
+__device__ __forceinline__ void load_row(const long long* __restrict__ U_in, const UpdateF& up, int N, int x, int j,
+                                         bool xin, bool xint, RowLoads<CNT>& r) {
     const long long idx = (long long)j * N + x;
-    long long v = U_in[idx];
-    if (CNT > 0 && xint && j >= 1 && j <= N - 2) {
-        float d = 0.0f;
+    r.U = xin ? U_in[idx] : 0;
+    const bool upd = xint && j >= 1 && j <= N - 2;
 #pragma unroll
-        for (int q = 0; q < CNT; ++q) d = __fmaf_rn(up.c[q], __ldg(up.z[q] + idx), d);
-        v += f2ll_rn(d);
-    }
-    return v;
+    for (int q = 0; q < CNT; ++q) r.z[q] = upd ? __ldg(up.z[q] + idx) : 0.0f;
+}
+
+template <int CNT>
+__device__ __forceinline__ long long finish_row(const RowLoads<CNT>& r, const UpdateF& up) {
+    if (CNT == 0) return r.U;
+    float d = 0.0f;
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) d = __fmaf_rn(up.c[q], r.z[q], d);
+    return r.U + f2ll_rn(d);
 }
 
 __device__ __forceinline__ void acc_prod(float khi, float klo, float f, float& hi, float& err) {
@@ -231,14 +243,20 @@ __device__ __forceinline__ void resid_rows(const float* __restrict__ s_hi, const
                                            float& srf, float& shf, bool& ovf) {
     const int N = g.N;
     const bool xin = x >= 0 && x <= N - 1, xint = x >= 1 && x <= N - 2;
-    long long um = load_updated<CNT>(U_in, up, N, x, j0 - 1, xin, xint);
-    long long uc = load_updated<CNT>(U_in, up, N, x, j0, xin, xint);
+    RowLoads<CNT> ra;
+    load_row<CNT>(U_in, up, N, x, j0 - 1, xin, xint, ra);
+    long long um = finish_row<CNT>(ra, up);
+    load_row<CNT>(U_in, up, N, x, j0, xin, xint, ra);
+    long long uc = finish_row<CNT>(ra, up);
+    load_row<CNT>(U_in, up, N, x, j0 + 1, xin, xint, ra);     // rows j0+1 .. j1+1 <= N-1 exist
     const long long lim = 1LL << 60;
     for (int j = j0; j <= j1; ++j) {
-        const long long un = load_updated<CNT>(U_in, up, N, x, j + 1, xin, xint);
+        const long long un = finish_row<CNT>(ra, up);
+        if (j + 2 <= j1 + 1) load_row<CNT>(U_in, up, N, x, j + 2, xin, xint, ra);
+        const long long idx = (long long)j * N + x;
+        const float sh = out_col ? __ldg(s_hi + idx) : 0.0f, sl = out_col ? __ldg(s_lo + idx) : 0.0f;
         const long long uw = __shfl_up_sync(0xffffffffu, uc, 1);
         const long long ue = __shfl_down_sync(0xffffffffu, uc, 1);
-        const long long idx = (long long)j * N + x;
         const long long D[4] = {2 * uc - uw - ue, 2 * uc - um - un, ue - uw, un - um};
         // Differences below 2^43 in modulus (the usual case: u is smooth on the
         // fine scale) need two 22-bit digits; otherwise the warp takes three.
@@ -268,7 +286,6 @@ __device__ __forceinline__ void resid_rows(const float* __restrict__ s_hi, const
             ovf |= (uc > lim) || (uc < -lim);
             if (CNT > 0) U_out[idx] = uc;
             // r = s - A u: TwoSum of the leading parts, then the small terms.
-            const float sh = __ldg(s_hi + idx), sl = __ldg(s_lo + idx);
             const float a = sh, b = -hi;
             const float s = __fadd_rn(a, b);
             const float bb = __fsub_rn(s, a);

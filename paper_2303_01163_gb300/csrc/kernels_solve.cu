@@ -33,21 +33,24 @@ namespace {
 
 constexpr int GT_N = 64;       // output columns per tile
 constexpr int GT_K = 32;       // reduction slice
-constexpr int GT_THREADS = 256;
-constexpr int KSPLIT = 8;      // CTAs of a cluster sharing one output tile
+constexpr int GT_THREADS = 128;
 
 // One BCR level as a GEMM: out[t][c] = sum_k A[t][k] F[k][c], the reduction
 // running over one factor (forward: -M (wl f_{i-s} + wr f_{i+s})) or two
 // (backward: B^{-1} f_i, then -M (wl x_{i-s} + wr x_{i+s})), i.e. K' = C or 2C.
-// A cluster of KSPLIT CTAs shares one TM x 64 output tile: CTA r multiplies the
-// 32-wide slices r, r+KSPLIT, ... of K', keeps its partial tile in shared
-// memory, and after a cluster barrier each CTA sums one eighth of the tile
-// over the 8 partials in rank order (deterministic) and writes it.
+// A CTA computes a TM x 64 output tile, 8 x 4 (TM = 64) or 2 x 4 (TM = 16)
+// outputs per thread, walking 32-wide slices of K' staged in shared memory;
+// the next slice is loaded into registers while the current one is used.
+// With KS > 1 a thread-block cluster of KS CTAs shares the tile: CTA r takes
+// the slices r, r+KS, ..., keeps its partial tile in shared memory and, after
+// a cluster barrier, sums 1/KS of the tile over the KS partials in rank order
+// (deterministic) and writes it.
 template <typename T, bool kBackward, int TM, int KS>
-__device__ __forceinline__ void bcr_level_body(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
-    constexpr int RPT = TM / 16;                       // output rows per thread
-    constexpr int A_PER_T = TM * GT_K / GT_THREADS;    // A-slice elements per thread (2 or 8)
-    constexpr int F_PER_T = GT_K * GT_N / GT_THREADS;  // factor-slice elements per thread (8)
+__global__ void __launch_bounds__(GT_THREADS, sizeof(T) == 4 ? 5 : 2)
+bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
+    constexpr int RPT = TM / 8;                        // output rows per thread
+    constexpr int A_PER_T = TM * GT_K / GT_THREADS;    // A-slice elements per thread
+    constexpr int F_PER_T = GT_K * GT_N / GT_THREADS;  // factor-slice elements per thread
     // The slices As [k][row], Fs [k][col] and, after the reduction loop, the
     // partial tile Part [row][col] share one buffer (Part fits in As + Fs).
     constexpr int AS_ELEMS = GT_K * (TM + 4), FS_ELEMS = GT_K * GT_N;
@@ -56,7 +59,8 @@ __device__ __forceinline__ void bcr_level_body(BcrSys<T> g0, BcrSys<T> g1, int n
     T (*As)[TM + 4] = reinterpret_cast<T (*)[TM + 4]>(smem_buf);
     T (*Fs)[GT_N] = reinterpret_cast<T (*)[GT_N]>(smem_buf + AS_ELEMS);
     T* Part = smem_buf;
-    const int rank = KS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    int rank = 0;
+    if constexpr (KS > 1) rank = (int)cg::this_cluster().block_rank();
     int z = blockIdx.z;
     const BcrSys<T>* gp = &g0;
     if (ngroups > 1 && z >= g0.nsys) { gp = &g1; z -= g0.nsys; }
@@ -87,8 +91,9 @@ __device__ __forceinline__ void bcr_level_body(BcrSys<T> g0, BcrSys<T> g1, int n
         for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
 
     const int nk = (C + GT_K - 1) / GT_K;        // slices per factor pass
-    const int passes = kBackward ? 2 : 1;
-    for (int q = rank; tile_ok && q < passes * nk; q += KS) {
+    const int total = (kBackward ? 2 : 1) * nk;
+    T av[A_PER_T], fv[F_PER_T];
+    auto load_slice = [&](int q) {
         const int pass = kBackward ? q / nk : 1;  // 0: B^{-1} f_i, 1: -M v_i
         const int k0 = (q % nk) * GT_K;
         const T* Fm = pass == 0 ? Bt : Mt;
@@ -108,39 +113,58 @@ __device__ __forceinline__ void bcr_level_body(BcrSys<T> g0, BcrSys<T> g1, int n
                     v = -v;
                 }
             }
-            As[kk][r] = v;
+            av[j] = v;
         }
 #pragma unroll
         for (int j = 0; j < F_PER_T; ++j) {
             const int e = tid + j * GT_THREADS;
             const int kk = e / GT_N, cc = e % GT_N;
             const int k = k0 + kk, c = c0 + cc;
-            Fs[kk][cc] = (k < C && c < C) ? __ldg(Fm + (size_t)k * C + c) : T(0);
+            fv[j] = (k < C && c < C) ? __ldg(Fm + (size_t)k * C + c) : T(0);
+        }
+    };
+    if (tile_ok && rank < total) load_slice(rank);
+    for (int q = rank; tile_ok && q < total; q += KS) {
+        __syncthreads();                          // the previous slice has been used
+#pragma unroll
+        for (int j = 0; j < A_PER_T; ++j) {
+            const int e = tid + j * GT_THREADS;
+            As[e % GT_K][e / GT_K] = av[j];
+        }
+#pragma unroll
+        for (int j = 0; j < F_PER_T; ++j) {
+            const int e = tid + j * GT_THREADS;
+            Fs[e / GT_N][e % GT_N] = fv[j];
         }
         __syncthreads();
+        if (q + KS < total) load_slice(q + KS);
 #pragma unroll 8
         for (int kk = 0; kk < GT_K; ++kk) {
-            T av[RPT], bv[4];
-            if constexpr (sizeof(T) == 4 && RPT == 4) {
-                const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-                av[0] = a4.x; av[1] = a4.y; av[2] = a4.z; av[3] = a4.w;
+            T a_[RPT], b_[4];
+            if constexpr (sizeof(T) == 4 && RPT == 8) {
+                const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+                const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+                a_[0] = a0.x; a_[1] = a0.y; a_[2] = a0.z; a_[3] = a0.w;
+                a_[4] = a1.x; a_[5] = a1.y; a_[6] = a1.z; a_[7] = a1.w;
+            } else if constexpr (sizeof(T) == 4 && RPT == 2) {
+                const float2 a0 = *reinterpret_cast<const float2*>(&As[kk][ty * 2]);
+                a_[0] = a0.x; a_[1] = a0.y;
             } else {
 #pragma unroll
-                for (int a = 0; a < RPT; ++a) av[a] = As[kk][ty * RPT + a];
+                for (int a = 0; a < RPT; ++a) a_[a] = As[kk][ty * RPT + a];
             }
             if constexpr (sizeof(T) == 4) {
                 const float4 b4 = *reinterpret_cast<const float4*>(&Fs[kk][tx * 4]);
-                bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
+                b_[0] = b4.x; b_[1] = b4.y; b_[2] = b4.z; b_[3] = b4.w;
             } else {
 #pragma unroll
-                for (int b = 0; b < 4; ++b) bv[b] = Fs[kk][tx * 4 + b];
+                for (int b = 0; b < 4; ++b) b_[b] = Fs[kk][tx * 4 + b];
             }
 #pragma unroll
             for (int a = 0; a < RPT; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+                for (int b = 0; b < 4; ++b) acc[a][b] += a_[a] * b_[b];
         }
-        __syncthreads();
     }
     if constexpr (KS == 1) {
         for (int a = 0; tile_ok && a < RPT; ++a) {
@@ -181,14 +205,39 @@ __device__ __forceinline__ void bcr_level_body(BcrSys<T> g0, BcrSys<T> g1, int n
     }
 }
 
+template <typename T, bool kBackward, int TM, int KS>
+cudaError_t launch_variant(dim3 grid, const BcrSys<T>& g0, const BcrSys<T>& g1, int ngroups, int level,
+                           cudaStream_t st) {
+    grid.x *= KS;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(GT_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = KS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = KS > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, bcr_level_kernel<T, kBackward, TM, KS>, g0, g1, ngroups, level);
+}
+
 template <typename T, bool kBackward, int TM>
-__global__ void __cluster_dims__(KSPLIT, 1, 1) __launch_bounds__(GT_THREADS, sizeof(T) == 4 ? 4 : 3)
-bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
-    bcr_level_body<T, kBackward, TM, KSPLIT>(g0, g1, ngroups, level);
+cudaError_t launch_ks(int ks, dim3 grid, const BcrSys<T>& g0, const BcrSys<T>& g1, int ngroups, int level,
+                      cudaStream_t st) {
+    switch (ks) {
+        case 1: return launch_variant<T, kBackward, TM, 1>(grid, g0, g1, ngroups, level, st);
+        case 2: return launch_variant<T, kBackward, TM, 2>(grid, g0, g1, ngroups, level, st);
+        case 4: return launch_variant<T, kBackward, TM, 4>(grid, g0, g1, ngroups, level, st);
+        case 8: return launch_variant<T, kBackward, TM, 8>(grid, g0, g1, ngroups, level, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T, bool kBackward>
-cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, cudaStream_t st) {
+cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, const BcrTune* tune, cudaStream_t st) {
     int maxC = 0, maxRows = 0, nsys = 0;
     for (int q = 0; q < ngroups; ++q) {
         const BcrSys<T>& g = groups[q];
@@ -201,21 +250,34 @@ cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, cudaSt
     if (maxRows <= 0 || nsys == 0) return cudaSuccess;
     BcrSys<T> g1 = ngroups > 1 ? groups[1] : groups[0];
     const int ctiles = (maxC + GT_N - 1) / GT_N;
-    if (maxRows >= 64) {
-        dim3 grid(KSPLIT * ctiles, (maxRows + 63) / 64, nsys);
-        bcr_level_kernel<T, kBackward, 64><<<grid, GT_THREADS, 0, st>>>(groups[0], g1, ngroups, level);
-    } else {
-        dim3 grid(KSPLIT * ctiles, (maxRows + 15) / 16, nsys);
-        bcr_level_kernel<T, kBackward, 16><<<grid, GT_THREADS, 0, st>>>(groups[0], g1, ngroups, level);
+    const int chunks = (kBackward ? 2 : 1) * ((maxC + GT_K - 1) / GT_K);
+    int tm = 0, ks = 0;
+    if (tune) {
+        const int v = tune->cfg[kBackward ? 1 : 0][level];
+        tm = v >> 8;
+        ks = v & 0xFF;
     }
+    if (tm != 16 && tm != 64) tm = maxRows >= 48 ? 64 : 16;
+    if (ks != 1 && ks != 2 && ks != 4 && ks != 8) {
+        // Split the reduction until the launch has about three CTAs per SM.
+        const long long tiles = (long long)ctiles * ((maxRows + tm - 1) / tm) * nsys;
+        const long long target = 3LL * (tune && tune->num_sms > 0 ? tune->num_sms : 152);
+        ks = 1;
+        while (ks < 8 && tiles * ks < target && 2 * ks <= chunks) ks *= 2;
+    }
+    if (ks > chunks) ks = 1;
+    dim3 grid(ctiles, (maxRows + tm - 1) / tm, nsys);
+    cudaError_t e = tm == 64 ? launch_ks<T, kBackward, 64>(ks, grid, groups[0], g1, ngroups, level, st)
+                             : launch_ks<T, kBackward, 16>(ks, grid, groups[0], g1, ngroups, level, st);
     note_launch();
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st) {
+cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st, const BcrTune* tune) {
     if (ngroups < 1 || ngroups > 2) return cudaErrorInvalidValue;
     int L = 0;
     for (int q = 0; q < ngroups; ++q) L = groups[q].L > L ? groups[q].L : L;
@@ -223,14 +285,14 @@ cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st) {
         if (groups[q].L != L) return cudaErrorInvalidValue;   // groups in one call share the level count
     cudaError_t e;
     for (int l = 0; l + 1 < L; ++l)
-        if ((e = launch_level<T, false>(groups, ngroups, l, st)) != cudaSuccess) return e;
+        if ((e = launch_level<T, false>(groups, ngroups, l, tune, st)) != cudaSuccess) return e;
     for (int l = L - 1; l >= 0; --l)
-        if ((e = launch_level<T, true>(groups, ngroups, l, st)) != cudaSuccess) return e;
+        if ((e = launch_level<T, true>(groups, ngroups, l, tune, st)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-template cudaError_t bcr_solve<float>(const BcrSys<float>*, int, cudaStream_t);
-template cudaError_t bcr_solve<double>(const BcrSys<double>*, int, cudaStream_t);
+template cudaError_t bcr_solve<float>(const BcrSys<float>*, int, cudaStream_t, const BcrTune*);
+template cudaError_t bcr_solve<double>(const BcrSys<double>*, int, cudaStream_t, const BcrTune*);
 
 // ---------------------------------------------------------------------------
 // Fused hole fill (Algorithm 3): one warp segment per hole.
