@@ -131,6 +131,16 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
 /* Replace the iteration options of an existing handle (e.g. precision). */
 int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts);
 
+/* Autotune the launch shapes of this handle's kernels for one precision
+ * (ASDSM_FP64 or ASDSM_MIXED): for every level of the block cyclic reductions
+ * of the submesh systems (eq. 2.4) the rows per CTA and the number of CTAs
+ * splitting the reduction, and the warps per CTA of the Filler (Algorithm 3)
+ * are timed with CUDA events on the handle's stream and the fastest kept.
+ * Not part of the paper's method; the arithmetic of a solve is the same up
+ * to the summation order inside the level products.  Synchronises the
+ * stream; takes tens of milliseconds.  Returns ASDSM_OK or an error. */
+int asdsm_autotune(asdsm_handle* h, int precision);
+
 /* Algorithm 4 (ASDSM).  The initial guess (Algorithm 1) is computed in FP64 in
  * both precisions; the mixed path then runs its sweeps as described above.
  * s: device N*N source term (boundary entries unused).

@@ -82,6 +82,8 @@ def load() -> ctypes.CDLL:
     lib.asdsm_setup.restype = ctypes.c_int
     lib.asdsm_set_opts.argtypes = [P, ctypes.POINTER(Opts)]
     lib.asdsm_set_opts.restype = ctypes.c_int
+    lib.asdsm_autotune.argtypes = [P, ctypes.c_int]
+    lib.asdsm_autotune.restype = ctypes.c_int
     lib.asdsm_solve.argtypes = [P, P, P, ctypes.POINTER(Stats)]
     lib.asdsm_solve.restype = ctypes.c_int
     lib.asdsm_initial_guess.argtypes = [P, P, P]
@@ -201,6 +203,13 @@ class Solver:
         rc = self._lib.asdsm_set_opts(self._h, ctypes.byref(self.opts))
         if rc != OK:
             raise AsdsmError(rc, "asdsm_set_opts")
+
+    def autotune(self, precision=None):
+        """Time and keep the fastest launch shapes for this handle (asdsm_autotune)."""
+        prec = self.opts.precision if precision is None else precision
+        rc = self._lib.asdsm_autotune(self._h, prec)
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_autotune")
 
     def solve(self, s, u, check: bool = True) -> SolveResult:
         st = Stats()

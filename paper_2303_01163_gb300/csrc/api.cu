@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <functional>
 
 using namespace asdsm;
 
@@ -103,6 +104,10 @@ struct asdsm_handle {
     int* hdone = nullptr;              // pinned [2]: done flags read between graph launches
     cudaEvent_t evc[2] = {nullptr, nullptr};
     cudaStream_t cap_st = nullptr, body_st = nullptr;
+    // Launch shapes (asdsm_autotune): BCR levels of the anisotropic pair and of
+    // A_cc, and warps per CTA of the Filler, per precision.
+    BcrTune tune_aniso[2] = {}, tune_cc[2] = {};
+    int fill_warps[2] = {0, 0};
     struct SweepGraph {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -161,12 +166,14 @@ BcrSys<T> sys_of(const DevBcr& d, void* X, void* Y, int nsys = 1) {
     return s;
 }
 
-// Hole factors into a FillArgs.
+// Hole factors (and the tuned CTA shape) into a FillArgs.
 template <typename T>
-void hole_factors(const DevBcr& d, FillArgs<T>* fa) {
+void hole_factors(const asdsm_handle* h, int pi, FillArgs<T>* fa) {
+    const DevBcr& d = h->hole[pi];
     fa->Mt = (const T*)d.Mt; fa->Bt = (const T*)d.Bt;
     for (int l = 0; l < d.L; ++l) { fa->wl[l] = (T)d.wl[l]; fa->wr[l] = (T)d.wr[l]; }
     fa->L = d.L;
+    fa->warps = h->fill_warps[pi];
 }
 
 template <typename T>
@@ -322,9 +329,9 @@ int initial_guess_to_z(asdsm_handle* h, const double* s, const double* u) {
     cudaStream_t st = h->st;
     CK(build_submesh_rhs<T>(s, u, g, h->alpha, h->beta, (T*)w.Xfc, (T*)w.Xcf, (T*)w.Xcc, st));
     BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
-    CK(bcr_solve<T>(sys, 2, st));                                       // steps 1.1, 1.2
+    CK(bcr_solve<T>(sys, 2, st, &h->tune_aniso[pi]));                                       // steps 1.1, 1.2
     BcrSys<T> scc = sys_of<T>(h->cc[pi], w.Xcc, w.Ycc);
-    CK(bcr_solve<T>(&scc, 1, st));                                      // step 1.3
+    CK(bcr_solve<T>(&scc, 1, st, &h->tune_cc[pi]));                                      // step 1.3
     T* z = (T*)w.z[0];
     CK(ring_from<T>(u, z, g, 0, st));
     MergeArgs<T> ma{};
@@ -339,7 +346,7 @@ int initial_guess_to_z(asdsm_handle* h, const double* s, const double* u) {
     fa.mode = FILL_WITH_SOURCE;
     fa.z = z; fa.out = z;
     if (sizeof(T) == 8) fa.src_d = s; else fa.src_hi = h->s_hi;
-    hole_factors<T>(h->hole[pi], &fa);
+    hole_factors<T>(h, pi, &fa);
     fa.n = g.n; fa.g = g; fa.sten = h->sten;
     CK(fill_holes<T>(fa, h->num_sms, st));                              // Algorithm 3 with b_ff
     // Restore the ring of z to zero for later use as a direction slot is done by the caller.
@@ -403,7 +410,7 @@ int enqueue_holefix(asdsm_handle* h, const double* s, double* u, int par, double
         fa.U = h->U[par];
         fa.fixed_scale = scale;
     }
-    hole_factors<T>(h->hole[pi], &fa);
+    hole_factors<T>(h, pi, &fa);
     fa.n = g.n; fa.g = g; fa.sten = h->sten;
     CK(fill_holes<T>(fa, h->num_sms, st));
     return ASDSM_OK;
@@ -416,7 +423,7 @@ int enqueue_sweep_body(asdsm_handle* h, int kc, int m, cudaStream_t st) {
     auto& w = h->w[pi];
     const Geometry& g = h->g;
     BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
-    CK(bcr_solve<T>(sys, 2, st));
+    CK(bcr_solve<T>(sys, 2, st, &h->tune_aniso[pi]));
     const T* av[2] = {(const T*)w.Yfc, (const T*)w.Ycf};
     int nb2 = 0;
     CK(multi_dot<T>(av, av, 2, (long long)g.Nf * g.Nc, h->partials, &nb2, st));
@@ -433,7 +440,7 @@ int enqueue_sweep_body(asdsm_handle* h, int kc, int m, cudaStream_t st) {
     FillArgs<T> fa{};
     fa.mode = FILL_HOMOGENEOUS;
     fa.z = z; fa.out = z;
-    hole_factors<T>(h->hole[pi], &fa);
+    hole_factors<T>(h, pi, &fa);
     fa.n = g.n; fa.g = g; fa.sten = h->sten;
     CK(fill_holes<T>(fa, h->num_sms, st));
     CK(skeleton_apply<T>(z, g, h->sten, (T*)w.q, st));
@@ -577,6 +584,89 @@ int graph_sweeps(asdsm_handle* h, const double* s, double* u, double bnorm, int 
     for (int b = 0; b < m + 2 && b < 20; ++b) ran += (long long)c.runs[b] * h->gr.body_launches[b];
     note_launch(ran);
     return ASDSM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of launch shapes: every BCR level (rows per CTA x cluster split)
+// and the Filler's warps per CTA are timed on the handle's own systems (on
+// scratch data, CUDA events on the handle's stream) and the fastest kept.
+// ---------------------------------------------------------------------------
+template <typename T>
+int time_ms(asdsm_handle* h, cudaEvent_t a, cudaEvent_t b, int reps, float* ms, const std::function<int()>& launch) {
+    if (int rc = launch()) return rc;                // warm-up
+    CK(cudaEventRecord(a, h->st));
+    for (int r = 0; r < reps; ++r)
+        if (int rc = launch()) return rc;
+    CK(cudaEventRecord(b, h->st));
+    CK(cudaEventSynchronize(b));
+    CK(cudaEventElapsedTime(ms, a, b));
+    *ms /= reps;
+    return ASDSM_OK;
+}
+
+template <typename T>
+int tune_bcr(asdsm_handle* h, const BcrSys<T>* sys, int ngroups, BcrTune* tune, cudaEvent_t a, cudaEvent_t b) {
+    const int L = sys[0].L;
+    for (int dir = 0; dir < 2; ++dir) {
+        for (int l = 0; l < (dir ? L : L - 1); ++l) {
+            float best = 1e30f;
+            int bestv = 0;
+            for (int tm : {64, 16}) {
+                for (int ks : {1, 2, 4, 8}) {
+                    tune->cfg[dir][l] = (tm << 8) | ks;
+                    float ms = 0.f;
+                    if (int rc = time_ms<T>(h, a, b, 5, &ms, [&]() -> int {
+                            CK(bcr_level<T>(sys, ngroups, l, dir == 1, tune, h->st));
+                            return ASDSM_OK;
+                        })) return rc;
+                    if (ms < best) { best = ms; bestv = tune->cfg[dir][l]; }
+                }
+            }
+            tune->cfg[dir][l] = bestv;
+        }
+    }
+    return ASDSM_OK;
+}
+
+template <typename T>
+int autotune_impl(asdsm_handle* h) {
+    const int pi = sizeof(T) == 8 ? 0 : 1;
+    if (int rc = ensure_work<T>(h, pi, 1)) return rc;
+    auto& w = h->w[pi];
+    const Geometry& g = h->g;
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    auto done = [&](int rc) { cudaEventDestroy(a); cudaEventDestroy(b); return rc; };
+    // Scratch right-hand sides (the tuning overwrites them).
+    CK(cudaMemsetAsync(w.Xfc, 0, (size_t)g.Nf * g.Nc * sizeof(T), h->st));
+    CK(cudaMemsetAsync(w.Xcf, 0, (size_t)g.Nf * g.Nc * sizeof(T), h->st));
+    CK(cudaMemsetAsync(w.Xcc, 0, (size_t)g.Nc * g.Nc * sizeof(T), h->st));
+    BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
+    if (int rc = tune_bcr<T>(h, sys, 2, &h->tune_aniso[pi], a, b)) return done(rc);
+    BcrSys<T> scc = sys_of<T>(h->cc[pi], w.Xcc, w.Ycc);
+    if (int rc = tune_bcr<T>(h, &scc, 1, &h->tune_cc[pi], a, b)) return done(rc);
+    // Filler (homogeneous mode on a zero grid).
+    FillArgs<T> fa{};
+    fa.mode = FILL_HOMOGENEOUS;
+    fa.z = (const T*)w.z[0]; fa.out = (T*)w.z[0];
+    hole_factors<T>(h, pi, &fa);
+    fa.n = g.n; fa.g = g; fa.sten = h->sten;
+    float best = 1e30f;
+    int bestw = 0;
+    for (int wv : {8, 4, 2, 1}) {
+        fa.warps = wv;
+        float ms = 0.f;
+        if (int rc = time_ms<T>(h, a, b, 3, &ms, [&]() -> int {
+                CK(fill_holes<T>(fa, h->num_sms, h->st));
+                return ASDSM_OK;
+            })) return done(rc);
+        if (ms < best) { best = ms; bestw = wv; }
+    }
+    h->fill_warps[pi] = bestw;
+    CK(cudaStreamSynchronize(h->st));
+    destroy_graph(h);                      // recapture with the new shapes
+    return done(ASDSM_OK);
 }
 
 // ---------------------------------------------------------------------------
@@ -743,7 +833,7 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
                 fa.U = h->U[Ucur];
                 fa.fixed_scale = scale;
             }
-            hole_factors<T>(h->hole[pi], &fa);
+            hole_factors<T>(h, pi, &fa);
             fa.n = g.n; fa.g = g; fa.sten = h->sten;
             CK(fill_holes<T>(fa, h->num_sms, st));
             ++hole_fixes;
@@ -757,7 +847,7 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
         {
             const ProfMark pm = prof_begin(h);
-            CK(bcr_solve<T>(sys, 2, st));
+            CK(bcr_solve<T>(sys, 2, st, &h->tune_aniso[pi]));
             const double flops = 2.0 * 2.0 * bcr_macs(g.Nf, g.Nc, h->fc[pi].L);
             const double bytes = ES * (4.0 * g.Nf * g.Nc) + ES * 2.0 * 3.0 * h->fc[pi].L * (double)g.Nc * g.Nc;
             prof_end(h, pm, PC_BCR, bytes, flops);
@@ -787,7 +877,7 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         FillArgs<T> fa{};
         fa.mode = FILL_HOMOGENEOUS;
         fa.z = z; fa.out = z;
-        hole_factors<T>(h->hole[pi], &fa);
+        hole_factors<T>(h, pi, &fa);
         fa.n = g.n; fa.g = g; fa.sten = h->sten;
         {
             const ProfMark pm = prof_begin(h);
@@ -940,6 +1030,7 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(set_cuda_error(e));
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int q = 0; q < 2; ++q) { h->tune_aniso[q].num_sms = h->num_sms; h->tune_cc[q].num_sms = h->num_sms; }
     Geometry& g = h->g;
     g.N = (int)N; g.M = (int)(N - 1); g.Nf = (int)(N - 2); g.mc = (int)mc; g.Nc = (int)(mc - 1); g.n = (int)n;
     g.skel = (long long)g.Nc * g.Nf + (long long)g.Nc * (g.Nf - g.Nc);
@@ -1008,6 +1099,15 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     asdsm_profile(h, 0);
     *out = h;
     return ASDSM_OK;
+}
+
+int asdsm_autotune(asdsm_handle* h, int precision) {
+    if (!h) return ASDSM_ERR_INVALID;
+    int rc;
+    if (precision == ASDSM_FP64) rc = autotune_impl<double>(h);
+    else if (precision == ASDSM_MIXED) rc = autotune_impl<float>(h);
+    else return ASDSM_ERR_INVALID;
+    return rc;
 }
 
 int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts) {
@@ -1126,13 +1226,13 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
         if (fp64) {
             FillArgs<double> fa{};
             fa.mode = FILL_ARRAY; fa.src_d = in; fa.out_d = out;
-            hole_factors<double>(h->hole[0], &fa);
+            hole_factors<double>(h, 0, &fa);
             fa.n = g.n; fa.g = g; fa.sten = h->sten;
             CK(fill_holes<double>(fa, h->num_sms, st));
         } else {
             FillArgs<float> fa{};
             fa.mode = FILL_ARRAY; fa.src_d = in; fa.out_d = out;
-            hole_factors<float>(h->hole[1], &fa);
+            hole_factors<float>(h, 1, &fa);
             fa.n = g.n; fa.g = g; fa.sten = h->sten;
             CK(fill_holes<float>(fa, h->num_sms, st));
         }

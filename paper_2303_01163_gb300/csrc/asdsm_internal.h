@@ -86,6 +86,10 @@ struct BcrTune {
 // Block cyclic reduction of up to 2 factor groups (e.g. the fc and cf families).
 template <typename T>
 cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st, const BcrTune* tune = nullptr);
+// One level of it (forward reduction or back substitution), for tuning.
+template <typename T>
+cudaError_t bcr_level(const BcrSys<T>* groups, int ngroups, int level, bool backward, const BcrTune* tune,
+                      cudaStream_t st);
 
 // Mode of the hole solve of Algorithm 3.
 enum FillMode : int {
@@ -113,6 +117,7 @@ struct FillArgs {
     int L, n;                 // hole systems are (n-1) x (n-1)
     Geometry g;
     Stencil sten;
+    int warps;                // warps per CTA (0: as many as shared memory allows, at most 8)
 };
 template <typename T>
 cudaError_t fill_holes(const FillArgs<T>& a, int num_sms, cudaStream_t st);

@@ -291,6 +291,16 @@ cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st, con
     return cudaSuccess;
 }
 
+template <typename T>
+cudaError_t bcr_level(const BcrSys<T>* groups, int ngroups, int level, bool backward, const BcrTune* tune,
+                      cudaStream_t st) {
+    if (ngroups < 1 || ngroups > 2) return cudaErrorInvalidValue;
+    return backward ? launch_level<T, true>(groups, ngroups, level, tune, st)
+                    : launch_level<T, false>(groups, ngroups, level, tune, st);
+}
+
+template cudaError_t bcr_level<float>(const BcrSys<float>*, int, int, bool, const BcrTune*, cudaStream_t);
+template cudaError_t bcr_level<double>(const BcrSys<double>*, int, int, bool, const BcrTune*, cudaStream_t);
 template cudaError_t bcr_solve<float>(const BcrSys<float>*, int, cudaStream_t, const BcrTune*);
 template cudaError_t bcr_solve<double>(const BcrSys<double>*, int, cudaStream_t, const BcrTune*);
 
@@ -569,8 +579,9 @@ size_t fill_smem_bytes(int n, int L) {
 
 template <typename T, int C>
 cudaError_t fill_holes_launch(const FillArgs<T>& a, int num_sms, cudaStream_t st) {
-    const int warps = fill_warps(sizeof(T), a.n, a.L);
-    if (warps < 1) return cudaErrorInvalidValue;
+    const int max_warps = fill_warps(sizeof(T), a.n, a.L);
+    if (max_warps < 1) return cudaErrorInvalidValue;
+    const int warps = a.warps > 0 && a.warps < max_warps ? a.warps : max_warps;
     const size_t smem = fill_factor_bytes(sizeof(T), a.n, a.L) + (size_t)warps * fill_warp_bytes(sizeof(T), a.n);
     cudaError_t e = cudaFuncSetAttribute(fill_holes_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -121,3 +121,30 @@ def test_graph_max_sweeps_and_stagnation(lib):
     assert res.status == lib.STAGNATED
     h = res.history
     assert h[-1] > 0.5 * h[-6]
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+def test_autotuned_shapes_keep_parity(lib, prec_name):
+    """After asdsm_autotune the level products may sum in another order; the
+    solves still meet the parity bars (FP64 iterates vs the oracle, mixed
+    convergence to the fine solution)."""
+    p = wl.random_fourier_2d(129, 7)
+    prec = lib.FP64 if prec_name == "fp64" else lib.MIXED
+    disc = orc.Discretisation2D(p.N, 16, p.alpha, p.beta)
+    b = disc.rhs(p.s, p.g)
+    if prec == lib.FP64:
+        uo, info = orc.asdsm(disc, b, tol=1e-30, max_sweeps=6, accel_m=4, seed=1, stagnation_window=10**9)
+        kw = dict(tol=1e-30, max_sweeps=6, accel_m=4, seed=1, stagnation_window=0)
+    else:
+        kw = dict(tol=1e-10, max_sweeps=300, accel_m=8)
+    with lib.Solver(p.N, 16, p.alpha, p.beta, precision=prec, **kw) as sv:
+        sv.autotune()
+        u = _dev(p.g)
+        res = sv.solve(_dev(p.s), u)
+        U = u.cpu().numpy()
+    if prec == lib.FP64:
+        assert _relerr(orc.interior(U), uo) <= 1e-12
+    else:
+        assert res.status == lib.OK
+        r, bb = orc.residual_grid(p.N, p.alpha, p.beta, p.s, U)
+        assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1e-10 * 1.01
