@@ -218,6 +218,47 @@ const char* asdsm_noalloc_last_error(void);
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void asdsm_destroy(asdsm_handle* h);
 
+/* ---- Batches of independent problems (instances of uneven sizes) ----------
+ * Not in the paper: a throughput interface for many problems of eq. (1.1) at
+ * once.  Each instance is a full handle (its own factors, work space and
+ * sweep graph) on its own internal CUDA stream; asdsm_solve_batch advances
+ * all instances stage by stage in turn (their initial guesses, then their
+ * graph replays of kSweepsPerGraph sweeps, the host never waiting on one
+ * instance while another can be launched), so their kernels overlap on the
+ * GPU.  Every instance's arithmetic is exactly that of asdsm_solve on the
+ * same inputs. */
+typedef struct asdsm_batch asdsm_batch;
+
+/* descs[count]: one description per instance (eq. 2.1 as for asdsm_setup);
+ * opts: shared by all instances (NULL = defaults).  stream: the caller's
+ * stream; solves are ordered after the work already queued on it and the
+ * stream waits for their end.  *out is NULL on error. */
+int asdsm_setup_batch(const asdsm_desc* descs, int count, const asdsm_opts* opts, void* stream,
+                      asdsm_batch** out);
+
+/* Instances in the batch. */
+int asdsm_batch_count(const asdsm_batch* b);
+
+/* Replace the options of every instance. */
+int asdsm_set_opts_batch(asdsm_batch* b, const asdsm_opts* opts);
+
+/* asdsm_autotune for every size class (N, mc) of the batch: one instance per
+ * class is tuned and the others take its shapes. */
+int asdsm_autotune_batch(asdsm_batch* b, int precision);
+
+/* Algorithm 4 for every instance.  s[i], u[i]: device arrays as for
+ * asdsm_solve (instance i's N*N).  stats: NULL or count entries; an instance
+ * that fails gets its error code in stats[i].status.  Returns ASDSM_OK when
+ * every instance reached tol, else the first non-OK status in instance
+ * order. */
+int asdsm_solve_batch(asdsm_batch* b, const double* const* s, double* const* u, asdsm_stats* stats);
+
+/* Residual history of instance `index` (as asdsm_history). */
+int asdsm_batch_history(const asdsm_batch* b, int index, double* hist, int cap);
+
+/* Release the batch and all its instances (NULL is a no-op). */
+void asdsm_destroy_batch(asdsm_batch* b);
+
 /* Static description of a status code. */
 const char* asdsm_strerror(int code);
 

@@ -106,6 +106,20 @@ def load() -> ctypes.CDLL:
     lib.asdsm_noalloc_last_error.restype = ctypes.c_char_p
     lib.asdsm_destroy.argtypes = [P]
     lib.asdsm_destroy.restype = None
+    lib.asdsm_setup_batch.argtypes = [ctypes.POINTER(Desc), ctypes.c_int, ctypes.POINTER(Opts), P, ctypes.POINTER(P)]
+    lib.asdsm_setup_batch.restype = ctypes.c_int
+    lib.asdsm_batch_count.argtypes = [P]
+    lib.asdsm_batch_count.restype = ctypes.c_int
+    lib.asdsm_set_opts_batch.argtypes = [P, ctypes.POINTER(Opts)]
+    lib.asdsm_set_opts_batch.restype = ctypes.c_int
+    lib.asdsm_autotune_batch.argtypes = [P, ctypes.c_int]
+    lib.asdsm_autotune_batch.restype = ctypes.c_int
+    lib.asdsm_solve_batch.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(Stats)]
+    lib.asdsm_solve_batch.restype = ctypes.c_int
+    lib.asdsm_batch_history.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    lib.asdsm_batch_history.restype = ctypes.c_int
+    lib.asdsm_destroy_batch.argtypes = [P]
+    lib.asdsm_destroy_batch.restype = None
     lib.asdsm_strerror.argtypes = [ctypes.c_int]
     lib.asdsm_strerror.restype = ctypes.c_char_p
     lib.asdsm_last_error.argtypes = []
@@ -272,3 +286,93 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+class BatchSolver:
+    """Many independent problems of eq. (1.1) (asdsm_setup_batch): problems is a
+    list of (N, mc, alpha, beta); solve takes lists of device tensors."""
+
+    def __init__(self, problems, *, precision: int = MIXED, tol: float = 1e-10, max_sweeps: int = 500,
+                 accel_m: int = 8, seed: int = 0, stream=None, **opt_overrides):
+        import torch
+        lib = load()
+        self._lib = lib
+        n = len(problems)
+        descs = (Desc * n)()
+        self.sizes = []
+        for i, (N, mc, alpha, beta) in enumerate(problems):
+            descs[i].d, descs[i].n, descs[i].mc = 2, int(N), int(mc)
+            for q in range(2):
+                descs[i].alpha[q] = float(alpha[q])
+                descs[i].beta[q] = float(beta[q])
+            self.sizes.append(int(N))
+        o = default_opts()
+        o.tol, o.max_sweeps, o.precision, o.accel_m, o.seed = tol, max_sweeps, precision, accel_m, seed
+        for k, v in opt_overrides.items():
+            setattr(o, k, v)
+        self.opts = o
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        rc = lib.asdsm_setup_batch(descs, n, ctypes.byref(o), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_setup_batch")
+        self._h = h
+        self.count = lib.asdsm_batch_count(h)
+
+    def set_opts(self, **kw):
+        for k, v in kw.items():
+            setattr(self.opts, k, v)
+        rc = self._lib.asdsm_set_opts_batch(self._h, ctypes.byref(self.opts))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_set_opts_batch")
+
+    def autotune(self, precision=None):
+        prec = self.opts.precision if precision is None else precision
+        rc = self._lib.asdsm_autotune_batch(self._h, prec)
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_autotune_batch")
+
+    def solve(self, s_list, u_list, check: bool = True):
+        """Returns (status, [stats dict per instance])."""
+        n = self.count
+        if len(s_list) != n or len(u_list) != n:
+            raise ValueError("one s and one u per instance")
+        for i in range(n):
+            N = self.sizes[i]
+            if s_list[i].numel() != N * N or u_list[i].numel() != N * N:
+                raise ValueError(f"instance {i}: expected {N}x{N} grids")
+        VP = ctypes.c_void_p
+        sp = (VP * n)(*[_ptr(t) for t in s_list])
+        up = (VP * n)(*[_ptr(t) for t in u_list])
+        st = (Stats * n)()
+        rc = self._lib.asdsm_solve_batch(self._h, sp, up, st)
+        if check and rc not in (OK, NOT_CONVERGED, STAGNATED):
+            raise AsdsmError(rc, "asdsm_solve_batch")
+        return rc, [st[i].as_dict() for i in range(n)]
+
+    def history(self, index: int) -> list:
+        cap = 100000
+        buf = (ctypes.c_double * cap)()
+        k = self._lib.asdsm_batch_history(self._h, int(index), buf, cap)
+        if k < 0:
+            raise AsdsmError(k, "asdsm_batch_history")
+        return [buf[i] for i in range(k)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.asdsm_destroy_batch(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

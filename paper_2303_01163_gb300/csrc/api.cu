@@ -87,7 +87,7 @@ struct asdsm_handle {
     int* dflag = nullptr;
     double* hsmall = nullptr;       // pinned host mirror of dsmall
     std::vector<double> hist;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evA = nullptr;
     // Per-kernel-family profiling (asdsm_profile).
     bool prof = false;
     asdsm_kprof pc[8] = {};
@@ -524,19 +524,40 @@ int ensure_graph(asdsm_handle* h, const double* s, double* u, int m, int S, doub
     return ASDSM_OK;
 }
 
-struct LoopResult {
-    int status = ASDSM_NOT_CONVERGED, k = 0, hole_fixes = 0, par = 0;
+// State of one solve of Algorithm 4, advanced in stages so that a batch can
+// interleave its instances on their streams:
+//   begin  : everything up to the first value the host must read (||b||, and
+//            max |u^(0)| for the fixed-point scale) is enqueued;
+//   middle : after those reads, the fixed-point conversion and the first
+//            sweeps are enqueued (or, host-driven, all sweeps are run);
+//   poll   : graph launches of kSweepsPerGraph sweeps, two in flight, until
+//            the device controller reports the end;
+//   finish : the iterate is copied out and the statistics filled.
+struct SolveRun {
+    const double* s = nullptr;
+    double* u = nullptr;
+    asdsm_stats* stats = nullptr;
+    int stage = 0;                   // 1 begun, 2 sweeps in flight, 3 sweeps ended
+    long long launches = 0;
+    int nb_max = 0;
+    double bnorm = 0.0;
+    int S = 0;
+    double scale = 1.0;
+    MixedCoefs mk{};
+    const double* u0d = nullptr;
+    double* ucur = nullptr;
+    double* unxt = nullptr;
+    int Ucur = 0;
+    int status = ASDSM_NOT_CONVERGED, k = 0, hole_fixes = 0;
     double rel0 = 0.0, rel = 0.0;
-    std::vector<double> hist;
+    std::vector<double> rhist;
+    int q = 0, max_q = 0, in_flight = 0;
+    bool done = false;
 };
 
-// The sweeps of Algorithm 4 as graph launches; the host only reads the done
-// flag of the previous launch while the next one runs.  At most
-// max_sweeps / kSweepsPerGraph + 2 launches: every sweep of a launch either
-// advances k or ends the solve, and k = max_sweeps ends it.
+// Device controller set up and the graph made ready; no launch yet.
 template <typename T>
-int graph_sweeps(asdsm_handle* h, const double* s, double* u, double bnorm, int S, double scale,
-                 const MixedCoefs& mk, LoopResult* out) {
+int graph_start(asdsm_handle* h, SolveRun& r) {
     const asdsm_opts& op = h->opts;
     const int m = std::max(1, std::min(op.accel_m, kMaxM));
     cudaStream_t st = h->st;
@@ -548,41 +569,74 @@ int graph_sweeps(asdsm_handle* h, const double* s, double* u, double bnorm, int 
         h->hist_cap = op.max_sweeps + 2;
         destroy_graph(h);                                   // the graph holds the old pointer
     }
-    if (int rc = ensure_graph<T>(h, s, u, m, S, scale, mk)) return rc;
+    if (int rc = ensure_graph<T>(h, r.s, r.u, m, r.S, r.scale, r.mk)) return rc;
     SweepCtl& c = *h->hctl;
     std::memset(&c, 0, sizeof(c));
-    c.bnorm = bnorm; c.tol = op.tol; c.hole_fix_ratio = op.hole_fix_ratio; c.hole_fix_growth = op.hole_fix_growth;
-    c.stagnation_factor = op.stagnation_factor; c.scale = scale; c.seed = op.seed;
+    c.bnorm = r.bnorm; c.tol = op.tol; c.hole_fix_ratio = op.hole_fix_ratio; c.hole_fix_growth = op.hole_fix_growth;
+    c.stagnation_factor = op.stagnation_factor; c.scale = r.scale; c.seed = op.seed;
     c.max_sweeps = op.max_sweeps; c.window = op.stagnation_window; c.m = m; c.mixed = sizeof(T) == 4;
     c.hist_cap = h->hist_cap;
     c.upd.live = 1;
     CK(cudaMemcpyAsync(h->dctl, &c, sizeof(c), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), st));
-    const int max_launches = op.max_sweeps / kSweepsPerGraph + 2;
-    int launched = 0;
-    bool done = false;
-    for (int q = 0; q < max_launches && !done; ++q) {
-        CK(cudaGraphLaunch(h->gr.exec, st));
-        CK(cudaMemcpyAsync(&h->hdone[q & 1], &h->dctl->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaEventRecord(h->evc[q & 1], st));
-        ++launched;
-        if (q >= 1) {
-            CK(cudaEventSynchronize(h->evc[(q - 1) & 1]));
-            done = h->hdone[(q - 1) & 1] != 0;
-        }
-    }
-    CK(cudaMemcpyAsync(h->hctl, h->dctl, sizeof(SweepCtl), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    out->hist.resize((size_t)std::min(c.nhist, c.hist_cap));
-    if (!out->hist.empty())
-        CK(cudaMemcpy(out->hist.data(), h->dhist, out->hist.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    // At most max_sweeps / kSweepsPerGraph + 2 launches: every replayed sweep
+    // either advances k or finds the solve ended, and k = max_sweeps ends it.
+    r.max_q = op.max_sweeps / kSweepsPerGraph + 2;
+    r.q = 0;
+    r.in_flight = 0;
+    r.done = false;
+    return ASDSM_OK;
+}
+
+// Read the controller's final state after the last launch.
+template <typename T>
+int graph_collect(asdsm_handle* h, SolveRun& r) {
+    const int m = std::max(1, std::min(h->opts.accel_m, kMaxM));
+    CK(cudaMemcpyAsync(h->hctl, h->dctl, sizeof(SweepCtl), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const SweepCtl& c = *h->hctl;
+    r.rhist.resize((size_t)std::min(c.nhist, c.hist_cap));
+    if (!r.rhist.empty())
+        CK(cudaMemcpy(r.rhist.data(), h->dhist, r.rhist.size() * sizeof(double), cudaMemcpyDeviceToHost));
     if (!c.done) { g_last_error = "device sweep control did not finish"; return ASDSM_ERR_CUDA; }
-    out->status = c.status; out->k = c.k; out->hole_fixes = c.hole_fixes; out->par = c.upd.par;
-    out->rel0 = c.rel0; out->rel = c.rel;
+    r.status = c.status; r.k = c.k; r.hole_fixes = c.hole_fixes;
+    r.rel0 = c.rel0; r.rel = c.rel;
+    if (sizeof(T) == 8) { if (c.upd.par) r.ucur = h->u_work; }
+    else r.Ucur = c.upd.par;
     // Kernels that ran: every replayed sweep's fixed part plus the bodies the switch nodes chose.
-    long long ran = (long long)launched * kSweepsPerGraph * h->gr.top_launches;
+    long long ran = (long long)r.q * kSweepsPerGraph * h->gr.top_launches;
     for (int b = 0; b < m + 2 && b < 20; ++b) ran += (long long)c.runs[b] * h->gr.body_launches[b];
     note_launch(ran);
+    r.stage = 3;
+    return ASDSM_OK;
+}
+
+// Keep two graph launches in flight and retire the oldest once it has
+// completed (block: wait for it; otherwise return if it is still running).
+template <typename T>
+int graph_poll(asdsm_handle* h, SolveRun& r, bool block) {
+    cudaStream_t st = h->st;
+    while (!r.done && r.in_flight < 2 && r.q < r.max_q) {
+        const int slot = r.q & 1;
+        CK(cudaGraphLaunch(h->gr.exec, st));
+        CK(cudaMemcpyAsync(&h->hdone[slot], &h->dctl->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(h->evc[slot], st));
+        ++r.q;
+        ++r.in_flight;
+    }
+    if (r.in_flight > 0) {
+        const int j = r.q - r.in_flight;
+        if (block) {
+            CK(cudaEventSynchronize(h->evc[j & 1]));
+        } else {
+            const cudaError_t e = cudaEventQuery(h->evc[j & 1]);
+            if (e == cudaErrorNotReady) return ASDSM_OK;
+            if (e != cudaSuccess) return set_cuda_error(e);
+        }
+        --r.in_flight;
+        if (h->hdone[j & 1]) r.done = true;
+    }
+    if (r.done || (r.q >= r.max_q && r.in_flight == 0)) return graph_collect<T>(h, r);
     return ASDSM_OK;
 }
 
@@ -672,95 +726,32 @@ int autotune_impl(asdsm_handle* h) {
 // ---------------------------------------------------------------------------
 // Algorithm 4.
 // ---------------------------------------------------------------------------
+// Host-driven sweeps (opts.sweep_graph = 0, and profiling): the host reads the
+// residual norms and the least-squares inner products every sweep.
 template <typename T>
-int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) {
+int host_sweeps(asdsm_handle* h, SolveRun& r) {
     const bool mixed = sizeof(T) == 4;
     const int pi = mixed ? 1 : 0;
-    if (int rc = ensure_work<T>(h, pi)) return rc;
     auto& w = h->w[pi];
     const Geometry& g = h->g;
     cudaStream_t st = h->st;
     const asdsm_opts& op = h->opts;
     const int m = std::max(1, std::min(op.accel_m, kMaxM));
-    const long long NN = (long long)g.N * g.N;
-    if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), 4096))) return rc;
-    h->hist.clear();
-    h->pend_ev.clear();
-    h->evnext = 0;
-    asdsm_stats stt{};
-    const long long launches0 = launch_count();
     const double NF2 = (double)g.Nf * g.Nf;
     const double ES = (double)sizeof(T);
-    CK(cudaEventRecord(h->ev0, st));
-
-    double b2 = 0.0;
-    if (int rc = bnorm2(h, s, u, &b2)) return rc;
-    const double bnorm = std::sqrt(b2);
-    if (!std::isfinite(bnorm)) return ASDSM_ERR_NAN;
-
-    // Iterate storage.  FP64: ping-pong between the caller's u and u_work (ring = g in both).
-    // Mixed: U[0]/U[1] (64-bit fixed point, u = U 2^-S).
-    double* ucur = u;
-    double* unxt = h->u_work;
-    int Ucur = 0;
-    int S = 0;
-    double scale = 1.0;
-    if (mixed) {
-        CK(split_source(s, h->s_hi, h->s_lo, NN, st));
-    }
-    CK(ring_from<double>(u, h->u_work, g, 0, st));
-
-    // Step 1: initial guess (or resume from u).  The mixed path computes
-    // Algorithm 1 once in FP64: an FP32 u^(0) carries rounding noise whose
-    // residual is rough, and ASDSM corrections reduce rough residuals slowly
-    // (the irregular-residual stagnation of Section 4, Example 2).
-    const double* u0d = u;           // FP64 grid holding u^(0) (ring = g)
-    if (!op.skip_initial_guess) {
-        if (!mixed) {
-            if (int rc = initial_guess_to_z<double>(h, s, u)) return rc;
-            CK(copy_interior<double, double>((const double*)w.z[0], u, g, st));
-        } else {
-            if (int rc = ensure_work<double>(h, 0, 1)) return rc;
-            if (int rc = initial_guess_to_z<double>(h, s, u)) return rc;
-            u0d = (const double*)h->w[0].z[0];
-        }
-    }
-    if (mixed) {
-        // Fixed-point scale from max |u| (interior and ring), with 2^5 headroom.
-        int nb = 0;
-        CK(maxabs<double>(u0d, NN, h->partials, &nb, st));
-        CK(cudaMemcpyAsync(h->hsmall, h->partials, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        double mx = 0.0;
-        for (int q = 0; q < nb; ++q) mx = std::max(mx, h->hsmall[q]);
-        if (!std::isfinite(mx)) return ASDSM_ERR_NAN;
-        if (mx <= 0.0) mx = 1.0;
-        int e2 = 0;
-        std::frexp(mx, &e2);               // mx < 2^e2
-        S = 58 - e2;                        // |U| < 2^58: 2^5 headroom below the 2^63 range and the 2^60 check
-        scale = std::ldexp(1.0, S);
-        CK(to_fixed(nullptr, u0d, h->U[0], scale, g, st));
-        CK(to_fixed(nullptr, u0d, h->U[1], scale, g, st));   // ring of the partner
-    }
-    // Direction slots need a zero ring again (slot 0 carried g).
-    if (!op.skip_initial_guess) CK(ring_from<double>(nullptr, (double*)h->w[0].z[0], g, 0, st));
-    CK(ring_from<T>(nullptr, (T*)w.z[0], g, 0, st));
-    CK(cudaEventRecord(h->ev1, st));
-    const MixedCoefs mk = mixed ? mixed_coefs(h, S) : MixedCoefs{};
-
-    int status = ASDSM_NOT_CONVERGED;
-    int k = 0;
-    int hole_fixes = 0;
-    double rel0 = 0.0, rel = 0.0;
-    std::vector<double> rhist;
-    if (op.sweep_graph && !h->prof) {
-        LoopResult lr;
-        if (int rc = graph_sweeps<T>(h, s, u, bnorm, S, scale, mk, &lr)) return rc;
-        status = lr.status; k = lr.k; hole_fixes = lr.hole_fixes; rel0 = lr.rel0; rel = lr.rel;
-        rhist = lr.hist;
-        if (!mixed) { if (lr.par) ucur = h->u_work; }
-        else Ucur = lr.par;
-    } else {
+    const double* s = r.s;
+    double*& ucur = r.ucur;
+    double*& unxt = r.unxt;
+    int& Ucur = r.Ucur;
+    const double scale = r.scale;
+    const MixedCoefs& mk = r.mk;
+    const double bnorm = r.bnorm;
+    int& status = r.status;
+    int& k = r.k;
+    int& hole_fixes = r.hole_fixes;
+    double& rel0 = r.rel0;
+    double& rel = r.rel;
+    std::vector<double>& rhist = r.rhist;
     // GCR bookkeeping (host, FP64).
     double Tm[kMaxM][kMaxM] = {};
     int kc = 0;                  // directions in the current cycle
@@ -941,31 +932,160 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
         }
         ++k;
     }
+    return ASDSM_OK;
+}
+
+template <typename T>
+int run_begin(asdsm_handle* h, SolveRun& r) {
+    const bool mixed = sizeof(T) == 4;
+    const int pi = mixed ? 1 : 0;
+    if (int rc = ensure_work<T>(h, pi)) return rc;
+    auto& w = h->w[pi];
+    const Geometry& g = h->g;
+    cudaStream_t st = h->st;
+    const asdsm_opts& op = h->opts;
+    const long long NN = (long long)g.N * g.N;
+    const double* s = r.s;
+    double* u = r.u;
+    if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), 4096))) return rc;
+    h->hist.clear();
+    h->pend_ev.clear();
+    h->evnext = 0;
+    CK(cudaEventRecord(h->ev0, st));
+    // ||b_ff||^2: the FP64 residual of the zero-interior grid (r = b there).
+    {
+        CK(ring_from<double>(u, h->u_work, g, 1, st));
+        int nb = 0;
+        ResidOut o{};
+        o.partials = h->partials;
+        UpdateTerms up{};
+        CK(residual_fp64(s, h->u_work, h->u_work, up, g, h->sten, o, &nb, st));
+        CK(reduce_partials(h->partials, nb, 2, h->dsmall, st));
+        CK(cudaMemcpyAsync(h->hsmall, h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     }
+    // Iterate storage.  FP64: ping-pong between the caller's u and u_work (ring = g in both).
+    // Mixed: U[0]/U[1] (64-bit fixed point, u = U 2^-S).
+    r.ucur = u;
+    r.unxt = h->u_work;
+    r.Ucur = 0;
+    if (mixed) CK(split_source(s, h->s_hi, h->s_lo, NN, st));
+    CK(ring_from<double>(u, h->u_work, g, 0, st));
+    // Step 1: initial guess (or resume from u).  The mixed path computes
+    // Algorithm 1 once in FP64: an FP32 u^(0) carries rounding noise whose
+    // residual is rough, and ASDSM corrections reduce rough residuals slowly
+    // (the irregular-residual stagnation of Section 4, Example 2).
+    r.u0d = u;                       // FP64 grid holding u^(0) (ring = g)
+    if (!op.skip_initial_guess) {
+        if (!mixed) {
+            if (int rc = initial_guess_to_z<double>(h, s, u)) return rc;
+            CK(copy_interior<double, double>((const double*)w.z[0], u, g, st));
+        } else {
+            if (int rc = ensure_work<double>(h, 0, 1)) return rc;
+            if (int rc = initial_guess_to_z<double>(h, s, u)) return rc;
+            r.u0d = (const double*)h->w[0].z[0];
+        }
+    }
+    if (mixed) {
+        // Fixed-point scale from max |u| (interior and ring): block maxima to the host.
+        int nb = 0;
+        CK(maxabs<double>(r.u0d, NN, h->partials, &nb, st));
+        if (nb > 4000) return ASDSM_ERR_INVALID;
+        CK(cudaMemcpyAsync(h->hsmall + 8, h->partials, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        r.nb_max = nb;
+    }
+    CK(cudaEventRecord(h->evA, st));
+    r.stage = 1;
+    return ASDSM_OK;
+}
+
+template <typename T>
+int run_middle(asdsm_handle* h, SolveRun& r) {
+    const bool mixed = sizeof(T) == 4;
+    const int pi = mixed ? 1 : 0;
+    auto& w = h->w[pi];
+    const Geometry& g = h->g;
+    cudaStream_t st = h->st;
+    const asdsm_opts& op = h->opts;
+    r.bnorm = std::sqrt(h->hsmall[0]);
+    if (!std::isfinite(r.bnorm)) return ASDSM_ERR_NAN;
+    if (mixed) {
+        double mx = 0.0;
+        for (int q = 0; q < r.nb_max; ++q) mx = std::max(mx, h->hsmall[8 + q]);
+        if (!std::isfinite(mx)) return ASDSM_ERR_NAN;
+        if (mx <= 0.0) mx = 1.0;
+        int e2 = 0;
+        std::frexp(mx, &e2);                // mx < 2^e2
+        r.S = 58 - e2;                      // |U| < 2^58: 2^5 headroom below the 2^63 range and the 2^60 check
+        r.scale = std::ldexp(1.0, r.S);
+        CK(to_fixed(nullptr, r.u0d, h->U[0], r.scale, g, st));
+        CK(to_fixed(nullptr, r.u0d, h->U[1], r.scale, g, st));   // ring of the partner
+    }
+    // Direction slots need a zero ring again (slot 0 carried g).
+    if (!op.skip_initial_guess) CK(ring_from<double>(nullptr, (double*)h->w[0].z[0], g, 0, st));
+    CK(ring_from<T>(nullptr, (T*)w.z[0], g, 0, st));
+    CK(cudaEventRecord(h->ev1, st));
+    r.mk = mixed ? mixed_coefs(h, r.S) : MixedCoefs{};
+    if (op.sweep_graph && !h->prof) {
+        if (int rc = graph_start<T>(h, r)) return rc;
+        r.stage = 2;
+    } else {
+        if (int rc = host_sweeps<T>(h, r)) return rc;
+        r.stage = 3;
+    }
+    return ASDSM_OK;
+}
+
+template <typename T>
+int run_finish(asdsm_handle* h, SolveRun& r) {
+    const bool mixed = sizeof(T) == 4;
+    const Geometry& g = h->g;
+    cudaStream_t st = h->st;
     // Final iterate to the caller's buffer.
     if (!mixed) {
-        if (ucur != u) CK(copy_interior<double, double>(ucur, u, g, st));
-    } else if (status != ASDSM_ERR_RANGE) {
-        CK(from_fixed(h->U[Ucur], std::ldexp(1.0, -S), u, g, st));
+        if (r.ucur != r.u) CK(copy_interior<double, double>(r.ucur, r.u, g, st));
+    } else if (r.status != ASDSM_ERR_RANGE) {
+        CK(from_fixed(h->U[r.Ucur], std::ldexp(1.0, -r.S), r.u, g, st));
     }
     CK(cudaEventRecord(h->ev2, st));
     CK(cudaEventSynchronize(h->ev2));
     float ms_setup = 0.f, ms_all = 0.f;
     cudaEventElapsedTime(&ms_setup, h->ev0, h->ev1);
     cudaEventElapsedTime(&ms_all, h->ev0, h->ev2);
-    h->hist = rhist;
+    h->hist = r.rhist;
     prof_resolve(h);
-    stt.launches = launch_count() - launches0;
-    stt.sweeps = k;
-    stt.status = status;
-    stt.hole_fixes = hole_fixes;
-    stt.fixed_shift = mixed ? S : 0;
-    stt.rel_res = rel;
-    stt.rel_res0 = rel0;
+    asdsm_stats stt{};
+    stt.launches = r.launches;
+    stt.sweeps = r.k;
+    stt.status = r.status;
+    stt.hole_fixes = r.hole_fixes;
+    stt.fixed_shift = mixed ? r.S : 0;
+    stt.rel_res = r.rel;
+    stt.rel_res0 = r.rel0;
     stt.setup_ms = ms_setup;
     stt.solve_ms = ms_all;
-    if (stats) *stats = stt;
-    return status;
+    if (r.stats) *r.stats = stt;
+    return r.status;
+}
+
+// Run one stage of a solve, attributing the kernel launches it makes.
+template <typename F>
+int staged(SolveRun& r, F&& fn) {
+    const long long a = launch_count();
+    const int rc = fn();
+    r.launches += launch_count() - a;
+    return rc;
+}
+
+template <typename T>
+int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) {
+    SolveRun r;
+    r.s = s; r.u = u; r.stats = stats;
+    if (int rc = staged(r, [&] { return run_begin<T>(h, r); })) return rc;
+    CK(cudaEventSynchronize(h->evA));
+    if (int rc = staged(r, [&] { return run_middle<T>(h, r); })) return rc;
+    while (r.stage == 2)
+        if (int rc = staged(r, [&] { return graph_poll<T>(h, r, true); })) return rc;
+    return staged(r, [&] { return run_finish<T>(h, r); });
 }
 
 }  // namespace
@@ -1090,6 +1210,7 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaEventCreate(&h->ev2)) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaEventCreateWithFlags(&h->evA, cudaEventDisableTiming)) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaMalloc(&h->dctl, sizeof(SweepCtl))) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaMallocHost(&h->hctl, sizeof(SweepCtl))) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaMallocHost(&h->hdone, 2 * sizeof(int))) != cudaSuccess) return fail(set_cuda_error(e));
@@ -1269,6 +1390,148 @@ int asdsm_profile_read(asdsm_handle* h, asdsm_kprof* out, int cap) {
 
 int64_t asdsm_launch_count(void) { return launch_count(); }
 
+// ---------------------------------------------------------------------------
+// Batches: independent instances on their own streams, advanced stage by
+// stage in turn so that their kernels overlap on the GPU.
+// ---------------------------------------------------------------------------
+struct asdsm_batch {
+    std::vector<asdsm_handle*> inst;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> ev_end;
+    cudaEvent_t ev_start = nullptr;
+    cudaStream_t caller = nullptr;
+};
+
+void asdsm_destroy_batch(asdsm_batch* b) {
+    if (!b) return;
+    for (auto* h : b->inst) asdsm_destroy(h);
+    for (auto st : b->streams) if (st) cudaStreamDestroy(st);
+    for (auto e : b->ev_end) if (e) cudaEventDestroy(e);
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    delete b;
+}
+
+int asdsm_setup_batch(const asdsm_desc* descs, int count, const asdsm_opts* opts, void* stream, asdsm_batch** out) {
+    if (!out) return ASDSM_ERR_INVALID;
+    *out = nullptr;
+    if (!descs || count < 1) return ASDSM_ERR_INVALID;
+    asdsm_batch* b = new asdsm_batch();
+    b->caller = (cudaStream_t)stream;
+    cudaError_t e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming);
+    if (e != cudaSuccess) { asdsm_destroy_batch(b); return set_cuda_error(e); }
+    for (int i = 0; i < count; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
+            asdsm_destroy_batch(b);
+            return set_cuda_error(e);
+        }
+        b->streams.push_back(st);
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            asdsm_destroy_batch(b);
+            return set_cuda_error(e);
+        }
+        b->ev_end.push_back(ev);
+        asdsm_handle* h = nullptr;
+        const int rc = asdsm_setup(&descs[i], opts, st, &h);
+        if (rc != ASDSM_OK) { asdsm_destroy_batch(b); return rc; }
+        b->inst.push_back(h);
+    }
+    *out = b;
+    return ASDSM_OK;
+}
+
+int asdsm_batch_count(const asdsm_batch* b) { return b ? (int)b->inst.size() : 0; }
+
+int asdsm_set_opts_batch(asdsm_batch* b, const asdsm_opts* opts) {
+    if (!b) return ASDSM_ERR_INVALID;
+    for (auto* h : b->inst)
+        if (int rc = asdsm_set_opts(h, opts)) return rc;
+    return ASDSM_OK;
+}
+
+int asdsm_autotune_batch(asdsm_batch* b, int precision) {
+    if (!b) return ASDSM_ERR_INVALID;
+    const int pi = precision == ASDSM_FP64 ? 0 : 1;
+    // Launch shapes depend on the sizes only: tune one instance per (N, mc) class.
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        asdsm_handle* h = b->inst[i];
+        asdsm_handle* src = nullptr;
+        for (size_t j = 0; j < i; ++j)
+            if (b->inst[j]->g.N == h->g.N && b->inst[j]->g.mc == h->g.mc) { src = b->inst[j]; break; }
+        if (!src) {
+            if (int rc = asdsm_autotune(h, precision)) return rc;
+        } else {
+            h->tune_aniso[pi] = src->tune_aniso[pi];
+            h->tune_cc[pi] = src->tune_cc[pi];
+            h->fill_warps[pi] = src->fill_warps[pi];
+            destroy_graph(h);
+        }
+    }
+    return ASDSM_OK;
+}
+
+}  // extern "C"
+namespace {
+template <typename T>
+int batch_stage_begin(asdsm_handle* h, SolveRun& r) { return staged(r, [&] { return run_begin<T>(h, r); }); }
+template <typename T>
+int batch_stage_middle(asdsm_handle* h, SolveRun& r) { return staged(r, [&] { return run_middle<T>(h, r); }); }
+template <typename T>
+int batch_stage_poll(asdsm_handle* h, SolveRun& r) { return staged(r, [&] { return graph_poll<T>(h, r, false); }); }
+template <typename T>
+int batch_stage_finish(asdsm_handle* h, SolveRun& r) { return staged(r, [&] { return run_finish<T>(h, r); }); }
+}  // namespace
+extern "C" {
+
+int asdsm_solve_batch(asdsm_batch* b, const double* const* s, double* const* u, asdsm_stats* stats) {
+    if (!b || !s || !u) return ASDSM_ERR_INVALID;
+    const size_t n = b->inst.size();
+    for (size_t i = 0; i < n; ++i)
+        if (!s[i] || !u[i]) return ASDSM_ERR_INVALID;
+    CK(cudaEventRecord(b->ev_start, b->caller));
+    for (size_t i = 0; i < n; ++i) CK(cudaStreamWaitEvent(b->streams[i], b->ev_start, 0));
+    std::vector<SolveRun> runs(n);
+    std::vector<int> rcs(n, ASDSM_OK);
+    auto is64 = [&](size_t i) { return b->inst[i]->opts.precision == ASDSM_FP64; };
+    for (size_t i = 0; i < n; ++i) {
+        runs[i].s = s[i]; runs[i].u = u[i]; runs[i].stats = stats ? &stats[i] : nullptr;
+        rcs[i] = is64(i) ? batch_stage_begin<double>(b->inst[i], runs[i]) : batch_stage_begin<float>(b->inst[i], runs[i]);
+    }
+    for (size_t i = 0; i < n; ++i) {
+        if (rcs[i] != ASDSM_OK) continue;
+        CK(cudaEventSynchronize(b->inst[i]->evA));
+        rcs[i] = is64(i) ? batch_stage_middle<double>(b->inst[i], runs[i]) : batch_stage_middle<float>(b->inst[i], runs[i]);
+    }
+    // Round-robin over the instances still sweeping; each poll launches up to
+    // two graph replays ahead and retires completed ones without blocking.
+    for (;;) {
+        bool any = false;
+        for (size_t i = 0; i < n; ++i) {
+            if (rcs[i] != ASDSM_OK || runs[i].stage != 2) continue;
+            any = true;
+            rcs[i] = is64(i) ? batch_stage_poll<double>(b->inst[i], runs[i]) : batch_stage_poll<float>(b->inst[i], runs[i]);
+        }
+        if (!any) break;
+    }
+    int worst = ASDSM_OK;
+    for (size_t i = 0; i < n; ++i) {
+        int rc = rcs[i];
+        if (rc == ASDSM_OK && runs[i].stage == 3)
+            rc = is64(i) ? batch_stage_finish<double>(b->inst[i], runs[i]) : batch_stage_finish<float>(b->inst[i], runs[i]);
+        else if (stats && rc != ASDSM_OK) { std::memset(&stats[i], 0, sizeof(asdsm_stats)); stats[i].status = rc; }
+        if (rc != ASDSM_OK && worst == ASDSM_OK) worst = rc;
+        CK(cudaEventRecord(b->ev_end[i], b->streams[i]));
+        CK(cudaStreamWaitEvent(b->caller, b->ev_end[i], 0));
+    }
+    return worst;
+}
+
+int asdsm_batch_history(const asdsm_batch* b, int index, double* out, int cap) {
+    if (!b || index < 0 || index >= (int)b->inst.size()) return ASDSM_ERR_INVALID;
+    return asdsm_history(b->inst[index], out, cap);
+}
+
 void asdsm_destroy(asdsm_handle* h) {
     if (!h) return;
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
@@ -1288,6 +1551,7 @@ void asdsm_destroy(asdsm_handle* h) {
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->ev2) cudaEventDestroy(h->ev2);
+    if (h->evA) cudaEventDestroy(h->evA);
     destroy_graph(h);
     fr(h->dctl); fr(h->dhist);
     if (h->hctl) cudaFreeHost(h->hctl);

@@ -165,3 +165,20 @@ def random_sine_3d(N: int, seed: int, beta_max: float = 5.0) -> Problem:
 def batch_sizes(count: int, seed: int, choices=(129, 257, 513, 1025, 2049)):
     rng = np.random.default_rng(seed)
     return [int(c) for c in rng.choice(np.asarray(choices), size=count)]
+
+
+def batch_hole(N: int) -> int:
+    """Hole size n (fine intervals per coarse interval) of a batch instance:
+    32, but at least 16 coarse intervals per axis on the small grids (with 4,
+    strongly advective 129 x 129 instances stagnate in FP64 and mixed alike)."""
+    return min(32, (N - 1) // 16)
+
+
+def batch_problems(count: int = 64, seed: int = 0, choices=(129, 257, 513, 1025, 2049), seed0: int = 1000):
+    """The uneven-size batch: sizes drawn from `choices`, instance i a
+    random-Fourier problem (random_fourier_2d with seed seed0 + i), and its
+    coarse interval count mc = (N - 1) / batch_hole(N)."""
+    sizes = batch_sizes(count, seed, choices)
+    probs = [random_fourier_2d(N, seed0 + i) for i, N in enumerate(sizes)]
+    mcs = [(N - 1) // batch_hole(N) for N in sizes]
+    return probs, mcs

@@ -1,0 +1,119 @@
+"""Batched solves (asdsm_setup_batch / asdsm_solve_batch) of uneven sizes.
+
+Every instance of a batch runs the kernels and decisions of a single
+asdsm_solve on the same inputs, only interleaved with the other instances on
+its own stream: the batch results are compared bit for bit with one-by-one
+solves, and against the oracle like any single solve.
+"""
+import numpy as np
+import pytest
+
+from oracle import asdsm2d as orc
+from paper_2303_01163_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_01163_gb300 import asdsm
+    return asdsm
+
+
+def _dev(a):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _relerr(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def _problems(sizes, seed0=100, hole=32):
+    return [wl.random_fourier_2d(N, seed0 + i) for i, N in enumerate(sizes)], [(N - 1) // hole for N in sizes]
+
+
+@pytest.mark.parametrize("prec_name", ["mixed", "fp64"])
+def test_batch_equals_single_solves_bitwise(lib, prec_name):
+    prec = lib.MIXED if prec_name == "mixed" else lib.FP64
+    sizes = [129, 65, 257, 129, 65, 513, 257]
+    probs, mcs = _problems(sizes)
+    kw = dict(precision=prec, tol=1e-10, max_sweeps=300, accel_m=8)
+    with lib.BatchSolver([(p.N, mc, p.alpha, p.beta) for p, mc in zip(probs, mcs)], **kw) as bs:
+        us = [_dev(p.g) for p in probs]
+        rc, stats = bs.solve([_dev(p.s) for p in probs], us)
+        got = [u.cpu().numpy() for u in us]
+        hists = [bs.history(i) for i in range(len(probs))]
+    singles = []
+    for i, (p, mc) in enumerate(zip(probs, mcs)):
+        with lib.Solver(p.N, mc, p.alpha, p.beta, **kw) as sv:
+            u = _dev(p.g)
+            res = sv.solve(_dev(p.s), u)
+        singles.append(res.status)
+        assert stats[i]["status"] == res.status
+        assert stats[i]["sweeps"] == res.stats["sweeps"]
+        assert np.array_equal(got[i], u.cpu().numpy()), i
+        assert hists[i] == res.history
+        assert stats[i]["launches"] > 0
+    assert rc == next((st for st in singles if st != lib.OK), lib.OK)
+
+
+def test_batch_instances_meet_the_parity_bars(lib):
+    sizes = [65, 129, 257]
+    probs, mcs = _problems(sizes, seed0=7)
+    with lib.BatchSolver([(p.N, mc, p.alpha, p.beta) for p, mc in zip(probs, mcs)], precision=lib.MIXED,
+                         tol=1e-10, max_sweeps=2000) as bs:
+        us = [_dev(p.g) for p in probs]
+        rc, stats = bs.solve([_dev(p.s) for p in probs], us)
+    assert rc == lib.OK
+    for p, mc, u in zip(probs, mcs, us):
+        U = u.cpu().numpy()
+        r, bb = orc.residual_grid(p.N, p.alpha, p.beta, p.s, U)
+        assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1e-10 * 1.01
+        disc = orc.Discretisation2D(p.N, mc, p.alpha, p.beta)
+        uff = disc.solve_fine(disc.rhs(p.s, p.g)[0])
+        assert _relerr(orc.interior(U), uff) <= 8 * (p.N - 1) ** 2 / np.pi**2 * 1e-10
+    # FP64 iterates of a fixed sweep count equal the oracle's
+    p, mc = probs[1], mcs[1]
+    disc = orc.Discretisation2D(p.N, mc, p.alpha, p.beta)
+    uo, info = orc.asdsm(disc, disc.rhs(p.s, p.g), tol=1e-30, max_sweeps=7, accel_m=4, seed=3, stagnation_window=10**9)
+    with lib.BatchSolver([(p.N, mc, p.alpha, p.beta)] * 2, precision=lib.FP64, tol=1e-30, max_sweeps=7, accel_m=4,
+                         seed=3, stagnation_window=0) as bs:
+        us = [_dev(p.g), _dev(p.g)]
+        bs.solve([_dev(p.s), _dev(p.s)], us)
+    for u in us:
+        assert _relerr(orc.interior(u.cpu().numpy()), uo) <= 1e-12
+
+
+def test_failing_instance_does_not_stop_the_others(lib):
+    import torch
+    sizes = [129, 129, 257]
+    probs, mcs = _problems(sizes, seed0=40)
+    with lib.BatchSolver([(p.N, mc, p.alpha, p.beta) for p, mc in zip(probs, mcs)], precision=lib.MIXED) as bs:
+        ss = [_dev(p.s) for p in probs]
+        ss[1][7, 9] = float("nan")
+        us = [_dev(p.g) for p in probs]
+        rc, stats = bs.solve(ss, us, check=False)
+    assert stats[1]["status"] == lib.ERR_NAN
+    for i in (0, 2):
+        assert stats[i]["status"] in (lib.OK, lib.NOT_CONVERGED, lib.STAGNATED)
+        assert stats[i]["sweeps"] > 0
+        assert torch.isfinite(us[i]).all()
+    assert rc == next(st["status"] for st in stats if st["status"] != lib.OK)
+
+
+def test_batch_autotune_per_size_class(lib):
+    sizes = wl.batch_sizes(6, 0, choices=(129, 257))
+    probs, mcs = _problems(sizes, seed0=60, hole=16)
+    with lib.BatchSolver([(p.N, mc, p.alpha, p.beta) for p, mc in zip(probs, mcs)], precision=lib.MIXED,
+                         max_sweeps=2000) as bs:
+        bs.autotune(lib.MIXED)
+        bs.autotune(lib.FP64)
+        us = [_dev(p.g) for p in probs]
+        rc, stats = bs.solve([_dev(p.s) for p in probs], us)
+    assert rc == lib.OK, [st["status"] for st in stats]
+    for p, u in zip(probs, us):
+        r, bb = orc.residual_grid(p.N, p.alpha, p.beta, p.s, u.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1e-10 * 1.01
