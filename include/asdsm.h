@@ -141,6 +141,13 @@ int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts);
  * stream; takes tens of milliseconds.  Returns ASDSM_OK or an error. */
 int asdsm_autotune(asdsm_handle* h, int precision);
 
+/* The handle's launch shapes (as chosen by asdsm_autotune, or 0 = built-in)
+ * as 130 integers, to save a tuning and apply it to another handle of the
+ * same sizes (asdsm_tune_set; n must be 130).  get returns the count written
+ * (cap >= 130) or ASDSM_ERR_INVALID. */
+int asdsm_tune_get(const asdsm_handle* h, int32_t* out, int cap);
+int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n);
+
 /* Algorithm 4 (ASDSM).  The initial guess (Algorithm 1) is computed in FP64 in
  * both precisions; the mixed path then runs its sweeps as described above.
  * s: device N*N source term (boundary entries unused).

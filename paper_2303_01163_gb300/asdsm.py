@@ -84,6 +84,10 @@ def load() -> ctypes.CDLL:
     lib.asdsm_set_opts.restype = ctypes.c_int
     lib.asdsm_autotune.argtypes = [P, ctypes.c_int]
     lib.asdsm_autotune.restype = ctypes.c_int
+    lib.asdsm_tune_get.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
+    lib.asdsm_tune_get.restype = ctypes.c_int
+    lib.asdsm_tune_set.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
+    lib.asdsm_tune_set.restype = ctypes.c_int
     lib.asdsm_solve.argtypes = [P, P, P, ctypes.POINTER(Stats)]
     lib.asdsm_solve.restype = ctypes.c_int
     lib.asdsm_initial_guess.argtypes = [P, P, P]
@@ -224,6 +228,19 @@ class Solver:
         rc = self._lib.asdsm_autotune(self._h, prec)
         if rc != OK:
             raise AsdsmError(rc, "asdsm_autotune")
+
+    def tune_state(self) -> list:
+        buf = (ctypes.c_int32 * 256)()
+        n = self._lib.asdsm_tune_get(self._h, buf, 256)
+        if n < 0:
+            raise AsdsmError(n, "asdsm_tune_get")
+        return [int(buf[i]) for i in range(n)]
+
+    def set_tune_state(self, values):
+        arr = (ctypes.c_int32 * len(values))(*values)
+        rc = self._lib.asdsm_tune_set(self._h, arr, len(values))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_tune_set")
 
     def solve(self, s, u, check: bool = True) -> SolveResult:
         st = Stats()

@@ -673,10 +673,16 @@ int tune_bcr(asdsm_handle* h, const BcrSys<T>* sys, int ngroups, BcrTune* tune, 
                             CK(bcr_level<T>(sys, ngroups, l, dir == 1, tune, h->st));
                             return ASDSM_OK;
                         })) return rc;
+                    if (std::getenv("ASDSM_TRACE"))
+                        std::fprintf(stderr, "asdsm tune: C=%d dir=%d level=%d tm=%d ks=%d  %.2f us\n", sys[0].C, dir, l,
+                                     tm, ks, ms * 1e3);
                     if (ms < best) { best = ms; bestv = tune->cfg[dir][l]; }
                 }
             }
             tune->cfg[dir][l] = bestv;
+            if (std::getenv("ASDSM_TRACE"))
+                std::fprintf(stderr, "asdsm tune: C=%d dir=%d level=%d chosen tm=%d ks=%d (%.2f us)\n", sys[0].C, dir, l,
+                             bestv >> 8, bestv & 0xFF, best * 1e3);
         }
     }
     return ASDSM_OK;
@@ -1151,6 +1157,8 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if (e != cudaSuccess) return fail(set_cuda_error(e));
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
     for (int q = 0; q < 2; ++q) { h->tune_aniso[q].num_sms = h->num_sms; h->tune_cc[q].num_sms = h->num_sms; }
+    if (std::getenv("ASDSM_TRACE_BCR"))
+        for (int q = 0; q < 2; ++q) { h->tune_aniso[q].trace = 1; h->tune_cc[q].trace = 1; }
     Geometry& g = h->g;
     g.N = (int)N; g.M = (int)(N - 1); g.Nf = (int)(N - 2); g.mc = (int)mc; g.Nc = (int)(mc - 1); g.n = (int)n;
     g.skel = (long long)g.Nc * g.Nf + (long long)g.Nc * (g.Nf - g.Nc);
@@ -1229,6 +1237,38 @@ int asdsm_autotune(asdsm_handle* h, int precision) {
     else if (precision == ASDSM_MIXED) rc = autotune_impl<float>(h);
     else return ASDSM_ERR_INVALID;
     return rc;
+}
+
+// Tuned launch shapes as plain integers: per precision (FP64 first), the
+// forward and backward level shapes of the anisotropic pair (2 x 16), of the
+// coarse system (2 x 16), then the Filler's warps per CTA.
+constexpr int kTuneInts = 2 * (4 * kMaxLevels + 1);
+
+int asdsm_tune_get(const asdsm_handle* h, int32_t* out, int cap) {
+    if (!h || !out || cap < kTuneInts) return ASDSM_ERR_INVALID;
+    int q = 0;
+    for (int pi = 0; pi < 2; ++pi) {
+        for (int d = 0; d < 2; ++d)
+            for (int l = 0; l < kMaxLevels; ++l) out[q++] = h->tune_aniso[pi].cfg[d][l];
+        for (int d = 0; d < 2; ++d)
+            for (int l = 0; l < kMaxLevels; ++l) out[q++] = h->tune_cc[pi].cfg[d][l];
+        out[q++] = h->fill_warps[pi];
+    }
+    return q;
+}
+
+int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n) {
+    if (!h || !in || n != kTuneInts) return ASDSM_ERR_INVALID;
+    int q = 0;
+    for (int pi = 0; pi < 2; ++pi) {
+        for (int d = 0; d < 2; ++d)
+            for (int l = 0; l < kMaxLevels; ++l) h->tune_aniso[pi].cfg[d][l] = in[q++];
+        for (int d = 0; d < 2; ++d)
+            for (int l = 0; l < kMaxLevels; ++l) h->tune_cc[pi].cfg[d][l] = in[q++];
+        h->fill_warps[pi] = in[q++];
+    }
+    destroy_graph(h);
+    return ASDSM_OK;
 }
 
 int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts) {

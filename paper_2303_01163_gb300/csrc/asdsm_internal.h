@@ -82,6 +82,7 @@ long long launch_count();
 struct BcrTune {
     int cfg[2][kMaxLevels];    // [0] forward, [1] backward
     int num_sms;
+    int trace;                 // print every launch shape (debugging)
 };
 // Block cyclic reduction of up to 2 factor groups (e.g. the fc and cf families).
 template <typename T>

@@ -24,6 +24,7 @@
 #include "asdsm_internal.h"
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
+#include <cstdio>
 
 namespace cg = cooperative_groups;
 
@@ -93,10 +94,21 @@ bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
     const int nk = (C + GT_K - 1) / GT_K;        // slices per factor pass
     const int total = (kBackward ? 2 : 1) * nk;
     T av[A_PER_T], fv[F_PER_T];
-    auto load_slice = [&](int q) {
-        const int pass = kBackward ? q / nk : 1;  // 0: B^{-1} f_i, 1: -M v_i
+    auto load_factor = [&](int q) {
+        const int pass = kBackward ? q / nk : 1;
         const int k0 = (q % nk) * GT_K;
         const T* Fm = pass == 0 ? Bt : Mt;
+#pragma unroll
+        for (int j = 0; j < F_PER_T; ++j) {
+            const int e = tid + j * GT_THREADS;
+            const int kk = e / GT_N, cc = e % GT_N;
+            const int k = k0 + kk, c = c0 + cc;
+            fv[j] = (k < C && c < C) ? __ldg(Fm + (size_t)k * C + c) : T(0);
+        }
+    };
+    auto load_rows = [&](int q) {
+        const int pass = kBackward ? q / nk : 1;  // 0: B^{-1} f_i, 1: -M v_i
+        const int k0 = (q % nk) * GT_K;
 #pragma unroll
         for (int j = 0; j < A_PER_T; ++j) {
             const int e = tid + j * GT_THREADS;
@@ -115,15 +127,14 @@ bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
             }
             av[j] = v;
         }
-#pragma unroll
-        for (int j = 0; j < F_PER_T; ++j) {
-            const int e = tid + j * GT_THREADS;
-            const int kk = e / GT_N, cc = e % GT_N;
-            const int k = k0 + kk, c = c0 + cc;
-            fv[j] = (k < C && c < C) ? __ldg(Fm + (size_t)k * C + c) : T(0);
-        }
     };
-    if (tile_ok && rank < total) load_slice(rank);
+    // Programmatic dependent launch: the next level may start launching now;
+    // this one prefetches its first factor slice (constant data) and then
+    // waits, in every CTA, for the grids it depends on before reading rows.
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (tile_ok && rank < total) load_factor(rank);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (tile_ok && rank < total) load_rows(rank);
     for (int q = rank; tile_ok && q < total; q += KS) {
         __syncthreads();                          // the previous slice has been used
 #pragma unroll
@@ -137,7 +148,7 @@ bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
             Fs[e / GT_N][e % GT_N] = fv[j];
         }
         __syncthreads();
-        if (q + KS < total) load_slice(q + KS);
+        if (q + KS < total) { load_factor(q + KS); load_rows(q + KS); }
 #pragma unroll 8
         for (int kk = 0; kk < GT_K; ++kk) {
             T a_[RPT], b_[4];
@@ -214,13 +225,15 @@ cudaError_t launch_variant(dim3 grid, const BcrSys<T>& g0, const BcrSys<T>& g1, 
     cfg.blockDim = dim3(GT_THREADS);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = KS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = KS;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = KS > 1 ? 1 : 0;
+    cfg.numAttrs = KS > 1 ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, bcr_level_kernel<T, kBackward, TM, KS>, g0, g1, ngroups, level);
 }
 
@@ -266,6 +279,9 @@ cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, const 
         while (ks < 8 && tiles * ks < target && 2 * ks <= chunks) ks *= 2;
     }
     if (ks > chunks) ks = 1;
+    if (tune && tune->trace)
+        std::fprintf(stderr, "asdsm bcr: bwd=%d level=%d rows=%d C=%d tm=%d ks=%d (table %d)\n", kBackward ? 1 : 0, level,
+                     maxRows, maxC, tm, ks, tune->cfg[kBackward ? 1 : 0][level]);
     dim3 grid(ctiles, (maxRows + tm - 1) / tm, nsys);
     cudaError_t e = tm == 64 ? launch_ks<T, kBackward, 64>(ks, grid, groups[0], g1, ngroups, level, st)
                              : launch_ks<T, kBackward, 16>(ks, grid, groups[0], g1, ngroups, level, st);
