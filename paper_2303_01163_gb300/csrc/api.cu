@@ -35,6 +35,8 @@ constexpr int kMaxM = 16;
 
 struct DevBcr {
     void* Mt = nullptr; void* Bt = nullptr;
+    void* Mw = nullptr; void* Bw = nullptr;      // FP32: wide tensor-core layout (BcrSys)
+    int KW = 0, CW = 0;
     double wl[kMaxLevels] = {}, wr[kMaxLevels] = {};
     int R = 0, C = 0, L = 0;
 };
@@ -144,6 +146,24 @@ int upload_bcr(const BcrFactors& f, DevBcr* d) {
     }
     for (int l = 0; l < f.L; ++l) { d->wl[l] = f.wl[l]; d->wr[l] = f.wr[l]; }
     d->R = f.R; d->C = f.C; d->L = f.L;
+    if (sizeof(T) == 4) {
+        // Padded, chunk-swizzled copies for the wide tensor-core level kernel.
+        const int C = f.C, KW = (C + 31) / 32 * 32, CW = (C + 255) / 256 * 256;
+        std::vector<float> wide((size_t)f.L * KW * CW);
+        void** wdst[2] = {&d->Mw, &d->Bw};
+        for (int q = 0; q < 2; ++q) {
+            std::fill(wide.begin(), wide.end(), 0.0f);
+            for (int l = 0; l < f.L; ++l)
+                for (int k = 0; k < C; ++k)
+                    for (int c = 0; c < C; ++c) {
+                        const int pos = (((c >> 2) ^ (2 * (k & 3))) << 2) | (c & 3);
+                        wide[((size_t)l * KW + k) * CW + pos] = (float)(*src[q])[((size_t)l * C + k) * C + c];
+                    }
+            CK(cudaMalloc(wdst[q], wide.size() * sizeof(float)));
+            CK(cudaMemcpy(*wdst[q], wide.data(), wide.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+        d->KW = KW; d->CW = CW;
+    }
     return ASDSM_OK;
 }
 
@@ -163,6 +183,8 @@ BcrSys<T> sys_of(const DevBcr& d, void* X, void* Y, int nsys = 1) {
     for (int l = 0; l < d.L; ++l) { s.wl[l] = (T)d.wl[l]; s.wr[l] = (T)d.wr[l]; }
     s.R = d.R; s.C = d.C; s.L = d.L; s.nsys = nsys;
     s.stride = (long long)d.R * d.C;
+    s.Mw = (const float*)d.Mw; s.Bw = (const float*)d.Bw;
+    s.KW = d.KW; s.CW = d.CW;
     return s;
 }
 
@@ -665,8 +687,10 @@ int tune_bcr(asdsm_handle* h, const BcrSys<T>* sys, int ngroups, BcrTune* tune, 
         for (int l = 0; l < (dir ? L : L - 1); ++l) {
             float best = 1e30f;
             int bestv = 0;
-            for (int tm : {64, 16}) {
+            for (int tm : {64, 16, 32}) {
+                if (tm == 32 && (sizeof(T) != 4 || !sys[0].Mw)) continue;
                 for (int ks : {1, 2, 4, 8}) {
+                    if (tm == 32 && ks != 1) continue;
                     tune->cfg[dir][l] = (tm << 8) | ks;
                     float ms = 0.f;
                     if (int rc = time_ms<T>(h, a, b, 5, &ms, [&]() -> int {
@@ -1578,7 +1602,7 @@ void asdsm_destroy(asdsm_handle* h) {
     auto fr = [](void* p) { if (p) cudaFree(p); };
     for (int p = 0; p < 2; ++p) {
         DevBcr* ds[4] = {&h->fc[p], &h->cf[p], &h->cc[p], &h->hole[p]};
-        for (auto* d : ds) { fr(d->Mt); fr(d->Bt); }
+        for (auto* d : ds) { fr(d->Mt); fr(d->Bt); fr(d->Mw); fr(d->Bw); }
         fr(h->Sm[p]);
         auto& w = h->w[p];
         void* bufs[] = {w.Xfc, w.Xcf, w.Yfc, w.Ycf, w.Xcc, w.Ycc, w.E1, w.E2, w.M1, w.M2, w.rskel, w.q, w.rfull};

@@ -51,6 +51,13 @@ struct BcrSys {
     int R, C, L;
     int nsys;          // systems sharing these factors
     long long stride;  // elements between consecutive systems
+    // FP32 only: the factors again for the wide tensor-core level kernel,
+    // [L][KW][CW] (rows padded to KW = 32-multiple, columns to CW = 256-multiple,
+    // zeros outside C x C), 16-byte column chunks XOR-swizzled within groups of
+    // 8 by 2*(k mod 4): element (k, c) at column ((c/4) ^ (2 (k mod 4))) * 4 + c mod 4.
+    const float* Mw;
+    const float* Bw;
+    int KW, CW;
 };
 
 // Stencil coefficients of A_ff (5-point, Section 2.3): A u = cc u_c + cw u_w + ce u_e + cs u_s + cn u_n.
@@ -78,7 +85,8 @@ long long launch_count();
 // ---------------------------------------------------------------------------
 // Launch shape of every BCR level: cfg[dir][level] = (TM << 8) | KS with TM
 // in {16, 64} output rows per CTA and KS in {1, 2, 4, 8} CTAs per cluster
-// splitting the reduction; 0 (or no table) = the built-in choice.
+// splitting the reduction, or TM = 32: the wide tensor-core kernel (FP32, 32
+// rows x 256 columns per CTA, KS = 1); 0 (or no table) = the built-in choice.
 struct BcrTune {
     int cfg[2][kMaxLevels];    // [0] forward, [1] backward
     int num_sms;

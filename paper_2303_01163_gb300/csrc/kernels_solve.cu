@@ -32,33 +32,95 @@ namespace asdsm {
 
 namespace {
 
+#ifndef ASDSM_SPLITK_TC
+#define ASDSM_SPLITK_TC 0
+#endif
 constexpr int GT_N = 64;       // output columns per tile
 constexpr int GT_K = 32;       // reduction slice
 constexpr int GT_THREADS = 128;
 
+// Tensor-core step for the FP32 level GEMM: mma.sync m16n8k8 on TF32
+// operands, each FP32 value split as hi = tf32(x), lo = tf32(x - hi) and the
+// product formed as lo*hi + hi*lo + hi*hi (the lo*lo term, ~2^-22 relative, is
+// dropped), accumulating in FP32.  Warp w owns rows 32(w/2) .. +32 and columns
+// 32(w%2) .. +32 of the 64 x 64 tile: 2 x 4 fragments of 16 x 8.
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+    unsigned h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float r = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+    hi = h;
+    lo = l;
+}
+
+__device__ __forceinline__ void mma_tf32(float* d, const unsigned* a, unsigned b0, unsigned b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// As: [k][row] with row stride AW, Fs: [k][col] with row stride FW; k0 the
+// first of the 8 reduction indices of this step.
+template <int AW, int FW>
+__device__ __forceinline__ void tc_step(const float* As, const float* Fs, int k0, int tid, float (*acc)[4]) {
+    const int lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int rb = (warp >> 1) * 32, cb = (warp & 1) * 32;
+    unsigned ah[2][4], al[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int r = rb + i * 16 + g;
+        // A fragment (16 x 8, row major): (g, q), (g+8, q), (g, q+4), (g+8, q+4)
+        split_tf32(As[(k0 + q) * AW + r], ah[i][0], al[i][0]);
+        split_tf32(As[(k0 + q) * AW + r + 8], ah[i][1], al[i][1]);
+        split_tf32(As[(k0 + q + 4) * AW + r], ah[i][2], al[i][2]);
+        split_tf32(As[(k0 + q + 4) * AW + r + 8], ah[i][3], al[i][3]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = cb + j * 8 + g;
+        // B fragment (8 x 8, column major): (k = q, n = g), (k = q+4, n = g)
+        unsigned bh0, bl0, bh1, bl1;
+        split_tf32(Fs[(k0 + q) * FW + c], bh0, bl0);
+        split_tf32(Fs[(k0 + q + 4) * FW + c], bh1, bl1);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            float* d = acc[i * 4 + j];
+            mma_tf32(d, al[i], bh0, bh1);
+            mma_tf32(d, ah[i], bl0, bl1);
+            mma_tf32(d, ah[i], bh0, bh1);
+        }
+    }
+}
+
 // One BCR level as a GEMM: out[t][c] = sum_k A[t][k] F[k][c], the reduction
 // running over one factor (forward: -M (wl f_{i-s} + wr f_{i+s})) or two
 // (backward: B^{-1} f_i, then -M (wl x_{i-s} + wr x_{i+s})), i.e. K' = C or 2C.
-// A CTA computes a TM x 64 output tile, 8 x 4 (TM = 64) or 2 x 4 (TM = 16)
-// outputs per thread, walking 32-wide slices of K' staged in shared memory;
+// A CTA computes a TM x 64 output tile (FP32, TM = 64: on the tensor cores,
+// tc_step; otherwise 8 x 4 or 2 x 4 outputs per thread on the FMA pipes),
+// walking 32-wide slices of K' staged in shared memory;
 // the next slice is loaded into registers while the current one is used.
 // With KS > 1 a thread-block cluster of KS CTAs shares the tile: CTA r takes
 // the slices r, r+KS, ..., keeps its partial tile in shared memory and, after
 // a cluster barrier, sums 1/KS of the tile over the KS partials in rank order
 // (deterministic) and writes it.
 template <typename T, bool kBackward, int TM, int KS>
-__global__ void __launch_bounds__(GT_THREADS, sizeof(T) == 4 ? 5 : 2)
+__global__ void __launch_bounds__(GT_THREADS, sizeof(T) == 4 ? (TM == 64 ? 4 : 5) : 2)
 bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
-    constexpr int RPT = TM / 8;                        // output rows per thread
+    // The split-K tiles stay on the FMA pipes (full FP32 products); the
+    // tensor-core path of tc_step is kept for comparison and off by default.
+    constexpr bool kTC = sizeof(T) == 4 && TM == 64 && ASDSM_SPLITK_TC;
+    constexpr int RPT = TM / 8;                        // output rows per thread (32 or 8 accumulators)
     constexpr int A_PER_T = TM * GT_K / GT_THREADS;    // A-slice elements per thread
     constexpr int F_PER_T = GT_K * GT_N / GT_THREADS;  // factor-slice elements per thread
+    constexpr int FSW = kTC ? GT_N + 8 : GT_N;         // padded factor rows: conflict-free fragment loads
     // The slices As [k][row], Fs [k][col] and, after the reduction loop, the
     // partial tile Part [row][col] share one buffer (Part fits in As + Fs).
-    constexpr int AS_ELEMS = GT_K * (TM + 4), FS_ELEMS = GT_K * GT_N;
+    constexpr int AS_ELEMS = GT_K * (TM + 4), FS_ELEMS = GT_K * FSW;
     static_assert(TM * GT_N <= AS_ELEMS + FS_ELEMS, "partial tile must fit in the slice buffers");
     __shared__ __align__(16) T smem_buf[AS_ELEMS + FS_ELEMS];
     T (*As)[TM + 4] = reinterpret_cast<T (*)[TM + 4]>(smem_buf);
-    T (*Fs)[GT_N] = reinterpret_cast<T (*)[GT_N]>(smem_buf + AS_ELEMS);
+    T (*Fs)[FSW] = reinterpret_cast<T (*)[FSW]>(smem_buf + AS_ELEMS);
     T* Part = smem_buf;
     int rank = 0;
     if constexpr (KS > 1) rank = (int)cg::this_cluster().block_rank();
@@ -149,6 +211,11 @@ bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
         }
         __syncthreads();
         if (q + KS < total) { load_factor(q + KS); load_rows(q + KS); }
+        if constexpr (kTC) {
+#pragma unroll
+            for (int ks = 0; ks < GT_K / 8; ++ks)
+                tc_step<TM + 4, FSW>(&As[0][0], &Fs[0][0], ks * 8, tid, acc);
+        } else {
 #pragma unroll 8
         for (int kk = 0; kk < GT_K; ++kk) {
             T a_[RPT], b_[4];
@@ -176,16 +243,29 @@ bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] += a_[a] * b_[b];
         }
+        }
     }
+    // Position in the tile of accumulator acc[a][b].
+    auto tile_pos = [&](int a, int b, int& r, int& c) {
+        if constexpr (kTC) {
+            const int lane = tid & 31, warp = tid >> 5;
+            r = (warp >> 1) * 32 + (a >> 2) * 16 + (lane >> 2) + ((b >> 1) << 3);
+            c = (warp & 1) * 32 + (a & 3) * 8 + 2 * (lane & 3) + (b & 1);
+        } else {
+            r = ty * RPT + a;
+            c = tx * 4 + b;
+        }
+    };
     if constexpr (KS == 1) {
-        for (int a = 0; tile_ok && a < RPT; ++a) {
-            const int t = t0 + ty * RPT + a;
-            if (t >= nrows) continue;
-            const int i = kBackward ? s * (2 * t + 1) : 2 * s * (t + 1);
+#pragma unroll
+        for (int a = 0; a < RPT; ++a) {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int c = c0 + tx * 4 + b;
-                if (c >= C) continue;
+                int r, cc;
+                tile_pos(a, b, r, cc);
+                const int t = t0 + r, c = c0 + cc;
+                if (!tile_ok || t >= nrows || c >= C) continue;
+                const int i = kBackward ? s * (2 * t + 1) : 2 * s * (t + 1);
                 if (kBackward) Y[(size_t)(i - 1) * C + c] = acc[a][b];
                 else X[(size_t)(i - 1) * C + c] += acc[a][b];
             }
@@ -196,7 +276,11 @@ bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
 #pragma unroll
         for (int a = 0; a < RPT; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) Part[(ty * RPT + a) * GT_N + tx * 4 + b] = acc[a][b];
+            for (int b = 0; b < 4; ++b) {
+                int r, cc;
+                tile_pos(a, b, r, cc);
+                Part[r * GT_N + cc] = acc[a][b];
+            }
         cluster.sync();
         // Rank r reduces elements [r*TM*64/KS, (r+1)*TM*64/KS) of the tile over the partials.
         constexpr int SLICE = TM * GT_N / KS;
@@ -214,6 +298,210 @@ bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
         }
         cluster.sync();          // partial tiles stay alive until every CTA has read them
     }
+}
+
+// ---------------------------------------------------------------------------
+// Wide tensor-core level kernel (FP32): a CTA of 8 warps owns 32 rows x 256
+// columns of a level's output, so one wave covers the big levels without
+// splitting the reduction.  Each 32-wide reduction slice - the factor slice
+// (32 x 256, from the padded, swizzled copy in BcrSys::Mw/Bw, 16-byte
+// copies) and the raw neighbour rows it multiplies (4-byte copies) - streams
+// through a 4-stage shared-memory ring by cp.async, three slices ahead: each
+// thread waits for its own copies, then a CTA barrier publishes the slice.
+// The row combination -(wl x_{i-s} + wr x_{i+s}) is formed when the A
+// fragments are read; products by the TF32 split (3 mma.sync per fragment).
+// ---------------------------------------------------------------------------
+constexpr int WD_ROWS = 32, WD_COLS = 256, WD_THREADS = 256, WD_STAGES = 4;
+constexpr int WD_AW = WD_ROWS + 4;     // row stride of the [k][row] slices
+constexpr int WD_STAGE_F = GT_K * WD_COLS;           // floats of a factor slice
+constexpr int WD_STAGE_A = GT_K * WD_AW;             // floats of one row slice
+constexpr int WD_STAGE = WD_STAGE_F + 2 * WD_STAGE_A;
+constexpr size_t wd_smem_bytes() { return sizeof(float) * (size_t)WD_STAGES * WD_STAGE; }
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4f(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit_w() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_w() { asm volatile("cp.async.wait_group %0;\n" ::"n"(WD_STAGES - 1) : "memory"); }
+
+// Column of element (k, c) in the swizzled factor rows.
+__device__ __forceinline__ int wd_swz(int k, int c) { return (((c >> 2) ^ (2 * (k & 3))) << 2) | (c & 3); }
+
+// A element (row r, reduction index kk) of the slice: the row itself (pass 0)
+// or -(wl x_{i-s} + wr x_{i+s}) (pass 1).
+__device__ __forceinline__ float wd_a(const float* R1, const float* R2, int kk, int r, bool combine, float wl, float wr) {
+    const float a = R1[kk * WD_AW + r];
+    if (!combine) return a;
+    return -(wl * a + wr * R2[kk * WD_AW + r]);
+}
+
+// 32 rows (2 fragments) x this warp's 32 columns (4 fragments), 8 reduction indices.
+__device__ __forceinline__ void tc_step_wide(const float* R1, const float* R2, bool combine, float wl, float wr,
+                                             const float* Fs, int k0, int tid, float (*acc)[4]) {
+    const int lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int cb = warp * 32;
+    unsigned ah[2][4], al[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int r = i * 16 + g;
+        split_tf32(wd_a(R1, R2, k0 + q, r, combine, wl, wr), ah[i][0], al[i][0]);
+        split_tf32(wd_a(R1, R2, k0 + q, r + 8, combine, wl, wr), ah[i][1], al[i][1]);
+        split_tf32(wd_a(R1, R2, k0 + q + 4, r, combine, wl, wr), ah[i][2], al[i][2]);
+        split_tf32(wd_a(R1, R2, k0 + q + 4, r + 8, combine, wl, wr), ah[i][3], al[i][3]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = cb + j * 8 + g;
+        unsigned bh0, bl0, bh1, bl1;
+        split_tf32(Fs[(k0 + q) * WD_COLS + wd_swz(k0 + q, c)], bh0, bl0);
+        split_tf32(Fs[(k0 + q + 4) * WD_COLS + wd_swz(k0 + q + 4, c)], bh1, bl1);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            float* d = acc[i * 4 + j];
+            mma_tf32(d, al[i], bh0, bh1);
+            mma_tf32(d, ah[i], bl0, bl1);
+            mma_tf32(d, ah[i], bh0, bh1);
+        }
+    }
+}
+
+template <bool kBackward>
+__global__ void __launch_bounds__(WD_THREADS, 1)
+bcr_level_wide_kernel(BcrSys<float> g0, BcrSys<float> g1, int ngroups, int level) {
+    extern __shared__ __align__(16) float wsm[];
+    int z = blockIdx.z;
+    const BcrSys<float>* gp = &g0;
+    if (ngroups > 1 && z >= g0.nsys) { gp = &g1; z -= g0.nsys; }
+    const BcrSys<float>& g = *gp;
+    const bool active = z < g.nsys && level < g.L;
+    const int R = g.R, C = g.C, KW = g.KW, CW = g.CW;
+    const int s = 1 << level;
+    const int nrows = active ? (kBackward ? ((R + 1) >> (level + 1)) : (((R + 1) >> (level + 1)) - 1)) : 0;
+    const int t0 = blockIdx.y * WD_ROWS;
+    const int c0 = blockIdx.x * WD_COLS;
+    const bool tile_ok = active && t0 < nrows && c0 < C;
+    const size_t lw = (size_t)KW * CW;
+    const float* Mw = g.Mw + (size_t)(active ? level : 0) * lw;
+    const float* Bw = g.Bw + (size_t)(active ? level : 0) * lw;
+    const float wl = active ? g.wl[level] : 0.0f, wr = active ? g.wr[level] : 0.0f;
+    float* X = g.X + (size_t)(active ? z : 0) * g.stride;
+    float* Y = g.Y + (size_t)(active ? z : 0) * g.stride;
+    const float* nb = kBackward ? Y : X;
+    const int tid = threadIdx.x;
+    const int nk = KW / GT_K;
+    const int total = (kBackward ? 2 : 1) * nk;
+    float acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+
+    auto stage_of = [&](int q) { return wsm + (size_t)(q % WD_STAGES) * WD_STAGE; };
+    auto issue_factor = [&](int q) {
+        const int pass = kBackward ? q / nk : 1;
+        const int k0 = (q % nk) * GT_K;
+        const float* Fm = pass == 0 ? Bw : Mw;
+        float* dst = stage_of(q);
+#pragma unroll
+        for (int j = 0; j < GT_K * WD_COLS / 4 / WD_THREADS; ++j) {      // 8 chunks of 16 B per thread
+            const int e = tid + j * WD_THREADS;
+            const int kk = e / (WD_COLS / 4), ch = e % (WD_COLS / 4);
+            cp_async16(dst + kk * WD_COLS + ch * 4, Fm + (size_t)(k0 + kk) * CW + c0 + ch * 4);
+        }
+    };
+    // Raw rows of slice q: R1 = x_i (pass 0) or x_{i-s} (pass 1), R2 = x_{i+s}; zero where absent.
+    auto issue_rows = [&](int q) {
+        const int pass = kBackward ? q / nk : 1;
+        const int k0 = (q % nk) * GT_K;
+        float* R1 = stage_of(q) + WD_STAGE_F;
+        float* R2 = R1 + WD_STAGE_A;
+#pragma unroll
+        for (int j = 0; j < WD_ROWS * GT_K / WD_THREADS; ++j) {          // 4 elements per thread
+            const int e = tid + j * WD_THREADS;
+            const int r = e / GT_K, kk = e % GT_K;
+            const int t = t0 + r, k = k0 + kk;
+            float* d1 = R1 + kk * WD_AW + r;
+            float* d2 = R2 + kk * WD_AW + r;
+            const bool ok = t < nrows && k < C;
+            const int i = kBackward ? s * (2 * t + 1) : 2 * s * (t + 1);
+            if (pass == 0) {
+                if (ok) cp_async4f(d1, X + (size_t)(i - 1) * C + k);
+                else *d1 = 0.0f;
+            } else {
+                if (ok && i - s >= 1) cp_async4f(d1, nb + (size_t)(i - s - 1) * C + k);
+                else *d1 = 0.0f;
+                if (ok && i + s <= R) cp_async4f(d2, nb + (size_t)(i + s - 1) * C + k);
+                else *d2 = 0.0f;
+            }
+        }
+    };
+    // Programmatic dependent launch: the first two factor slices (constant
+    // data) are requested before waiting for the grids this one depends on.
+    // Slices 0 .. WD_STAGES-2 are in flight before the loop (factor slices
+    // first, one group; then one group of rows per slice); the loop issues
+    // slice q + WD_STAGES - 1 and waits for slice q.
+    asm volatile("griddepcontrol.launch_dependents;");
+    for (int q = 0; tile_ok && q < WD_STAGES - 1 && q < total; ++q) issue_factor(q);
+    cp_commit_w();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int q = 0; q < WD_STAGES - 1; ++q) {
+        if (tile_ok && q < total) issue_rows(q);
+        cp_commit_w();
+    }
+    for (int q = 0; tile_ok && q < total; ++q) {
+        const int qn = q + WD_STAGES - 1;
+        if (qn < total) { issue_factor(qn); issue_rows(qn); }          // its stage was released last iteration
+        cp_commit_w();
+        cp_wait_w();                                                   // this thread's copies of slice q landed
+        __syncthreads();                                               // everyone's copies of slice q visible
+        const float* st = stage_of(q);
+        const float* R1 = st + WD_STAGE_F;
+        const float* R2 = R1 + WD_STAGE_A;
+        const bool combine = !(kBackward && q < nk);
+#pragma unroll
+        for (int ks = 0; ks < GT_K / 8; ++ks) tc_step_wide(R1, R2, combine, wl, wr, st, ks * 8, tid, acc);
+        __syncthreads();                                               // slice q's stage is free
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int r = (a >> 2) * 16 + (lane >> 2) + ((b >> 1) << 3);
+            const int cc = warp * 32 + (a & 3) * 8 + 2 * (lane & 3) + (b & 1);
+            const int t = t0 + r, c = c0 + cc;
+            if (!tile_ok || t >= nrows || c >= C) continue;
+            const int i = kBackward ? s * (2 * t + 1) : 2 * s * (t + 1);
+            if (kBackward) Y[(size_t)(i - 1) * C + c] = acc[a][b];
+            else X[(size_t)(i - 1) * C + c] += acc[a][b];
+        }
+    }
+}
+
+template <bool kBackward>
+cudaError_t launch_wide(dim3 grid, const BcrSys<float>& g0, const BcrSys<float>& g1, int ngroups, int level,
+                        cudaStream_t st) {
+    const size_t smem = wd_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(bcr_level_wide_kernel<kBackward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(WD_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bcr_level_wide_kernel<kBackward>, g0, g1, ngroups, level);
 }
 
 template <typename T, bool kBackward, int TM, int KS>
@@ -269,6 +557,20 @@ cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, const 
         const int v = tune->cfg[kBackward ? 1 : 0][level];
         tm = v >> 8;
         ks = v & 0xFF;
+    }
+    bool wide_ok = sizeof(T) == 4;
+    for (int q = 0; q < ngroups; ++q) wide_ok = wide_ok && groups[q].Mw && groups[q].Bw;
+    if (tm == 32 && wide_ok) {
+        int CW = groups[0].CW;
+        dim3 grid(CW / WD_COLS, (maxRows + WD_ROWS - 1) / WD_ROWS, nsys);
+        cudaError_t e = cudaSuccess;
+        if constexpr (sizeof(T) == 4) {
+            e = launch_wide<kBackward>(grid, reinterpret_cast<const BcrSys<float>&>(groups[0]),
+                                       reinterpret_cast<const BcrSys<float>&>(g1), ngroups, level, st);
+        }
+        note_launch();
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
     }
     if (tm != 16 && tm != 64) tm = maxRows >= 48 ? 64 : 16;
     if (ks != 1 && ks != 2 && ks != 4 && ks != 8) {
