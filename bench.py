@@ -368,6 +368,14 @@ def run_ours(args):
 
     roof = roofline_of(name, f)
     roof_resid = roofline_of("residual", prof["residual"])
+    # DRAM traffic per launch from the committed ncu capture (profiles/), where one exists.
+    tpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "ncu_traffic_4097_mixed.json")
+    if N == N_GRID and mc == MC and os.path.exists(tpath):
+        with open(tpath) as tf:
+            traffic = json.load(tf)
+        for rl in (roof, roof_resid):
+            if rl["kernel"] in traffic:
+                rl["traffic"] = traffic[rl["kernel"]]["traffic_bytes_per_launch"]
     total_prof_ms = sum(v["ms"] for v in prof.values())
     shares = {k: round(v["ms"] / total_prof_ms, 4) for k, v in prof.items() if v["ms"] > 0}
 

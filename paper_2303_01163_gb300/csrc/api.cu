@@ -1374,7 +1374,7 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
             } else {
                 CK(cudaMemcpyAsync(X, in, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
             }
-            CK(bcr_solve<double>(&s, 1, st));
+            CK(bcr_solve<double>(&s, 1, st, mesh == 2 ? &h->tune_cc[0] : &h->tune_aniso[0]));
             if (mesh == 0) {
                 std::vector<double> hy(n), hout(n);
                 CK(cudaMemcpy(hy.data(), Y, n * sizeof(double), cudaMemcpyDeviceToHost));
@@ -1396,7 +1396,7 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
             }
             std::vector<float> hf(hx.begin(), hx.end());
             CK(cudaMemcpy(X, hf.data(), n * sizeof(float), cudaMemcpyHostToDevice));
-            CK(bcr_solve<float>(&s, 1, st));
+            CK(bcr_solve<float>(&s, 1, st, mesh == 2 ? &h->tune_cc[1] : &h->tune_aniso[1]));
             CK(cudaMemcpy(hf.data(), Y, n * sizeof(float), cudaMemcpyDeviceToHost));
             std::vector<double> hout(n);
             if (mesh == 0) {

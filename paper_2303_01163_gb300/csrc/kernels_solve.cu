@@ -312,7 +312,7 @@ bcr_level_kernel(BcrSys<T> g0, BcrSys<T> g1, int ngroups, int level) {
 // fragments are read; products by the TF32 split (3 mma.sync per fragment).
 // ---------------------------------------------------------------------------
 constexpr int WD_ROWS = 32, WD_COLS = 256, WD_THREADS = 256, WD_STAGES = 4;
-constexpr int WD_AW = WD_ROWS + 4;     // row stride of the [k][row] slices
+constexpr int WD_AW = WD_ROWS + 8;     // row stride of the [k][row] slices (= 8 mod 32: conflict-free fragments)
 constexpr int WD_STAGE_F = GT_K * WD_COLS;           // floats of a factor slice
 constexpr int WD_STAGE_A = GT_K * WD_AW;             // floats of one row slice
 constexpr int WD_STAGE = WD_STAGE_F + 2 * WD_STAGE_A;

@@ -256,3 +256,35 @@ def test_resume_from_a_given_iterate(lib):
             r2 = sv.solve(_dev(p.s), u)
             assert r2.status == lib.OK
             assert r2.stats["rel_res0"] <= r1.stats["rel_res"] * 1.5
+
+
+@pytest.mark.parametrize("name,make,mc", CASES[:3] + [("fourier257", lambda: wl.random_fourier_2d(257, 5), 8)])
+def test_tensor_core_level_kernels_match_oracle(lib, name, make, mc):
+    """Every level of the FP32 anisotropic solves forced onto the wide
+    tensor-core kernel (TF32 split products): A_fc^-1 and A_cf^-1 within the
+    FP32 bar, and a mixed solve still reaches the fine solution."""
+    import torch
+    p = make()
+    disc = orc.Discretisation2D(p.N, mc, p.alpha, p.beta)
+    m = disc.m
+    rng = np.random.default_rng(3)
+    with lib.Solver(p.N, mc, p.alpha, p.beta, precision=lib.MIXED, tol=1e-10, max_sweeps=600) as sv:
+        state = sv.tune_state()
+        # layout: per precision [aniso fwd 16, aniso bwd 16, cc fwd 16, cc bwd 16, fill]; FP32 second
+        base = 4 * 16 + 1
+        for q in range(32):
+            state[base + q] = (32 << 8) | 1
+        sv.set_tune_state(state)
+        for mesh, size, lu in ((lib.MESH_FC, m.Nc * m.Nf, disc.lu_fc), (lib.MESH_CF, m.Nc * m.Nf, disc.lu_cf)):
+            f = rng.normal(size=size)
+            out = torch.zeros(size, dtype=torch.float64, device="cuda")
+            sv.submesh_solve(mesh, _dev(f), out)
+            ref = lu.solve(f)
+            assert _relerr(out.cpu().numpy(), ref) <= 2e-5, (mesh, _relerr(out.cpu().numpy(), ref))
+        u = _dev(p.g)
+        res = sv.solve(_dev(p.s), u)
+    if res.status == lib.OK:
+        r, bb = orc.residual_grid(p.N, p.alpha, p.beta, p.s, u.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1e-10 * 1.01
+    else:
+        assert res.status in (lib.NOT_CONVERGED, lib.STAGNATED)
