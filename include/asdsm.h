@@ -266,6 +266,35 @@ int asdsm_batch_history(const asdsm_batch* b, int index, double* hist, int cap);
 /* Release the batch and all its instances (NULL is a no-op). */
 void asdsm_destroy_batch(asdsm_batch* b);
 
+/* ---- Learned correction network (not in the paper) -------------------------
+ * A 4-layer convolutional net, channels 6 -> 32 -> 32 -> 32 -> 1 with 3x3
+ * kernels (cross-correlation, zero padding) and ReLU after layers 1..3, with
+ * its own forward, backpropagation (half-MSE loss) and Adam kernels.  Images
+ * are device FP32 arrays in NCHW order.  Parameters are one flat FP32 vector
+ * [W1, b1, W2, b2, W3, b3, W4, b4], W_l of shape (C_out, C_in, 3, 3).  With
+ * bf16_operands the factors of every product are rounded to BF16 (FP32
+ * accumulation); otherwise the arithmetic is FP32. */
+typedef struct asdsm_cnn asdsm_cnn;
+
+/* Parameter count (20545). */
+int asdsm_cnn_param_count(void);
+/* Create from host parameters (n = asdsm_cnn_param_count()). */
+int asdsm_cnn_create(const float* params, int n, int bf16_operands, asdsm_cnn** out);
+int asdsm_cnn_get_params(const asdsm_cnn* net, float* params, int n);
+/* Replace the parameters; resets the Adam moments. */
+int asdsm_cnn_set_params(asdsm_cnn* net, const float* params, int n);
+/* y (B,1,H,W) = net(x (B,6,H,W)).  Stream-ordered. */
+int asdsm_cnn_forward(asdsm_cnn* net, const float* x, float* y, int B, int H, int W, void* stream);
+/* Forward, loss L = sum (y - t)^2 / (2 B H W) and its gradient, kept on the
+ * device for asdsm_cnn_adam; loss and grad_host (param_count floats) are
+ * filled when non-NULL (the call then synchronises the stream). */
+int asdsm_cnn_backward(asdsm_cnn* net, const float* x, const float* t, int B, int H, int W, double* loss,
+                       float* grad_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
+int asdsm_cnn_adam(asdsm_cnn* net, float lr, void* stream);
+const char* asdsm_cnn_last_error(void);
+void asdsm_cnn_destroy(asdsm_cnn* net);
+
 /* Static description of a status code. */
 const char* asdsm_strerror(int code);
 

@@ -124,6 +124,25 @@ def load() -> ctypes.CDLL:
     lib.asdsm_batch_history.restype = ctypes.c_int
     lib.asdsm_destroy_batch.argtypes = [P]
     lib.asdsm_destroy_batch.restype = None
+    lib.asdsm_cnn_param_count.argtypes = []
+    lib.asdsm_cnn_param_count.restype = ctypes.c_int
+    lib.asdsm_cnn_create.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]
+    lib.asdsm_cnn_create.restype = ctypes.c_int
+    lib.asdsm_cnn_get_params.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.asdsm_cnn_get_params.restype = ctypes.c_int
+    lib.asdsm_cnn_set_params.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.asdsm_cnn_set_params.restype = ctypes.c_int
+    lib.asdsm_cnn_forward.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    lib.asdsm_cnn_forward.restype = ctypes.c_int
+    lib.asdsm_cnn_backward.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), P]
+    lib.asdsm_cnn_backward.restype = ctypes.c_int
+    lib.asdsm_cnn_adam.argtypes = [P, ctypes.c_float, P]
+    lib.asdsm_cnn_adam.restype = ctypes.c_int
+    lib.asdsm_cnn_last_error.argtypes = []
+    lib.asdsm_cnn_last_error.restype = ctypes.c_char_p
+    lib.asdsm_cnn_destroy.argtypes = [P]
+    lib.asdsm_cnn_destroy.restype = None
     lib.asdsm_strerror.argtypes = [ctypes.c_int]
     lib.asdsm_strerror.restype = ctypes.c_char_p
     lib.asdsm_last_error.argtypes = []
@@ -387,6 +406,81 @@ class BatchSolver:
 
     def __exit__(self, *exc):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cnn:
+    """The learned-correction network (asdsm_cnn_*): device FP32 NCHW tensors in and out."""
+
+    def __init__(self, params, bf16: bool = True, stream=None):
+        import numpy as np
+        import torch
+        lib = load()
+        self._lib = lib
+        self.n = lib.asdsm_cnn_param_count()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.n:
+            raise ValueError(f"expected {self.n} parameters")
+        h = ctypes.c_void_p()
+        rc = lib.asdsm_cnn_create(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.n, 1 if bf16 else 0,
+                                  ctypes.byref(h))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_cnn_create")
+        self._h = h
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+
+    def params(self):
+        import numpy as np
+        out = np.empty(self.n, dtype=np.float32)
+        rc = self._lib.asdsm_cnn_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.n)
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_cnn_get_params")
+        return out
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        rc = self._lib.asdsm_cnn_set_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.n)
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_cnn_set_params")
+
+    def forward(self, x):
+        import torch
+        B, C, H, W = x.shape
+        y = torch.empty((B, 1, H, W), dtype=torch.float32, device=x.device)
+        rc = self._lib.asdsm_cnn_forward(self._h, _ptr(x, "float32"), _ptr(y, "float32"), B, H, W,
+                                         ctypes.c_void_p(self._stream.cuda_stream))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_cnn_forward")
+        return y
+
+    def backward(self, x, t, want_grad: bool = False):
+        """Returns (loss, gradient as numpy or None)."""
+        import numpy as np
+        B, C, H, W = x.shape
+        loss = ctypes.c_double()
+        g = np.empty(self.n, dtype=np.float32) if want_grad else None
+        rc = self._lib.asdsm_cnn_backward(self._h, _ptr(x, "float32"), _ptr(t, "float32"), B, H, W, ctypes.byref(loss),
+                                          g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if want_grad else None,
+                                          ctypes.c_void_p(self._stream.cuda_stream))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_cnn_backward")
+        return loss.value, g
+
+    def adam(self, lr: float):
+        rc = self._lib.asdsm_cnn_adam(self._h, float(lr), ctypes.c_void_p(self._stream.cuda_stream))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_cnn_adam")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.asdsm_cnn_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:
