@@ -285,15 +285,33 @@ int asdsm_cnn_get_params(const asdsm_cnn* net, float* params, int n);
 int asdsm_cnn_set_params(asdsm_cnn* net, const float* params, int n);
 /* y (B,1,H,W) = net(x (B,6,H,W)).  Stream-ordered. */
 int asdsm_cnn_forward(asdsm_cnn* net, const float* x, float* y, int B, int H, int W, void* stream);
-/* Forward, loss L = sum (y - t)^2 / (2 B H W) and its gradient, kept on the
- * device for asdsm_cnn_adam; loss and grad_host (param_count floats) are
- * filled when non-NULL (the call then synchronises the stream). */
-int asdsm_cnn_backward(asdsm_cnn* net, const float* x, const float* t, int B, int H, int W, double* loss,
-                       float* grad_host, void* stream);
+/* Forward, loss L = sum w (y - t)^2 / (2 B H W) (w: optional per-pixel
+ * weights (B,1,H,W), 1 when NULL) and its gradient, kept on the device for
+ * asdsm_cnn_adam; loss and grad_host (param_count floats) are filled when
+ * non-NULL (the call then synchronises the stream). */
+int asdsm_cnn_backward(asdsm_cnn* net, const float* x, const float* t, const float* weights, int B, int H, int W,
+                       double* loss, float* grad_host, void* stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
 int asdsm_cnn_adam(asdsm_cnn* net, float lr, void* stream);
 const char* asdsm_cnn_last_error(void);
 void asdsm_cnn_destroy(asdsm_cnn* net);
+
+/* Use `net` (NULL: none) as a learned correction in the handle's mixed-
+ * precision solves: every sweep, after the ASDSM correction e of Algorithm 4
+ * step 5, the network maps [r, e (each scaled to unit RMS over the interior),
+ * alpha_x, alpha_y, beta_x h, beta_y h] to a direction; its skeleton values,
+ * completed by the homogeneous Filler (Algorithm 3), enter the same GCR(m)
+ * cycle as a second direction (least squares over [e, e_cnn]); a dependent
+ * direction is dropped, so the plain correction is the fallback.  Needs
+ * accel_m > 1; solves with a network run host-driven sweeps.  The handle does
+ * not own `net`. */
+int asdsm_attach_cnn(asdsm_handle* h, asdsm_cnn* net);
+/* Learned directions accepted by the GCR steps of the last solve. */
+int asdsm_cnn_directions(const asdsm_handle* h);
+/* Training features of an iterate: r_out = s - A u (steps 3 of Algorithm 4)
+ * and e_out = the correction of steps 4-5 (Algorithm 1 without b_cc, choice
+ * of sweep k), both FP32 N*N device grids (computed in FP64). */
+int asdsm_correction(asdsm_handle* h, const double* s, const double* u, float* r_out, float* e_out, int k);
 
 /* Static description of a status code. */
 const char* asdsm_strerror(int code);

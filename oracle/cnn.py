@@ -12,7 +12,8 @@ ASDSM sweep to a correction direction.  Definitions, written out plainly:
   (cross-correlation, zero "same" padding).
 * layers: channels 6 -> 32 -> 32 -> 32 -> 1; a_l = relu(z_l) after layers
   1..3, the output y = z_4 is linear.
-* loss L = 1/(2 n) * sum (y - t)^2, n = number of output values.
+* loss L = 1/(2 n) * sum w (y - t)^2, n = number of output values, w optional
+  per-point weights (1 when absent).
 * Adam (Kingma and Ba, 2015): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
   theta -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 
@@ -82,19 +83,21 @@ def forward(theta, x, channels=CHANNELS):
     return acts[-1], acts
 
 
-def loss(theta, x, t, channels=CHANNELS) -> float:
+def loss(theta, x, t, channels=CHANNELS, w=None) -> float:
     y, _ = forward(theta, x, channels)
-    return 0.5 * float(np.mean((y - t) ** 2))
+    wt = 1.0 if w is None else w
+    return 0.5 * float(np.mean(wt * (y - t) ** 2))
 
 
-def grad(theta, x, t, channels=CHANNELS):
+def grad(theta, x, t, channels=CHANNELS, w=None):
     """(loss, dL/dtheta) by backpropagation through the definitions above."""
     y, acts = forward(theta, x, channels)
     layers = unpack(theta, channels)
     n = y.size
     g = np.zeros_like(theta)
     gl = unpack(g, channels)
-    dz = (y - t) / n                                     # dL/dz_4
+    wt = 1.0 if w is None else w
+    dz = wt * (y - t) / n                                # dL/dz_4
     for l in range(len(layers) - 1, -1, -1):
         W, _ = layers[l]
         a_in = acts[l]
@@ -115,7 +118,7 @@ def grad(theta, x, t, channels=CHANNELS):
                 dpad[:, :, p:p + H, q:q + Wd] += np.einsum("oc,bohw->bchw", W[:, :, p, q], dz)
         da = dpad[:, :, 1:-1, 1:-1]
         dz = da * (acts[l] > 0)                          # through relu of layer l
-    return 0.5 * float(np.mean((y - t) ** 2)), g
+    return 0.5 * float(np.mean(wt * (y - t) ** 2)), g
 
 
 class Adam:

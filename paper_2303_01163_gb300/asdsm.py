@@ -134,7 +134,7 @@ def load() -> ctypes.CDLL:
     lib.asdsm_cnn_set_params.restype = ctypes.c_int
     lib.asdsm_cnn_forward.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
     lib.asdsm_cnn_forward.restype = ctypes.c_int
-    lib.asdsm_cnn_backward.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+    lib.asdsm_cnn_backward.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), P]
     lib.asdsm_cnn_backward.restype = ctypes.c_int
     lib.asdsm_cnn_adam.argtypes = [P, ctypes.c_float, P]
@@ -143,6 +143,12 @@ def load() -> ctypes.CDLL:
     lib.asdsm_cnn_last_error.restype = ctypes.c_char_p
     lib.asdsm_cnn_destroy.argtypes = [P]
     lib.asdsm_cnn_destroy.restype = None
+    lib.asdsm_attach_cnn.argtypes = [P, P]
+    lib.asdsm_attach_cnn.restype = ctypes.c_int
+    lib.asdsm_cnn_directions.argtypes = [P]
+    lib.asdsm_cnn_directions.restype = ctypes.c_int
+    lib.asdsm_correction.argtypes = [P, P, P, P, P, ctypes.c_int]
+    lib.asdsm_correction.restype = ctypes.c_int
     lib.asdsm_strerror.argtypes = [ctypes.c_int]
     lib.asdsm_strerror.restype = ctypes.c_char_p
     lib.asdsm_last_error.argtypes = []
@@ -247,6 +253,26 @@ class Solver:
         rc = self._lib.asdsm_autotune(self._h, prec)
         if rc != OK:
             raise AsdsmError(rc, "asdsm_autotune")
+
+    def attach_cnn(self, net):
+        """Use a Cnn as the learned correction (None detaches); keep `net` alive meanwhile."""
+        self._cnn = net
+        rc = self._lib.asdsm_attach_cnn(self._h, net._h if net is not None else None)
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_attach_cnn")
+
+    def cnn_directions(self) -> int:
+        return self._lib.asdsm_cnn_directions(self._h)
+
+    def correction(self, s, u, k: int = 0):
+        """(r, e) of iterate u as FP32 N x N tensors (asdsm_correction)."""
+        import torch
+        r = torch.empty((self.N, self.N), dtype=torch.float32, device=u.device)
+        e = torch.empty_like(r)
+        rc = self._lib.asdsm_correction(self._h, _ptr(s), _ptr(u), _ptr(r, "float32"), _ptr(e, "float32"), int(k))
+        if rc != OK:
+            raise AsdsmError(rc, "asdsm_correction")
+        return r, e
 
     def tune_state(self) -> list:
         buf = (ctypes.c_int32 * 256)()
@@ -459,13 +485,14 @@ class Cnn:
             raise AsdsmError(rc, "asdsm_cnn_forward")
         return y
 
-    def backward(self, x, t, want_grad: bool = False):
-        """Returns (loss, gradient as numpy or None)."""
+    def backward(self, x, t, want_grad: bool = False, weights=None):
+        """Returns (loss, gradient as numpy or None); weights: optional (B,1,H,W) per-pixel loss weights."""
         import numpy as np
         B, C, H, W = x.shape
         loss = ctypes.c_double()
         g = np.empty(self.n, dtype=np.float32) if want_grad else None
-        rc = self._lib.asdsm_cnn_backward(self._h, _ptr(x, "float32"), _ptr(t, "float32"), B, H, W, ctypes.byref(loss),
+        wp = _ptr(weights, "float32") if weights is not None else None
+        rc = self._lib.asdsm_cnn_backward(self._h, _ptr(x, "float32"), _ptr(t, "float32"), wp, B, H, W, ctypes.byref(loss),
                                           g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if want_grad else None,
                                           ctypes.c_void_p(self._stream.cuda_stream))
         if rc != OK:

@@ -110,6 +110,11 @@ struct asdsm_handle {
     // A_cc, and warps per CTA of the Filler, per precision.
     BcrTune tune_aniso[2] = {}, tune_cc[2] = {};
     int fill_warps[2] = {0, 0};
+    // Learned correction (asdsm_attach_cnn): the network and its input/output grids.
+    asdsm_cnn* cnn = nullptr;
+    float* cnn_x = nullptr;            // 6 x N x N
+    float* cnn_y = nullptr;            // N x N
+    int cnn_dirs = 0;                  // learned directions used in the last solve
     struct SweepGraph {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -753,6 +758,31 @@ int autotune_impl(asdsm_handle* h) {
     return done(ASDSM_OK);
 }
 
+// Learned correction direction of a mixed sweep into zc (skeleton values; the
+// caller fills the holes): the network applied to [r, e normalised to unit
+// RMS over the interior, alpha_x, alpha_y, beta_x h, beta_y h].
+int cnn_direction(asdsm_handle* h, double r2, const float* e, float* zc) {
+    const Geometry& g = h->g;
+    cudaStream_t st = h->st;
+    const long long NN = (long long)g.N * g.N;
+    const float* ev[1] = {e};
+    int nb = 0;
+    CK(multi_dot<float>(ev, ev, 1, NN, h->partials, &nb, st));
+    CK(reduce_partials(h->partials, nb, 1, h->dsmall + 210, st));
+    CK(cudaMemcpyAsync(h->hsmall + 210, h->dsmall + 210, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double n = (double)g.Nf * g.Nf;
+    const double e2 = h->hsmall[210];
+    const float rs = r2 > 0 ? (float)std::sqrt(n / r2) : 0.0f;
+    const float es = e2 > 0 ? (float)std::sqrt(n / e2) : 0.0f;
+    const double hh = 1.0 / g.M;
+    const float c[4] = {(float)h->alpha[0], (float)h->alpha[1], (float)(h->beta[0] * hh), (float)(h->beta[1] * hh)};
+    CK(cnn_features((const float*)h->w[1].rfull, e, rs, es, c, NN, h->cnn_x, st));
+    if (int rc = asdsm_cnn_forward(h->cnn, h->cnn_x, h->cnn_y, 1, g.N, g.N, st)) return rc;
+    CK(skeleton_from(h->cnn_y, g, zc, st));
+    return ASDSM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Algorithm 4.
 // ---------------------------------------------------------------------------
@@ -792,7 +822,8 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
     for (;;) {
         // ---- step 3: residual (with the pending step-7 update fused) ----
         ResidOut o{};
-        o.rfc = w.Xfc; o.rcf = w.Xcf; o.rskel = w.rskel; o.rfull = nullptr; o.partials = h->partials;
+        o.rfc = w.Xfc; o.rcf = w.Xcf; o.rskel = w.rskel; o.partials = h->partials;
+        o.rfull = (mixed && h->cnn) ? w.rfull : nullptr;    // the learned correction reads r on the full grid
         int nb = 0;
         {
             // Algorithmic bytes: read u and s, read each pending direction, write u when updated,
@@ -908,25 +939,31 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
             const double bytes = ES * (holes * (g.n - 1.0) * (g.n - 1.0) + holes * 4.0 * (g.n - 1.0));
             prof_end(h, pm, PC_FILL, bytes, flops);
         }
-        // ---- step 6: least squares on the skeleton rows ----
-        const ProfMark pm_lsq = prof_begin(h);
-        CK(skeleton_apply<T>(z, g, h->sten, (T*)w.q, st));
-        const T* qpv[kMaxM];
-        for (int j = 0; j < kc; ++j) qpv[j] = (const T*)w.qp[j];
-        const int nd = 2 + 2 * kc;      // <q,q>, <q,r>, then <q,q'_j>, <r,q'_j>
-        int nb3 = 0;
-        CK(gcr_dots<T>((const T*)w.q, (const T*)w.rskel, qpv, kc, g.skel, h->partials, &nb3, st));
-        CK(reduce_partials(h->partials, nb3, nd, h->dsmall, st));
-        prof_end(h, pm_lsq, PC_LSQ, ES * (double)g.skel * (6.0 + 2.0 + kc), 2.0 * (double)g.skel * nd);
-        if (int rc = read_small(h, nd)) return rc;
-        const double qq = h->hsmall[0], qr = h->hsmall[1];
-        if (m == 1) {
-            // Paper's step 6: s_hat = argmin_{s >= 0} ||r - s A e||.
-            const double shat = qq > 0 ? std::max(0.0, qr / qq) : 0.0;
-            pend.count = 1;
-            pend.z[0] = z;
-            pend.coef[0] = shat;
-        } else {
+        // ---- step 6: least squares on the skeleton rows (GCR(m) step for direction zd) ----
+        // Returns 1 when the direction is dependent (the cycle restarts), 0 otherwise;
+        // with `add` the step's update is added to the pending one (a second
+        // direction in the same sweep: by orthogonality its coefficient uses the
+        // same residual).
+        auto gcr_step = [&](T* zd, bool add) -> int {
+            const ProfMark pm_lsq = prof_begin(h);
+            CK(skeleton_apply<T>(zd, g, h->sten, (T*)w.q, st));
+            const T* qpv[kMaxM];
+            for (int j = 0; j < kc; ++j) qpv[j] = (const T*)w.qp[j];
+            const int nd = 2 + 2 * kc;      // <q,q>, <q,r>, then <q,q'_j>, <r,q'_j>
+            int nb3 = 0;
+            CK(gcr_dots<T>((const T*)w.q, (const T*)w.rskel, qpv, kc, g.skel, h->partials, &nb3, st));
+            CK(reduce_partials(h->partials, nb3, nd, h->dsmall, st));
+            prof_end(h, pm_lsq, PC_LSQ, ES * (double)g.skel * (6.0 + 2.0 + kc), 2.0 * (double)g.skel * nd);
+            if (int rc = read_small(h, nd)) return rc;
+            const double qq = h->hsmall[0], qr = h->hsmall[1];
+            if (m == 1) {
+                // Paper's step 6: s_hat = argmin_{s >= 0} ||r - s A e||.
+                const double shat = qq > 0 ? std::max(0.0, qr / qq) : 0.0;
+                pend.count = 1;
+                pend.z[0] = zd;
+                pend.coef[0] = shat;
+                return 0;
+            }
             // GCR(m): orthogonalise A e against the cycle's previous directions.
             double beta_[kMaxM] = {}, rq[kMaxM] = {};
             double nu2 = qq;
@@ -935,11 +972,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
                 rq[j] = h->hsmall[3 + 2 * j];
                 nu2 -= beta_[j] * beta_[j];
             }
-            if (!(nu2 > 1e-24 * qq) || !(qq > 0)) {
-                kc = 0;                       // dependent direction: restart the cycle
-                ++k;
-                continue;
-            }
+            if (!(nu2 > 1e-24 * qq) || !(qq > 0)) return 1;
             const double nu = std::sqrt(nu2);
             double alpha_ = qr;
             for (int j = 0; j < kc; ++j) alpha_ -= beta_[j] * rq[j];
@@ -949,16 +982,39 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
             Tm[kc][kc] = 1.0 / nu;
             for (int j = 0; j < kc; ++j)
                 for (int i = 0; i <= j; ++i) Tm[i][kc] -= beta_[j] * Tm[i][j] / nu;
-            pend.count = kc + 1;
             for (int i = 0; i <= kc; ++i) {
                 pend.z[i] = w.z[i];
-                pend.coef[i] = alpha_ * Tm[i][kc];
+                pend.coef[i] = (add && i < pend.count ? pend.coef[i] : 0.0) + alpha_ * Tm[i][kc];
             }
+            pend.count = kc + 1;
             const T* qps[kMaxM];
             for (int j = 0; j < kc; ++j) qps[j] = (const T*)w.qp[j];
             CK(combine_skeleton<T>((const T*)w.q, qps, beta_, kc, 1.0 / nu, g.skel, (T*)w.qp[kc], st));
             ++kc;
             if (kc >= m) kc = 0;
+            return 0;
+        };
+        const int dep = gcr_step(z, false);
+        if (dep < 0) return dep;
+        if (dep == 1) {
+            kc = 0;                           // dependent direction: restart the cycle
+            ++k;
+            continue;
+        }
+        // Learned correction: one more direction in the same cycle (not in a new one,
+        // whose slots the pending update still reads).
+        if (mixed && h->cnn && m > 1 && kc != 0) {
+            T* zc = (T*)w.z[kc];
+            if (int rc = cnn_direction(h, r2, (const float*)z, (float*)zc)) return rc;
+            FillArgs<T> fc{};
+            fc.mode = FILL_HOMOGENEOUS;
+            fc.z = zc; fc.out = zc;
+            hole_factors<T>(h, pi, &fc);
+            fc.n = g.n; fc.g = g; fc.sten = h->sten;
+            CK(fill_holes<T>(fc, h->num_sms, st));
+            const int dep2 = gcr_step(zc, true);
+            if (dep2 < 0) return dep2;
+            if (dep2 == 0) ++h->cnn_dirs;
         }
         ++k;
     }
@@ -981,6 +1037,7 @@ int run_begin(asdsm_handle* h, SolveRun& r) {
     h->hist.clear();
     h->pend_ev.clear();
     h->evnext = 0;
+    h->cnn_dirs = 0;
     CK(cudaEventRecord(h->ev0, st));
     // ||b_ff||^2: the FP64 residual of the zero-interior grid (r = b there).
     {
@@ -1055,7 +1112,7 @@ int run_middle(asdsm_handle* h, SolveRun& r) {
     CK(ring_from<T>(nullptr, (T*)w.z[0], g, 0, st));
     CK(cudaEventRecord(h->ev1, st));
     r.mk = mixed ? mixed_coefs(h, r.S) : MixedCoefs{};
-    if (op.sweep_graph && !h->prof) {
+    if (op.sweep_graph && !h->prof && !h->cnn) {
         if (int rc = graph_start<T>(h, r)) return rc;
         r.stage = 2;
     } else {
@@ -1292,6 +1349,61 @@ int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n) {
         h->fill_warps[pi] = in[q++];
     }
     destroy_graph(h);
+    return ASDSM_OK;
+}
+
+int asdsm_attach_cnn(asdsm_handle* h, asdsm_cnn* net) {
+    if (!h) return ASDSM_ERR_INVALID;
+    if (h->cnn_x) { cudaFree(h->cnn_x); h->cnn_x = nullptr; }
+    if (h->cnn_y) { cudaFree(h->cnn_y); h->cnn_y = nullptr; }
+    h->cnn = nullptr;
+    if (!net) return ASDSM_OK;
+    const size_t NN = (size_t)h->g.N * h->g.N;
+    CK(cudaMalloc(&h->cnn_x, 6 * NN * sizeof(float)));
+    CK(cudaMalloc(&h->cnn_y, NN * sizeof(float)));
+    h->cnn = net;
+    return ASDSM_OK;
+}
+
+int asdsm_cnn_directions(const asdsm_handle* h) { return h ? h->cnn_dirs : ASDSM_ERR_INVALID; }
+
+int asdsm_correction(asdsm_handle* h, const double* s, const double* u, float* r_out, float* e_out, int k) {
+    if (!h || !s || !u || !r_out || !e_out || k < 0) return ASDSM_ERR_INVALID;
+    if (int rc = ensure_work<double>(h, 0, 1)) return rc;
+    if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(h->g), 4096))) return rc;
+    auto& w = h->w[0];
+    const Geometry& g = h->g;
+    cudaStream_t st = h->st;
+    ResidOut o{};
+    o.rfc = w.Xfc; o.rcf = w.Xcf; o.rskel = w.rskel; o.rfull = w.rfull; o.partials = h->partials;
+    UpdateTerms none{};
+    int nb = 0;
+    CK(residual_fp64(s, u, const_cast<double*>(u), none, g, h->sten, o, &nb, st));
+    BcrSys<double> sys[2] = {sys_of<double>(h->fc[0], w.Xfc, w.Yfc), sys_of<double>(h->cf[0], w.Xcf, w.Ycf)};
+    CK(bcr_solve<double>(sys, 2, st, &h->tune_aniso[0]));
+    const double* av[2] = {(const double*)w.Yfc, (const double*)w.Ycf};
+    int nb2 = 0;
+    CK(multi_dot<double>(av, av, 2, (long long)g.Nf * g.Nc, h->partials, &nb2, st));
+    CK(reduce_partials(h->partials, nb2, 2, h->dsmall + 200, st));
+    double* z = (double*)w.z[0];
+    MergeArgs<double> ma{};
+    ma.Yfc = (double*)w.Yfc; ma.Ycf = (double*)w.Ycf; ma.Ycc = nullptr;
+    ma.norms2 = h->dsmall + 200; ma.re_mode = 0; ma.choice = choice_bit(h->opts.seed, k);
+    ma.Sm = (const double*)h->Sm[0];
+    ma.E1 = (double*)w.E1; ma.E2 = (double*)w.E2; ma.M1 = (double*)w.M1; ma.M2 = (double*)w.M2;
+    ma.z = z; ma.g = g;
+    CK(merge_knots<double>(ma, st));
+    CK(merge_write<double>(ma, st));
+    FillArgs<double> fa{};
+    fa.mode = FILL_HOMOGENEOUS;
+    fa.z = z; fa.out = z;
+    hole_factors<double>(h, 0, &fa);
+    fa.n = g.n; fa.g = g; fa.sten = h->sten;
+    CK(fill_holes<double>(fa, h->num_sms, st));
+    const long long NN = (long long)g.N * g.N;
+    CK(convert_array<double, float>((const double*)w.rfull, r_out, NN, st));
+    CK(convert_array<double, float>(z, e_out, NN, st));
+    CK(cudaStreamSynchronize(st));
     return ASDSM_OK;
 }
 
@@ -1616,6 +1728,7 @@ void asdsm_destroy(asdsm_handle* h) {
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->ev2) cudaEventDestroy(h->ev2);
     if (h->evA) cudaEventDestroy(h->evA);
+    fr(h->cnn_x); fr(h->cnn_y);
     destroy_graph(h);
     fr(h->dctl); fr(h->dhist);
     if (h->hctl) cudaFreeHost(h->hctl);

@@ -260,6 +260,12 @@ cudaError_t ctl_after_residual(SweepCtl* c, const double* sums, int* overflow, d
 // After the least-squares inner products: the step lengths of step 6 / GCR(m).
 cudaError_t ctl_after_dots(SweepCtl* c, const double* dots, cudaStream_t st);
 
+// Learned correction: input channels [r rs, e es, c0..c3] of the full grid,
+// and the network output kept on the interior skeleton points of z.
+cudaError_t cnn_features(const float* r, const float* e, float rs, float es, const float c[4], long long nn, float* x,
+                         cudaStream_t st);
+cudaError_t skeleton_from(const float* y, const Geometry& g, float* z, cudaStream_t st);
+
 // Grid utilities -------------------------------------------------------------
 template <typename T>
 cudaError_t fill_value(T* p, long long n, T v, cudaStream_t st);

@@ -156,15 +156,16 @@ __global__ void sum_partials_kernel(const float* __restrict__ partials, long lon
     }
 }
 
-// dY = (y - t) / n; per-block sums of (y - t)^2.
-__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, long long n,
-                           float* __restrict__ dy, double* __restrict__ part) {
+// dY = w (y - t) / n; per-block sums of w (y - t)^2 (w = 1 when no weights).
+__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, const float* __restrict__ wt,
+                           long long n, float* __restrict__ dy, double* __restrict__ part) {
     __shared__ double red[256];
     double s = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const float d = y[e] - t[e];
-        dy[e] = d / (float)n;
-        s += (double)d * d;
+        const float we = wt ? wt[e] : 1.0f;
+        dy[e] = we * d / (float)n;
+        s += (double)we * d * d;
     }
     red[threadIdx.x] = s;
     __syncthreads();
@@ -322,8 +323,8 @@ int asdsm_cnn_forward(asdsm_cnn* net, const float* x, float* y, int B, int H, in
     return forward_impl(net, x, y, B, H, W, (cudaStream_t)stream);
 }
 
-int asdsm_cnn_backward(asdsm_cnn* net, const float* x, const float* t, int B, int H, int W, double* loss,
-                       float* grad_host, void* stream) {
+int asdsm_cnn_backward(asdsm_cnn* net, const float* x, const float* t, const float* weights, int B, int H, int W,
+                       double* loss, float* grad_host, void* stream) {
     if (!net || !x || !t || B < 1 || H < 1 || W < 1) return ASDSM_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     if (int rc = forward_impl(net, x, nullptr, B, H, W, st)) return rc;
@@ -332,7 +333,7 @@ int asdsm_cnn_backward(asdsm_cnn* net, const float* x, const float* t, int B, in
     dim3 grid((W + TILE - 1) / TILE, (H + TILE - 1) / TILE, B);
     // dL/dz_4 and the loss.
     const int nb = 512;
-    mse_kernel<<<nb, 256, 0, st>>>(net->act[CNN_LAYERS], t, pix, net->dz[0], net->dpart);
+    mse_kernel<<<nb, 256, 0, st>>>(net->act[CNN_LAYERS], t, weights, pix, net->dz[0], net->dpart);
     asdsm::note_launch();
     CNN_CK(cudaGetLastError());
     int cur = 0;

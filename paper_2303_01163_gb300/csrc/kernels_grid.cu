@@ -944,6 +944,52 @@ cudaError_t combine_skeleton_dyn(const T* q, const T* const* Qp, int k, const Ct
     return cudaGetLastError();
 }
 
+// Input channels of the learned correction on the full N x N grid:
+// [r * rs, e * es, c2, c3, c4, c5] (channel-major, x fastest).
+__global__ void cnn_features_kernel(const float* __restrict__ r, const float* __restrict__ e, float rs, float es,
+                                    float c2, float c3, float c4, float c5, long long nn, float* __restrict__ x) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nn; q += (long long)gridDim.x * blockDim.x) {
+        x[q] = r[q] * rs;
+        x[nn + q] = e[q] * es;
+        x[2 * nn + q] = c2;
+        x[3 * nn + q] = c3;
+        x[4 * nn + q] = c4;
+        x[5 * nn + q] = c5;
+    }
+}
+
+// z = y on the interior skeleton points (holes and ring untouched).
+__global__ void skeleton_from_kernel(const float* __restrict__ y, Geometry g, float* __restrict__ z) {
+    const int N = g.N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.skel; e += (long long)gridDim.x * blockDim.x) {
+        int i, j;
+        if (e < (long long)g.Nc * g.Nf) {
+            i = (int)(e % g.Nf) + 1;
+            j = ((int)(e / g.Nf) + 1) * g.n;
+        } else {
+            const long long f = e - (long long)g.Nc * g.Nf;
+            const int yr = (int)(f / g.Nc), k = (int)(f % g.Nc);
+            j = yr + yr / (g.n - 1) + 1;
+            i = (k + 1) * g.n;
+        }
+        const long long idx = (long long)j * N + i;
+        z[idx] = y[idx];
+    }
+}
+
+cudaError_t cnn_features(const float* r, const float* e, float rs, float es, const float c[4], long long nn, float* x,
+                         cudaStream_t st) {
+    cnn_features_kernel<<<grid_for(nn), 256, 0, st>>>(r, e, rs, es, c[0], c[1], c[2], c[3], nn, x);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t skeleton_from(const float* y, const Geometry& g, float* z, cudaStream_t st) {
+    skeleton_from_kernel<<<grid_for(g.skel), 256, 0, st>>>(y, g, z);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t fill_value(T* p, long long n, T v, cudaStream_t st) {
     fill_value_kernel<T><<<grid_for(n), 256, 0, st>>>(p, n, v);

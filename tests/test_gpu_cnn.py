@@ -98,3 +98,15 @@ def test_training_lowers_the_loss(lib):
     l1, _ = net.backward(xd, td)
     assert l1 < 0.2 * l0, (l0, l1)
     net.close()
+
+
+def test_weighted_loss_gradient_matches_oracle(lib):
+    theta, x, t = _data(7)
+    rng = np.random.default_rng(7)
+    w = ((rng.random(size=t.shape) < 0.3) * 3.0).astype(np.float32).astype(np.float64)
+    net = lib.Cnn(theta, bf16=False)
+    loss, g = net.backward(_dev32(x), _dev32(t), want_grad=True, weights=_dev32(w))
+    lo, go = orc.grad(theta, x, t, w=w)
+    assert abs(loss - lo) <= 1e-5 * lo
+    assert _rel(g, go) <= 1e-4
+    net.close()

@@ -1,0 +1,72 @@
+"""The learned correction end to end on the GPU: pairs generated by the
+library's own solves, training with its own kernels, and solves with the
+trained network attached.  What the network gains is measured and printed
+(sweeps to 1e-10 with and without it, at equal GCR memory per sweep); the
+test requires that training lowers the loss, that the learned directions are
+used, and that the solves still reach the fine solution."""
+import numpy as np
+import pytest
+
+from oracle import asdsm2d as orc
+from oracle import cnn as ocnn
+from paper_2303_01163_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_01163_gb300 import asdsm
+    return asdsm
+
+
+def test_learned_correction_trains_and_keeps_the_solve_exact(lib):
+    import torch
+    from paper_2303_01163_gb300 import learned
+    train_probs = [wl.random_fourier_2d(129, 1000 + i) for i in range(4)]
+    X, T, W = learned.make_pairs(train_probs, lambda N: (N - 1) // 16, sweeps=(0, 2, 4, 8), crop=32,
+                                 crops_per_iterate=8)
+    net, losses = learned.train(X, T, ocnn.init_params(0), steps=400, batch=32, lr=1e-3, W=W)
+    assert losses[-1] < 0.7 * losses[0], losses
+    gains = []
+    for sd in (9000, 9001):
+        p = wl.random_fourier_2d(129, sd)
+        s = torch.tensor(p.s, device="cuda")
+        g = torch.tensor(p.g, device="cuda")
+        counts = {}
+        for use, m in ((False, 16), (True, 16)):
+            with lib.Solver(129, 8, p.alpha, p.beta, precision=lib.MIXED, tol=1e-10, max_sweeps=1500, accel_m=m,
+                            sweep_graph=0) as sv:
+                if use:
+                    sv.attach_cnn(net)
+                u = g.clone()
+                res = sv.solve(s, u)
+                counts[use] = res.stats["sweeps"]
+                assert res.status == lib.OK, res.stats
+                if use:
+                    assert sv.cnn_directions() > 0
+                r, bb = orc.residual_grid(129, p.alpha, p.beta, p.s, u.cpu().numpy())
+                assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1.01e-10
+        gains.append(counts[False] / counts[True])
+        print(f"learned correction, 129^2 seed {sd}: sweeps plain {counts[False]}, with network {counts[True]}")
+    print("sweep ratio plain / learned:", [round(x, 2) for x in gains])
+    net.close()
+
+
+def test_detached_network_gives_the_plain_solve(lib):
+    import torch
+    from paper_2303_01163_gb300 import asdsm
+    p = wl.random_fourier_2d(129, 5)
+    net = lib.Cnn(ocnn.init_params(1), bf16=True)
+    with lib.Solver(129, 8, p.alpha, p.beta, precision=lib.MIXED, tol=1e-10, max_sweeps=800, sweep_graph=0) as sv:
+        u1 = torch.tensor(p.g, device="cuda")
+        r1 = sv.solve(torch.tensor(p.s, device="cuda"), u1)
+        sv.attach_cnn(net)
+        sv.attach_cnn(None)
+        u2 = torch.tensor(p.g, device="cuda")
+        r2 = sv.solve(torch.tensor(p.s, device="cuda"), u2)
+    assert r1.stats["sweeps"] == r2.stats["sweeps"]
+    assert torch.equal(u1, u2)
+    net.close()

@@ -103,3 +103,21 @@ def test_parameter_layout():
     assert layers[0][0].shape == (32, 6, 3, 3) and layers[0][0][0, 0, 0, 0] == 0
     assert layers[0][1][0] == 32 * 6 * 9
     assert layers[3][0].shape == (1, 32, 3, 3) and layers[3][1].shape == (1,)
+
+
+def test_weighted_gradient_matches_central_differences():
+    rng = np.random.default_rng(6)
+    ch = (6, 4, 4, 3, 1)
+    theta = cnn.init_params(7, ch)
+    x = rng.normal(size=(1, 6, 5, 6))
+    t = rng.normal(size=(1, 1, 5, 6))
+    w = (rng.random(size=t.shape) < 0.4).astype(float) * 2.5
+    _, g = cnn.grad(theta, x, t, ch, w=w)
+    for k in rng.choice(theta.size, size=25, replace=False):
+        e = np.zeros_like(theta)
+        e[k] = 1e-6
+        fd = (cnn.loss(theta + e, x, t, ch, w=w) - cnn.loss(theta - e, x, t, ch, w=w)) / 2e-6
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9
+    # zero weights where the target differs make those points irrelevant
+    t2 = t + (w == 0) * 5.0
+    assert abs(cnn.loss(theta, x, t, ch, w=w) - cnn.loss(theta, x, t2, ch, w=w)) < 1e-14
