@@ -39,6 +39,7 @@ struct DevBcr {
     int KW = 0, CW = 0;
     double wl[kMaxLevels] = {}, wr[kMaxLevels] = {};
     int R = 0, C = 0, L = 0;
+    BcrCoefs k{};                                // the system itself (refinement residuals)
 };
 
 uint64_t splitmix64_out(uint64_t state) {
@@ -377,6 +378,78 @@ int initial_guess_to_z(asdsm_handle* h, const double* s, const double* u) {
     fa.n = g.n; fa.g = g; fa.sten = h->sten;
     CK(fill_holes<T>(fa, h->num_sms, st));                              // Algorithm 3 with b_ff
     // Restore the ring of z to zero for later use as a direction slot is done by the caller.
+    return ASDSM_OK;
+}
+
+// Algorithm 1 for the mixed path, to FP64 quality without FP64 solves: each
+// submesh system is solved by FP32 block cyclic reduction with two steps of
+// iterative refinement (FP64 residual of the system, FP32 solve of the
+// correction), the merge of Algorithm 2 runs in FP64, and the holes are
+// filled in FP32 (Algorithm 3 with b_ff) straight into the FP64 grid and
+// refined once (FP64 residual, FP32 hole solve of it, added in FP64).
+// Result in h->w[0].z[0] (ring = g), as initial_guess_to_z.
+int initial_guess_refined(asdsm_handle* h, const double* s, const double* u) {
+    if (int rc = ensure_work<double>(h, 0, 1)) return rc;
+    auto& w64 = h->w[0];
+    auto& w32 = h->w[1];
+    const Geometry& g = h->g;
+    cudaStream_t st = h->st;
+    CK(build_submesh_rhs<double>(s, u, g, h->alpha, h->beta, (double*)w64.Xfc, (double*)w64.Xcf, (double*)w64.Xcc, st));
+    struct Fam { const DevBcr* d32; void* b64; void* x64; void* r32; void* y32; int R, C; };
+    const Fam fam[3] = {
+        {&h->fc[1], w64.Xfc, w64.Yfc, w32.Xfc, w32.Yfc, g.Nf, g.Nc},
+        {&h->cf[1], w64.Xcf, w64.Ycf, w32.Xcf, w32.Ycf, g.Nf, g.Nc},
+        {&h->cc[1], w64.Xcc, w64.Ycc, w32.Xcc, w32.Ycc, g.Nc, g.Nc}};
+    for (const Fam& f : fam) {
+        const long long n = (long long)f.R * f.C;
+        CK(cudaMemsetAsync(f.x64, 0, n * sizeof(double), st));
+        CK(convert_array<double, float>((const double*)f.b64, (float*)f.r32, n, st));
+    }
+    constexpr int kRefine = 2;
+    for (int it = 0; it <= kRefine; ++it) {
+        BcrSys<float> pair[2] = {sys_of<float>(h->fc[1], w32.Xfc, w32.Yfc), sys_of<float>(h->cf[1], w32.Xcf, w32.Ycf)};
+        CK(bcr_solve<float>(pair, 2, st, &h->tune_aniso[1]));                         // steps 1.1, 1.2
+        BcrSys<float> scc = sys_of<float>(h->cc[1], w32.Xcc, w32.Ycc);
+        CK(bcr_solve<float>(&scc, 1, st, &h->tune_cc[1]));                            // step 1.3
+        for (const Fam& f : fam) {
+            CK(add_float((double*)f.x64, (const float*)f.y32, (long long)f.R * f.C, st));
+            if (it < kRefine)
+                CK(bcr_residual((const double*)f.x64, (const double*)f.b64, (float*)f.r32, f.R, f.C, f.d32->k, st));
+        }
+    }
+    double* z = (double*)w64.z[0];
+    CK(ring_from<double>(u, z, g, 0, st));
+    MergeArgs<double> ma{};
+    ma.Yfc = (double*)w64.Yfc; ma.Ycf = (double*)w64.Ycf; ma.Ycc = (double*)w64.Ycc;
+    ma.norms2 = nullptr; ma.re_mode = 1; ma.choice = 0;
+    ma.Sm = (const double*)h->Sm[0];
+    ma.E1 = (double*)w64.E1; ma.E2 = (double*)w64.E2; ma.M1 = (double*)w64.M1; ma.M2 = (double*)w64.M2;
+    ma.z = z; ma.g = g;
+    CK(merge_knots<double>(ma, st));                                    // Algorithm 2 steps 1-4
+    CK(merge_write<double>(ma, st));                                    // steps 5-6
+    float* z32 = (float*)w32.z[0];
+    CK(convert_array<double, float>(z, z32, (long long)g.N * g.N, st)); // skeleton and ring for the FP32 fill
+    FillArgs<float> fa{};
+    fa.mode = FILL_WITH_SOURCE;
+    fa.z = z32; fa.out = z32; fa.out_d = z;
+    fa.src_hi = h->s_hi;
+    hole_factors<float>(h, 1, &fa);
+    fa.n = g.n; fa.g = g; fa.sten = h->sten;
+    CK(fill_holes<float>(fa, h->num_sms, st));                          // Algorithm 3 with b_ff
+    // One refinement of the holes: FP64 residual, FP32 hole solve of it added in FP64.
+    ResidOut o{};
+    o.rfull = w64.rfull; o.partials = h->partials;
+    UpdateTerms none{};
+    int nb = 0;
+    CK(residual_fp64(s, z, z, none, g, h->sten, o, &nb, st));
+    CK(convert_array<double, float>((const double*)w64.rfull, (float*)w32.rfull, (long long)g.N * g.N, st));
+    FillArgs<float> fr{};
+    fr.mode = FILL_RESIDUAL_TO_U;
+    fr.src_hi = (const float*)w32.rfull;
+    fr.u_d = z;
+    hole_factors<float>(h, 1, &fr);
+    fr.n = g.n; fr.g = g; fr.sten = h->sten;
+    CK(fill_holes<float>(fr, h->num_sms, st));
     return ASDSM_OK;
 }
 
@@ -1067,8 +1140,7 @@ int run_begin(asdsm_handle* h, SolveRun& r) {
             if (int rc = initial_guess_to_z<double>(h, s, u)) return rc;
             CK(copy_interior<double, double>((const double*)w.z[0], u, g, st));
         } else {
-            if (int rc = ensure_work<double>(h, 0, 1)) return rc;
-            if (int rc = initial_guess_to_z<double>(h, s, u)) return rc;
+            if (int rc = initial_guess_refined(h, s, u)) return rc;
             r.u0d = (const double*)h->w[0].z[0];
         }
     }
@@ -1274,6 +1346,9 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if (!make_bcr(g.Nc, yl_H, yd_H, yu_H, g.Nc, xl_H, xd_H, xu_H, &fcc)) return fail(ASDSM_ERR_INVALID);
     // Hole blocks A_(ij): rows y, columns x, both fine.
     if (!make_bcr(g.n - 1, yl_h, yd_h, yu_h, g.n - 1, xl_h, xd_h, xu_h, &fho)) return fail(ASDSM_ERR_INVALID);
+    const BcrCoefs kfc{xl_h, xd_h, xu_h, yl_H, yd_H, yu_H}, kcf{yl_h, yd_h, yu_h, xl_H, xd_H, xu_H},
+        kcc{yl_H, yd_H, yu_H, xl_H, xd_H, xu_H};
+    for (int q = 0; q < 2; ++q) { h->fc[q].k = kfc; h->cf[q].k = kcf; h->cc[q].k = kcc; }
     int rc;
     if ((rc = upload_bcr<double>(ffc, &h->fc[0])) || (rc = upload_bcr<float>(ffc, &h->fc[1])) ||
         (rc = upload_bcr<double>(fcf, &h->cf[0])) || (rc = upload_bcr<float>(fcf, &h->cf[1])) ||

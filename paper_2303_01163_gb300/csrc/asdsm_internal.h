@@ -95,6 +95,14 @@ struct BcrTune {
 // Block cyclic reduction of up to 2 factor groups (e.g. the fc and cf families).
 template <typename T>
 cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st, const BcrTune* tune = nullptr);
+// Coefficients of a system make_bcr factors: a x_{i-1} + (d I + T) x_i + c x_{i+1},
+// T = tridiag(tl, td, tu).
+struct BcrCoefs { double a, d, c, tl, td, tu; };
+// r32 = (float)(b - A x) over the R x C system (FP64 arithmetic).
+cudaError_t bcr_residual(const double* x, const double* b, float* r32, int R, int C, const BcrCoefs& k,
+                         cudaStream_t st);
+// x += (double) y over n elements.
+cudaError_t add_float(double* x, const float* y, long long n, cudaStream_t st);
 // One level of it (forward reduction or back substitution), for tuning.
 template <typename T>
 cudaError_t bcr_level(const BcrSys<T>* groups, int ngroups, int level, bool backward, const BcrTune* tune,
@@ -117,7 +125,7 @@ struct FillArgs {
     T* out;                   // full grid, receives hole values (modes 0, 1, 3)
     const double* src_d;      // FP64 source grid (mode 0, FP64 path) / rhs grid (mode 3)
     const float* src_hi;      // FP32 source (mode 0, mixed path) / residual grid (mode 2)
-    double* out_d;            // mode 3: FP64 output grid (hole points written)
+    double* out_d;            // modes 0, 1, 3: if set, hole values written here as FP64 (instead of out)
     double* u_d;              // mode 2, FP64 path: u += v on holes
     long long* U;             // mode 2, mixed path: U += round(v * scale)
     double fixed_scale;       // 2^S for mode 2 mixed

@@ -617,6 +617,49 @@ cudaError_t bcr_level(const BcrSys<T>* groups, int ngroups, int level, bool back
                     : launch_level<T, false>(groups, ngroups, level, tune, st);
 }
 
+// ---------------------------------------------------------------------------
+// Iterative refinement of the separable systems: r = b - A x in FP64 for
+// A = block tridiagonal (a I, d I + T, c I), T = tridiag(tl, td, tu) (the
+// systems make_bcr factors), written as FP32 for the next FP32 solve; and
+// x += y (FP32 correction into the FP64 solution).
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void bcr_residual_kernel(const double* __restrict__ x, const double* __restrict__ b, float* __restrict__ r32,
+                                    int R, int C, double a, double d, double c, double tl, double td, double tu) {
+    const long long n = (long long)R * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / C), k = (int)(e % C);
+        double ax = (d + td) * x[e];
+        if (k > 0) ax += tl * x[e - 1];
+        if (k + 1 < C) ax += tu * x[e + 1];
+        if (i > 0) ax += a * x[e - C];
+        if (i + 1 < R) ax += c * x[e + C];
+        r32[e] = (float)(b[e] - ax);
+    }
+}
+__global__ void add_float_kernel(double* __restrict__ x, const float* __restrict__ y, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        x[e] += (double)y[e];
+}
+unsigned refine_grid(long long n) {
+    long long b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b));
+}
+}  // namespace
+
+cudaError_t bcr_residual(const double* x, const double* b, float* r32, int R, int C, const BcrCoefs& k,
+                         cudaStream_t st) {
+    bcr_residual_kernel<<<refine_grid((long long)R * C), 256, 0, st>>>(x, b, r32, R, C, k.a, k.d, k.c, k.tl, k.td, k.tu);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t add_float(double* x, const float* y, long long n, cudaStream_t st) {
+    add_float_kernel<<<refine_grid(n), 256, 0, st>>>(x, y, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template cudaError_t bcr_level<float>(const BcrSys<float>*, int, int, bool, const BcrTune*, cudaStream_t);
 template cudaError_t bcr_level<double>(const BcrSys<double>*, int, int, bool, const BcrTune*, cudaStream_t);
 template cudaError_t bcr_solve<float>(const BcrSys<float>*, int, cudaStream_t, const BcrTune*);
@@ -858,7 +901,7 @@ fill_holes_kernel(FillArgs<T> a) {
                 if (a.mode == FILL_RESIDUAL_TO_U) {
                     if (a.U) a.U[gidx] += __double2ll_rn((double)v * a.fixed_scale);
                     else a.u_d[gidx] += (double)v;
-                } else if (a.mode == FILL_ARRAY && a.out_d) {
+                } else if (a.out_d) {
                     a.out_d[gidx] = (double)v;
                 } else {
                     a.out[gidx] = v;
