@@ -700,20 +700,20 @@ gcr_dots_kernel(const T* __restrict__ q, const T* __restrict__ r, GcrDotArgs<T> 
     }
 }
 
-__global__ void reduce_partials_kernel(const double* partials, int nblocks, int ncols, double* out) {
-    __shared__ double red[32];
-    for (int q = 0; q < ncols; ++q) {
-        double acc = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += partials[(long long)b * ncols + q];
-        acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double v = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-            v = warp_sum(v);
-            if (threadIdx.x == 0) out[q] = v;
-        }
-        __syncthreads();
+// One CTA per column q: out[q] = sum over blocks of partials[b][q], in a fixed
+// order (strided per thread, then a fixed tree), so results are reproducible.
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const double* partials, int nblocks, int ncols, double* out) {
+    __shared__ double red[8];
+    const int q = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += partials[(long long)b * ncols + q];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) out[q] = v;
     }
 }
 
@@ -845,7 +845,8 @@ cudaError_t build_submesh_rhs(const double* s, const double* u, const Geometry& 
 }
 
 cudaError_t reduce_partials(const double* partials, int nblocks, int ncols, double* out, cudaStream_t st) {
-    reduce_partials_kernel<<<1, 1024, 0, st>>>(partials, nblocks, ncols, out);
+    if (ncols < 1) return cudaSuccess;
+    reduce_partials_kernel<<<ncols, 256, 0, st>>>(partials, nblocks, ncols, out);
     note_launch();
     return cudaGetLastError();
 }
