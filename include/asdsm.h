@@ -148,8 +148,9 @@ int asdsm_autotune(asdsm_handle* h, int precision);
 int asdsm_tune_get(const asdsm_handle* h, int32_t* out, int cap);
 int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n);
 
-/* Algorithm 4 (ASDSM).  The initial guess (Algorithm 1) is computed in FP64 in
- * both precisions; the mixed path then runs its sweeps as described above.
+/* Algorithm 4 (ASDSM).  The initial guess (Algorithm 1) has FP64 quality in
+ * both precisions (see asdsm_initial_guess); the mixed path then runs its
+ * sweeps as described above.
  * s: device N*N source term (boundary entries unused).
  * u: device N*N; its boundary ring carries the Dirichlet data g on input and
  * is never written; its interior is overwritten by the solution (or used as
@@ -158,9 +159,12 @@ int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n);
  * ASDSM_STAGNATED otherwise (u then holds the last iterate), or an error. */
 int asdsm_solve(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats);
 
-/* Algorithm 1 with b_cc given (the initial guess u^(0)), computed in the
- * handle's precision (FP32 steps for ASDSM_MIXED).  Same s/u contract as
- * asdsm_solve; writes the interior of u. */
+/* Algorithm 1 with b_cc given (the initial guess u^(0)) as asdsm_solve
+ * computes it: in FP64 for ASDSM_FP64; for ASDSM_MIXED with FP32 solves
+ * refined to FP64 quality (each submesh system: FP32 block cyclic reduction
+ * plus two refinement steps with its FP64 residual; merge in FP64; holes
+ * filled in FP32 and refined once).  Same s/u contract as asdsm_solve;
+ * writes the interior of u. */
 int asdsm_initial_guess(asdsm_handle* h, const double* s, double* u);
 
 /* Fine residual of Algorithm 4 step 3: r = b_ff - A_ff u over the interior,

@@ -1506,10 +1506,13 @@ int asdsm_initial_guess(asdsm_handle* h, const double* s, double* u) {
         CK(copy_interior<double, double>((const double*)h->w[0].z[0], u, h->g, h->st));
         CK(ring_from<double>(nullptr, (double*)h->w[0].z[0], h->g, 0, h->st));
     } else {
+        // The solver's mixed-path initial guess: FP32 solves refined to FP64 quality.
         CK(split_source(s, h->s_hi, h->s_lo, (long long)h->g.N * h->g.N, h->st));
         if ((rc = ensure_work<float>(h, 1))) return rc;
-        if ((rc = initial_guess_to_z<float>(h, s, u))) return rc;
-        CK(copy_interior<float, double>((const float*)h->w[1].z[0], u, h->g, h->st));
+        if ((rc = ensure_partials(h, std::max(2 * residual_grid_blocks(h->g), 4096)))) return rc;
+        if ((rc = initial_guess_refined(h, s, u))) return rc;
+        CK(copy_interior<double, double>((const double*)h->w[0].z[0], u, h->g, h->st));
+        CK(ring_from<double>(nullptr, (double*)h->w[0].z[0], h->g, 0, h->st));
         CK(ring_from<float>(nullptr, (float*)h->w[1].z[0], h->g, 0, h->st));
     }
     CK(cudaStreamSynchronize(h->st));

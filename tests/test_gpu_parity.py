@@ -83,7 +83,10 @@ def test_initial_guess_matches_oracle(lib, name, make, mc):
     disc = orc.Discretisation2D(p.N, mc, p.alpha, p.beta)
     b = disc.rhs(p.s, p.g)
     ref = disc.initial_guess(*b)
-    for prec, tol in ((lib.FP64, 1e-12), (lib.MIXED, 3e-5)):
+    # Mixed: FP32 solves with FP64-residual refinement (two steps per submesh
+    # system, one for the holes) reach the FP64 result to the refinement's
+    # contraction (~1e-6 per step) times the FP32 hole rounding.
+    for prec, tol in ((lib.FP64, 1e-12), (lib.MIXED, 1e-10)):
         with lib.Solver(p.N, mc, p.alpha, p.beta, precision=prec) as sv:
             u = _dev(p.g)
             sv.initial_guess(_dev(p.s), u)
