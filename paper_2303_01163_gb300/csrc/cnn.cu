@@ -5,9 +5,11 @@
 //   conv3x3(a; W, b)[o, i, j] = b[o] + sum_c sum_{p,q} W[o, c, p, q] a[c, i+p-1, j+q-1]
 //   (zero outside the image), images NCHW in FP32.
 //
-// Operands of every product (weights and activations) are optionally rounded
-// to BF16 when they are staged in shared memory; products accumulate in FP32
-// on the FMA pipes.  With rounding off the kernels are plain FP32.
+// With BF16 operands the 32-output-channel convolutions (the forward layers
+// 1-3 and the backward-data convolutions) run on the tensor cores (mma.sync
+// BF16, FP32 accumulation); the one-channel output layer and the weight
+// gradient round their operands to BF16 and accumulate in FP32 on the FMA
+// pipes.  With BF16 off every kernel is plain FP32 on the FMA pipes.
 #include "asdsm.h"
 #include "asdsm_internal.h"
 #include <cuda_runtime.h>
@@ -88,6 +90,111 @@ conv3x3_kernel(const float* __restrict__ in, int cin, const float* __restrict__ 
         if (mask) r = mask[idx] > 0.0f ? r : 0.0f;
         out[idx] = r;
     }
+}
+
+// The same convolution for 32 output channels on the tensor cores (BF16
+// operands, FP32 accumulation): an implicit GEMM out[pixel][o] =
+// sum_k A[pixel][k] W[o][k] with k = c*9 + 3p + q (zero beyond 9 cin, padded
+// to a multiple of 16), mma.sync m16n8k16.  A CTA owns 16 x 16 pixels; warp w
+// computes tile rows 2w, 2w+1 (one m16 fragment each: the 16 pixels of the
+// row) x 32 channels (4 n8 fragments).  The input tile of every channel (with
+// its halo) and the weights, as [o][k] rows padded to keep the B-fragment
+// loads conflict-free, are staged once in shared memory as BF16.
+__device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+__global__ void __launch_bounds__(CONV_THREADS)
+conv3x3_tc_kernel(const float* __restrict__ in, int cin, const float* __restrict__ W, const float* __restrict__ bias,
+                  float* __restrict__ out, int H, int Wd, int relu_out, const float* __restrict__ mask) {
+    extern __shared__ __align__(16) unsigned char tc_smem[];
+    constexpr int TP = TILE + 2;                        // 18
+    const int K = cin * 9;
+    const int Kp = (K + 15) / 16 * 16;
+    const int KS = Kp + 8;                              // row stride of the weight rows
+    __nv_bfloat16* tin = reinterpret_cast<__nv_bfloat16*>(tc_smem);        // [cin][18][18]
+    __nv_bfloat16* ws = tin + ((cin * TP * TP + 7) / 8) * 8;               // [32][KS]
+    const int b = blockIdx.z;
+    const int i0 = blockIdx.y * TILE, j0 = blockIdx.x * TILE;
+    const size_t plane = (size_t)H * Wd;
+    for (int e = threadIdx.x; e < cin * TP * TP; e += CONV_THREADS) {
+        const int c = e / (TP * TP), rq = e % (TP * TP);
+        const int ii = i0 + rq / TP - 1, jj = j0 + rq % TP - 1;
+        const float v = (ii >= 0 && ii < H && jj >= 0 && jj < Wd) ? in[((size_t)b * cin + c) * plane + (size_t)ii * Wd + jj] : 0.0f;
+        tin[e] = __float2bfloat16_rn(v);
+    }
+    for (int e = threadIdx.x; e < 32 * KS; e += CONV_THREADS) {
+        const int o = e / KS, k = e % KS;
+        ws[e] = __float2bfloat16_rn(k < K ? W[(size_t)o * K + k] : 0.0f);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    for (int kb = 0; kb < Kp; kb += 16) {
+        // the four reduction indices of this lane: kb + 2q + {0, 1, 8, 9}
+        int off[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = kb + 2 * q + (u & 1) + (u >> 1) * 8;
+            ok[u] = k < K;
+            const int c = ok[u] ? k / 9 : 0, t = ok[u] ? k % 9 : 0;
+            off[u] = c * TP * TP + (t / 3) * TP + (t % 3);
+        }
+        unsigned a[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int row = (2 * warp + i) * TP;        // tile row of this fragment (pixels along x)
+            auto at = [&](int u, int x) { return ok[u] ? tin[off[u] + row + x] : zero; };
+            a[i][0] = pack_bf16(at(0, g), at(1, g));
+            a[i][1] = pack_bf16(at(0, g + 8), at(1, g + 8));
+            a[i][2] = pack_bf16(at(2, g), at(3, g));
+            a[i][3] = pack_bf16(at(2, g + 8), at(3, g + 8));
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __nv_bfloat16* wr = ws + (size_t)(j * 8 + g) * KS + kb + 2 * q;
+            const unsigned b0 = *reinterpret_cast<const unsigned*>(wr);
+            const unsigned b1 = *reinterpret_cast<const unsigned*>(wr + 8);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                float* d = acc[i][j];
+                asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                             : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                             : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b0), "r"(b1));
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int y = i0 + 2 * warp + i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int x = j0 + g + ((e >> 1) << 3);
+                const int o = j * 8 + 2 * q + (e & 1);
+                if (y >= H || x >= Wd) continue;
+                const size_t idx = ((size_t)b * 32 + o) * plane + (size_t)y * Wd + x;
+                float r = acc[i][j][e] + (bias ? bias[o] : 0.0f);
+                if (relu_out) r = fmaxf(r, 0.0f);
+                if (mask) r = mask[idx] > 0.0f ? r : 0.0f;
+                out[idx] = r;
+            }
+    }
+}
+
+size_t conv_tc_smem(int cin) {
+    const int K = cin * 9, Kp = (K + 15) / 16 * 16;
+    return sizeof(__nv_bfloat16) * ((size_t)((cin * (TILE + 2) * (TILE + 2) + 7) / 8) * 8 + (size_t)32 * (Kp + 8));
 }
 
 // W'[c, o, 2-p, 2-q] = W[o, c, p, q]: the backward-data convolution is a
@@ -251,7 +358,14 @@ int ensure_space(asdsm_cnn* net, long long pix, long long ntiles) {
 cudaError_t conv(const float* in, int cin, int cout, const float* W, const float* bias, float* out, int B, int H,
                  int Wd, int relu, const float* mask, int bf16, cudaStream_t st) {
     dim3 grid((Wd + TILE - 1) / TILE, (H + TILE - 1) / TILE, B);
-    if (cout == 32) conv3x3_kernel<32><<<grid, CONV_THREADS, 0, st>>>(in, cin, W, bias, out, H, Wd, relu, mask, bf16);
+    if (cout == 32 && bf16) {
+        const size_t smem = conv_tc_smem(cin);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        conv3x3_tc_kernel<<<grid, CONV_THREADS, smem, st>>>(in, cin, W, bias, out, H, Wd, relu, mask);
+    } else if (cout == 32) conv3x3_kernel<32><<<grid, CONV_THREADS, 0, st>>>(in, cin, W, bias, out, H, Wd, relu, mask, bf16);
     else if (cout == 1) conv3x3_kernel<1><<<grid, CONV_THREADS, 0, st>>>(in, cin, W, bias, out, H, Wd, relu, mask, bf16);
     else return cudaErrorInvalidValue;
     asdsm::note_launch();
