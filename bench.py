@@ -147,6 +147,37 @@ def oracle_sample(sweeps_needed, N_full=N_GRID, N_sample=1025, mc_sample=64, see
             "seconds_measured": t3 - t0}
 
 
+# ---------------------------------------------------------------------------
+# Multi-rank host logic (one process per GPU under torchrun; weak scaling:
+# every rank solves its own instance, seed = rank, with no collective on the
+# data path).  The timing of a region is the maximum over ranks and the
+# job's throughput counts every rank's unknowns.
+# ---------------------------------------------------------------------------
+def rank_env():
+    """(world, rank, local_rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def instance_seed(rank: int) -> int:
+    return rank
+
+
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """The slowest rank's time (an all-reduce of one scalar), ms itself on one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, unknowns_per_rank: int, steps: int, ms: float) -> float:
+    """Unknowns solved by all ranks per second of the (max-over-ranks) time."""
+    return world * unknowns_per_rank * steps / (ms * 1e-3)
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, one bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -178,9 +209,7 @@ def run_ours(args):
     ge.build()
     from paper_2303_01163_gb300 import asdsm, workloads as wl
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -190,7 +219,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
 
     N, mc = args.grid, args.mc
-    p = wl.random_fourier_2d(N, rank)
+    p = wl.random_fourier_2d(N, instance_seed(rank))
     s = torch.tensor(p.s, dtype=torch.float64, device=dev)
     g = torch.tensor(p.g, dtype=torch.float64, device=dev)
     u = g.clone()
@@ -243,11 +272,7 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     # Per-kernel-family times from separate profiled solves (event pairs around
     # each family on the handle's stream; the profiled loop is host-driven, the
     # kernels are the ones the timed solves ran).
@@ -258,7 +283,7 @@ def run_ours(args):
     prof = solver.profile_read()
     solver.profile(False)
     unknowns = (N - 2) ** 2
-    value = world * unknowns * args.steps / (ms * 1e-3)
+    value = job_throughput(world, unknowns, args.steps, ms)
 
     # End to end through the public API with host buffers (pinned), per step:
     # H2D of s and of u's initial grid (ring = g), the solve, D2H of u.
@@ -281,12 +306,8 @@ def run_ours(args):
             raise RuntimeError(f"e2e solve did not converge: {r2.stats}")
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": world * unknowns * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    e2e = {"value": job_throughput(world, unknowns, args.steps, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": 2 * N * N * 8, "d2h_bytes_per_step": N * N * 8}
 
     # Plain FP64 GPU ASDSM on the same problem (the comparison the metric names).
