@@ -134,8 +134,10 @@ int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts);
 /* Autotune the launch shapes of this handle's kernels for one precision
  * (ASDSM_FP64 or ASDSM_MIXED): for every level of the block cyclic reductions
  * of the submesh systems (eq. 2.4) the rows per CTA and the number of CTAs
- * splitting the reduction, and the warps per CTA of the Filler (Algorithm 3)
- * are timed with CUDA events on the handle's stream and the fastest kept.
+ * splitting the reduction, and the Filler's kernel (Algorithm 3: the
+ * tensor-core kernel for n = 16 on the mixed path, or the block cyclic
+ * reduction kernel at 8, 4, 2 or 1 warps per CTA) are timed with CUDA events
+ * on the handle's stream and the fastest kept.
  * Not part of the paper's method; the arithmetic of a solve is the same up
  * to the summation order inside the level products.  Synchronises the
  * stream; takes tens of milliseconds.  Returns ASDSM_OK or an error. */
@@ -143,7 +145,9 @@ int asdsm_autotune(asdsm_handle* h, int precision);
 
 /* The handle's launch shapes (as chosen by asdsm_autotune, or 0 = built-in)
  * as 130 integers, to save a tuning and apply it to another handle of the
- * same sizes (asdsm_tune_set; n must be 130).  get returns the count written
+ * same sizes (asdsm_tune_set; n must be 130).  The Filler entry of each
+ * precision is 16 for the tensor-core kernel, 1..8 for the block cyclic
+ * reduction kernel's warps per CTA, 0 for the default.  get returns the count written
  * (cap >= 130) or ASDSM_ERR_INVALID. */
 int asdsm_tune_get(const asdsm_handle* h, int32_t* out, int cap);
 int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n);
@@ -182,6 +186,12 @@ int asdsm_residual(asdsm_handle* h, const double* s, const double* u, double* r,
  *   2 = A_cc on Omega^{H,H}: layout [y][x]
  *   3 = the holes (P A P^T of Algorithm 3): in/out are N*N grids; only hole
  *       points are read and written (others are left untouched in out).
+ *   4 = Algorithm 3 with zero source (the form every sweep uses): out's hole
+ *       points receive the hole solutions whose Dirichlet data are in's
+ *       skeleton values (in: N*N grid, only skeleton points read); other
+ *       points of out are left untouched.  For n = 16 on the mixed path this
+ *       is the tensor-core Filler unless the tuned state selects the block
+ *       cyclic reduction kernel.
  * in/out: device FP64 arrays; they may not alias. */
 int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out);
 

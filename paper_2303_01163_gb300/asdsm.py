@@ -30,7 +30,7 @@ ERR_RANGE = -7
 FP64 = 0
 MIXED = 1
 
-MESH_FC, MESH_CF, MESH_CC, MESH_HOLES = 0, 1, 2, 3
+MESH_FC, MESH_CF, MESH_CC, MESH_HOLES, MESH_HOLES_HOMOGENEOUS = 0, 1, 2, 3, 4
 
 
 class Desc(ctypes.Structure):

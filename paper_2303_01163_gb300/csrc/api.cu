@@ -111,6 +111,10 @@ struct asdsm_handle {
     // A_cc, and warps per CTA of the Filler, per precision.
     BcrTune tune_aniso[2] = {}, tune_cc[2] = {};
     int fill_warps[2] = {0, 0};
+    // Tensor-core Filler (holes of 15 x 15): the swizzled image of the hole
+    // extension operator G and the kernel's timeout flag.
+    float* fill_tc_img = nullptr;
+    int* dtcerr = nullptr;
     // Learned correction (asdsm_attach_cnn): the network and its input/output grids.
     asdsm_cnn* cnn = nullptr;
     float* cnn_x = nullptr;            // 6 x N x N
@@ -202,6 +206,32 @@ void hole_factors(const asdsm_handle* h, int pi, FillArgs<T>* fa) {
     for (int l = 0; l < d.L; ++l) { fa->wl[l] = (T)d.wl[l]; fa->wr[l] = (T)d.wr[l]; }
     fa->L = d.L;
     fa->warps = h->fill_warps[pi];
+}
+
+// The Filler's kernel for precision pi: fill_warps[pi] == kFillTcCode selects
+// the tensor-core kernel, 1..8 the warps per CTA of the block cyclic reduction
+// kernel, 0 the default (the tensor-core kernel where it applies).
+constexpr int kFillTcCode = 16;
+bool use_fill_tc(const asdsm_handle* h, int pi) {
+    return pi == 1 && h->fill_tc_img && (h->fill_warps[1] == 0 || h->fill_warps[1] == kFillTcCode);
+}
+
+// Algorithm 3 with zero source on the direction z (in place): the hole values
+// of z from its skeleton values.
+template <typename T>
+cudaError_t fill_homogeneous(const asdsm_handle* h, int pi, T* z, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (use_fill_tc(h, pi)) {
+            FillTcArgs ta{h->fill_tc_img, z, nullptr, h->g.N, h->g.mc, h->dtcerr};
+            return fill_tc(ta, h->num_sms, st);
+        }
+    }
+    FillArgs<T> fa{};
+    fa.mode = FILL_HOMOGENEOUS;
+    fa.z = z; fa.out = z;
+    hole_factors<T>(h, pi, &fa);
+    fa.n = h->g.n; fa.g = h->g; fa.sten = h->sten;
+    return fill_holes<T>(fa, h->num_sms, st);
 }
 
 template <typename T>
@@ -537,12 +567,7 @@ int enqueue_sweep_body(asdsm_handle* h, int kc, int m, cudaStream_t st) {
     ma.z = z; ma.g = g;
     CK(merge_knots<T>(ma, st));
     CK(merge_write<T>(ma, st));
-    FillArgs<T> fa{};
-    fa.mode = FILL_HOMOGENEOUS;
-    fa.z = z; fa.out = z;
-    hole_factors<T>(h, pi, &fa);
-    fa.n = g.n; fa.g = g; fa.sten = h->sten;
-    CK(fill_holes<T>(fa, h->num_sms, st));
+    CK(fill_homogeneous<T>(h, pi, z, st));
     CK(skeleton_apply<T>(z, g, h->sten, (T*)w.q, st));
     const T* qpv[kMaxM];
     for (int j = 0; j < kc; ++j) qpv[j] = (const T*)w.qp[j];
@@ -808,19 +833,16 @@ int autotune_impl(asdsm_handle* h) {
     if (int rc = tune_bcr<T>(h, sys, 2, &h->tune_aniso[pi], a, b)) return done(rc);
     BcrSys<T> scc = sys_of<T>(h->cc[pi], w.Xcc, w.Ycc);
     if (int rc = tune_bcr<T>(h, &scc, 1, &h->tune_cc[pi], a, b)) return done(rc);
-    // Filler (homogeneous mode on a zero grid).
-    FillArgs<T> fa{};
-    fa.mode = FILL_HOMOGENEOUS;
-    fa.z = (const T*)w.z[0]; fa.out = (T*)w.z[0];
-    hole_factors<T>(h, pi, &fa);
-    fa.n = g.n; fa.g = g; fa.sten = h->sten;
+    // Filler (homogeneous mode): the tensor-core kernel where it applies, and
+    // the block cyclic reduction kernel at 8, 4, 2, 1 warps per CTA.
     float best = 1e30f;
     int bestw = 0;
-    for (int wv : {8, 4, 2, 1}) {
-        fa.warps = wv;
+    for (int wv : {kFillTcCode, 8, 4, 2, 1}) {
+        if (wv == kFillTcCode && !(pi == 1 && h->fill_tc_img)) continue;
+        h->fill_warps[pi] = wv;
         float ms = 0.f;
         if (int rc = time_ms<T>(h, a, b, 3, &ms, [&]() -> int {
-                CK(fill_holes<T>(fa, h->num_sms, h->st));
+                CK(fill_homogeneous<T>(h, pi, (T*)w.z[0], h->st));
                 return ASDSM_OK;
             })) return done(rc);
         if (ms < best) { best = ms; bestw = wv; }
@@ -999,14 +1021,9 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
             CK(merge_write<T>(ma, st));
             prof_end(h, pm, PC_MERGE, ES * 4.0 * g.Nf * g.Nc, 0.0);
         }
-        FillArgs<T> fa{};
-        fa.mode = FILL_HOMOGENEOUS;
-        fa.z = z; fa.out = z;
-        hole_factors<T>(h, pi, &fa);
-        fa.n = g.n; fa.g = g; fa.sten = h->sten;
         {
             const ProfMark pm = prof_begin(h);
-            CK(fill_holes<T>(fa, h->num_sms, st));
+            CK(fill_homogeneous<T>(h, pi, z, st));
             const double holes = (double)g.mc * g.mc;
             const double flops = 2.0 * holes * bcr_macs(g.n - 1, g.n - 1, h->hole[pi].L);
             const double bytes = ES * (holes * (g.n - 1.0) * (g.n - 1.0) + holes * 4.0 * (g.n - 1.0));
@@ -1079,12 +1096,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
         if (mixed && h->cnn && m > 1 && kc != 0) {
             T* zc = (T*)w.z[kc];
             if (int rc = cnn_direction(h, r2, (const float*)z, (float*)zc)) return rc;
-            FillArgs<T> fc{};
-            fc.mode = FILL_HOMOGENEOUS;
-            fc.z = zc; fc.out = zc;
-            hole_factors<T>(h, pi, &fc);
-            fc.n = g.n; fc.g = g; fc.sten = h->sten;
-            CK(fill_holes<T>(fc, h->num_sms, st));
+            CK(fill_homogeneous<T>(h, pi, zc, st));
             const int dep2 = gcr_step(zc, true);
             if (dep2 < 0) return dep2;
             if (dep2 == 0) ++h->cnn_dirs;
@@ -1205,8 +1217,15 @@ int run_finish(asdsm_handle* h, SolveRun& r) {
     } else if (r.status != ASDSM_ERR_RANGE) {
         CK(from_fixed(h->U[r.Ucur], std::ldexp(1.0, -r.S), r.u, g, st));
     }
+    int* tcerr = reinterpret_cast<int*>(h->hsmall + 4095);
+    *tcerr = 0;
+    CK(cudaMemcpyAsync(tcerr, h->dtcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(h->ev2, st));
     CK(cudaEventSynchronize(h->ev2));
+    if (*tcerr) {
+        g_last_error = "tensor-core Filler: a wait timed out";
+        return ASDSM_ERR_CUDA;
+    }
     float ms_setup = 0.f, ms_all = 0.f;
     cudaEventElapsedTime(&ms_setup, h->ev0, h->ev1);
     cudaEventElapsedTime(&ms_all, h->ev0, h->ev2);
@@ -1370,6 +1389,17 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if ((e = cudaMalloc(&h->s_lo, NN * sizeof(float))) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaMalloc(&h->dsmall, 256 * sizeof(double))) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaMalloc(&h->dflag, sizeof(int))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMalloc(&h->dtcerr, sizeof(int))) != cudaSuccess) return fail(set_cuda_error(e));
+    if ((e = cudaMemset(h->dtcerr, 0, sizeof(int))) != cudaSuccess) return fail(set_cuda_error(e));
+    if (g.n == kFillTcN) {
+        std::vector<double> G;
+        if (!hole_extension_operator(g.n - 1, h->sten, &G)) return fail(ASDSM_ERR_INVALID);
+        std::vector<float> img;
+        fill_tc_image(G, &img);
+        if ((e = cudaMalloc(&h->fill_tc_img, fill_tc_image_bytes())) != cudaSuccess) return fail(set_cuda_error(e));
+        if ((e = cudaMemcpy(h->fill_tc_img, img.data(), fill_tc_image_bytes(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(set_cuda_error(e));
+    }
     if ((e = cudaMallocHost(&h->hsmall, 4096 * sizeof(double))) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess) return fail(set_cuda_error(e));
     if ((e = cudaEventCreate(&h->ev1)) != cudaSuccess) return fail(set_cuda_error(e));
@@ -1611,6 +1641,36 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
             fa.n = g.n; fa.g = g; fa.sten = h->sten;
             CK(fill_holes<float>(fa, h->num_sms, st));
         }
+    } else if (mesh == 4) {
+        if (fp64) {
+            FillArgs<double> fa{};
+            fa.mode = FILL_HOMOGENEOUS; fa.z = in; fa.out_d = out;
+            hole_factors<double>(h, 0, &fa);
+            fa.n = g.n; fa.g = g; fa.sten = h->sten;
+            CK(fill_holes<double>(fa, h->num_sms, st));
+        } else {
+            float* z32 = (float*)w.z[0];
+            CK(convert_array<double, float>(in, z32, (long long)g.N * g.N, st));
+            if (use_fill_tc(h, 1)) {
+                CK(cudaMemsetAsync(h->dtcerr, 0, sizeof(int), st));
+                FillTcArgs ta{h->fill_tc_img, z32, out, g.N, g.mc, h->dtcerr};
+                CK(fill_tc(ta, h->num_sms, st));
+                int err = 0;
+                CK(cudaMemcpyAsync(h->hsmall, h->dtcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                std::memcpy(&err, h->hsmall, sizeof(int));
+                if (err) {
+                    g_last_error = "tensor-core Filler: a wait timed out";
+                    return ASDSM_ERR_CUDA;
+                }
+            } else {
+                FillArgs<float> fa{};
+                fa.mode = FILL_HOMOGENEOUS; fa.z = z32; fa.out_d = out;
+                hole_factors<float>(h, 1, &fa);
+                fa.n = g.n; fa.g = g; fa.sten = h->sten;
+                CK(fill_holes<float>(fa, h->num_sms, st));
+            }
+        }
     } else {
         return ASDSM_ERR_INVALID;
     }
@@ -1800,7 +1860,7 @@ void asdsm_destroy(asdsm_handle* h) {
         for (int q = 0; q < w.nz; ++q) { fr(w.z[q]); fr(w.qp[q]); }
     }
     fr(h->u_work); fr(h->U[0]); fr(h->U[1]); fr(h->s_hi); fr(h->s_lo);
-    fr(h->partials); fr(h->dsmall); fr(h->dflag);
+    fr(h->partials); fr(h->dsmall); fr(h->dflag); fr(h->dtcerr); fr(h->fill_tc_img);
     if (h->hsmall) cudaFreeHost(h->hsmall);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);

@@ -141,6 +141,26 @@ cudaError_t fill_holes(const FillArgs<T>& a, int num_sms, cudaStream_t st);
 template <typename T>
 size_t fill_smem_bytes(int n, int L);
 
+// Discrete harmonic extension of a C x C hole (Algorithm 3 with zero source,
+// host_math.cu): the hole values v (row by row, y = 1..C, x = 1..C) are G z
+// for the 4C ring values z ordered west (y = 1..C), east (y = 1..C), south
+// (x = 1..C), north (x = 1..C); G = -A_hh^{-1} A_hs, [C*C][4C] row-major.
+bool hole_extension_operator(int C, const Stencil& s, std::vector<double>* G);
+
+// Tensor-core Filler (fill_tc.cu): the homogeneous fill for holes of
+// kFillTcN - 1 = 15 points per side (n = 16), FP32 results.
+constexpr int kFillTcN = 16;
+struct FillTcArgs {
+    const float* gimg;   // fill_tc_image() of G, fill_tc_image_bytes() bytes, 16-byte aligned
+    float* z;            // full grid: ring values read, hole values written (unless out_d)
+    double* out_d;       // if set, hole values written here in FP64 instead of into z
+    int N, mc;           // N = 16 mc + 1
+    int* err;            // set to 1 when a wait timed out (the fill is then incomplete)
+};
+size_t fill_tc_image_bytes();
+void fill_tc_image(const std::vector<double>& G, std::vector<float>* img);
+cudaError_t fill_tc(const FillTcArgs& a, int num_sms, cudaStream_t st);
+
 // Right-hand sides of eq. (2.4) on the submeshes (Dirichlet lifting from u's ring).
 template <typename T>
 cudaError_t build_submesh_rhs(const double* s, const double* u, const Geometry& g,

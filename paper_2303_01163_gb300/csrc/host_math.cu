@@ -78,6 +78,33 @@ void transpose_into(const double* M, double* out, int n) {
 
 }  // namespace
 
+bool hole_extension_operator(int C, const Stencil& s, std::vector<double>* G) {
+    const int n = C * C, K = 4 * C;
+    auto id = [C](int y, int x) { return (y - 1) * C + (x - 1); };
+    std::vector<double> A((size_t)n * n, 0.0);
+    for (int y = 1; y <= C; ++y)
+        for (int x = 1; x <= C; ++x) {
+            const size_t r = (size_t)id(y, x) * n;
+            A[r + id(y, x)] = s.cc;
+            if (x > 1) A[r + id(y, x - 1)] = s.cw;
+            if (x < C) A[r + id(y, x + 1)] = s.ce;
+            if (y > 1) A[r + id(y - 1, x)] = s.cs;
+            if (y < C) A[r + id(y + 1, x)] = s.cn;
+        }
+    if (!invert(A, n)) return false;
+    // Ring value k enters the equation of one hole point q with coefficient c:
+    // column k of G is -c times column q of A_hh^{-1}.
+    G->assign((size_t)n * K, 0.0);
+    for (int i = 1; i <= C; ++i) {
+        const int ks[4] = {i - 1, C + i - 1, 2 * C + i - 1, 3 * C + i - 1};
+        const int qs[4] = {id(i, 1), id(i, C), id(1, i), id(C, i)};
+        const double cf[4] = {s.cw, s.ce, s.cs, s.cn};
+        for (int t = 0; t < 4; ++t)
+            for (int p = 0; p < n; ++p) (*G)[(size_t)p * K + ks[t]] = -cf[t] * A[(size_t)p * n + qs[t]];
+    }
+    return true;
+}
+
 bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, double tu, BcrFactors* out) {
     int L = 0;
     while (((1 << L) - 1) < R) ++L;
