@@ -58,6 +58,12 @@ struct BcrSys {
     const float* Mw;
     const float* Bw;
     int KW, CW;
+    // FP32 only: the factors for the tensor-core level kernel (bcr_tc.cu),
+    // B operand blocks [L][pass: B^-1, M][split: hi, lo][TCB][TKC] of 128
+    // columns x 32 reduction values, swizzled; null when absent.
+    const float* Ti;
+    int TKC, TCB;
+    int* tc_err;       // set to 1 when a tensor-core kernel's wait timed out
 };
 
 // Stencil coefficients of A_ff (5-point, Section 2.3): A u = cc u_c + cw u_w + ce u_e + cs u_s + cn u_n.
@@ -86,7 +92,8 @@ long long launch_count();
 // Launch shape of every BCR level: cfg[dir][level] = (TM << 8) | KS with TM
 // in {16, 64} output rows per CTA and KS in {1, 2, 4, 8} CTAs per cluster
 // splitting the reduction, or TM = 32: the wide tensor-core kernel (FP32, 32
-// rows x 256 columns per CTA, KS = 1); 0 (or no table) = the built-in choice.
+// rows x 256 columns per CTA, mma.sync, KS = 1), or TM = 128: the tcgen05
+// kernel (FP32, 128 x 128 per CTA, KS = 1); 0 (or no table) = the built-in choice.
 struct BcrTune {
     int cfg[2][kMaxLevels];    // [0] forward, [1] backward
     int num_sms;
@@ -140,6 +147,12 @@ template <typename T>
 cudaError_t fill_holes(const FillArgs<T>& a, int num_sms, cudaStream_t st);
 template <typename T>
 size_t fill_smem_bytes(int n, int L);
+
+// Tensor-core BCR level kernel (bcr_tc.cu), FP32 systems: the image of the
+// factors (BcrSys::Ti, TKC, TCB) and one level for 1 or 2 groups.
+void bcr_tc_image(const BcrFactors& f, std::vector<float>* img, int* KC, int* CB);
+cudaError_t bcr_tc_level(const BcrSys<float>& g0, const BcrSys<float>& g1, int ngroups, int level, bool backward,
+                         int maxRows, int nsys, cudaStream_t st);
 
 // Discrete harmonic extension of a C x C hole (Algorithm 3 with zero source,
 // host_math.cu): the hole values v (row by row, y = 1..C, x = 1..C) are G z

@@ -22,6 +22,7 @@
 // Every wait on an mbarrier is bounded (1 s by %globaltimer); on a timeout the
 // kernel sets *err, stops, and frees its tensor memory.
 #include "asdsm_internal.h"
+#include "tc_common.cuh"
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstring>
@@ -43,85 +44,16 @@ constexpr int TC_A_BYTES = 2 * TC_MT * 2 * TC_BLK;     // [hi/lo][mt][kb] = 128 
 constexpr int TC_B_BYTES = 2 * 2 * TC_BLK;             // [hi/lo][kb] = 64 KB
 constexpr int TC_SMEM = TC_A_BYTES + TC_B_BYTES + 1024;  // + alignment slack
 constexpr uint32_t TC_TMEM_COLS = 2 * TC_HOLES;        // 256
-constexpr unsigned long long kTcWaitNs = 1000000000ull;
 
 // Byte offset of element (row r, k) inside one [mt] image of 2 K blocks:
 // rows 128 bytes apart, 16-byte chunks XOR-swizzled by r mod 8.
 __host__ __device__ __forceinline__ int tc_offset(int r, int k) {
-    const int kb = k >> 5, kk = k & 31;
-    return kb * TC_BLK + r * 128 + ((((kk >> 2) ^ (r & 7))) << 4) + (kk & 3) * 4;
+    return (k >> 5) * TC_BLK + tc::swz_offset(r, k & 31);
 }
 
-// Instruction descriptor of tcgen05.mma kind::tf32: D F32, A and B TF32, both
-// K-major, N = 128, M = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_HOLES >> 3) << 17) |
-                              ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t kTcIdesc128 = tc::idesc_tf32(128, TC_HOLES);
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long now_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = now_ns();
-    while (!mbar_try(bar, parity))
-        if (now_ns() - t0 > kTcWaitNs) return false;
-    return true;
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-        :
-        : "r"(d), "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_before_sync() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after_sync() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
+using namespace tc;
 
 __global__ void __launch_bounds__(TC_THREADS, 1) fill_tc_kernel(FillTcArgs a) {
     extern __shared__ unsigned char tc_raw[];
@@ -134,30 +66,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fill_tc_kernel(FillTcArgs a) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t bar_g = smem_u32(&bars[0]), bar_m = smem_u32(&bars[1]);
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_g) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_m) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init(bar_g, 1);
+        mbar_init(bar_m, 1);
+        mbar_init_fence();
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                     "r"(TC_TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_holder), TC_TMEM_COLS);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tbase = tmem_holder;
     // The A operand (G, hi and lo) by bulk copies into the swizzled image.
     if (tid == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_g), "r"(TC_A_BYTES) : "memory");
+        mbar_expect_tx(bar_g, TC_A_BYTES);
         const unsigned char* src = reinterpret_cast<const unsigned char*>(a.gimg);
-        for (int c = 0; c < TC_A_BYTES / TC_BLK; ++c)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    sA + c * TC_BLK),
-                "l"(src + (size_t)c * TC_BLK), "r"(TC_BLK), "r"(bar_g)
-                : "memory");
+        for (int c = 0; c < TC_A_BYTES / TC_BLK; ++c) bulk_g2s(sA + c * TC_BLK, src + (size_t)c * TC_BLK, TC_BLK, bar_g);
     }
     bool ok = __syncthreads_and(mbar_wait(bar_g, 0)) != 0;
     const int N = a.N, mc = a.mc;
@@ -182,13 +104,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fill_tc_kernel(FillTcArgs a) {
 #pragma unroll
             for (int k = 0; k < TC_K; ++k) {
                 const float v = k < TC_RING ? zr[k] : 0.f;
-                const float hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+                const float hi = tc::tf32_hi(v);
                 const int off = tc_offset(tid, k);
                 *reinterpret_cast<float*>(pB + off) = hi;
                 *reinterpret_cast<float*>(pB + 2 * TC_BLK + off) = v - hi;
             }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_async_smem();
         fence_before_sync();
         __syncthreads();
         if (tid == 0) {
@@ -203,13 +125,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fill_tc_kernel(FillTcArgs a) {
                     const uint64_t aLo = sw128_desc(sA + (uint32_t)((1 * TC_MT + mt) * 2 * TC_BLK) + koff);
                     const uint64_t bHi = sw128_desc(sB + koff);
                     const uint64_t bLo = sw128_desc(sB + 2 * TC_BLK + koff);
-                    tc_mma(d, aLo, bHi, ks > 0 ? 1u : 0u);    // small terms first
-                    tc_mma(d, aHi, bLo, 1u);
-                    tc_mma(d, aHi, bHi, 1u);
+                    tc_mma(d, aLo, bHi, kTcIdesc128, ks > 0 ? 1u : 0u);    // small terms first
+                    tc_mma(d, aHi, bLo, kTcIdesc128, 1u);
+                    tc_mma(d, aHi, bHi, kTcIdesc128, 1u);
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_m)
-                         : "memory");
+            tc_commit(bar_m);
         }
         const bool done = mbar_wait(bar_m, phase);
         phase ^= 1u;
@@ -254,7 +175,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fill_tc_kernel(FillTcArgs a) {
     __syncthreads();
     if (warp == 0) {
         fence_after_sync();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_TMEM_COLS) : "memory");
+        tmem_dealloc(tbase, TC_TMEM_COLS);
     }
 }
 
@@ -272,11 +193,7 @@ void fill_tc_image(const std::vector<double>& G, std::vector<float>* img) {
             const int hp = y * TC_C + (x - 1);         // hole point (y+1, x) in row-major order
             for (int k = 0; k < TC_RING; ++k) {
                 const double gv = G[(size_t)hp * TC_RING + k];
-                float hi = (float)gv;
-                uint32_t bits;
-                std::memcpy(&bits, &hi, 4);
-                bits &= 0xFFFFE000u;
-                std::memcpy(&hi, &bits, 4);
+                const float hi = tc::tf32_hi((float)gv);
                 const float lo = (float)(gv - (double)hi);
                 const int off = tc_offset(r, k);
                 std::memcpy(base + (size_t)(0 * TC_MT + mt) * 2 * TC_BLK + off, &hi, 4);

@@ -558,8 +558,21 @@ cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, const 
         tm = v >> 8;
         ks = v & 0xFF;
     }
-    bool wide_ok = sizeof(T) == 4;
-    for (int q = 0; q < ngroups; ++q) wide_ok = wide_ok && groups[q].Mw && groups[q].Bw;
+    bool wide_ok = sizeof(T) == 4, tc_ok = sizeof(T) == 4;
+    for (int q = 0; q < ngroups; ++q) {
+        wide_ok = wide_ok && groups[q].Mw && groups[q].Bw;
+        tc_ok = tc_ok && groups[q].Ti;
+    }
+    if (tm == 128 && tc_ok) {
+        cudaError_t e = cudaSuccess;
+        if constexpr (sizeof(T) == 4) {
+            e = bcr_tc_level(reinterpret_cast<const BcrSys<float>&>(groups[0]), reinterpret_cast<const BcrSys<float>&>(g1),
+                             ngroups, level, kBackward, maxRows, nsys, st);
+        }
+        note_launch();
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     if (tm == 32 && wide_ok) {
         int CW = groups[0].CW;
         dim3 grid(CW / WD_COLS, (maxRows + WD_ROWS - 1) / WD_ROWS, nsys);

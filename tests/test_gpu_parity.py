@@ -261,11 +261,14 @@ def test_resume_from_a_given_iterate(lib):
             assert r2.stats["rel_res0"] <= r1.stats["rel_res"] * 1.5
 
 
-@pytest.mark.parametrize("name,make,mc", CASES[:3] + [("fourier257", lambda: wl.random_fourier_2d(257, 5), 8)])
-def test_tensor_core_level_kernels_match_oracle(lib, name, make, mc):
-    """Every level of the FP32 anisotropic solves forced onto the wide
-    tensor-core kernel (TF32 split products): A_fc^-1 and A_cf^-1 within the
-    FP32 bar, and a mixed solve still reaches the fine solution."""
+@pytest.mark.parametrize("tm", [32, 128])
+@pytest.mark.parametrize("name,make,mc", CASES[:3] + [("fourier257", lambda: wl.random_fourier_2d(257, 5), 8),
+                                                      ("fourier513_c255", lambda: wl.random_fourier_2d(513, 6), 256)])
+def test_tensor_core_level_kernels_match_oracle(lib, name, make, mc, tm):
+    """Every level of the FP32 submesh solves forced onto a tensor-core kernel
+    (TF32 split products; tm = 32: the mma.sync kernel for A_fc and A_cf,
+    tm = 128: the tcgen05 kernel for A_fc, A_cf and A_cc): the solves within
+    the FP32 bar, and a mixed solve still reaches the fine solution."""
     import torch
     p = make()
     disc = orc.Discretisation2D(p.N, mc, p.alpha, p.beta)
@@ -275,10 +278,13 @@ def test_tensor_core_level_kernels_match_oracle(lib, name, make, mc):
         state = sv.tune_state()
         # layout: per precision [aniso fwd 16, aniso bwd 16, cc fwd 16, cc bwd 16, fill]; FP32 second
         base = 4 * 16 + 1
-        for q in range(32):
-            state[base + q] = (32 << 8) | 1
+        for q in range(64 if tm == 128 else 32):
+            state[base + q] = (tm << 8) | 1
         sv.set_tune_state(state)
-        for mesh, size, lu in ((lib.MESH_FC, m.Nc * m.Nf, disc.lu_fc), (lib.MESH_CF, m.Nc * m.Nf, disc.lu_cf)):
+        meshes = [(lib.MESH_FC, m.Nc * m.Nf, disc.lu_fc), (lib.MESH_CF, m.Nc * m.Nf, disc.lu_cf)]
+        if tm == 128:
+            meshes.append((lib.MESH_CC, m.Nc * m.Nc, disc.lu_cc))
+        for mesh, size, lu in meshes:
             f = rng.normal(size=size)
             out = torch.zeros(size, dtype=torch.float64, device="cuda")
             sv.submesh_solve(mesh, _dev(f), out)
