@@ -83,6 +83,7 @@ struct asdsm_handle {
         void* rskel = nullptr; void* q = nullptr;
         void* qp[kMaxM] = {};
         void* rfull = nullptr;   // full-grid residual for hole corrections
+        void* zv = nullptr;      // FP32 with the tensor-core Filler: line values [N][mc+1] (MergeArgs::zv)
     } w[2];
     double* u_work = nullptr;       // FP64 ping-pong partner of the caller's u
     long long* U[2] = {nullptr, nullptr};
@@ -228,11 +229,12 @@ bool use_fill_tc(const asdsm_handle* h, int pi) {
 
 // Algorithm 3 with zero source on the direction z (in place): the hole values
 // of z from its skeleton values.
+// zv: the line values merge_write stored apart (MergeArgs::zv), or null.
 template <typename T>
-cudaError_t fill_homogeneous(const asdsm_handle* h, int pi, T* z, cudaStream_t st) {
+cudaError_t fill_homogeneous(const asdsm_handle* h, int pi, T* z, cudaStream_t st, const T* zv = nullptr) {
     if constexpr (sizeof(T) == 4) {
         if (use_fill_tc(h, pi)) {
-            FillTcArgs ta{h->fill_tc_img, z, nullptr, h->g.N, h->g.mc, h->dtcerr};
+            FillTcArgs ta{h->fill_tc_img, z, nullptr, zv, h->g.N, h->g.mc, h->dtcerr};
             return fill_tc(ta, h->num_sms, st);
         }
     }
@@ -262,6 +264,11 @@ int ensure_work(asdsm_handle* h, int pi, int slots = -1) {
         CK(cudaMalloc(&w.q, (size_t)g.skel * sizeof(T)));
         CK(cudaMalloc(&w.rfull, (size_t)g.N * g.N * sizeof(T)));
         CK(cudaMemsetAsync(w.rfull, 0, (size_t)g.N * g.N * sizeof(T), h->st));
+        if (sizeof(T) == 4 && h->fill_tc_img) {
+            const size_t zvb = (size_t)g.N * (g.mc + 1) * sizeof(float);
+            CK(cudaMalloc(&w.zv, zvb));
+            CK(cudaMemsetAsync(w.zv, 0, zvb, h->st));        // columns 0 and mc (the boundary) stay zero
+        }
         w.ready = true;
     }
     while (w.nz < m) {
@@ -575,9 +582,10 @@ int enqueue_sweep_body(asdsm_handle* h, int kc, int m, cudaStream_t st) {
     ma.Sm = (const T*)h->Sm[pi];
     ma.E1 = (T*)w.E1; ma.E2 = (T*)w.E2; ma.M1 = (T*)w.M1; ma.M2 = (T*)w.M2;
     ma.z = z; ma.g = g;
+    ma.zv = use_fill_tc(h, pi) ? (T*)w.zv : nullptr;
     CK(merge_knots<T>(ma, st));
     CK(merge_write<T>(ma, st));
-    CK(fill_homogeneous<T>(h, pi, z, st));
+    CK(fill_homogeneous<T>(h, pi, z, st, (const T*)ma.zv));
     CK(skeleton_apply<T>(z, g, h->sten, (T*)w.q, st));
     const T* qpv[kMaxM];
     for (int j = 0; j < kc; ++j) qpv[j] = (const T*)w.qp[j];
@@ -1062,6 +1070,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
         ma.Sm = (const T*)h->Sm[pi];
         ma.E1 = (T*)w.E1; ma.E2 = (T*)w.E2; ma.M1 = (T*)w.M1; ma.M2 = (T*)w.M2;
         ma.z = z; ma.g = g;
+        ma.zv = use_fill_tc(h, pi) ? (T*)w.zv : nullptr;
         {
             const ProfMark pm = prof_begin(h);
             CK(merge_knots<T>(ma, st));
@@ -1070,7 +1079,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
         }
         {
             const ProfMark pm = prof_begin(h);
-            CK(fill_homogeneous<T>(h, pi, z, st));
+            CK(fill_homogeneous<T>(h, pi, z, st, (const T*)ma.zv));
             const double holes = (double)g.mc * g.mc;
             const double flops = 2.0 * holes * bcr_macs(g.n - 1, g.n - 1, h->hole[pi].L);
             const double bytes = ES * (holes * (g.n - 1.0) * (g.n - 1.0) + holes * 4.0 * (g.n - 1.0));
@@ -1702,7 +1711,7 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
             CK(convert_array<double, float>(in, z32, (long long)g.N * g.N, st));
             if (use_fill_tc(h, 1)) {
                 CK(cudaMemsetAsync(h->dtcerr, 0, sizeof(int), st));
-                FillTcArgs ta{h->fill_tc_img, z32, out, g.N, g.mc, h->dtcerr};
+                FillTcArgs ta{h->fill_tc_img, z32, out, nullptr, g.N, g.mc, h->dtcerr};
                 CK(fill_tc(ta, h->num_sms, st));
                 int err = 0;
                 CK(cudaMemcpyAsync(h->hsmall, h->dtcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1904,7 +1913,7 @@ void asdsm_destroy(asdsm_handle* h) {
         for (auto* d : ds) { fr(d->Mt); fr(d->Bt); fr(d->Mw); fr(d->Bw); fr(d->Ti); }
         fr(h->Sm[p]);
         auto& w = h->w[p];
-        void* bufs[] = {w.Xfc, w.Xcf, w.Yfc, w.Ycf, w.Xcc, w.Ycc, w.E1, w.E2, w.M1, w.M2, w.rskel, w.q, w.rfull};
+        void* bufs[] = {w.Xfc, w.Xcf, w.Yfc, w.Ycf, w.Xcc, w.Ycc, w.E1, w.E2, w.M1, w.M2, w.rskel, w.q, w.rfull, w.zv};
         for (void* b : bufs) fr(b);
         for (int q = 0; q < w.nz; ++q) { fr(w.z[q]); fr(w.qp[q]); }
     }

@@ -167,6 +167,9 @@ struct FillTcArgs {
     const float* gimg;   // fill_tc_image() of G, fill_tc_image_bytes() bytes, 16-byte aligned
     float* z;            // full grid: ring values read, hole values written (unless out_d)
     double* out_d;       // if set, hole values written here in FP64 instead of into z
+    const float* zv;     // if set: the values on the lines x = k n, [N][mc+1] (column k; columns 0
+                         // and mc zero): west / east ring values are read here, and every hole row
+                         // is written whole, its skeleton point x = k n taken from here
     int N, mc;           // N = 16 mc + 1
     int* err;            // set to 1 when a wait timed out (the fill is then incomplete)
 };
@@ -250,6 +253,8 @@ struct MergeArgs {
     T* E1; T* E2;             // [Nc][Nc] knot errors (fc lines: E1[l][k]; cf columns: E2[l][k])
     T* M1; T* M2;             // moments: M1[l][mc+1], M2[k][mc+1]
     T* z;                     // full grid output (skeleton written)
+    T* zv;                    // non-null: the points of the lines x = k n (k = 1..mc-1) between knots go
+                              // here, [N][mc+1] (column k), instead of into z
     Geometry g;
 };
 template <typename T> cudaError_t merge_knots(const MergeArgs<T>& a, cudaStream_t st);

@@ -570,7 +570,9 @@ __global__ void merge_write_kernel(MergeArgs<T> a) {
             const T yk = ki == 0 ? T(0) : a.E2[(long long)(ki - 1) * Nc + k];
             const T yk1 = ki + 1 >= g.mc ? T(0) : a.E2[(long long)ki * Nc + k];
             const T corr = sw[p][0] * Mv[ki] + sw[p][1] * Mv[ki + 1] + sw[p][2] * yk + sw[p][3] * yk1;
-            a.z[(long long)j * N + (k + 1) * n] = a.Ycf[(long long)y * Nc + k] * inv2 + corr;
+            const T val = a.Ycf[(long long)y * Nc + k] * inv2 + corr;
+            if (a.zv) a.zv[(long long)j * (g.mc + 1) + k + 1] = val;
+            else a.z[(long long)j * N + (k + 1) * n] = val;
         }
     }
 }
