@@ -200,6 +200,17 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
  * array hist and returns that count (or a negative error). */
 int asdsm_history(asdsm_handle* h, double* hist, int cap);
 
+/* The hole extension operator of Algorithm 3 with zero source, as the
+ * tensor-core Filler applies it (host FP64, no device work, no handle):
+ * for the problem (N, mc, alpha, beta as in asdsm_desc) and holes of
+ * C = (N-1)/mc - 1 points per side, G is (C*C) x (4C), row-major, with
+ *   hole values (row by row: y = 1..C, x = 1..C) = G * ring values,
+ * the ring ordered west (y = 1..C), east (y = 1..C), south (x = 1..C),
+ * north (x = 1..C); G = -A_hh^-1 A_hs for the 5-point stencil of Section 2.3.
+ * G: host array of C*C*4*C doubles.  Returns ASDSM_OK or ASDSM_ERR_INVALID
+ * (sizes as asdsm_setup requires, alpha/beta/G non-null). */
+int asdsm_hole_extension_operator(int N, int mc, const double* alpha, const double* beta, double* G);
+
 /* Turn per-kernel-family CUDA-event timing on (1) or off (0) and clear the
  * accumulated counters.  Timing adds two event records per kernel group. */
 int asdsm_profile(asdsm_handle* h, int enable);

@@ -98,6 +98,9 @@ def load() -> ctypes.CDLL:
     lib.asdsm_submesh_solve.restype = ctypes.c_int
     lib.asdsm_history.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.asdsm_history.restype = ctypes.c_int
+    lib.asdsm_hole_extension_operator.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.asdsm_hole_extension_operator.restype = ctypes.c_int
     lib.asdsm_profile.argtypes = [P, ctypes.c_int]
     lib.asdsm_profile.restype = ctypes.c_int
     lib.asdsm_profile_read.argtypes = [P, ctypes.POINTER(KProf), ctypes.c_int]
@@ -201,6 +204,20 @@ def residual_noalloc(N: int, alpha, beta, s, u, r=None, stream=None) -> float:
         raise RuntimeError(f"asdsm_residual_noalloc: {lib.asdsm_strerror(rc).decode()} ({rc}): "
                            f"{lib.asdsm_noalloc_last_error().decode()}")
     return rel.value
+
+
+def hole_extension_operator(N: int, mc: int, alpha, beta):
+    """G of asdsm_hole_extension_operator as a (C*C, 4C) numpy array (host, no GPU)."""
+    import numpy as np
+    lib = load()
+    C = (N - 1) // mc - 1
+    G = np.zeros((C * C, 4 * C), dtype=np.float64)
+    a = (ctypes.c_double * 2)(*[float(x) for x in alpha])
+    b = (ctypes.c_double * 2)(*[float(x) for x in beta])
+    rc = lib.asdsm_hole_extension_operator(int(N), int(mc), a, b, G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != OK:
+        raise AsdsmError(rc, "asdsm_hole_extension_operator")
+    return G
 
 
 @dataclass

@@ -147,6 +147,17 @@ int set_cuda_error(cudaError_t e) {
         if (e__ != cudaSuccess) return set_cuda_error(e__); \
     } while (0)
 
+// Section 2.3 stencil of A_ff on the fine spacing hh.
+Stencil stencil_of(double ax, double ay, double bx, double by, double hh) {
+    Stencil s;
+    s.cc = 2 * ax / (hh * hh) + 2 * ay / (hh * hh);
+    s.cw = -ax / (hh * hh) - bx / (2 * hh);
+    s.ce = -ax / (hh * hh) + bx / (2 * hh);
+    s.cs = -ay / (hh * hh) - by / (2 * hh);
+    s.cn = -ay / (hh * hh) + by / (2 * hh);
+    return s;
+}
+
 template <typename T>
 int upload_bcr(const BcrFactors& f, DevBcr* d, bool tc_image = true) {
     const size_t n = f.Mt.size();
@@ -1395,12 +1406,7 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     for (int q = 0; q < 2; ++q) { h->alpha[q] = desc->alpha[q]; h->beta[q] = desc->beta[q]; }
     const double ax = h->alpha[0], ay = h->alpha[1], bx = h->beta[0], by = h->beta[1];
     const double hh = 1.0 / g.M, HH = 1.0 / g.mc;
-    // Section 2.3 stencil of A_ff.
-    h->sten.cc = 2 * ax / (hh * hh) + 2 * ay / (hh * hh);
-    h->sten.cw = -ax / (hh * hh) - bx / (2 * hh);
-    h->sten.ce = -ax / (hh * hh) + bx / (2 * hh);
-    h->sten.cs = -ay / (hh * hh) - by / (2 * hh);
-    h->sten.cn = -ay / (hh * hh) + by / (2 * hh);
+    h->sten = stencil_of(ax, ay, bx, by, hh);
     // Block cyclic reduction factors (eq. 2.4 systems; rows = the fine axis of each family).
     auto row = [](double a, double b, double sp, double* lo, double* d, double* up) {
         *lo = -a / (sp * sp) - b / (2 * sp);
@@ -1733,6 +1739,17 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
         return ASDSM_ERR_INVALID;
     }
     CK(cudaStreamSynchronize(st));
+    return ASDSM_OK;
+}
+
+int asdsm_hole_extension_operator(int N, int mc, const double* alpha, const double* beta, double* G) {
+    if (N < 3 || mc < 2 || !alpha || !beta || !G || (N - 1) % mc != 0) return ASDSM_ERR_INVALID;
+    const int n = (N - 1) / mc;
+    if (n < 2 || n > 32) return ASDSM_ERR_INVALID;
+    const Stencil st = stencil_of(alpha[0], alpha[1], beta[0], beta[1], 1.0 / (N - 1));
+    std::vector<double> g;
+    if (!hole_extension_operator(n - 1, st, &g)) return ASDSM_ERR_INVALID;
+    std::copy(g.begin(), g.end(), G);
     return ASDSM_OK;
 }
 

@@ -601,15 +601,36 @@ __global__ void skeleton_apply_kernel(const T* __restrict__ z, Geometry g, Stenc
 template <typename T>
 struct CombineArgs { const T* Qp[16]; double beta[16]; };
 
+// out = (q - sum_j beta_j Qp_j) * inv_nu on a grid-strided range, in the
+// vectors' own precision and in the same order per element; FP32 vectors are
+// read and written four at a time (the arrays are 16-byte aligned), the tail
+// one by one.
 template <typename T>
-__global__ void combine_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
-                               double inv_nu, long long n, T* __restrict__ out) {
-    // Arithmetic in the vectors' own precision.
-    T beta[16];
+__device__ __forceinline__ void combine_range(const T* __restrict__ q, const CombineArgs<T>& c, int k, const T* beta,
+                                              T inu, long long n, T* __restrict__ out) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long done = 0;
+    if constexpr (sizeof(T) == 4) {
+        const long long n4 = n >> 2;
+        for (long long e = tid; e < n4; e += stride) {
+            float4 v = __ldg(reinterpret_cast<const float4*>(q) + e);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)c.beta[j] : T(0);
-    const T inu = (T)inv_nu;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+            for (int j = 0; j < 16; ++j) {
+                if (j < k) {
+                    const float4 p = __ldg(reinterpret_cast<const float4*>(c.Qp[j]) + e);
+                    v.x -= beta[j] * p.x;
+                    v.y -= beta[j] * p.y;
+                    v.z -= beta[j] * p.z;
+                    v.w -= beta[j] * p.w;
+                }
+            }
+            v.x *= inu; v.y *= inu; v.z *= inu; v.w *= inu;
+            reinterpret_cast<float4*>(out)[e] = v;
+        }
+        done = n4 << 2;
+    }
+    for (long long e = done + tid; e < n; e += stride) {
         T v = q[e];
 #pragma unroll
         for (int j = 0; j < 16; ++j)
@@ -619,20 +640,22 @@ __global__ void combine_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
 }
 
 template <typename T>
+__global__ void combine_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
+                               double inv_nu, long long n, T* __restrict__ out) {
+    T beta[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)c.beta[j] : T(0);
+    combine_range<T>(q, c, k, beta, (T)inv_nu, n, out);
+}
+
+template <typename T>
 __global__ void combine_dyn_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
                                    const CtlCombine* __restrict__ ctl, long long n, T* __restrict__ out) {
     if (!ctl->run) return;
     T beta[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)ctl->beta[j] : T(0);
-    const T inu = (T)ctl->inv_nu;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        T v = q[e];
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-            if (j < k) v -= beta[j] * __ldg(c.Qp[j] + e);
-        out[e] = v * inu;
-    }
+    combine_range<T>(q, c, k, beta, (T)ctl->inv_nu, n, out);
 }
 
 // Multi-dot partials: blockDim 256, partials[block][ndots].
@@ -931,7 +954,7 @@ cudaError_t combine_skeleton(const T* q, const T* const* Qp, const double* beta,
     if (k > 16) return cudaErrorInvalidValue;
     CombineArgs<T> c{};
     for (int j = 0; j < k; ++j) { c.Qp[j] = Qp[j]; c.beta[j] = beta[j]; }
-    combine_kernel<T><<<grid_for(n), 256, 0, st>>>(q, c, k, inv_nu, n, out);
+    combine_kernel<T><<<grid_for(sizeof(T) == 4 ? (n + 3) / 4 : n), 256, 0, st>>>(q, c, k, inv_nu, n, out);
     note_launch();
     return cudaGetLastError();
 }
@@ -942,7 +965,7 @@ cudaError_t combine_skeleton_dyn(const T* q, const T* const* Qp, int k, const Ct
     if (k > 16) return cudaErrorInvalidValue;
     CombineArgs<T> c{};
     for (int j = 0; j < k; ++j) c.Qp[j] = Qp[j];
-    combine_dyn_kernel<T><<<grid_for(n), 256, 0, st>>>(q, c, k, ctl, n, out);
+    combine_dyn_kernel<T><<<grid_for(sizeof(T) == 4 ? (n + 3) / 4 : n), 256, 0, st>>>(q, c, k, ctl, n, out);
     note_launch();
     return cudaGetLastError();
 }
