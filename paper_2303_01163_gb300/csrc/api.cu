@@ -159,7 +159,7 @@ Stencil stencil_of(double ax, double ay, double bx, double by, double hh) {
 }
 
 template <typename T>
-int upload_bcr(const BcrFactors& f, DevBcr* d, bool tc_image = true) {
+int upload_bcr(const BcrFactors& f, DevBcr* d) {
     const size_t n = f.Mt.size();
     std::vector<T> tmp(n);
     void** dst[2] = {&d->Mt, &d->Bt};
@@ -188,12 +188,6 @@ int upload_bcr(const BcrFactors& f, DevBcr* d, bool tc_image = true) {
             CK(cudaMemcpy(*wdst[q], wide.data(), wide.size() * sizeof(float), cudaMemcpyHostToDevice));
         }
         d->KW = KW; d->CW = CW;
-        if (tc_image) {
-            std::vector<float> img;
-            bcr_tc_image(f, &img, &d->TKC, &d->TCB);
-            CK(cudaMalloc(&d->Ti, img.size() * sizeof(float)));
-            CK(cudaMemcpy(d->Ti, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice));
-        }
     }
     return ASDSM_OK;
 }
@@ -228,6 +222,37 @@ void hole_factors(const asdsm_handle* h, int pi, FillArgs<T>* fa) {
     for (int l = 0; l < d.L; ++l) { fa->wl[l] = (T)d.wl[l]; fa->wr[l] = (T)d.wr[l]; }
     fa->L = d.L;
     fa->warps = h->fill_warps[pi];
+}
+
+// Factor images of the tcgen05 level kernel for the FP32 systems (A_fc, A_cf,
+// A_cc), built on first need from the FP64 factors on the device: when the
+// autotuner considers the kernel, or a tune state selects it.
+int ensure_tc_images(asdsm_handle* h) {
+    DevBcr* fam[3][2] = {{&h->fc[0], &h->fc[1]}, {&h->cf[0], &h->cf[1]}, {&h->cc[0], &h->cc[1]}};
+    for (auto& pr : fam) {
+        const DevBcr& d64 = *pr[0];
+        DevBcr& d32 = *pr[1];
+        if (d32.Ti) continue;
+        BcrFactors f;
+        f.R = d64.R; f.C = d64.C; f.L = d64.L;
+        const size_t n = (size_t)d64.L * d64.C * d64.C;
+        f.Mt.resize(n);
+        f.Bt.resize(n);
+        CK(cudaMemcpy(f.Mt.data(), d64.Mt, n * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(f.Bt.data(), d64.Bt, n * sizeof(double), cudaMemcpyDeviceToHost));
+        std::vector<float> img;
+        bcr_tc_image(f, &img, &d32.TKC, &d32.TCB);
+        CK(cudaMalloc(&d32.Ti, img.size() * sizeof(float)));
+        CK(cudaMemcpy(d32.Ti, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return ASDSM_OK;
+}
+
+bool tune_wants_tc(const BcrTune& t) {
+    for (int d = 0; d < 2; ++d)
+        for (int l = 0; l < kMaxLevels; ++l)
+            if ((t.cfg[d][l] >> 8) == 128) return true;
+    return false;
 }
 
 // The Filler's kernel for precision pi: fill_warps[pi] == kFillTcCode selects
@@ -885,6 +910,8 @@ template <typename T>
 int autotune_impl(asdsm_handle* h) {
     const int pi = sizeof(T) == 8 ? 0 : 1;
     if (int rc = ensure_work<T>(h, pi, 1)) return rc;
+    if (sizeof(T) == 4)
+        if (int rc = ensure_tc_images(h)) return rc;
     auto& w = h->w[pi];
     const Geometry& g = h->g;
     cudaEvent_t a, b;
@@ -1434,7 +1461,7 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if ((rc = upload_bcr<double>(ffc, &h->fc[0])) || (rc = upload_bcr<float>(ffc, &h->fc[1])) ||
         (rc = upload_bcr<double>(fcf, &h->cf[0])) || (rc = upload_bcr<float>(fcf, &h->cf[1])) ||
         (rc = upload_bcr<double>(fcc, &h->cc[0])) || (rc = upload_bcr<float>(fcc, &h->cc[1])) ||
-        (rc = upload_bcr<double>(fho, &h->hole[0])) || (rc = upload_bcr<float>(fho, &h->hole[1], false)))
+        (rc = upload_bcr<double>(fho, &h->hole[0])) || (rc = upload_bcr<float>(fho, &h->hole[1])))
         return fail(rc);
     // Spline moment operator, stored transposed ([knot][moment]) for the merge kernel.
     const std::vector<double> Sm = spline_moment_operator(g.mc);
@@ -1517,6 +1544,8 @@ int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n) {
             for (int l = 0; l < kMaxLevels; ++l) h->tune_cc[pi].cfg[d][l] = in[q++];
         h->fill_warps[pi] = in[q++];
     }
+    if (tune_wants_tc(h->tune_aniso[1]) || tune_wants_tc(h->tune_cc[1]))
+        if (int rc = ensure_tc_images(h)) return rc;
     destroy_graph(h);
     return ASDSM_OK;
 }
@@ -1854,6 +1883,8 @@ int asdsm_autotune_batch(asdsm_batch* b, int precision) {
             h->tune_aniso[pi] = src->tune_aniso[pi];
             h->tune_cc[pi] = src->tune_cc[pi];
             h->fill_warps[pi] = src->fill_warps[pi];
+            if (pi == 1 && (tune_wants_tc(h->tune_aniso[1]) || tune_wants_tc(h->tune_cc[1])))
+                if (int rc = ensure_tc_images(h)) return rc;
             destroy_graph(h);
         }
     }
