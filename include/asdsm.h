@@ -42,7 +42,9 @@ extern "C" {
 /* ---- status codes ------------------------------------------------------- */
 #define ASDSM_OK                 0
 #define ASDSM_ERR_INVALID       -1   /* bad argument: sizes violate eq. 2.1 / powers of two, alpha <= 0, null pointer */
-#define ASDSM_ERR_CUDA          -2   /* a CUDA runtime call failed (message in asdsm_last_error) */
+#define ASDSM_ERR_CUDA          -2   /* a CUDA runtime call failed, or a tensor-core kernel's bounded
+                                        wait ran out (1 s; sticky for the handle); message in
+                                        asdsm_last_error */
 #define ASDSM_ERR_OOM           -3   /* device allocation failed */
 #define ASDSM_ERR_NAN           -4   /* a NaN/Inf appeared in the residual (bad input data) */
 #define ASDSM_NOT_CONVERGED     -5   /* max_sweeps reached above tol; u holds the last iterate */

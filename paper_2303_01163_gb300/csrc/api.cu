@@ -325,6 +325,21 @@ int ensure_partials(asdsm_handle* h, int n) {
     return ASDSM_OK;
 }
 
+// The tcgen05 kernels' timeout flag, read after the stream drained.  It is
+// sticky: a wait that ran out means the device stopped making progress, and
+// every later call on the handle reports it as well.
+int tc_status(asdsm_handle* h, cudaStream_t st) {
+    int* f = reinterpret_cast<int*>(h->hsmall + 4095);
+    *f = 0;
+    CK(cudaMemcpyAsync(f, h->dtcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*f) {
+        g_last_error = "tensor-core kernel: a wait timed out";
+        return ASDSM_ERR_CUDA;
+    }
+    return ASDSM_OK;
+}
+
 // Copy `count` doubles of dsmall to the host and wait.
 int read_small(asdsm_handle* h, int count) {
     CK(cudaMemcpyAsync(h->hsmall, h->dsmall, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -941,7 +956,7 @@ int autotune_impl(asdsm_handle* h) {
         if (ms < best) { best = ms; bestw = wv; }
     }
     h->fill_warps[pi] = bestw;
-    CK(cudaStreamSynchronize(h->st));
+    if (int rc = tc_status(h, h->st)) return done(rc);
     destroy_graph(h);                      // recapture with the new shapes
     return done(ASDSM_OK);
 }
@@ -1317,7 +1332,7 @@ int run_finish(asdsm_handle* h, SolveRun& r) {
     CK(cudaEventRecord(h->ev2, st));
     CK(cudaEventSynchronize(h->ev2));
     if (*tcerr) {
-        g_last_error = "tensor-core Filler: a wait timed out";
+        g_last_error = "tensor-core kernel: a wait timed out";
         return ASDSM_ERR_CUDA;
     }
     float ms_setup = 0.f, ms_all = 0.f;
@@ -1745,17 +1760,8 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
             float* z32 = (float*)w.z[0];
             CK(convert_array<double, float>(in, z32, (long long)g.N * g.N, st));
             if (use_fill_tc(h, 1)) {
-                CK(cudaMemsetAsync(h->dtcerr, 0, sizeof(int), st));
                 FillTcArgs ta{h->fill_tc_img, z32, out, nullptr, g.N, g.mc, h->dtcerr};
                 CK(fill_tc(ta, h->num_sms, st));
-                int err = 0;
-                CK(cudaMemcpyAsync(h->hsmall, h->dtcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                std::memcpy(&err, h->hsmall, sizeof(int));
-                if (err) {
-                    g_last_error = "tensor-core Filler: a wait timed out";
-                    return ASDSM_ERR_CUDA;
-                }
             } else {
                 FillArgs<float> fa{};
                 fa.mode = FILL_HOMOGENEOUS; fa.z = z32; fa.out_d = out;
@@ -1767,8 +1773,7 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
     } else {
         return ASDSM_ERR_INVALID;
     }
-    CK(cudaStreamSynchronize(st));
-    return ASDSM_OK;
+    return tc_status(h, st);
 }
 
 int asdsm_hole_extension_operator(int N, int mc, const double* alpha, const double* beta, double* G) {
