@@ -350,8 +350,10 @@ int read_small(asdsm_handle* h, int count) {
 // ---------------------------------------------------------------------------
 // Profiling: event pairs around kernel groups, resolved after the solve syncs.
 // ---------------------------------------------------------------------------
-enum ProfCat { PC_RESID = 0, PC_BCR, PC_FILL, PC_MERGE, PC_LSQ, PC_NORM, PC_OTHER, PC_COUNT };
-const char* kProfNames[PC_COUNT] = {"residual", "bcr_aniso", "fill_holes", "merge", "least_squares", "norms", "other"};
+enum ProfCat { PC_RESID = 0, PC_BCR, PC_FILL, PC_MERGE, PC_LSQ, PC_NORM, PC_OTHER, PC_FILL_TC, PC_COUNT };
+const char* kProfNames[PC_COUNT] = {"residual", "bcr_aniso", "fill_holes", "merge", "least_squares", "norms", "other",
+                                    "fill_tc"};
+static_assert(PC_COUNT <= 8, "asdsm_handle::pc holds 8 families");
 
 struct ProfMark { int ev = -1; long long l0 = 0; };
 
@@ -1133,10 +1135,15 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
         {
             const ProfMark pm = prof_begin(h);
             CK(fill_homogeneous<T>(h, pi, z, st, (const T*)ma.zv));
-            const double holes = (double)g.mc * g.mc;
-            const double flops = 2.0 * holes * bcr_macs(g.n - 1, g.n - 1, h->hole[pi].L);
-            const double bytes = ES * (holes * (g.n - 1.0) * (g.n - 1.0) + holes * 4.0 * (g.n - 1.0));
-            prof_end(h, pm, PC_FILL, bytes, flops);
+            const double holes = (double)g.mc * g.mc, C = g.n - 1.0;
+            const double bytes = ES * (holes * C * C + holes * 4.0 * C);
+            if (use_fill_tc(h, pi)) {
+                // The map v = G z: 2 (C^2) (4C) flops per hole (the TF32 split products
+                // the tensor cores issue are about 3.4 times that).
+                prof_end(h, pm, PC_FILL_TC, bytes, 2.0 * holes * C * C * 4.0 * C);
+            } else {
+                prof_end(h, pm, PC_FILL, bytes, 2.0 * holes * bcr_macs(g.n - 1, g.n - 1, h->hole[pi].L));
+            }
         }
         // ---- step 6: least squares on the skeleton rows (GCR(m) step for direction zd) ----
         // Returns 1 when the direction is dependent (the cycle restarts), 0 otherwise;
