@@ -230,10 +230,13 @@ int64_t asdsm_launch_count(void);
  * graph (allocation is not a capturable operation), services whose device
  * memory is reserved up front by their own pool, loops where an allocation
  * would stall the device.  It needs no handle.
- * desc: only d (= 2), n (N, 3 <= N <= 8193), alpha and beta are read.
- * s, u: device N*N FP64 arrays as for asdsm_residual (u's ring = g).
- * r: device N*N or NULL; its interior receives r = b_ff - A_ff u (the ring is
- * not written).  rel_norm: host pointer or NULL; receives ||r||/||b_ff||
+ * desc: only d, n, alpha and beta are read.  d = 2: N*N grids, 3 <= N <= 8193,
+ * the 5-point operator of Section 2.3.  d = 3: N*N*N grids (z slowest, x
+ * fastest), 3 <= N <= 2049, the 7-point operator of the 3D extension (alpha,
+ * beta per axis x, y, z).
+ * s, u: device FP64 grids as for asdsm_residual (u's boundary = g).
+ * r: device grid or NULL; its interior receives r = b_ff - A_ff u (the
+ * boundary is not written).  rel_norm: host pointer or NULL; receives ||r||/||b_ff||
  * (the call then synchronises `stream`).  stream: cudaStream_t or NULL.
  * Scratch: statically allocated device arrays of about 1 MiB held by every
  * GPU that loads the library until the process exits.  The first call on a

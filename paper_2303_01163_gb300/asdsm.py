@@ -187,12 +187,14 @@ def _ptr(t, dtype_name="float64"):
 
 
 def residual_noalloc(N: int, alpha, beta, s, u, r=None, stream=None) -> float:
-    """asdsm_residual_noalloc: residual and ||r||/||b|| with no device allocation."""
+    """asdsm_residual_noalloc: residual and ||r||/||b|| with no device allocation
+    (2D: two alpha/beta per axis and N*N grids; 3D: three and N*N*N grids)."""
     import torch
     lib = load()
     d = Desc()
-    d.d, d.n = 2, int(N)
-    for q in range(2):
+    dim = len(alpha)
+    d.d, d.n = dim, int(N)
+    for q in range(dim):
         d.alpha[q] = float(alpha[q])
         d.beta[q] = float(beta[q])
     if stream is None:

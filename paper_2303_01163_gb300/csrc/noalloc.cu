@@ -110,6 +110,63 @@ residual_norms_kernel(const double* __restrict__ s, const double* __restrict__ u
     }
 }
 
+// 3D (the 7-point operator of the 3D extension): the same two quantities,
+// one interior point per thread in a grid-strided loop over the N_f^3 points
+// (x fastest); neighbours come from L1/L2.
+struct Stencil7 {
+    double cc, cw, ce, cs, cn, cd, cu;    // centre; x-1, x+1; y-1, y+1; z-1, z+1
+};
+constexpr int NA3_BLOCKS = 152 * 8;
+constexpr int NA3_MAX_N = 2049;
+static_assert(NA3_BLOCKS <= NA_MAX_BLOCKS, "3D partials fit the scratch");
+
+__global__ void __launch_bounds__(NA_THREADS)
+residual_norms_3d_kernel(const double* __restrict__ s, const double* __restrict__ u, double* __restrict__ r,
+                         int N, Stencil7 c, double* __restrict__ partials) {
+    __shared__ double red[2][NA_THREADS / 32];
+    const long long Nf = N - 2, total = Nf * Nf * Nf;
+    const long long sy = N, sz = (long long)N * N;
+    double sr = 0.0, sb = 0.0;
+    for (long long e = blockIdx.x * (long long)NA_THREADS + threadIdx.x; e < total; e += (long long)gridDim.x * NA_THREADS) {
+        const int i = (int)(e % Nf) + 1;
+        const long long t = e / Nf;
+        const int j = (int)(t % Nf) + 1, l = (int)(t / Nf) + 1;
+        const long long idx = (l * sy + j) * (long long)N + i;
+        const double uc = u[idx];
+        const double uw = u[idx - 1], ue = u[idx + 1];
+        const double us = u[idx - sy], un = u[idx + sy];
+        const double ud = u[idx - sz], uu = u[idx + sz];
+        const double Au = c.cc * uc + c.cw * uw + c.ce * ue + c.cs * us + c.cn * un + c.cd * ud + c.cu * uu;
+        const double rv = s[idx] - Au;
+        double lift = 0.0;                        // Dirichlet lifting: neighbours on the boundary
+        if (i == 1) lift += c.cw * uw;
+        if (i == N - 2) lift += c.ce * ue;
+        if (j == 1) lift += c.cs * us;
+        if (j == N - 2) lift += c.cn * un;
+        if (l == 1) lift += c.cd * ud;
+        if (l == N - 2) lift += c.cu * uu;
+        const double bv = s[idx] - lift;
+        sr += rv * rv;
+        sb += bv * bv;
+        if (r) r[idx] = rv;
+    }
+    sr = na_warp_sum(sr);
+    sb = na_warp_sum(sb);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][w] = sr; red[1][w] = sb; }
+    __syncthreads();
+    if (w == 0) {
+        sr = lane < NA_THREADS / 32 ? red[0][lane] : 0.0;
+        sb = lane < NA_THREADS / 32 ? red[1][lane] : 0.0;
+        sr = na_warp_sum(sr);
+        sb = na_warp_sum(sb);
+        if (lane == 0) {
+            partials[2 * blockIdx.x] = sr;
+            partials[2 * blockIdx.x + 1] = sb;
+        }
+    }
+}
+
 // Fixed-order sum of the block partials into totals[0..1].
 __global__ void totals_kernel(const double* __restrict__ partials, int nblocks, double* __restrict__ totals) {
     __shared__ double red[2][32];
@@ -163,18 +220,53 @@ int asdsm_residual_noalloc(const asdsm_desc* desc, const double* s, const double
                            double* rel_norm, void* stream) {
     g_na_error.clear();
     if (!desc || !s || !u) { g_na_error = "null argument"; return ASDSM_ERR_INVALID; }
-    if (desc->d != 2) { g_na_error = "only d = 2 is supported"; return ASDSM_ERR_INVALID; }
+    if (desc->d != 2 && desc->d != 3) { g_na_error = "d must be 2 or 3"; return ASDSM_ERR_INVALID; }
     const int N = desc->n;
+    const bool d3 = desc->d == 3;
     if (N < 3) { g_na_error = "grid needs at least 3 points per axis"; return ASDSM_ERR_INVALID; }
-    if (N > NA_MAX_N) {
-        g_na_error = "grid larger than the statically allocated scratch allows (at most 8193 points per axis)";
+    if (N > (d3 ? NA3_MAX_N : NA_MAX_N)) {
+        g_na_error = d3 ? "3D grid larger than 2049 points per axis"
+                        : "grid larger than the statically allocated scratch allows (at most 8193 points per axis)";
         return ASDSM_ERR_INVALID;
     }
-    if (!(desc->alpha[0] > 0) || !(desc->alpha[1] > 0)) { g_na_error = "alpha must be positive"; return ASDSM_ERR_INVALID; }
+    if (!(desc->alpha[0] > 0) || !(desc->alpha[1] > 0) || (d3 && !(desc->alpha[2] > 0))) {
+        g_na_error = "alpha must be positive";
+        return ASDSM_ERR_INVALID;
+    }
     DeviceScratch* sc = nullptr;
     int rc = scratch_for_current_device(&sc);
     if (rc != ASDSM_OK) return rc;
     const double h = 1.0 / (N - 1);
+    if (d3) {
+        const double* al = desc->alpha;
+        const double* be = desc->beta;
+        Stencil7 c7;
+        c7.cc = 2 * (al[0] + al[1] + al[2]) / (h * h);
+        c7.cw = -al[0] / (h * h) - be[0] / (2 * h);
+        c7.ce = -al[0] / (h * h) + be[0] / (2 * h);
+        c7.cs = -al[1] / (h * h) - be[1] / (2 * h);
+        c7.cn = -al[1] / (h * h) + be[1] / (2 * h);
+        c7.cd = -al[2] / (h * h) - be[2] / (2 * h);
+        c7.cu = -al[2] / (h * h) + be[2] / (2 * h);
+        cudaStream_t st3 = (cudaStream_t)stream;
+        const long long Nf = N - 2, total = Nf * Nf * Nf;
+        long long nb = (total + NA_THREADS - 1) / NA_THREADS;
+        const int nblocks = (int)(nb < NA3_BLOCKS ? nb : NA3_BLOCKS);
+        residual_norms_3d_kernel<<<nblocks, NA_THREADS, 0, st3>>>(s, u, r, N, c7, sc->partials);
+        cudaError_t e3 = cudaGetLastError();
+        if (e3 != cudaSuccess) { g_na_error = cudaGetErrorString(e3); return ASDSM_ERR_CUDA; }
+        totals_kernel<<<1, 1024, 0, st3>>>(sc->partials, nblocks, sc->totals);
+        e3 = cudaGetLastError();
+        if (e3 != cudaSuccess) { g_na_error = cudaGetErrorString(e3); return ASDSM_ERR_CUDA; }
+        if (rel_norm) {
+            double tot[2] = {0.0, 0.0};
+            e3 = cudaMemcpyAsync(tot, sc->totals, sizeof(tot), cudaMemcpyDeviceToHost, st3);
+            if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(st3);
+            if (e3 != cudaSuccess) { g_na_error = cudaGetErrorString(e3); return ASDSM_ERR_CUDA; }
+            *rel_norm = tot[1] > 0 ? std::sqrt(tot[0] / tot[1]) : std::sqrt(tot[0]);
+        }
+        return ASDSM_OK;
+    }
     const double ax = desc->alpha[0], ay = desc->alpha[1], bx = desc->beta[0], by = desc->beta[1];
     asdsm::Stencil c;
     c.cc = 2 * ax / (h * h) + 2 * ay / (h * h);

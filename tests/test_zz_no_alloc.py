@@ -69,3 +69,48 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
                                     None, ctypes.byref(rel), None)
     assert rc == asdsm.ERR_INVALID
     assert b"8193" in lib.asdsm_noalloc_last_error()
+
+
+@pytest.mark.parametrize("N", [3, 17, 20, 65])
+def test_noalloc_residual_3d_matches_the_3d_oracle(N):
+    """d = 3: the 7-point residual of the 3D extension against the FP64 3D
+    oracle's operator and Dirichlet lifting (N = 3: one interior point;
+    N = 20: a size that no coarse mesh divides)."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_01163_gb300 import asdsm
+    from oracle import asdsm3d as o3
+    alpha, beta = (0.7, 1.3, 0.4), (2.0, -3.0, 1.0)
+    rng = np.random.default_rng(N)
+    U = rng.normal(size=(N, N, N))
+    S = rng.normal(size=(N, N, N))
+    M, Nf, h = N - 1, N - 2, 1.0 / (N - 1)
+    fine = np.arange(1, M)
+    pts = o3.Meshes3D._product(fine, fine, fine)
+    b = o3.rhs_on_mesh(pts, (h, h, h), alpha, beta, S, U, M)
+    r_ref = b - o3.operator_3d(Nf, h, Nf, h, Nf, h, alpha, beta) @ o3.interior(U)
+    rel_ref = np.linalg.norm(r_ref) / np.linalg.norm(b)
+    s = torch.tensor(S, dtype=torch.float64, device="cuda")
+    u = torch.tensor(U, dtype=torch.float64, device="cuda")
+    r = torch.full_like(u, 5.0)
+    rel = asdsm.residual_noalloc(N, alpha, beta, s, u, r)
+    got = r.cpu().numpy()
+    scale = (2 * sum(alpha) / h**2 * 2 + sum(abs(x) for x in beta) / h) * np.abs(U).max() + np.abs(S).max()
+    assert np.abs(o3.interior(got) - r_ref).max() <= 1e-14 * scale
+    assert abs(rel - rel_ref) <= 1e-12 * rel_ref
+    ring = np.ones((N, N, N), dtype=bool)
+    ring[1:-1, 1:-1, 1:-1] = False
+    assert np.all(got[ring] == 5.0)                    # boundary untouched
+
+
+def test_noalloc_3d_rejects_invalid_descriptions():
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_01163_gb300 import asdsm
+    s = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError):
+        asdsm.residual_noalloc(2050, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), s, s)
+    with pytest.raises(RuntimeError):
+        asdsm.residual_noalloc(17, (1.0, 1.0, 0.0), (0.0, 0.0, 0.0), s, s)
