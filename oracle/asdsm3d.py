@@ -405,15 +405,3 @@ def to_grid(u_ff, g_grid):
     n = out.shape[0] - 2
     out[1:-1, 1:-1, 1:-1] = u_ff.reshape(n, n, n)
     return out
-
-
-def manufactured_sine(N: int, alpha, beta):
-    """u = sin(pi x) sin(pi y) sin(pi z) on the grid and the source s of eq. (1.1) it implies."""
-    x = np.linspace(0.0, 1.0, N)
-    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
-    sx, sy, sz = np.sin(np.pi * X), np.sin(np.pi * Y), np.sin(np.pi * Z)
-    cx, cy, cz = np.cos(np.pi * X), np.cos(np.pi * Y), np.cos(np.pi * Z)
-    u = sx * sy * sz
-    s = (sum(alpha) * np.pi**2 * u + beta[0] * np.pi * cx * sy * sz + beta[1] * np.pi * sx * cy * sz
-         + beta[2] * np.pi * sx * sy * cz)
-    return u, s

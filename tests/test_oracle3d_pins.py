@@ -26,6 +26,7 @@ import numpy as np
 import pytest
 
 from oracle import asdsm3d as o3
+from paper_2303_01163_gb300 import workloads as wl
 
 
 def _lam(k, h):
@@ -78,7 +79,8 @@ def test_fine_solution_is_second_order():
     errs = []
     for N in (9, 17, 33):
         disc = o3.Discretisation3D(N, 2, alpha, beta)
-        u, s = o3.manufactured_sine(N, alpha, beta)
+        p = wl.manufactured_sine_3d(N, alpha, beta)
+        u, s = p.u_exact, p.s
         b = disc.rhs(s, np.zeros_like(u))
         errs.append(np.max(np.abs(disc.solve_fine(b[0]) - o3.interior(u))))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
@@ -147,7 +149,8 @@ def test_filler_on_cube_holes_recovers_linear_fields():
 def test_asdsm3d_gcr_reaches_the_fine_solution(N, mc):
     alpha, beta = (1.0, 0.5, 0.8), (1.5, -1.0, 0.5)
     disc = o3.Discretisation3D(N, mc, alpha, beta)
-    u_ex, s = o3.manufactured_sine(N, alpha, beta)
+    p = wl.manufactured_sine_3d(N, alpha, beta)
+    u_ex, s = p.u_exact, p.s
     b = disc.rhs(s, np.zeros_like(u_ex))
     u, info = o3.asdsm(disc, b, tol=1e-10, max_sweeps=300, accel_m=8)
     assert info["status"] == "converged", info["status"]
@@ -160,7 +163,8 @@ def test_asdsm3d_paper_step_never_increases_the_skeleton_residual():
     N, mc = 17, 4
     alpha, beta = (1.0, 0.5, 0.8), (1.5, -1.0, 0.5)
     disc = o3.Discretisation3D(N, mc, alpha, beta)
-    u_ex, s = o3.manufactured_sine(N, alpha, beta)
+    p = wl.manufactured_sine_3d(N, alpha, beta)
+    u_ex, s = p.u_exact, p.s
     b = disc.rhs(s, np.zeros_like(u_ex))
     u, info = o3.asdsm(disc, b, tol=1e-14, max_sweeps=12, accel_m=1, stagnation_window=10**9)
     h = np.array(info["hist"])
