@@ -213,6 +213,16 @@ int asdsm_history(asdsm_handle* h, double* hist, int cap);
  * (sizes as asdsm_setup requires, alpha/beta/G non-null). */
 int asdsm_hole_extension_operator(int N, int mc, const double* alpha, const double* beta, double* G);
 
+/* The same for the cube holes of the 3D extension (host FP64, no device work):
+ * alpha, beta per axis (x, y, z), C = (N-1)/mc - 1; G is (C^3) x (6 C^2),
+ * row-major, with hole values (x fastest, then y, then z) = G * face values,
+ * the faces ordered west (x = 0), east (x = C+1), south (y = 0), north
+ * (y = C+1), down (z = 0), up (z = C+1), each face's C*C values with its
+ * second axis slowest (west/east: y fastest, z; south/north: x, z; down/up:
+ * x, y); G = -A_hh^-1 A_hs for the 7-point stencil.  G: host array of
+ * C^3 * 6 C^2 doubles.  Returns ASDSM_OK or ASDSM_ERR_INVALID. */
+int asdsm_hole_extension_operator_3d(int N, int mc, const double* alpha, const double* beta, double* G);
+
 /* Turn per-kernel-family CUDA-event timing on (1) or off (0) and clear the
  * accumulated counters.  Timing adds two event records per kernel group. */
 int asdsm_profile(asdsm_handle* h, int enable);

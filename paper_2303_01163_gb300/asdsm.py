@@ -101,6 +101,9 @@ def load() -> ctypes.CDLL:
     lib.asdsm_hole_extension_operator.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.asdsm_hole_extension_operator.restype = ctypes.c_int
+    lib.asdsm_hole_extension_operator_3d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.asdsm_hole_extension_operator_3d.restype = ctypes.c_int
     lib.asdsm_profile.argtypes = [P, ctypes.c_int]
     lib.asdsm_profile.restype = ctypes.c_int
     lib.asdsm_profile_read.argtypes = [P, ctypes.POINTER(KProf), ctypes.c_int]
@@ -206,6 +209,20 @@ def residual_noalloc(N: int, alpha, beta, s, u, r=None, stream=None) -> float:
         raise RuntimeError(f"asdsm_residual_noalloc: {lib.asdsm_strerror(rc).decode()} ({rc}): "
                            f"{lib.asdsm_noalloc_last_error().decode()}")
     return rel.value
+
+
+def hole_extension_operator_3d(N: int, mc: int, alpha, beta):
+    """G of asdsm_hole_extension_operator_3d as a (C^3, 6 C^2) numpy array (host, no GPU)."""
+    import numpy as np
+    lib = load()
+    C = (N - 1) // mc - 1
+    G = np.zeros((C ** 3, 6 * C * C), dtype=np.float64)
+    a = (ctypes.c_double * 3)(*[float(x) for x in alpha])
+    b = (ctypes.c_double * 3)(*[float(x) for x in beta])
+    rc = lib.asdsm_hole_extension_operator_3d(int(N), int(mc), a, b, G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != OK:
+        raise AsdsmError(rc, "asdsm_hole_extension_operator_3d")
+    return G
 
 
 def hole_extension_operator(N: int, mc: int, alpha, beta):

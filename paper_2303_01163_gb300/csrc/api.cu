@@ -1794,6 +1794,23 @@ int asdsm_hole_extension_operator(int N, int mc, const double* alpha, const doub
     return ASDSM_OK;
 }
 
+int asdsm_hole_extension_operator_3d(int N, int mc, const double* alpha, const double* beta, double* G) {
+    if (N < 3 || mc < 2 || !alpha || !beta || !G || (N - 1) % mc != 0) return ASDSM_ERR_INVALID;
+    const int n = (N - 1) / mc;
+    if (n < 2 || n > 32 || !(alpha[0] > 0) || !(alpha[1] > 0) || !(alpha[2] > 0)) return ASDSM_ERR_INVALID;
+    const double hh = 1.0 / (N - 1);
+    double s7[7];
+    s7[0] = 2 * (alpha[0] + alpha[1] + alpha[2]) / (hh * hh);
+    for (int a = 0; a < 3; ++a) {
+        s7[1 + 2 * a] = -alpha[a] / (hh * hh) - beta[a] / (2 * hh);
+        s7[2 + 2 * a] = -alpha[a] / (hh * hh) + beta[a] / (2 * hh);
+    }
+    std::vector<double> g;
+    if (!hole_extension_operator_3d(n - 1, s7, &g)) return ASDSM_ERR_INVALID;
+    std::copy(g.begin(), g.end(), G);
+    return ASDSM_OK;
+}
+
 int asdsm_history(asdsm_handle* h, double* hist, int cap) {
     if (!h || (!hist && cap > 0)) return ASDSM_ERR_INVALID;
     const int n = std::min<int>(cap, (int)h->hist.size());

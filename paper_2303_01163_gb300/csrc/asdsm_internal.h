@@ -160,6 +160,15 @@ cudaError_t bcr_tc_level(const BcrSys<float>& g0, const BcrSys<float>& g1, int n
 // (x = 1..C), north (x = 1..C); G = -A_hh^{-1} A_hs, [C*C][4C] row-major.
 bool hole_extension_operator(int C, const Stencil& s, std::vector<double>* G);
 
+// The same for the cube holes of the 3D extension (host_math.cu): the C^3
+// hole values (x fastest, then y, then z) are G z for the 6 C^2 face values z
+// ordered west (x = 0), east (x = C+1), south (y = 0), north (y = C+1), down
+// (z = 0), up (z = C+1), each face's C x C values with its second axis
+// slowest (west/east: (y, z); south/north: (x, z); down/up: (x, y)).
+// sten7 = {cc, cw, ce, cs, cn, cd, cu} (centre; x-1, x+1; y-1, y+1; z-1, z+1).
+// G is [C^3][6 C^2] row-major.
+bool hole_extension_operator_3d(int C, const double sten7[7], std::vector<double>* G);
+
 // Tensor-core Filler (fill_tc.cu): the homogeneous fill for holes of
 // kFillTcN - 1 = 15 points per side (n = 16), FP32 results.
 constexpr int kFillTcN = 16;

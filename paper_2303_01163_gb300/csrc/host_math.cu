@@ -105,6 +105,107 @@ bool hole_extension_operator(int C, const Stencil& s, std::vector<double>* G) {
     return true;
 }
 
+namespace {
+
+// Gaussian elimination with partial pivoting of an n x n band matrix with kl
+// sub- and ku super-diagonals, stored by rows with room for the fill-in of the
+// row exchanges (ku + kl super-diagonals): row i holds columns i-kl .. i+ku+kl
+// at offsets 0 .. 2 kl + ku.  Multipliers overwrite the eliminated entries.
+struct BandLU {
+    int n = 0, kl = 0, ku2 = 0, W = 0;
+    std::vector<double> a;
+    std::vector<int> piv;
+    double& at(int i, int j) { return a[(size_t)i * W + (j - i + kl)]; }
+    bool factor() {
+        piv.assign(n, 0);
+        for (int k = 0; k < n; ++k) {
+            int p = k;
+            double best = std::fabs(at(k, k));
+            const int last = std::min(n - 1, k + kl);
+            for (int i = k + 1; i <= last; ++i)
+                if (std::fabs(at(i, k)) > best) { best = std::fabs(at(i, k)); p = i; }
+            if (!(best > 0.0) || !std::isfinite(best)) return false;
+            piv[k] = p;
+            const int jend = std::min(n - 1, k + ku2);
+            if (p != k)
+                for (int j = k; j <= jend; ++j) std::swap(at(k, j), at(p, j));
+            const double inv = 1.0 / at(k, k);
+            for (int i = k + 1; i <= last; ++i) {
+                const double l = at(i, k) * inv;
+                at(i, k) = l;
+                if (l == 0.0) continue;
+                for (int j = k + 1; j <= jend; ++j) at(i, j) -= l * at(k, j);
+            }
+        }
+        return true;
+    }
+    void solve(double* b) {
+        for (int k = 0; k < n; ++k) {                      // L (unit) with the row exchanges
+            if (piv[k] != k) std::swap(b[k], b[piv[k]]);
+            const int last = std::min(n - 1, k + kl);
+            for (int i = k + 1; i <= last; ++i) b[i] -= at(i, k) * b[k];
+        }
+        for (int k = n - 1; k >= 0; --k) {                 // U
+            const int jend = std::min(n - 1, k + ku2);
+            double v = b[k];
+            for (int j = k + 1; j <= jend; ++j) v -= at(k, j) * b[j];
+            b[k] = v / at(k, k);
+        }
+    }
+};
+
+}  // namespace
+
+bool hole_extension_operator_3d(int C, const double sten7[7], std::vector<double>* G) {
+    if (C < 1) return false;
+    const int n = C * C * C, F = C * C, K = 6 * F;
+    auto id = [C](int x, int y, int z) { return (z * C + y) * C + x; };   // 0-based hole coordinates
+    BandLU lu;
+    lu.n = n;
+    lu.kl = F;
+    lu.ku2 = 2 * F;
+    lu.W = lu.kl + lu.ku2 + 1;
+    lu.a.assign((size_t)n * lu.W, 0.0);
+    for (int z = 0; z < C; ++z)
+        for (int y = 0; y < C; ++y)
+            for (int x = 0; x < C; ++x) {
+                const int r = id(x, y, z);
+                lu.at(r, r) = sten7[0];
+                if (x > 0) lu.at(r, id(x - 1, y, z)) = sten7[1];
+                if (x < C - 1) lu.at(r, id(x + 1, y, z)) = sten7[2];
+                if (y > 0) lu.at(r, id(x, y - 1, z)) = sten7[3];
+                if (y < C - 1) lu.at(r, id(x, y + 1, z)) = sten7[4];
+                if (z > 0) lu.at(r, id(x, y, z - 1)) = sten7[5];
+                if (z < C - 1) lu.at(r, id(x, y, z + 1)) = sten7[6];
+            }
+    if (!lu.factor()) return false;
+    G->assign((size_t)n * K, 0.0);
+    // Face value k touches one hole point q with coefficient c: column k of G is
+    // -c times column q of A_hh^{-1}.  Columns are solved once per distinct q.
+    std::vector<double> col(n);
+    std::vector<int> done(n, 0);
+    std::vector<std::vector<std::pair<int, double>>> users(n);
+    for (int v = 0; v < C; ++v)
+        for (int u = 0; u < C; ++u) {
+            const int f = v * C + u;
+            users[id(0, u, v)].push_back({0 * F + f, sten7[1]});       // west: (y, z) = (u, v)
+            users[id(C - 1, u, v)].push_back({1 * F + f, sten7[2]});   // east
+            users[id(u, 0, v)].push_back({2 * F + f, sten7[3]});       // south: (x, z)
+            users[id(u, C - 1, v)].push_back({3 * F + f, sten7[4]});   // north
+            users[id(u, v, 0)].push_back({4 * F + f, sten7[5]});       // down: (x, y)
+            users[id(u, v, C - 1)].push_back({5 * F + f, sten7[6]});   // up
+        }
+    for (int q = 0; q < n; ++q) {
+        if (users[q].empty()) continue;
+        std::fill(col.begin(), col.end(), 0.0);
+        col[q] = 1.0;
+        lu.solve(col.data());
+        for (const auto& kc : users[q])
+            for (int p = 0; p < n; ++p) (*G)[(size_t)p * K + kc.first] = -kc.second * col[p];
+    }
+    return true;
+}
+
 bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, double tu, BcrFactors* out) {
     int L = 0;
     while (((1 << L) - 1) < R) ++L;
