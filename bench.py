@@ -178,6 +178,34 @@ def job_throughput(world: int, unknowns_per_rank: int, steps: int, ms: float) ->
     return world * unknowns_per_rank * steps / (ms * 1e-3)
 
 
+def family_roofline(fname, frec, peaks, peak_src, num_sms, sm_max):
+    """Roofline entry of one kernel family from its profile record (launches, ms,
+    algorithmic bytes and flops): the tensor-core Filler against the TF32 dense
+    peak (measured bf16 burst x the nominal TF32/BF16 ratio 1.1/2.25), the block
+    cyclic reductions and the reduction Filler against the derived FP32 FMA peak,
+    every other family against the measured HBM bandwidth."""
+    avg_ms = frec["ms"] / max(1, frec["launches"])
+    if fname == "fill_tc" and frec["flops"] > 0:
+        achieved = frec["flops"] / (frec["ms"] * 1e-3) / 1e12
+        peak = float(peaks["bf16_tflops"]) * 1.1 / 2.25
+        return {"kernel": fname, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_src} bf16_tflops x 1.1/2.25 (nominal TF32/BF16 dense)",
+                "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
+    if frec["flops"] > 0 and fname in ("bcr_aniso", "fill_holes"):
+        achieved = frec["flops"] / (frec["ms"] * 1e-3) / 1e12
+        peak = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        return {"kernel": fname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: {num_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
+    achieved = frec["bytes"] / (frec["ms"] * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"kernel": fname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+            "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, one bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -373,28 +401,7 @@ def run_ours(args):
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     def roofline_of(fname, frec):
-        avg_ms = frec["ms"] / max(1, frec["launches"])
-        if fname == "fill_tc" and frec["flops"] > 0:
-            # TF32 tensor-core contraction: the measured bf16 burst peak times the
-            # nominal dense TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s).
-            achieved = frec["flops"] / (frec["ms"] * 1e-3) / 1e12
-            peak = float(peaks["bf16_tflops"]) * 1.1 / 2.25
-            return {"kernel": fname, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"{peak_src} bf16_tflops x 1.1/2.25 (nominal TF32/BF16 dense)",
-                    "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
-        if frec["flops"] > 0 and fname in ("bcr_aniso", "fill_holes"):
-            achieved = frec["flops"] / (frec["ms"] * 1e-3) / 1e12
-            peak = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-            return {"kernel": fname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"derived: {num_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz",
-                    "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
-        achieved = frec["bytes"] / (frec["ms"] * 1e-3) / 1e9
-        peak = float(peaks["hbm_gbs"])
-        return {"kernel": fname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
-                "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
+        return family_roofline(fname, frec, peaks, peak_src, num_sms, sm_max)
 
     roof = roofline_of(name, f)
     roof_resid = roofline_of("residual", prof["residual"])

@@ -59,3 +59,23 @@ def test_single_rank_defaults(monkeypatch):
     assert bench.rank_env() == (1, 0, 0)
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_throughput(1, 100, 2, 10.0) == pytest.approx(2e4)
+
+
+def test_family_roofline_arithmetic():
+    """bench.py's roofline entries: achieved = algorithmic work / summed event
+    time, peaks from the measured figures (TF32 = bf16 x 1.1/2.25) or the
+    derived FP32 FMA peak."""
+    import bench
+    peaks = {"hbm_gbs": 6756.2, "bf16_tflops": 1914.9}
+    r = bench.family_roofline("residual", {"launches": 2, "ms": 0.4, "bytes": 1.24e9, "flops": 0.0},
+                              peaks, "measured", 152, 2070.0)
+    assert r["bound"] == "hbm" and abs(r["achieved"] - 3100.0) < 1e-9 and abs(r["frac"] - 3100.0 / 6756.2) < 1e-12
+    assert abs(r["avg_launch_us"] - 200.0) < 1e-9
+    r = bench.family_roofline("bcr_aniso", {"launches": 10, "ms": 1.0, "bytes": 0.0, "flops": 2.0e10},
+                              peaks, "measured", 152, 2070.0)
+    fp32 = 152 * 128 * 2 * 2070e6 / 1e12
+    assert r["bound"] == "alu" and abs(r["peak"] - fp32) < 1e-9 and abs(r["achieved"] - 20.0) < 1e-9
+    r = bench.family_roofline("fill_tc", {"launches": 1, "ms": 0.03, "bytes": 7.5e7, "flops": 1.77e9},
+                              peaks, "measured", 152, 2070.0)
+    assert r["bound"] == "tensor" and abs(r["peak"] - 1914.9 * 1.1 / 2.25) < 1e-9
+    assert abs(r["achieved"] - 59.0) < 1e-9
