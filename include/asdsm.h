@@ -147,9 +147,14 @@ int asdsm_autotune(asdsm_handle* h, int precision);
 
 /* The handle's launch shapes (as chosen by asdsm_autotune, or 0 = built-in)
  * as 130 integers, to save a tuning and apply it to another handle of the
- * same sizes (asdsm_tune_set; n must be 130).  The Filler entry of each
- * precision is 16 for the tensor-core kernel, 1..8 for the block cyclic
- * reduction kernel's warps per CTA, 0 for the default.  get returns the count written
+ * same sizes (asdsm_tune_set; n must be 130).  Layout per precision (FP64
+ * first): forward and backward levels of the anisotropic pair (2 x 16), of
+ * the coarse system (2 x 16), then the Filler.  A level entry is
+ * (TM << 8) | KS: TM = 16 or 64 rows per CTA on the FMA pipes with KS = 1, 2,
+ * 4 or 8 CTAs per cluster splitting the reduction; TM = 32 the mma.sync
+ * tensor-core kernel, TM = 128 the tcgen05 kernel (FP32 only, KS = 1); 0 the
+ * built-in choice.  The Filler entry is 16 for the tensor-core kernel, 1..8
+ * for the block cyclic reduction kernel's warps per CTA, 0 for the default.  get returns the count written
  * (cap >= 130) or ASDSM_ERR_INVALID. */
 int asdsm_tune_get(const asdsm_handle* h, int32_t* out, int cap);
 int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n);
