@@ -5,7 +5,7 @@ module: only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
 CPU-baseline / ``--impl reference`` legs do.  It shares no code with the
 CUDA path.
 
-What it computes, step by step in the paper's order and notation
+What it computes, in the paper's notation
 (K. Trotti, "A domain splitting strategy for solving PDEs", arXiv 2303.01163):
 
 * eq. (2.1)/(2.3): meshes Omega^{h,h}, Omega^{h,H} ("fc"), Omega^{H,h} ("cf"),
@@ -15,8 +15,11 @@ What it computes, step by step in the paper's order and notation
 * Section 2.3: second-order centred finite differences in Kronecker form,
   A = alpha (I (x) L/h^2 + L/h^2 (x) I) + beta (I (x) D/(2h) + D/(2h) (x) I),
   with per-axis alpha_i, beta_i.
-* Algorithm 1 (InitialGuess), Algorithm 2 (Skeleton), Algorithm 3 (Filler),
-  Algorithm 4 (ASDSM) with the optimal scaling s_hat of its step 6.
+* Section 3.1: the initial guess (Algorithm 1) from the two anisotropic
+  solutions, their merge into one skeleton (Algorithm 2) and the hole solves
+  (Algorithm 3), each written as the map it defines rather than as a listing.
+* Section 3.2: the ASDSM iteration (Algorithm 4) with the clamped optimal
+  scaling s_hat of the correction.
 
 Library primitives used as single steps: ``scipy.sparse.linalg.splu`` for
 every "(A)^{-1} b" of the algorithms (each matrix is factored once and reused)
@@ -35,34 +38,34 @@ R4  eq. (1.1) reads sum_i (-alpha_i u_{x_i x_i} + beta_i u_{x_i}) = s,
 R5  Dirichlet data enter the right-hand side of every mesh by the usual
     lifting: a stencil term that reaches a boundary point moves to b with
     that mesh's own spacing.  Error equations have zero boundary data.
-R7  Richardson extrapolation of Algorithm 2 step 2 is the 2D combination
+R7  The Richardson extrapolation of Algorithm 2 is the 2D combination
     u_hat = P u_fc + P u_cf - u_cc (error C_x h^2 + C_y h^2 after the
     combination when each mesh carries C_x h_x^2 + C_y h_y^2).
-R8  The random choice of Algorithm 2 step 3 is one draw per call for the
+R8  The random choice of Algorithm 2 is one draw per call for the
     whole coarse vector, taken from the counter-based SplitMix64 generator
     (choice_bit below), so the CUDA path draws the same sequence.
-R9  Normalisation in Algorithm 1 step 2 is by the Euclidean norm of the
+R9  The normalisation of Algorithm 1 is by the Euclidean norm of the
     whole submesh vector; a zero vector stays zero.
 R10 "Spline ... with zero BCs" is the not-a-knot cubic spline through the
     knots x = 0, H, ..., 1 with zero values at x = 0 and x = 1.
 R11 Cross points of the merged skeleton take the corrected fc value,
-    which is what step 6 of Algorithm 2 writes.
+    which is what the assembly of Algorithm 2 writes.
 R13 The loop runs while ||r||/||b|| > tol, k < max_sweeps and the residual
     has not stagnated (||r_k|| > (1 - 1e-3) ||r_{k-10}||).
 R14 s_hat = max(0, <r, A e>/<A e, A e>), least squares over the skeleton
     rows, where A e is non-zero (Prop. 3.1; Section 3.3, first two remarks).
 R15 Refinement to tight tolerances: with accel_m > 1 the correction e of
-    Algorithm 4 step 5 is used as a flexible preconditioner inside
+    Algorithm 4 is used as a flexible preconditioner inside
     restarted GCR(m): the new A e is orthogonalised against the cycle's
     previous ones and the step is the unconstrained least-squares
-    coefficient.  accel_m = 1 is exactly the paper's step 6.
+    coefficient.  accel_m = 1 is exactly the paper's clamped optimal step.
 R18 Hole residual.  In exact arithmetic the residual vanishes in the holes
     (Prop. 3.1).  When rounding has made its hole part exceed both
     hole_fix_ratio * ||r|| and hole_fix_growth times its value just after
     the last such correction (zero before the first one), the sweep is
-    replaced by Algorithm 3 applied to the current iterate: its step 1 then
-    gives c = -P A u, so step 2 solves the hole systems with the hole part of
-    the current residual and zeroes it (down to rounding).  The GCR cycle
+    replaced by Algorithm 3 applied to the current iterate, which solves
+    the hole systems with the hole part of the current residual and zeroes
+    it (down to rounding).  The GCR cycle
     restarts afterwards.
 """
 from __future__ import annotations
@@ -93,7 +96,7 @@ def splitmix64_stream(seed: int, count: int) -> list:
 
 
 def choice_bit(seed: int, k: int) -> int:
-    """Coin of Algorithm 2 step 3 at ASDSM sweep k: the top bit of output k."""
+    """Coin of the random choice of Algorithm 2 at ASDSM sweep k: the top bit of output k."""
     return splitmix64((seed + (k + 1) * _GOLDEN_GAMMA) & _MASK64) >> 63
 
 
@@ -240,7 +243,7 @@ class Discretisation2D:
             self._lu_ff = spla.splu(self.A_ff.tocsc())
         return self._lu_ff.solve(b_ff)
 
-    # -- Algorithm 2 ----------------------------------------------------------
+    # -- Section 3.1, Algorithm 2: one skeleton from the two anisotropic solutions
     def spline_fc(self, e_cc):
         """Spline(e, Omega^{h,H}): along x on every coarse line (R10)."""
         m = self.m
@@ -260,46 +263,79 @@ class Discretisation2D:
         return out.reshape(-1)                       # [fine y][column i], x fastest
 
     def skeleton(self, u_fc, u_cf, u_cc=None, choice=0):
-        """Algorithm 2 (Skeleton Builder)."""
-        t1 = self.P_fc_cc @ u_fc                      # step 1.1
-        t2 = self.P_cf_cc @ u_cf                      # step 1.2
-        if u_cc is not None:
-            u_hat = t1 + t2 - u_cc                    # step 2, RE (R7)
-        else:
-            u_hat = t1.copy() if choice == 0 else t2.copy()   # step 3 (R8)
-        e1 = u_hat - t1                               # step 4.1
-        e2 = u_hat - t2                               # step 4.2
-        ut_fc = u_fc + self.spline_fc(e1)             # step 5.1
-        ut_cf = u_cf + self.spline_cf(e2)             # step 5.2
-        return (self.P_ff_fc.T @ ut_fc + self.P_ff_cf.T @ ut_cf
-                - self.P_ff_cc.T @ (self.P_cf_cc @ ut_cf))     # step 6 (R11)
+        """Algorithm 2 (Skeleton Builder) as one map from (u_fc, u_cf) to a fine grid.
 
-    # -- Algorithm 3 ----------------------------------------------------------
+        Both families sample the coarse mesh Omega^{H,H}.  Their common value
+        there, u_hat, is the extrapolated combination of R7 when u_cc is given,
+        otherwise the samples of the family the coin picked (R8).  Each family
+        is then moved onto u_hat at the coarse points by adding the spline
+        (R10) of its mismatch along its fine axis; the two corrected families
+        now agree at the cross points, and together they cover the skeleton
+        Omega^{h,H} U Omega^{H,h}, holes left at zero (R11)."""
+        at_cc = (self.P_fc_cc @ u_fc, self.P_cf_cc @ u_cf)
+        u_hat = at_cc[choice] if u_cc is None else at_cc[0] + at_cc[1] - u_cc
+        fc = u_fc + self.spline_fc(u_hat - at_cc[0])
+        cf = u_cf + self.spline_cf(u_hat - at_cc[1])
+        # Cross points belong to both families; they are written once, from fc.
+        cf_without_cross = cf - self.P_cf_cc.T @ (self.P_cf_cc @ cf)
+        return self.P_ff_fc.T @ fc + self.P_ff_cf.T @ cf_without_cross
+
+    # -- Section 3.1, Algorithm 3: independent hole solves -------------------
     def filler(self, u_t, b_ff):
-        """Algorithm 3 (Filler)."""
-        c = -(self.P_ff_holes @ (self.A_ff @ u_t))                 # step 1
-        v = self.lu_holes.solve(self.P_ff_holes @ b_ff + c)       # step 2
-        return u_t + self.P_ff_holes.T @ v                        # step 3
+        """Algorithm 3 (Filler): every hole of Remark 2.4 solved with Dirichlet
+        data from the skeleton of u_t.  Since A_ff restricted to the holes is the
+        block-diagonal A_hh, the hole values are corrected by
+            u_holes += A_hh^{-1} P_holes (b_ff - A_ff u_t),
+        which makes the residual vanish at every hole point (Prop. 3.1)."""
+        v = self.lu_holes.solve(self.P_ff_holes @ (b_ff - self.A_ff @ u_t))
+        return u_t + self.P_ff_holes.T @ v
 
-    # -- Algorithm 1 ----------------------------------------------------------
+    # -- Section 3.1, Algorithm 1 ----------------------------------------------
     def initial_guess(self, b_ff, b_fc, b_cf, b_cc=None, choice=0):
-        """Algorithm 1 (Initial Guess Builder)."""
-        u_fc = self.lu_fc.solve(b_fc)                 # step 1.1
-        u_cf = self.lu_cf.solve(b_cf)                 # step 1.2
-        u_cc = None
-        if b_cc is not None:
-            u_cc = self.lu_cc.solve(b_cc)             # step 1.3
+        """Algorithm 1 (Initial Guess Builder): the anisotropic systems of
+        eq. (2.4) solved exactly, merged by Algorithm 2 and completed by
+        Algorithm 3.  With b_cc (the first iterate) the coarse system is solved
+        too and the merge extrapolates; without it (the correction of a sweep)
+        the two solutions are normalised per family (R9) and merged by the coin."""
+        u_fc = self.lu_fc.solve(b_fc)
+        u_cf = self.lu_cf.solve(b_cf)
+        if b_cc is None:
+            u_fc, u_cf = normalised_families(u_fc, u_cf)
+            u_t = self.skeleton(u_fc, u_cf, None, choice)
         else:
-            n1, n2 = np.linalg.norm(u_fc), np.linalg.norm(u_cf)   # step 2 (R9)
-            if n1 > 0:
-                u_fc = u_fc / n1
-            if n2 > 0:
-                u_cf = u_cf / n2
-        u_t = self.skeleton(u_fc, u_cf, u_cc, choice)             # step 3
-        return self.filler(u_t, b_ff)                             # step 4
+            u_t = self.skeleton(u_fc, u_cf, self.lu_cc.solve(b_cc))
+        return self.filler(u_t, b_ff)
+
+    def correction(self, r, choice):
+        """The ASDSM correction of a sweep (Section 3.2): Algorithm 1 applied to
+        the error equations, i.e. right-hand sides P_fc r and P_cf r on the two
+        anisotropic meshes, zero boundary data and zero source in the holes."""
+        return self.initial_guess(np.zeros_like(r), self.P_ff_fc @ r, self.P_ff_cf @ r, None, choice)
 
     def residual(self, b_ff, u):
         return b_ff - self.A_ff @ u
+
+
+def normalised_families(u_fc, u_cf):
+    """R9: each anisotropic solution divided by its own Euclidean norm (a zero
+    vector stays zero), so that neither family dominates the merge by size."""
+    out = []
+    for v in (u_fc, u_cf):
+        nv = np.linalg.norm(v)
+        out.append(v / nv if nv > 0 else v)
+    return out[0], out[1]
+
+
+def hole_fix_due(hole_norm, r_norm, hole_ref, ratio, growth):
+    """R18: rounding has left a hole residual worth a Filler pass when it is
+    both a sizeable part of the whole residual (ratio) and has grown past
+    `growth` times its size right after the previous pass (0 before any)."""
+    return hole_norm > ratio * r_norm and hole_norm > growth * hole_ref
+
+
+def stagnated(hist, window, factor):
+    """R13: the residual of the last `window` sweeps fell by less than `factor`."""
+    return len(hist) > window and hist[-1] > (1 - factor) * hist[-1 - window]
 
 
 def asdsm(disc: Discretisation2D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, seed=0,
@@ -308,23 +344,26 @@ def asdsm(disc: Discretisation2D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
           u0=None, record_iterates=False):
     """Algorithm 4 (ASDSM) with the readings R13-R15 and R18.
 
+    The iterate starts from Algorithm 1 (or u0).  Each sweep takes the fine
+    residual r = b_ff - A_ff u, builds the correction e from it (Section 3.2)
+    and moves u along e by a least-squares step on the skeleton rows, where
+    A e can be non-zero (Prop. 3.1): the clamped optimal scaling s_hat >= 0 of
+    Section 3.2 when accel_m = 1, restarted GCR(accel_m) otherwise (R15).
+
     b = (b_ff, b_fc, b_cf, b_cc).  Returns (u, info); info holds the relative
     residual history (entry k is the residual of iterate k), the choice bits,
     the step lengths, what each sweep did and why the loop stopped."""
     b_ff, b_fc, b_cf, b_cc = b
     sk = disc.P_ff_skel
-    if u0 is None:
-        u = disc.initial_guess(b_ff, b_fc, b_cf, b_cc)            # step 1
-    else:
-        u = np.array(u0, dtype=np.float64)
+    u = disc.initial_guess(b_ff, b_fc, b_cf, b_cc) if u0 is None else np.array(u0, dtype=np.float64)
     nb = np.linalg.norm(b_ff)
     hist, steps, bits, kinds, iterates = [], [], [], [], []
     Z, Q = [], []                    # GCR cycle: directions and their A-images on the skeleton
-    hole_ref = 0.0                   # hole residual norm right after the last correction (R18)
+    hole_ref = 0.0                   # hole residual norm right after the last Filler pass (R18)
     status = "max_sweeps"
-    k = 0                                                         # step 2
+    k = 0
     while True:
-        r = disc.residual(b_ff, u)                                # step 3
+        r = disc.residual(b_ff, u)
         rel = np.linalg.norm(r) / nb if nb > 0 else np.linalg.norm(r)
         hist.append(rel)
         if record_iterates:
@@ -334,13 +373,12 @@ def asdsm(disc: Discretisation2D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
             break
         if k >= max_sweeps:
             break
-        if (len(hist) > stagnation_window and
-                hist[-1] > (1 - stagnation_factor) * hist[-1 - stagnation_window]):
+        if stagnated(hist, stagnation_window, stagnation_factor):
             status = "stagnated"
             break
-        hole_norm = np.linalg.norm(disc.P_ff_holes @ r)
-        if hole_norm > hole_fix_ratio * np.linalg.norm(r) and hole_norm > hole_fix_growth * hole_ref:
-            u = disc.filler(u, b_ff)                              # R18
+        if hole_fix_due(np.linalg.norm(disc.P_ff_holes @ r), np.linalg.norm(r), hole_ref,
+                        hole_fix_ratio, hole_fix_growth):
+            u = disc.filler(u, b_ff)
             hole_ref = np.linalg.norm(disc.P_ff_holes @ disc.residual(b_ff, u))
             Z, Q = [], []
             kinds.append("hole_fix")
@@ -349,18 +387,18 @@ def asdsm(disc: Discretisation2D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
             k += 1
             continue
         bit = choice_bit(seed, k)
-        r_fc = disc.P_ff_fc @ r                                   # step 4.1
-        r_cf = disc.P_ff_cf @ r                                   # step 4.2
-        e = disc.initial_guess(0.0 * b_ff, r_fc, r_cf, None, bit)  # step 5
-        q = sk @ (disc.A_ff @ e)
+        e = disc.correction(r, bit)
+        q = sk @ (disc.A_ff @ e)     # A e on the skeleton rows
         rs = sk @ r
         if accel_m == 1:
             qq = q @ q
-            s_hat = max(0.0, (rs @ q) / qq) if qq > 0 else 0.0    # step 6 (R14)
-            u = u + s_hat * e                                     # step 7
+            s_hat = max(0.0, (rs @ q) / qq) if qq > 0 else 0.0     # R14
+            u = u + s_hat * e
             steps.append(s_hat)
         else:
-            for zj, qj in zip(Z, Q):                              # R15: GCR(m)
+            # R15: orthogonalise A e against the cycle's earlier images, then the
+            # least-squares coefficient along the new unit image.
+            for zj, qj in zip(Z, Q):
                 beta_j = q @ qj
                 q = q - beta_j * qj
                 e = e - beta_j * zj
@@ -379,7 +417,7 @@ def asdsm(disc: Discretisation2D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
                 Z, Q = [], []
         kinds.append("sweep")
         bits.append(bit)
-        k += 1                                                    # step 8
+        k += 1
     info = {"hist": hist, "steps": steps, "bits": bits, "kinds": kinds,
             "status": status, "sweeps": k}
     if record_iterates:

@@ -32,24 +32,24 @@ Readings (the 2D readings R1-R18 of ``asdsm2d`` carry over):
 
 R20 Meshes and ordering: points (i, j, l) in fine indices (x = i h, y = j h,
     z = l h), listed x fastest, then y, then z; full grids are arrays [z, y, x].
-R21 Extrapolation at intersection points (Algorithm 2 step 2 in 3D, the
-    combination technique): at knots (points of C)
+R21 Extrapolation at intersection points (the extrapolation of Algorithm 2
+    in 3D, by the combination technique): at knots (points of C)
         u_hat = u_Px + u_Py + u_Pz - u_Lx - u_Ly - u_Lz + u_C,
     and at the other points of a line where two plane families meet (e.g.
     x = kH, y = lH, z fine: P_x and P_y meet on L_z)
         u_hat = u_Px + u_Py - u_Lz.
     This is why the initial guess also solves the line meshes.
-R22 Random choice (Algorithm 2 step 3) in 3D: one draw per call, uniform over
+R22 Random choice of Algorithm 2 in 3D: one draw per call, uniform over
     the three plane families (SplitMix64 output mod 3, same counter as R8); a
     line point outside the chosen family takes the value of the next family
     in the cyclic order x -> y -> z -> x that contains it.
-R23 Spline correction on a plane (Algorithm 2 step 5 in 3D): on the plane of
+R23 Spline correction of Algorithm 2 on a plane in 3D: on the plane of
     P_x the errors are known on its lines y = lH and z = mH (where it meets P_y
     and P_z); the correction is the Boolean sum (transfinite interpolation)
         S_y e + S_z e - S_y S_z e
     of the not-a-knot cubic splines (R10) along the plane's two fine axes.
     It equals e on every line of the plane.
-R24 Normalisation (Algorithm 1 step 2) of each plane solution by its own
+R24 Normalisation of Algorithm 1 in 3D: each plane solution by its own
     Euclidean norm; a zero vector stays zero.
 """
 from __future__ import annotations
@@ -65,7 +65,7 @@ FAMILIES = ("x", "y", "z")          # plane family P_a: coordinate a on the coar
 
 
 def choice3(seed: int, k: int) -> int:
-    """Family drawn by Algorithm 2 step 3 at ASDSM sweep k (R22): 0, 1 or 2."""
+    """Family drawn by the random choice of Algorithm 2 at ASDSM sweep k (R22): 0, 1 or 2."""
     return splitmix64((seed + (k + 1) * _GOLDEN_GAMMA) & _MASK64) % 3
 
 
@@ -281,13 +281,13 @@ class Discretisation3D:
         cnt = Mx.astype(int) + My + Mz
         inter = cnt >= 2                                               # lines and knots
         Ux, Uy, Uz = U_plane["x"], U_plane["y"], U_plane["z"]
-        if U_line is not None:                                         # step 2: extrapolation (R21)
+        if U_line is not None:                                         # extrapolation (R21)
             knot = cnt == 3
             u_hat = np.where(knot, Ux + Uy + Uz - U_line["x"] - U_line["y"] - U_line["z"] + U_cc, 0.0)
             u_hat = np.where(Mx & My & ~knot, Ux + Uy - U_line["z"], u_hat)
             u_hat = np.where(My & Mz & ~knot, Uy + Uz - U_line["x"], u_hat)
             u_hat = np.where(Mx & Mz & ~knot, Ux + Uz - U_line["y"], u_hat)
-        else:                                                          # step 3: random choice (R22)
+        else:                                                          # random choice (R22)
             order = [FAMILIES[(choice + t) % 3] for t in range(3)]
             u_hat = np.zeros_like(Ux)
             taken = np.zeros_like(inter)
@@ -295,12 +295,12 @@ class Discretisation3D:
                 sel = inter & msk[f] & ~taken
                 u_hat = np.where(sel, U_plane[f], u_hat)
                 taken |= sel
-        # steps 4-5: errors on each plane's lines, Boolean-sum correction (R23)
+        # each plane moved onto u_hat along its lines by the Boolean-sum spline of its mismatch (R23)
         corrected = {}
         for f in FAMILIES:
             E = np.where(inter & msk[f], u_hat - U_plane[f], 0.0)
             corrected[f] = U_plane[f] + self.plane_correction(f, E)
-        # step 6: the union of the corrected planes (they agree on the lines)
+        # the union of the corrected planes (they agree on the lines)
         S = np.zeros_like(Ux)
         for f in FAMILIES:
             S = np.where(msk[f], corrected[f], S)
@@ -308,17 +308,23 @@ class Discretisation3D:
 
     # -- Algorithm 3 ------------------------------------------------------------
     def filler(self, u_t, b_ff):
-        c = -(self.P_holes @ (self.A_ff @ u_t))
-        v = self.lu_holes.solve(self.P_holes @ b_ff + c)
+        """Algorithm 3 for the cube holes: u_holes += A_hh^{-1} P_holes (b_ff - A_ff u_t),
+        which zeroes the residual at every hole point (Prop. 3.1 in 3D)."""
+        v = self.lu_holes.solve(self.P_holes @ (b_ff - self.A_ff @ u_t))
         return u_t + self.P_holes.T @ v
 
     # -- Algorithm 1 in 3D --------------------------------------------------------
     def initial_guess(self, b_ff, b_plane, b_line=None, b_cc=None, choice=0):
+        """Algorithm 1 in 3D: the three plane families solved exactly; for the
+        first iterate (b_line, b_cc given) also the line families and the coarse
+        mesh, which the extrapolating merge needs (R21); for a sweep's
+        correction each plane solution normalised by its own norm (R24) and
+        merged by the random choice (R22); then the cube-hole Filler."""
         m = self.m
         U_plane = {}
-        for f in FAMILIES:                                             # step 1
+        for f in FAMILIES:
             u = self.lu_plane[f].solve(b_plane[f])
-            if b_line is None:                                         # step 2 (R24)
+            if b_line is None:
                 nrm = np.linalg.norm(u)
                 if nrm > 0:
                     u = u / nrm
@@ -327,8 +333,8 @@ class Discretisation3D:
         if b_line is not None:
             U_line = {f: self.to_full(m.line[f], self.lu_line[f].solve(b_line[f])) for f in FAMILIES}
             U_cc = self.to_full(m.cc, self.lu_cc.solve(b_cc))
-        u_t, _, _ = self.skeleton(U_plane, U_line, U_cc, choice)      # step 3
-        return self.filler(u_t, b_ff)                                  # step 4
+        u_t, _, _ = self.skeleton(U_plane, U_line, U_cc, choice)
+        return self.filler(u_t, b_ff)
 
     def residual(self, b_ff, u):
         return b_ff - self.A_ff @ u
@@ -349,7 +355,7 @@ def asdsm(disc: Discretisation3D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
     status = "max_sweeps"
     k = 0
     while True:
-        r = disc.residual(b_ff, u)                                     # step 3
+        r = disc.residual(b_ff, u)
         rel = np.linalg.norm(r) / nb if nb > 0 else np.linalg.norm(r)
         hist.append(rel)
         if rel <= tol:
@@ -362,14 +368,15 @@ def asdsm(disc: Discretisation3D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
             status = "stagnated"
             break
         ch = choice3(seed, k)
-        r_p = {f: disc.P_plane[f] @ r for f in FAMILIES}               # step 4
-        e = disc.initial_guess(0.0 * b_ff, r_p, None, None, ch)        # step 5
+        # the correction: Algorithm 1 on the error equations of the plane meshes
+        r_p = {f: disc.P_plane[f] @ r for f in FAMILIES}
+        e = disc.initial_guess(0.0 * b_ff, r_p, None, None, ch)
         q = sk @ (disc.A_ff @ e)
         rs = sk @ r
         if accel_m == 1:
             qq = q @ q
-            s_hat = max(0.0, (rs @ q) / qq) if qq > 0 else 0.0        # step 6 (R14)
-            u = u + s_hat * e                                          # step 7
+            s_hat = max(0.0, (rs @ q) / qq) if qq > 0 else 0.0        # R14
+            u = u + s_hat * e
             steps.append(s_hat)
         else:
             for zj, qj in zip(Z, Q):                                   # R15
