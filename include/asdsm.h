@@ -72,10 +72,10 @@ typedef struct {
     double   tol;               /* stop when ||b - A u||_2 / ||b||_2 <= tol */
     int32_t  max_sweeps;        /* sweeps of Algorithm 4 (hole corrections count as sweeps) */
     int32_t  precision;         /* ASDSM_FP64 or ASDSM_MIXED */
-    int32_t  accel_m;           /* 1: the paper's step 6 (s_hat >= 0); m > 1: restarted GCR(m) with the
+    int32_t  accel_m;           /* 1: the paper's clamped optimal scaling (s_hat >= 0); m > 1: restarted GCR(m) with the
                                    Algorithm-1 correction as flexible preconditioner */
     int32_t  skip_initial_guess;/* 1: start from the interior of u as given (resume); 0: Algorithm 1 */
-    uint64_t seed;              /* SplitMix64 seed of the random choice of Algorithm 2 step 3 */
+    uint64_t seed;              /* SplitMix64 seed of the random choice of Algorithm 2 */
     double   hole_fix_ratio;    /* re-fill holes when ||r_holes|| > ratio*||r|| ... */
     double   hole_fix_growth;   /* ... and > growth * (hole residual after the last fill) */
     int32_t  stagnation_window; /* stagnated if ||r_k|| > (1 - stagnation_factor) ||r_{k-window}|| */
@@ -157,7 +157,16 @@ int asdsm_autotune(asdsm_handle* h, int precision);
  * for the block cyclic reduction kernel's warps per CTA, 0 for the default.  get returns the count written
  * (cap >= 130) or ASDSM_ERR_INVALID. */
 int asdsm_tune_get(const asdsm_handle* h, int32_t* out, int cap);
+/* set checks the entries as asdsm_tune_check does and returns
+ * ASDSM_ERR_INVALID, leaving the handle unchanged, when one does not fit. */
 int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n);
+
+/* Check a saved tuning (n = 130 entries, layout as above) against the
+ * encoding without a handle or any device work: every level entry 0,
+ * (TM << 8) | KS with TM in {16, 64} and KS in {1, 2, 4, 8}, or - FP32 half
+ * only - TM in {32, 128} with KS = 1; every Filler entry 0..8, or 16 in the
+ * FP32 half.  Returns ASDSM_OK or ASDSM_ERR_INVALID. */
+int asdsm_tune_check(const int32_t* in, int n);
 
 /* Algorithm 4 (ASDSM).  The initial guess (Algorithm 1) has FP64 quality in
  * both precisions (see asdsm_initial_guess); the mixed path then runs its
@@ -178,7 +187,7 @@ int asdsm_solve(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats)
  * writes the interior of u. */
 int asdsm_initial_guess(asdsm_handle* h, const double* s, double* u);
 
-/* Fine residual of Algorithm 4 step 3: r = b_ff - A_ff u over the interior,
+/* Fine residual of Algorithm 4: r = b_ff - A_ff u over the interior,
  * b_ff being s plus the Dirichlet lifting of u's boundary ring.  s, u:
  * device N*N.  r: device N*N or NULL; when given, its interior receives r and
  * its boundary ring zeros.  rel_norm (host, may be NULL) receives
@@ -241,10 +250,10 @@ int64_t asdsm_launch_count(void);
 
 /* Fine residual and relative residual norm WITHOUT ANY DEVICE ALLOCATION.
  * The paper has no counterpart: this serves callers that cannot call
- * cudaMalloc when they need the residual - code being recorded into a CUDA
- * graph (allocation is not a capturable operation), services whose device
- * memory is reserved up front by their own pool, loops where an allocation
- * would stall the device.  It needs no handle.
+ * cudaMalloc when they need the residual - services whose device memory is
+ * reserved up front by their own pool allocator, loops where an allocation
+ * would stall or synchronise the device.  It needs no handle (creating one
+ * allocates).
  * desc: only d, n, alpha and beta are read.  d = 2: N*N grids, 3 <= N <= 8193,
  * the 5-point operator of Section 2.3.  d = 3: N*N*N grids (z slowest, x
  * fastest), 3 <= N <= 2049, the 7-point operator of the 3D extension (alpha,
@@ -252,14 +261,16 @@ int64_t asdsm_launch_count(void);
  * s, u: device FP64 grids as for asdsm_residual (u's boundary = g).
  * r: device grid or NULL; its interior receives r = b_ff - A_ff u (the
  * boundary is not written).  rel_norm: host pointer or NULL; receives ||r||/||b_ff||
- * (the call then synchronises `stream`).  stream: cudaStream_t or NULL.
+ * (the call then copies the two norms to the host and synchronises `stream`;
+ * with NULL it only enqueues work).  stream: cudaStream_t or NULL.
  * Scratch: statically allocated device arrays of about 1 MiB held by every
  * GPU that loads the library until the process exits.  The first call on a
  * device looks up their device address (cudaGetSymbolAddress) with that
  * device current, so make that first call before any stream capture.  All
  * calls share the scratch; each call rewrites every slot it reads, so nothing
- * carries over, but calls that overlap on the GPU race.  Grids larger than
- * 8193 points per axis return ASDSM_ERR_INVALID (message in
+ * carries over, but calls that overlap on the GPU race.  Grids beyond the
+ * scratch's size - N > 8193 for d = 2, N > 2049 for d = 3 - return
+ * ASDSM_ERR_INVALID before any device work (message in
  * asdsm_noalloc_last_error). */
 int asdsm_residual_noalloc(const asdsm_desc* desc, const double* s, const double* u, double* r,
                            double* rel_norm, void* stream);
@@ -343,7 +354,7 @@ void asdsm_cnn_destroy(asdsm_cnn* net);
 
 /* Use `net` (NULL: none) as a learned correction in the handle's mixed-
  * precision solves: every sweep, after the ASDSM correction e of Algorithm 4
- * step 5, the network maps [r, e (each scaled to unit RMS over the interior),
+ * (Algorithm 1 on the residual), the network maps [r, e (each scaled to unit RMS over the interior),
  * alpha_x, alpha_y, beta_x h, beta_y h] to a direction; its skeleton values,
  * completed by the homogeneous Filler (Algorithm 3), enter the same GCR(m)
  * cycle as a second direction (least squares over [e, e_cnn]); a dependent
@@ -353,8 +364,8 @@ void asdsm_cnn_destroy(asdsm_cnn* net);
 int asdsm_attach_cnn(asdsm_handle* h, asdsm_cnn* net);
 /* Learned directions accepted by the GCR steps of the last solve. */
 int asdsm_cnn_directions(const asdsm_handle* h);
-/* Training features of an iterate: r_out = s - A u (steps 3 of Algorithm 4)
- * and e_out = the correction of steps 4-5 (Algorithm 1 without b_cc, choice
+/* Training features of an iterate: r_out = s - A u (the fine residual of Algorithm 4)
+ * and e_out = the correction of Algorithm 4 (Algorithm 1 without b_cc, choice
  * of sweep k), both FP32 N*N device grids (computed in FP64). */
 int asdsm_correction(asdsm_handle* h, const double* s, const double* u, float* r_out, float* e_out, int k);
 

@@ -88,6 +88,8 @@ def load() -> ctypes.CDLL:
     lib.asdsm_tune_get.restype = ctypes.c_int
     lib.asdsm_tune_set.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
     lib.asdsm_tune_set.restype = ctypes.c_int
+    lib.asdsm_tune_check.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
+    lib.asdsm_tune_check.restype = ctypes.c_int
     lib.asdsm_solve.argtypes = [P, P, P, ctypes.POINTER(Stats)]
     lib.asdsm_solve.restype = ctypes.c_int
     lib.asdsm_initial_guess.argtypes = [P, P, P]

@@ -2,14 +2,14 @@
 // Algorithm 4 on one GPU stream.
 //
 // Per sweep (all on the handle's stream):
-//   residual kernel  : step 7 of the previous sweep fused with step 3
+//   residual kernel  : the previous sweep's update fused with the fine residual
 //                      (u += sum_j delta_j z_j ; r = b - A u ; r on the skeleton
-//                      gathered for steps 4.1/4.2 and the least squares)
-//   bcr_solve        : steps 1.1/1.2 of Algorithm 1 (both families in one batch)
-//   multi_dot        : norms of step 2 of Algorithm 1
+//                      gathered for the submesh right-hand sides and the least squares)
+//   bcr_solve        : the anisotropic solves of Algorithm 1 (both families in one batch)
+//   multi_dot        : norms of the normalisation of Algorithm 1
 //   merge_knots/write: Algorithm 2 (random choice, spline correction, merge)
 //   fill_holes       : Algorithm 3 with 0 b
-//   skeleton_apply   : A e on the skeleton rows (step 6 least squares)
+//   skeleton_apply   : A e on the skeleton rows (least squares of the step length)
 //   multi_dot        : the least-squares / GCR(m) inner products
 // The host reads two small reductions per sweep (the residual norms and the
 // least-squares inner products) and keeps the m x m GCR bookkeeping.
@@ -51,7 +51,7 @@ uint64_t splitmix64_out(uint64_t state) {
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
 }
-// Coin of Algorithm 2 step 3 at sweep k: top bit of SplitMix64 output k.
+// Coin of the random choice of Algorithm 2 at sweep k: top bit of SplitMix64 output k.
 int choice_bit(uint64_t seed, int k) {
     const uint64_t state = seed + (uint64_t)(k + 1) * 0x9E3779B97F4A7C15ULL;
     return (int)(splitmix64_out(state) >> 63);
@@ -457,9 +457,9 @@ int initial_guess_to_z(asdsm_handle* h, const double* s, const double* u) {
     cudaStream_t st = h->st;
     CK(build_submesh_rhs<T>(s, u, g, h->alpha, h->beta, (T*)w.Xfc, (T*)w.Xcf, (T*)w.Xcc, st));
     BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
-    CK(bcr_solve<T>(sys, 2, st, &h->tune_aniso[pi]));                                       // steps 1.1, 1.2
+    CK(bcr_solve<T>(sys, 2, st, &h->tune_aniso[pi]));                                       // u_fc, u_cf
     BcrSys<T> scc = sys_of<T>(h->cc[pi], w.Xcc, w.Ycc);
-    CK(bcr_solve<T>(&scc, 1, st, &h->tune_cc[pi]));                                      // step 1.3
+    CK(bcr_solve<T>(&scc, 1, st, &h->tune_cc[pi]));                                      // u_cc
     T* z = (T*)w.z[0];
     CK(ring_from<T>(u, z, g, 0, st));
     MergeArgs<T> ma{};
@@ -468,8 +468,8 @@ int initial_guess_to_z(asdsm_handle* h, const double* s, const double* u) {
     ma.Sm = (const T*)h->Sm[pi];
     ma.E1 = (T*)w.E1; ma.E2 = (T*)w.E2; ma.M1 = (T*)w.M1; ma.M2 = (T*)w.M2;
     ma.z = z; ma.g = g;
-    CK(merge_knots<T>(ma, st));                                         // Algorithm 2 steps 1-4
-    CK(merge_write<T>(ma, st));                                         // steps 5-6
+    CK(merge_knots<T>(ma, st));                                         // Algorithm 2: cross-point errors
+    CK(merge_write<T>(ma, st));                                         // spline corrections, skeleton
     FillArgs<T> fa{};
     fa.mode = FILL_WITH_SOURCE;
     fa.z = z; fa.out = z;
@@ -508,9 +508,9 @@ int initial_guess_refined(asdsm_handle* h, const double* s, const double* u) {
     constexpr int kRefine = 2;
     for (int it = 0; it <= kRefine; ++it) {
         BcrSys<float> pair[2] = {sys_of<float>(h->fc[1], w32.Xfc, w32.Yfc), sys_of<float>(h->cf[1], w32.Xcf, w32.Ycf)};
-        CK(bcr_solve<float>(pair, 2, st, &h->tune_aniso[1]));                         // steps 1.1, 1.2
+        CK(bcr_solve<float>(pair, 2, st, &h->tune_aniso[1]));                         // u_fc, u_cf
         BcrSys<float> scc = sys_of<float>(h->cc[1], w32.Xcc, w32.Ycc);
-        CK(bcr_solve<float>(&scc, 1, st, &h->tune_cc[1]));                            // step 1.3
+        CK(bcr_solve<float>(&scc, 1, st, &h->tune_cc[1]));                            // u_cc
         for (const Fam& f : fam) {
             CK(add_float((double*)f.x64, (const float*)f.y32, (long long)f.R * f.C, st));
             if (it < kRefine)
@@ -525,8 +525,8 @@ int initial_guess_refined(asdsm_handle* h, const double* s, const double* u) {
     ma.Sm = (const double*)h->Sm[0];
     ma.E1 = (double*)w64.E1; ma.E2 = (double*)w64.E2; ma.M1 = (double*)w64.M1; ma.M2 = (double*)w64.M2;
     ma.z = z; ma.g = g;
-    CK(merge_knots<double>(ma, st));                                    // Algorithm 2 steps 1-4
-    CK(merge_write<double>(ma, st));                                    // steps 5-6
+    CK(merge_knots<double>(ma, st));                                    // Algorithm 2: cross-point errors
+    CK(merge_write<double>(ma, st));                                    // spline corrections, skeleton
     float* z32 = (float*)w32.z[0];
     CK(convert_array<double, float>(z, z32, (long long)g.N * g.N, st)); // skeleton and ring for the FP32 fill
     FillArgs<float> fa{};
@@ -616,7 +616,7 @@ int enqueue_holefix(asdsm_handle* h, const double* s, double* u, int par, double
     return ASDSM_OK;
 }
 
-// Steps 4-6 with the new direction in slot kc, then the step lengths.
+// The correction of Algorithm 4 into direction slot kc, then the step lengths.
 template <typename T>
 int enqueue_sweep_body(asdsm_handle* h, int kc, int m, cudaStream_t st) {
     const int pi = sizeof(T) == 8 ? 0 : 1;
@@ -1020,12 +1020,12 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
     // GCR bookkeeping (host, FP64).
     double Tm[kMaxM][kMaxM] = {};
     int kc = 0;                  // directions in the current cycle
-    UpdateTerms pend{};          // step 7 of the previous sweep, applied by the next residual kernel
+    UpdateTerms pend{};          // the previous sweep's update, applied by the next residual kernel
     double hole_ref = 0.0;       // hole residual right after the last correction (0 before the first)
     bool hole_ref_pending = false;
     const bool trace = std::getenv("ASDSM_TRACE") != nullptr;
     for (;;) {
-        // ---- step 3: residual (with the pending step-7 update fused) ----
+        // ---- fine residual (with the pending update fused) ----
         ResidOut o{};
         o.rfc = w.Xfc; o.rcf = w.Xcf; o.rskel = w.rskel; o.partials = h->partials;
         o.rfull = (mixed && h->cnn) ? w.rfull : nullptr;    // the learned correction reads r on the full grid
@@ -1099,7 +1099,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
             ++k;
             continue;
         }
-        // ---- steps 4-5: the error guess of Algorithm 1 without b_cc ----
+        // ---- the correction: Algorithm 1 without b_cc on the residual ----
         const int bit = choice_bit(op.seed, k);
         BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
         {
@@ -1145,7 +1145,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
                 prof_end(h, pm, PC_FILL, bytes, 2.0 * holes * bcr_macs(g.n - 1, g.n - 1, h->hole[pi].L));
             }
         }
-        // ---- step 6: least squares on the skeleton rows (GCR(m) step for direction zd) ----
+        // ---- least squares on the skeleton rows (GCR(m) step for direction zd) ----
         // Returns 1 when the direction is dependent (the cycle restarts), 0 otherwise;
         // with `add` the step's update is added to the pending one (a second
         // direction in the same sweep: by orthogonality its coefficient uses the
@@ -1163,7 +1163,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
             if (int rc = read_small(h, nd)) return rc;
             const double qq = h->hsmall[0], qr = h->hsmall[1];
             if (m == 1) {
-                // Paper's step 6: s_hat = argmin_{s >= 0} ||r - s A e||.
+                // The paper's clamped optimal scaling: s_hat = argmin_{s >= 0} ||r - s A e||.
                 const double shat = qq > 0 ? std::max(0.0, qr / qq) : 0.0;
                 pend.count = 1;
                 pend.z[0] = zd;
@@ -1258,7 +1258,7 @@ int run_begin(asdsm_handle* h, SolveRun& r) {
     r.Ucur = 0;
     if (mixed) CK(split_source(s, h->s_hi, h->s_lo, NN, st));
     CK(ring_from<double>(u, h->u_work, g, 0, st));
-    // Step 1: initial guess (or resume from u).  The mixed path computes
+    // Initial guess (or resume from u).  The mixed path computes
     // Algorithm 1 once in FP64: an FP32 u^(0) carries rounding noise whose
     // residual is rough, and ASDSM corrections reduce rough residuals slowly
     // (the irregular-residual stagnation of Section 4, Example 2).
@@ -1556,8 +1556,27 @@ int asdsm_tune_get(const asdsm_handle* h, int32_t* out, int cap) {
     return q;
 }
 
+int asdsm_tune_check(const int32_t* in, int n) {
+    if (!in || n != kTuneInts) return ASDSM_ERR_INVALID;
+    int q = 0;
+    for (int pi = 0; pi < 2; ++pi) {
+        for (int k = 0; k < 4 * kMaxLevels; ++k) {
+            const int v = in[q++];
+            if (v == 0) continue;
+            const int tm = v >> 8, ks = v & 0xFF;
+            const bool split_k = (tm == 16 || tm == 64) && (ks == 1 || ks == 2 || ks == 4 || ks == 8);
+            const bool tensor = pi == 1 && (tm == 32 || tm == 128) && ks == 1;
+            if (v < 0 || !(split_k || tensor)) return ASDSM_ERR_INVALID;
+        }
+        const int f = in[q++];
+        if (!(f >= 0 && f <= 8) && !(pi == 1 && f == 16)) return ASDSM_ERR_INVALID;
+    }
+    return ASDSM_OK;
+}
+
 int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n) {
-    if (!h || !in || n != kTuneInts) return ASDSM_ERR_INVALID;
+    if (!h) return ASDSM_ERR_INVALID;
+    if (int rc = asdsm_tune_check(in, n)) return rc;
     int q = 0;
     for (int pi = 0; pi < 2; ++pi) {
         for (int d = 0; d < 2; ++d)
@@ -1939,19 +1958,30 @@ int asdsm_solve_batch(asdsm_batch* b, const double* const* s, double* const* u, 
     for (size_t i = 0; i < n; ++i)
         if (!s[i] || !u[i]) return ASDSM_ERR_INVALID;
     CK(cudaEventRecord(b->ev_start, b->caller));
-    for (size_t i = 0; i < n; ++i) CK(cudaStreamWaitEvent(b->streams[i], b->ev_start, 0));
+    // From here on every exit goes through the join below, so that the
+    // caller's stream never runs ahead of work still queued on the instance
+    // streams (which read s and write u), even after a CUDA error.
+    int fail = ASDSM_OK;
+    auto ok = [&](cudaError_t e) {
+        if (e != cudaSuccess && fail == ASDSM_OK) fail = set_cuda_error(e);
+        return fail == ASDSM_OK;
+    };
+    for (size_t i = 0; i < n; ++i) ok(cudaStreamWaitEvent(b->streams[i], b->ev_start, 0));
     std::vector<SolveRun> runs(n);
-    std::vector<int> rcs(n, ASDSM_OK);
+    std::vector<int> rcs(n, fail);
     auto is64 = [&](size_t i) { return b->inst[i]->opts.precision == ASDSM_FP64; };
-    for (size_t i = 0; i < n; ++i) {
+    for (size_t i = 0; i < n && fail == ASDSM_OK; ++i) {
         runs[i].s = s[i]; runs[i].u = u[i]; runs[i].stats = stats ? &stats[i] : nullptr;
         rcs[i] = is64(i) ? batch_stage_begin<double>(b->inst[i], runs[i]) : batch_stage_begin<float>(b->inst[i], runs[i]);
     }
-    for (size_t i = 0; i < n; ++i) {
+    for (size_t i = 0; i < n && fail == ASDSM_OK; ++i) {
         if (rcs[i] != ASDSM_OK) continue;
-        CK(cudaEventSynchronize(b->inst[i]->evA));
+        if (!ok(cudaEventSynchronize(b->inst[i]->evA))) break;
         rcs[i] = is64(i) ? batch_stage_middle<double>(b->inst[i], runs[i]) : batch_stage_middle<float>(b->inst[i], runs[i]);
     }
+    if (fail != ASDSM_OK)
+        for (size_t i = 0; i < n; ++i)
+            if (rcs[i] == ASDSM_OK) rcs[i] = fail;
     // Round-robin over the instances still sweeping; each poll launches up to
     // two graph replays ahead and retires completed ones without blocking.
     for (;;) {
@@ -1970,10 +2000,10 @@ int asdsm_solve_batch(asdsm_batch* b, const double* const* s, double* const* u, 
             rc = is64(i) ? batch_stage_finish<double>(b->inst[i], runs[i]) : batch_stage_finish<float>(b->inst[i], runs[i]);
         else if (stats && rc != ASDSM_OK) { std::memset(&stats[i], 0, sizeof(asdsm_stats)); stats[i].status = rc; }
         if (rc != ASDSM_OK && worst == ASDSM_OK) worst = rc;
-        CK(cudaEventRecord(b->ev_end[i], b->streams[i]));
-        CK(cudaStreamWaitEvent(b->caller, b->ev_end[i], 0));
+        ok(cudaEventRecord(b->ev_end[i], b->streams[i]));
+        ok(cudaStreamWaitEvent(b->caller, b->ev_end[i], 0));
     }
-    return worst;
+    return fail != ASDSM_OK ? fail : worst;
 }
 
 int asdsm_batch_history(const asdsm_batch* b, int index, double* out, int cap) {

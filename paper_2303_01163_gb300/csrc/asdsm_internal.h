@@ -118,7 +118,7 @@ cudaError_t bcr_level(const BcrSys<T>* groups, int ngroups, int level, bool back
 // Mode of the hole solve of Algorithm 3.
 enum FillMode : int {
     FILL_WITH_SOURCE = 0,   // rhs = s - A_hs z  (inhomogeneous Filler of the initial guess; z carries g on its ring)
-    FILL_HOMOGENEOUS = 1,   // rhs = - A_hs z     (Filler with 0 b of Algorithm 4 step 5)
+    FILL_HOMOGENEOUS = 1,   // rhs = - A_hs z     (Filler with zero source, in the correction of Algorithm 4)
     FILL_RESIDUAL_TO_U = 2, // rhs = r (holes);  u_holes += solution   (hole-residual correction)
     FILL_ARRAY = 3          // rhs = given array (holes), no skeleton term; write solution to out
 };
@@ -200,7 +200,7 @@ struct ResidOut {
     void* rfull;        // float or double full grid (optional)
     double* partials;   // [nblocks][2]: sum r^2, sum r^2 over holes
 };
-// Step 7 of Algorithm 4 as state on the device (sweeps driven from the GPU):
+// The update of Algorithm 4 as state on the device (sweeps driven from the GPU):
 // the residual kernel of the next sweep reads the pending step lengths and
 // which of the two iterate buffers is current.
 struct DynUpdate {
@@ -254,9 +254,9 @@ cudaError_t gcr_dots(const T* q, const T* r, const T* const* p, int k, long long
 template <typename T>
 struct MergeArgs {
     const T* Yfc;  const T* Ycf;  const T* Ycc;  // solutions; Ycc used when re_mode
-    const double* norms2;     // [2]: ||Yfc||^2, ||Ycf||^2 (normalisation of Algorithm 1 step 2)
+    const double* norms2;     // [2]: ||Yfc||^2, ||Ycf||^2 (normalisation of Algorithm 1)
     int re_mode;              // 1: Richardson (u_cc given), 0: random choice
-    int choice;               // 0 or 1 (Algorithm 2 step 3)
+    int choice;               // 0 or 1 (random choice of Algorithm 2)
     const int* choice_dev;    // non-null: the choice is read from the device instead
     const T* Sm;              // spline moment operator, transposed: [Nc knots][mc+1 moments]
     T* E1; T* E2;             // [Nc][Nc] knot errors (fc lines: E1[l][k]; cf columns: E2[l][k])
@@ -312,7 +312,7 @@ struct SweepCtl {
 // the graph's switch node (value m + 2 = nothing: the solve has ended).
 cudaError_t ctl_after_residual(SweepCtl* c, const double* sums, int* overflow, double* hist,
                                cudaGraphConditionalHandle sw, cudaStream_t st);
-// After the least-squares inner products: the step lengths of step 6 / GCR(m).
+// After the least-squares inner products: the step lengths (clamped optimal scaling / GCR(m)).
 cudaError_t ctl_after_dots(SweepCtl* c, const double* dots, cudaStream_t st);
 
 // Learned correction: input channels [r rs, e es, c0..c3] of the full grid,

@@ -5,7 +5,7 @@
 // FP64 arithmetic: the stopping tests of Algorithm 4 (tolerance, sweep limit,
 // stagnation), the hole-residual correction (Proposition 3.1: after an exact
 // Filler the residual vanishes in the holes, so a large hole residual is
-// rounding to be removed by one more Filler), and the step lengths of step 6
+// rounding to be removed by one more Filler), and the step lengths of Algorithm 4
 // (the clamped s_hat, or the GCR(m) least squares over the cycle's
 // directions).  With them a run of sweeps is a fixed sequence of launches that
 // a CUDA graph replays; the branch taken by a sweep (new direction in slot kc,
@@ -25,7 +25,7 @@ __device__ unsigned long long splitmix64_dev(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-// Coin of Algorithm 2 step 3 at sweep k: top bit of SplitMix64 output k.
+// Coin of the random choice of Algorithm 2 at sweep k: top bit of SplitMix64 output k.
 __device__ int choice_bit_dev(unsigned long long seed, int k) {
     const unsigned long long state = seed + (unsigned long long)(k + 1) * 0x9E3779B97F4A7C15ULL;
     return (int)(splitmix64_dev(state) >> 63);
@@ -93,7 +93,7 @@ __global__ void ctl_after_dots_kernel(SweepCtl* c, const double* __restrict__ do
     const double qq = dots[0], qr = dots[1];
     c->comb.run = 0;
     if (m == 1) {
-        // Step 6: s_hat = argmin_{s >= 0} ||r - s A e||.
+        // The paper's clamped optimal scaling: s_hat = argmin_{s >= 0} ||r - s A e||.
         const double shat = qq > 0 ? fmax(0.0, qr / qq) : 0.0;
         c->upd.count = 1;
         c->upd.coef[0] = shat;

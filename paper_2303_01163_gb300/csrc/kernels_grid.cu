@@ -1,7 +1,7 @@
 // Grid-wide kernels of the ASDSM sweep on sm_103a: the fine residual of
-// Algorithm 4 step 3 (with the previous step-7 update fused in), the
+// The fine residual of Algorithm 4 (with the previous sweep's update fused in), the
 // right-hand sides of eq. (2.4), the merge of Algorithm 2, the skeleton
-// operator for the step-6 least squares, reductions and conversions.
+// operator for the least-squares step length, reductions and conversions.
 #include "asdsm_internal.h"
 #include <cuda_runtime.h>
 #include <atomic>
@@ -162,7 +162,7 @@ __device__ __forceinline__ long long f2ll_rn(float d) {
 
 // ---------------------------------------------------------------------------
 // Mixed residual: U (64-bit fixed point, u = U 2^-S) is the accumulator.
-//   U_out = U_in + round(sum_j c_j z_j)              (step 7 of the previous sweep, c_j carry 2^S)
+//   U_out = U_in + round(sum_j c_j z_j)              (the previous sweep's update, c_j carry 2^S)
 //   A u   = kxx (2U_c - U_w - U_e) + kyy (2U_c - U_s - U_n) + kx (U_e - U_w) + ky (U_n - U_s)
 // The integer differences are exact; each splits exactly into 22-bit pieces
 // whose products with FP32 pairs of the coefficients (carrying 2^-S and the
@@ -394,7 +394,7 @@ __global__ void submesh_rhs_kernel(const double* __restrict__ s, const double* _
 // solutions, the chosen/extrapolated u_hat, the errors e and the spline
 // moments of the correction along every coarse line.
 // merge_write: every skeleton point gets its anisotropic value plus the spline
-// correction (step 5) and the merged skeleton is stored (step 6).
+// correction and the merged skeleton is stored.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T cross_t1(const MergeArgs<T>& a, T inv1, int l, int k) {
@@ -407,7 +407,7 @@ __device__ __forceinline__ T cross_t2(const MergeArgs<T>& a, T inv2, int l, int 
     return a.Ycf[(long long)((l + 1) * a.g.n - 1) * a.g.Nc + k] * inv2;
 }
 
-// 1/||u|| of Algorithm 1 step 2 (FP32 reciprocal square root on the mixed path:
+// 1/||u|| of the normalisation of Algorithm 1 (FP32 reciprocal square root on the mixed path:
 // a single scale factor, and FP64 division and square root are slow on this part).
 template <typename T>
 __device__ __forceinline__ void inv_norms(const MergeArgs<T>& a, T* inv1, T* inv2) {
@@ -424,7 +424,7 @@ __device__ __forceinline__ void inv_norms(const MergeArgs<T>& a, T* inv1, T* inv
 
 // Knot errors and spline moments as one small GEMM per family:
 //   M[line][r] = sum_q Sm[r][q] e[line][q]
-// with e (Algorithm 2 steps 2-4) formed on the fly from the cross points.  A CTA
+// with the cross-point errors of Algorithm 2 formed on the fly from the cross points.  A CTA
 // owns MK_L lines x MK_R moments and walks the knots in chunks of MK_Q staged
 // in shared memory (Sm is stored transposed, [knot q][moment r], so the staging
 // reads are coalesced); the next chunk is loaded into registers while the
@@ -437,9 +437,9 @@ __device__ __forceinline__ T knot_error(const MergeArgs<T>& a, int fam, int line
     const int k = fam == 0 ? q : line;       // cf column k: knots along y (l = q)
     const T t1 = cross_t1(a, inv1, l, k), t2 = cross_t2(a, inv2, l, k);
     T uh;
-    if (a.re_mode) uh = t1 + t2 - a.Ycc[(long long)l * a.g.Nc + k];   // step 2: combination RE
-    else uh = choice ? t2 : t1;                                        // step 3
-    return fam == 0 ? uh - t1 : uh - t2;                               // step 4
+    if (a.re_mode) uh = t1 + t2 - a.Ycc[(long long)l * a.g.Nc + k];   // Richardson extrapolation (combination)
+    else uh = choice ? t2 : t1;                                        // random choice
+    return fam == 0 ? uh - t1 : uh - t2;                               // cross-point error
 }
 
 template <typename T>
@@ -545,7 +545,7 @@ __global__ void merge_write_kernel(MergeArgs<T> a) {
     const long long total = 2LL * Nf * Nc;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         if (e < (long long)Nf * Nc) {
-            // fc line l, fine x: u_fc/||u_fc|| + Spline(e1) (step 5.1); cross points too (step 6).
+            // fc line l, fine x: u_fc/||u_fc|| + Spline(e1); cross points too (written from fc).
             const int l = (int)(e / Nf), x = (int)(e % Nf);
             const int i = x + 1, ki = i / n, p = i % n;
             T corr;

@@ -813,7 +813,7 @@ fill_holes_kernel(FillArgs<T> a) {
         const bool hole_ok = c < C && hole < nholes;
         const int bi = hole_ok ? (int)(hole % mc) : 0, bj = hole_ok ? (int)(hole / mc) : 0;
         const int gx = bi * n + c + 1;          // grid x of this lane's column
-        // Right-hand side of step 2: P b + c with c = -P A (skeleton).
+        // Right-hand side of the hole system: P b - P A (skeleton).
         if (homog) {
             T ring[4];
 #pragma unroll
@@ -905,7 +905,7 @@ fill_holes_kernel(FillArgs<T> a) {
             }
             __syncwarp();
         }
-        // Step 3: write the hole values.
+        // Write the hole values.
         if (hole_ok) {
 #pragma unroll
             for (int y = 1; y <= R; ++y) {

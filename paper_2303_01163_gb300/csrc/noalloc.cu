@@ -2,9 +2,9 @@
 // device allocation, for callers that cannot call cudaMalloc.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// residual: code being recorded into a CUDA graph by stream capture (cudaMalloc
-// is not a capturable operation), services whose device memory is reserved up
-// front by their own pool, and tight loops where an allocation would stall or
+// residual: services whose device memory is reserved up front by their own
+// pool allocator (a cudaMalloc beside the pool can fail, or fragment what the
+// pool expects to own), and tight loops where an allocation would stall or
 // synchronise the device.  This entry point needs no handle (creating one
 // allocates) and uses, for its only scratch - the per-block partial sums of
 // the norms and their totals - arrays that live in this file as statically

@@ -78,3 +78,28 @@ def test_product_package_does_not_import_the_oracle():
     for path in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
         src = open(path).read()
         assert "oracle" not in re.findall(r"^\s*(?:from|import)\s+(\w+)", src, flags=re.M), path
+
+
+def _tune_check(lib, entries):
+    arr = (ctypes.c_int32 * len(entries))(*entries)
+    return lib.asdsm_tune_check(arr, len(entries))
+
+
+def test_saved_tuning_passes_the_check_and_bad_entries_fail(lib):
+    import json
+    saved = json.load(open(os.path.join(ROOT, "profiles", "tune_state_4097_mixed.json")))
+    assert len(saved) == 130
+    assert _tune_check(lib, saved) == 0
+    assert _tune_check(lib, [0] * 130) == 0
+    assert _tune_check(lib, saved[:129]) == -1                      # wrong count
+    for index, value in [(0, (48 << 8) | 1),       # rows per CTA not in {16, 64}
+                         (1, (16 << 8) | 3),       # split factor not a power of two up to 8
+                         (2, (128 << 8) | 1),      # tcgen05 kernel in the FP64 half
+                         (3, (32 << 8) | 1),       # mma.sync kernel in the FP64 half
+                         (65, (128 << 8) | 2),     # tcgen05 kernel split
+                         (64, 16),                 # tensor-core Filler in the FP64 half
+                         (129, 9),                 # Filler warps above 8
+                         (70, -1)]:
+        bad = list(saved)
+        bad[index] = value
+        assert _tune_check(lib, bad) == -1, (index, value)

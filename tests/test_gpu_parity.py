@@ -292,8 +292,17 @@ def test_tensor_core_level_kernels_match_oracle(lib, name, make, mc, tm):
             assert _relerr(out.cpu().numpy(), ref) <= 2e-5, (mesh, _relerr(out.cpu().numpy(), ref))
         u = _dev(p.g)
         res = sv.solve(_dev(p.s), u)
-    if res.status == lib.OK:
-        r, bb = orc.residual_grid(p.N, p.alpha, p.beta, p.s, u.cpu().numpy())
-        assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1e-10 * 1.01
-    else:
-        assert res.status in (lib.NOT_CONVERGED, lib.STAGNATED)
+    assert res.status == lib.OK, (name, tm, res.status, res.stats)
+    r, bb = orc.residual_grid(p.N, p.alpha, p.beta, p.s, u.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1e-10 * 1.01
+
+
+def test_tune_set_rejects_a_bad_entry_and_keeps_the_handle(lib):
+    p = wl.random_fourier_2d(129, 2)
+    with lib.Solver(129, 8, p.alpha, p.beta, precision=lib.MIXED, tol=1e-10, max_sweeps=400) as sv:
+        before = sv.tune_state()
+        bad = list(before)
+        bad[3] = (48 << 8) | 1
+        with pytest.raises(lib.AsdsmError):
+            sv.set_tune_state(bad)
+        assert sv.tune_state() == before

@@ -1,6 +1,7 @@
 """GPU test of asdsm_residual_noalloc, the residual entry point that allocates
-no device memory (for callers that cannot call cudaMalloc, e.g. during CUDA
-graph capture).  It is called through the C ABI and compared with the
+no device memory (for callers that cannot call cudaMalloc: services whose
+device memory belongs to their own pool allocator, loops that must not stall
+on an allocation).  It is called through the C ABI and compared with the
 existing asdsm_residual on two calls in a row, within the tolerance of the
 residual parity test.  This file is collected last on purpose."""
 import ctypes
