@@ -49,7 +49,10 @@ extern "C" {
 #define ASDSM_ERR_NAN           -4   /* a NaN/Inf appeared in the residual (bad input data) */
 #define ASDSM_NOT_CONVERGED     -5   /* max_sweeps reached above tol; u holds the last iterate */
 #define ASDSM_STAGNATED         -6   /* residual stopped decreasing (Remark after Alg. 4); u holds the last iterate */
-#define ASDSM_ERR_RANGE         -7   /* mixed path: the fixed-point accumulator would overflow */
+#define ASDSM_ERR_RANGE         -7   /* mixed path: the fixed-point accumulator would still overflow after
+                                        12 restarts with ever smaller shifts (each restart resumes from the
+                                        last iterate that fitted, with at least 16x more range); u holds
+                                        that iterate.  asdsm_solve_batch does not restart. */
 
 /* ---- precision modes ---------------------------------------------------- */
 #define ASDSM_FP64   0   /* every step in FP64 (the plain method) */
@@ -96,6 +99,13 @@ typedef struct {
     double  setup_ms;      /* right-hand sides + initial guess, GPU time */
     double  solve_ms;      /* whole call, GPU time */
     int64_t launches;      /* kernels this call launched */
+    double  rel_res_fp64;  /* ||b - A u||_2 / ||b||_2 of the returned u, recomputed in FP64 arithmetic
+                              from the caller's s and u at the end of every solve */
+    double  hole_res_max;  /* max |b - A u| over the hole points of the returned u (FP64; zero in exact
+                              arithmetic by Prop. 3.1) */
+    int32_t rescales;      /* mixed path: restarts with a smaller fixed-point shift after the
+                              accumulator would have overflowed (see ASDSM_ERR_RANGE) */
+    int32_t pad_;
 } asdsm_stats;
 
 /* Per-kernel-family timing of the last asdsm_solve calls (enabled with

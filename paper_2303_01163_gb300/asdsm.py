@@ -49,7 +49,9 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("status", ctypes.c_int32), ("hole_fixes", ctypes.c_int32),
                 ("fixed_shift", ctypes.c_int32), ("rel_res", ctypes.c_double), ("rel_res0", ctypes.c_double),
-                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("launches", ctypes.c_int64)]
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("rel_res_fp64", ctypes.c_double), ("hole_res_max", ctypes.c_double),
+                ("rescales", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -749,6 +749,8 @@ struct SolveRun {
     std::vector<double> rhist;
     int q = 0, max_q = 0, in_flight = 0;
     bool done = false;
+    bool resume = false;             // start from u as given (a rescaled restart), whatever the options say
+    int S_cap = 1 << 20;             // mixed path: largest fixed-point shift allowed
 };
 
 // Device controller set up and the graph made ready; no launch yet.
@@ -1263,7 +1265,8 @@ int run_begin(asdsm_handle* h, SolveRun& r) {
     // residual is rough, and ASDSM corrections reduce rough residuals slowly
     // (the irregular-residual stagnation of Section 4, Example 2).
     r.u0d = u;                       // FP64 grid holding u^(0) (ring = g)
-    if (!op.skip_initial_guess) {
+    const bool guess = !op.skip_initial_guess && !r.resume;
+    if (guess) {
         if (!mixed) {
             if (int rc = initial_guess_to_z<double>(h, s, u)) return rc;
             CK(copy_interior<double, double>((const double*)w.z[0], u, g, st));
@@ -1302,13 +1305,13 @@ int run_middle(asdsm_handle* h, SolveRun& r) {
         if (mx <= 0.0) mx = 1.0;
         int e2 = 0;
         std::frexp(mx, &e2);                // mx < 2^e2
-        r.S = 58 - e2;                      // |U| < 2^58: 2^5 headroom below the 2^63 range and the 2^60 check
+        r.S = std::min(58 - e2, r.S_cap);   // |U| < 2^58: 2^5 headroom below the 2^63 range and the 2^60 check
         r.scale = std::ldexp(1.0, r.S);
         CK(to_fixed(nullptr, r.u0d, h->U[0], r.scale, g, st));
         CK(to_fixed(nullptr, r.u0d, h->U[1], r.scale, g, st));   // ring of the partner
     }
     // Direction slots need a zero ring again (slot 0 carried g).
-    if (!op.skip_initial_guess) CK(ring_from<double>(nullptr, (double*)h->w[0].z[0], g, 0, st));
+    if (!op.skip_initial_guess && !r.resume) CK(ring_from<double>(nullptr, (double*)h->w[0].z[0], g, 0, st));
     CK(ring_from<T>(nullptr, (T*)w.z[0], g, 0, st));
     CK(cudaEventRecord(h->ev1, st));
     r.mk = mixed ? mixed_coefs(h, r.S) : MixedCoefs{};
@@ -1330,9 +1333,16 @@ int run_finish(asdsm_handle* h, SolveRun& r) {
     // Final iterate to the caller's buffer.
     if (!mixed) {
         if (r.ucur != r.u) CK(copy_interior<double, double>(r.ucur, r.u, g, st));
-    } else if (r.status != ASDSM_ERR_RANGE) {
-        CK(from_fixed(h->U[r.Ucur], std::ldexp(1.0, -r.S), r.u, g, st));
+    } else {
+        // After an overflow the current buffer holds the update that did not
+        // fit; the other one holds the last iterate that did.
+        const int buf = r.status == ASDSM_ERR_RANGE ? 1 - r.Ucur : r.Ucur;
+        CK(from_fixed(h->U[buf], std::ldexp(1.0, -r.S), r.u, g, st));
     }
+    // The returned iterate judged in FP64 (residual norm, largest hole residual).
+    CK(final_check(r.s, r.u, g, h->sten, h->partials, std::min(8 * h->num_sms, h->partials_cap / 2),
+                   h->dsmall + 220, st));
+    CK(cudaMemcpyAsync(h->hsmall + 220, h->dsmall + 220, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     int* tcerr = reinterpret_cast<int*>(h->hsmall + 4095);
     *tcerr = 0;
     CK(cudaMemcpyAsync(tcerr, h->dtcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1357,6 +1367,8 @@ int run_finish(asdsm_handle* h, SolveRun& r) {
     stt.rel_res0 = r.rel0;
     stt.setup_ms = ms_setup;
     stt.solve_ms = ms_all;
+    stt.rel_res_fp64 = r.bnorm > 0 ? std::sqrt(h->hsmall[220]) / r.bnorm : std::sqrt(h->hsmall[220]);
+    stt.hole_res_max = h->hsmall[221];
     if (r.stats) *r.stats = stt;
     return r.status;
 }
@@ -1371,15 +1383,54 @@ int staged(SolveRun& r, F&& fn) {
 }
 
 template <typename T>
-int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) {
-    SolveRun r;
-    r.s = s; r.u = u; r.stats = stats;
+int solve_pass(asdsm_handle* h, SolveRun& r) {
     if (int rc = staged(r, [&] { return run_begin<T>(h, r); })) return rc;
     CK(cudaEventSynchronize(h->evA));
     if (int rc = staged(r, [&] { return run_middle<T>(h, r); })) return rc;
     while (r.stage == 2)
         if (int rc = staged(r, [&] { return graph_poll<T>(h, r, true); })) return rc;
     return staged(r, [&] { return run_finish<T>(h, r); });
+}
+
+// A solve, and on the mixed path its restarts after a fixed-point overflow:
+// the shift S was chosen from max |u^(0)|, which says little when the
+// iterate grows far beyond its start (a resume from a small or zero
+// interior).  Each restart resumes from the last iterate that fitted (u,
+// now in FP64) with S lowered by at least 4, and at most kMaxRescales times.
+constexpr int kMaxRescales = 12;
+
+template <typename T>
+int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) {
+    asdsm_stats total{};
+    std::vector<double> hist;
+    int S_cap = 1 << 20;
+    for (int pass = 0;; ++pass) {
+        SolveRun r;
+        asdsm_stats st{};
+        r.s = s; r.u = u; r.stats = &st;
+        r.resume = pass > 0;
+        r.S_cap = S_cap;
+        const int rc = solve_pass<T>(h, r);
+        if (r.stage != 3 || (rc != r.status && rc != ASDSM_OK)) return rc;     // an error before any result
+        if (pass == 0) {
+            total = st;
+            hist = h->hist;
+        } else {
+            total.sweeps += st.sweeps; total.hole_fixes += st.hole_fixes; total.launches += st.launches;
+            total.solve_ms += st.solve_ms;
+            total.status = st.status; total.fixed_shift = st.fixed_shift; total.rel_res = st.rel_res;
+            total.rel_res_fp64 = st.rel_res_fp64; total.hole_res_max = st.hole_res_max;
+            hist.insert(hist.end(), h->hist.begin() + (h->hist.empty() ? 0 : 1), h->hist.end());
+        }
+        total.rescales = pass;
+        if (sizeof(T) == 4 && rc == ASDSM_ERR_RANGE && pass < kMaxRescales) {
+            S_cap = r.S - 4;
+            continue;
+        }
+        h->hist = hist;
+        if (stats) *stats = total;
+        return rc;
+    }
 }
 
 }  // namespace

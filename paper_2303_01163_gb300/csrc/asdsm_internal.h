@@ -236,6 +236,12 @@ cudaError_t residual_mixed(const float* s_hi, const float* s_lo, const long long
                            ResidOut out, int* nblocks, int* overflow_flag, cudaStream_t st);
 int residual_grid_blocks(const Geometry& g);
 
+// FP64 check of a returned iterate (s, u: FP64 grids, u's ring = g):
+// out[0] = ||s - A u||^2 over the interior, out[1] = max |s - A u| over the
+// hole points.  partials: at least 2 * max_blocks doubles.
+cudaError_t final_check(const double* s, const double* u, const Geometry& g, const Stencil& c, double* partials,
+                        int max_blocks, double* out, cudaStream_t st);
+
 // Reductions ----------------------------------------------------------------
 // out[j] = sum over blocks of partials[b][j]  (fixed order, 1 CTA), j < ncols
 cudaError_t reduce_partials(const double* partials, int nblocks, int ncols, double* out, cudaStream_t st);

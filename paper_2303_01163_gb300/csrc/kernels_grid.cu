@@ -869,6 +869,67 @@ cudaError_t build_submesh_rhs(const double* s, const double* u, const Geometry& 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// FP64 check of a returned iterate: per block the sum of r^2 over the
+// interior and the largest |r| over the hole points, r = s - A u in FP64
+// (A's 5-point stencil of Section 2.3, u's ring carrying g); then one CTA
+// folds the blocks in a fixed order into out[0] = ||r||^2, out[1] = max |r|.
+// ---------------------------------------------------------------------------
+constexpr int FC_THREADS = 256;
+
+__global__ void __launch_bounds__(FC_THREADS)
+final_check_kernel(const double* __restrict__ s, const double* __restrict__ u, Geometry g, Stencil c,
+                   double* partials) {
+    const int N = g.N;
+    double sr = 0.0, mh = 0.0;
+    for (int j = 1 + blockIdx.x; j <= N - 2; j += gridDim.x) {
+        const long long row = (long long)j * N;
+        for (int i = 1 + threadIdx.x; i <= N - 2; i += FC_THREADS) {
+            const long long idx = row + i;
+            const double Au = c.cc * u[idx] + c.cw * u[idx - 1] + c.ce * u[idx + 1]
+                            + c.cs * u[idx - N] + c.cn * u[idx + N];
+            const double r = s[idx] - Au;
+            sr += r * r;
+            if (skel_kind(i, j, g.n) == 0) mh = fmax(mh, fabs(r));
+        }
+    }
+    __shared__ double ws[FC_THREADS / 32][2];
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_down_sync(0xFFFFFFFFu, sr, o);
+        mh = fmax(mh, __shfl_down_sync(0xFFFFFFFFu, mh, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { ws[wid][0] = sr; ws[wid][1] = mh; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, m = 0.0;
+        for (int w = 0; w < FC_THREADS / 32; ++w) { a += ws[w][0]; m = fmax(m, ws[w][1]); }
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = m;
+    }
+}
+
+__global__ void __launch_bounds__(32)
+fold_sum_max_kernel(const double* __restrict__ partials, int nblocks, double* out) {
+    double a = 0.0, m = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32) { a += partials[2 * b]; m = fmax(m, partials[2 * b + 1]); }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+        m = fmax(m, __shfl_down_sync(0xFFFFFFFFu, m, o));
+    }
+    if (threadIdx.x == 0) { out[0] = a; out[1] = m; }
+}
+
+cudaError_t final_check(const double* s, const double* u, const Geometry& g, const Stencil& c, double* partials,
+                        int max_blocks, double* out, cudaStream_t st) {
+    int nb = g.Nf < max_blocks ? g.Nf : max_blocks;
+    if (nb < 1) nb = 1;
+    final_check_kernel<<<nb, FC_THREADS, 0, st>>>(s, u, g, c, partials);
+    fold_sum_max_kernel<<<1, 32, 0, st>>>(partials, nb, out);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
 cudaError_t reduce_partials(const double* partials, int nblocks, int ncols, double* out, cudaStream_t st) {
     if (ncols < 1) return cudaSuccess;
     reduce_partials_kernel<<<ncols, 256, 0, st>>>(partials, nblocks, ncols, out);

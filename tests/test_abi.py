@@ -44,7 +44,7 @@ def test_structs_match_the_header_layout(lib):
     from paper_2303_01163_gb300 import asdsm
     assert ctypes.sizeof(asdsm.Desc) == 4 * 4 + 6 * 8
     assert ctypes.sizeof(asdsm.Opts) == 8 + 4 * 4 + 8 + 8 + 8 + 4 + 4 + 8
-    assert ctypes.sizeof(asdsm.Stats) == 4 * 4 + 4 * 8 + 8
+    assert ctypes.sizeof(asdsm.Stats) == 4 * 4 + 4 * 8 + 8 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(asdsm.KProf) == 24 + 2 * 8 + 3 * 8
 
 

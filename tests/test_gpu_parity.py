@@ -261,6 +261,28 @@ def test_resume_from_a_given_iterate(lib):
             assert r2.stats["rel_res0"] <= r1.stats["rel_res"] * 1.5
 
 
+def test_resume_from_a_zero_interior_rescales_the_accumulator(lib):
+    """A resume from a zero interior gives the fixed-point shift no hint of the
+    solution's size (max |u*| is about 68 here, while the first shift leaves
+    room for |u| < 4): the solve restarts with smaller shifts from the last
+    iterate that fitted and still reaches 1e-10, judged by the oracle."""
+    p = wl.random_fourier_2d(257, 4)
+    s = p.s * 1e4
+    with lib.Solver(257, 16, p.alpha, p.beta, precision=lib.MIXED, tol=1e-10, max_sweeps=600,
+                    skip_initial_guess=1) as sv:
+        u = _dev(p.g)
+        res = sv.solve(_dev(s), u)
+        assert res.status == lib.OK, res.stats
+        assert res.stats["rescales"] >= 1
+        hist = sv.history()
+        assert len(hist) <= res.stats["sweeps"] + 1 and hist[-1] <= 1e-10
+    ug = u.cpu().numpy()
+    r, b = orc.residual_grid(257, p.alpha, p.beta, s, ug)
+    rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rel <= 1.01e-10
+    assert abs(res.stats["rel_res_fp64"] - rel) <= 1e-3 * rel
+
+
 @pytest.mark.parametrize("tm", [32, 128])
 @pytest.mark.parametrize("name,make,mc", CASES[:3] + [("fourier257", lambda: wl.random_fourier_2d(257, 5), 8),
                                                       ("fourier513_c255", lambda: wl.random_fourier_2d(513, 6), 256)])
