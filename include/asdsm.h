@@ -255,6 +255,27 @@ int asdsm_profile(asdsm_handle* h, int enable);
  * returns the number of families or a negative error. */
 int asdsm_profile_read(asdsm_handle* h, asdsm_kprof* out, int cap);
 
+/* Real Schur form of an upper Hessenberg n x n matrix A (host FP64, no
+ * device work, no handle): A = Q T Q^T with Q orthogonal and T quasi upper
+ * triangular, 2 x 2 diagonal blocks only for complex conjugate eigenvalue
+ * pairs.  The 3D extension (Section 3.5) uses it on the coarse-axis operator
+ * of each plane family: in the basis of Q a plane system becomes a block
+ * back-substitution of shifted 2D fine-plane systems.  A, Q, T: host n*n
+ * row-major arrays (1 <= n <= 512).  Returns ASDSM_OK, or ASDSM_ERR_INVALID
+ * for bad arguments or if the QR iteration does not converge. */
+int asdsm_real_schur(int n, const double* A, double* Q, double* T);
+
+/* Failure-path self-test of the tensor-core kernels (no counterpart in the
+ * paper): on the handle's stream, one CTA takes tensor memory as the
+ * tcgen05 kernels do and waits on an mbarrier that nothing arrives at, with
+ * no copy or MMA in flight.  Its wait gives up after limit_ns (0 < limit_ns
+ * <= 2e9), it frees its tensor memory and sets the handle's timeout flag, so
+ * the call returns ASDSM_ERR_CUDA ("a wait timed out") - the status a solve
+ * returns when a tensor-core kernel stalls.  The flag is sticky: later solves
+ * on this handle return ASDSM_ERR_CUDA as well; destroy the handle.  The GPU
+ * context stays usable. */
+int asdsm_selftest_wait_timeout(asdsm_handle* h, long long limit_ns);
+
 /* Kernels launched by this library in this process so far. */
 int64_t asdsm_launch_count(void);
 

@@ -90,6 +90,11 @@ def load() -> ctypes.CDLL:
     lib.asdsm_tune_get.restype = ctypes.c_int
     lib.asdsm_tune_set.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
     lib.asdsm_tune_set.restype = ctypes.c_int
+    lib.asdsm_real_schur.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
+    lib.asdsm_real_schur.restype = ctypes.c_int
+    lib.asdsm_selftest_wait_timeout.argtypes = [P, ctypes.c_longlong]
+    lib.asdsm_selftest_wait_timeout.restype = ctypes.c_int
     lib.asdsm_tune_check.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
     lib.asdsm_tune_check.restype = ctypes.c_int
     lib.asdsm_solve.argtypes = [P, P, P, ctypes.POINTER(Stats)]

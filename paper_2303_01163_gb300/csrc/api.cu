@@ -1853,6 +1853,21 @@ int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out
     return tc_status(h, st);
 }
 
+int asdsm_real_schur(int n, const double* A, double* Q, double* T) {
+    if (n < 1 || n > 512 || !A || !Q || !T) return ASDSM_ERR_INVALID;
+    std::vector<double> a(A, A + (size_t)n * n), q, t;
+    if (!real_schur(n, a, &q, &t)) return ASDSM_ERR_INVALID;
+    std::memcpy(Q, q.data(), q.size() * sizeof(double));
+    std::memcpy(T, t.data(), t.size() * sizeof(double));
+    return ASDSM_OK;
+}
+
+int asdsm_selftest_wait_timeout(asdsm_handle* h, long long limit_ns) {
+    if (!h || limit_ns <= 0 || limit_ns > 2000000000LL) return ASDSM_ERR_INVALID;
+    CK(wait_selftest(h->dtcerr, limit_ns, h->st));
+    return tc_status(h, h->st);
+}
+
 int asdsm_hole_extension_operator(int N, int mc, const double* alpha, const double* beta, double* G) {
     if (N < 3 || mc < 2 || !alpha || !beta || !G || (N - 1) % mc != 0) return ASDSM_ERR_INVALID;
     const int n = (N - 1) / mc;

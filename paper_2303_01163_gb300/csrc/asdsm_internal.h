@@ -31,6 +31,19 @@ struct BcrFactors {
 };
 bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, double tu, BcrFactors* out);
 
+// The same with a dense C x C diagonal block:  a x_{i-1} + K x_i + c x_{i+1} = f_i
+// (K row-major; the 3D extension's submesh systems have Kronecker-sum blocks).
+bool make_bcr_dense(int R, double a, double c, int C, const std::vector<double>& K, BcrFactors* out);
+
+// Real Schur form A = Q T Q^T of an upper Hessenberg n x n matrix (row-major):
+// Q orthogonal, T quasi upper triangular with 2 x 2 blocks only for complex
+// conjugate eigenvalue pairs.  False if the QR iteration does not converge.
+bool real_schur(int n, const std::vector<double>& A, std::vector<double>* Q, std::vector<double>* T);
+
+// Values at the fine interior points p h (p = 1..mc n - 1) of the not-a-knot
+// spline with zero end values and value 1 at interior knot m: (mc n - 1) x (mc - 1).
+std::vector<double> spline_value_operator(int mc, int n);
+
 // Moments of the not-a-knot cubic spline on the uniform knots 0, H, .., 1
 // (mc intervals) through values (0, y_1, .., y_{mc-1}, 0): M = Sm y with
 // Sm of shape (mc+1) x (mc-1), row-major.
@@ -182,6 +195,9 @@ struct FillTcArgs {
     int N, mc;           // N = 16 mc + 1
     int* err;            // set to 1 when a wait timed out (the fill is then incomplete)
 };
+// One CTA that holds tensor memory and waits, bounded by limit_ns, on an
+// mbarrier nothing arrives at; sets *err = 1 when the wait gives up.
+cudaError_t wait_selftest(int* err, long long limit_ns, cudaStream_t st);
 size_t fill_tc_image_bytes();
 void fill_tc_image(const std::vector<double>& G, std::vector<float>* img);
 cudaError_t fill_tc(const FillTcArgs& a, int num_sms, cudaStream_t st);

@@ -279,7 +279,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fill_tc_kernel(FillTcArgs a) {
     }
 }
 
+// Self-test of the failure path of the tensor-core kernels: one CTA takes
+// tensor memory as they do, then thread 0 waits on an mbarrier that no thread
+// arrives at, with no bulk copy and no MMA in flight.  The bounded wait gives
+// up after limit_ns; the kernel then sets *err and frees its tensor memory,
+// which is what a tensor-core kernel does when one of its hand-overs stalls.
+__global__ void __launch_bounds__(64) wait_selftest_kernel(int* err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_holder;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_holder), 32);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = tmem_holder;
+    if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0, limit_ns)) atomicExch(err, 1);
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        tmem_dealloc(tbase, 32);
+    }
+}
+
 }  // namespace
+
+cudaError_t wait_selftest(int* err, long long limit_ns, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 64, 0, st>>>(err, (unsigned long long)limit_ns);
+    note_launch();
+    return cudaGetLastError();
+}
 
 size_t fill_tc_image_bytes() { return (size_t)TC_A_BYTES; }
 

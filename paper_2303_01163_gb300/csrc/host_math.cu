@@ -297,3 +297,217 @@ std::vector<double> spline_moment_operator(int mc) {
 }
 
 }  // namespace asdsm
+
+// ---------------------------------------------------------------------------
+// Additions for the 3D extension (Section 3.5)
+// ---------------------------------------------------------------------------
+namespace asdsm {
+
+// Block cyclic reduction factors of  a x_{i-1} + K x_i + c x_{i+1} = f_i  with
+// a dense C x C diagonal block K.  Because A_0 = a I and C_0 = c I commute with
+// K, every level's blocks are A_l = alpha_l F_l, C_l = gamma_l F_l with one
+// matrix F_l commuting with B_l, and
+//     B_{l+1} = B_l - 2 alpha_l gamma_l F_l B_l^{-1} F_l,
+//     F_{l+1} = F_l B_l^{-1} F_l,  alpha_{l+1} = -alpha_l^2,  gamma_{l+1} = -gamma_l^2,
+// so a level costs one inverse and two products.  F absorbs the scale and the
+// sign so that the dominant weight is +1 (the layout of BcrFactors).
+bool make_bcr_dense(int R, double a, double c, int C, const std::vector<double>& K, BcrFactors* out) {
+    int L = 0;
+    while (((1 << L) - 1) < R) ++L;
+    if (((1 << L) - 1) != R || C < 1 || L > 16 || K.size() != (size_t)C * C) return false;
+    const size_t n2 = (size_t)C * C;
+    out->R = R; out->C = C; out->L = L;
+    out->Mt.assign((size_t)L * n2, 0.0);
+    out->Bt.assign((size_t)L * n2, 0.0);
+    out->wl.assign(L, 0.0);
+    out->wr.assign(L, 0.0);
+    std::vector<double> B = K, F(n2, 0.0), Binv, FB(n2), G(n2);
+    for (int k = 0; k < C; ++k) F[(size_t)k * C + k] = 1.0;
+    double al = a, ga = c;
+    for (int l = 0; l < L; ++l) {
+        // Normalise: the dominant weight becomes +1, F carries the factor.
+        const double mu = std::fabs(al) >= std::fabs(ga) ? al : ga;
+        if (mu == 0.0) {
+            al = ga = 0.0;
+        } else {
+            for (double& v : F) v *= mu;
+            al /= mu;
+            ga /= mu;
+        }
+        Binv = B;
+        if (!invert(Binv, C)) return false;
+        matmul(F.data(), Binv.data(), FB.data(), C);                 // M_l = F_l B_l^{-1}
+        transpose_into(FB.data(), out->Mt.data() + (size_t)l * n2, C);
+        transpose_into(Binv.data(), out->Bt.data() + (size_t)l * n2, C);
+        out->wl[l] = al;
+        out->wr[l] = ga;
+        if (l + 1 == L) break;
+        matmul(FB.data(), F.data(), G.data(), C);                     // F B^{-1} F
+        for (size_t e = 0; e < n2; ++e) B[e] -= 2.0 * al * ga * G[e];
+        F.swap(G);
+        al = -al * al;
+        ga = -ga * ga;
+    }
+    for (double v : out->Mt) if (!std::isfinite(v)) return false;
+    for (double v : out->Bt) if (!std::isfinite(v)) return false;
+    return true;
+}
+
+namespace {
+
+// y = P x for the 3 (or 2) rows r0.. of an n x n row-major matrix, P = I - 2 v v^T / (v^T v),
+// applied to columns [c0, c1).
+void house_left(std::vector<double>& H, int n, int r0, int m, const double* v, int c0, int c1) {
+    double vv = 0.0;
+    for (int t = 0; t < m; ++t) vv += v[t] * v[t];
+    if (vv == 0.0) return;
+    for (int j = c0; j < c1; ++j) {
+        double d = 0.0;
+        for (int t = 0; t < m; ++t) d += v[t] * H[(size_t)(r0 + t) * n + j];
+        d *= 2.0 / vv;
+        for (int t = 0; t < m; ++t) H[(size_t)(r0 + t) * n + j] -= d * v[t];
+    }
+}
+
+// The same transformation from the right on columns r0.. of rows [q0, q1).
+void house_right(std::vector<double>& H, int n, int r0, int m, const double* v, int q0, int q1) {
+    double vv = 0.0;
+    for (int t = 0; t < m; ++t) vv += v[t] * v[t];
+    if (vv == 0.0) return;
+    for (int i = q0; i < q1; ++i) {
+        double d = 0.0;
+        for (int t = 0; t < m; ++t) d += H[(size_t)i * n + r0 + t] * v[t];
+        d *= 2.0 / vv;
+        for (int t = 0; t < m; ++t) H[(size_t)i * n + r0 + t] -= d * v[t];
+    }
+}
+
+// Householder vector v with (I - 2 v v^T / v^T v) x = (-sign(x0) |x|, 0, ..).
+void house_vec(const double* x, int m, double* v) {
+    double nx = 0.0;
+    for (int t = 0; t < m; ++t) nx += x[t] * x[t];
+    nx = std::sqrt(nx);
+    for (int t = 0; t < m; ++t) v[t] = x[t];
+    if (nx == 0.0) return;
+    v[0] += x[0] >= 0.0 ? nx : -nx;
+}
+
+}  // namespace
+
+// Real Schur form of an upper Hessenberg n x n matrix (row-major):
+// A = Q T Q^T with Q orthogonal and T quasi upper triangular, whose 2 x 2
+// diagonal blocks carry complex conjugate eigenvalue pairs and whose 1 x 1
+// blocks the real eigenvalues.  Francis double-shift QR iteration with
+// deflation (Golub and Van Loan, Sections 7.5.5-7.5.6), every transformation
+// accumulated into Q and applied to the whole matrix; 2 x 2 blocks with real
+// eigenvalues are split by one more rotation.  Returns false when the
+// iteration does not converge.
+bool real_schur(int n, const std::vector<double>& A, std::vector<double>* Qo, std::vector<double>* To) {
+    if (n < 1 || A.size() != (size_t)n * n) return false;
+    std::vector<double> H = A, Q((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+    for (int i = 2; i < n; ++i)
+        for (int j = 0; j < i - 1; ++j) H[(size_t)i * n + j] = 0.0;     // exact Hessenberg form
+    auto at = [&](int i, int j) -> double& { return H[(size_t)i * n + j]; };
+    const double eps = 2.220446049250313e-16;
+    int m = n - 1, iter = 0, total = 0;
+    while (m >= 1) {
+        int l = m;
+        for (; l >= 1; --l) {
+            const double s = std::fabs(at(l - 1, l - 1)) + std::fabs(at(l, l));
+            if (std::fabs(at(l, l - 1)) <= eps * (s > 0.0 ? s : 1.0)) { at(l, l - 1) = 0.0; break; }
+        }
+        if (l < 1) l = 0;
+        if (l == m) { m -= 1; iter = 0; continue; }
+        if (l == m - 1) { m -= 2; iter = 0; continue; }
+        if (++total > 60 * n) return false;
+        ++iter;
+        // Shifts: the eigenvalues of the trailing 2 x 2 block (exceptional ones now and then).
+        double s = at(m - 1, m - 1) + at(m, m);
+        double t = at(m - 1, m - 1) * at(m, m) - at(m - 1, m) * at(m, m - 1);
+        if (iter % 11 == 10) {
+            const double w = std::fabs(at(m, m - 1)) + std::fabs(at(m - 1, m - 2));
+            s = 1.5 * w + at(m, m);
+            t = w * w;
+        }
+        double x = at(l, l) * at(l, l) + at(l, l + 1) * at(l + 1, l) - s * at(l, l) + t;
+        double y = at(l + 1, l) * (at(l, l) + at(l + 1, l + 1) - s);
+        double z = at(l + 1, l) * at(l + 2, l + 1);
+        for (int k = l - 1; k <= m - 3; ++k) {
+            const double xv[3] = {x, y, z};
+            double v[3];
+            house_vec(xv, 3, v);
+            const int c0 = std::max(l, k);
+            house_left(H, n, k + 1, 3, v, c0, n);
+            house_right(H, n, k + 1, 3, v, 0, std::min(k + 4, m) + 1);
+            house_right(Q, n, k + 1, 3, v, 0, n);
+            if (k + 1 > l) { at(k + 2, k) = 0.0; at(k + 3, k) = 0.0; }
+            x = at(k + 2, k + 1);
+            y = at(k + 3, k + 1);
+            if (k < m - 3) z = at(k + 4, k + 1);
+        }
+        const double xv[2] = {x, y};
+        double v[2];
+        house_vec(xv, 2, v);
+        house_left(H, n, m - 1, 2, v, m - 2, n);
+        house_right(H, n, m - 1, 2, v, 0, m + 1);
+        house_right(Q, n, m - 1, 2, v, 0, n);
+        at(m, m - 2) = 0.0;
+    }
+    // Split the 2 x 2 blocks whose eigenvalues are real.
+    for (int i = 0; i + 1 < n; ++i) {
+        if (at(i + 1, i) == 0.0) continue;
+        const double a = at(i, i), b = at(i, i + 1), c = at(i + 1, i), d = at(i + 1, i + 1);
+        const double p = 0.5 * (a - d), disc = p * p + b * c;
+        if (disc < 0.0) { ++i; continue; }                            // a complex pair: keep the block
+        // An eigenvector (b, lambda - a) of the block for lambda = d + p +/- sqrt(disc).
+        const double lam = d + p + (p >= 0.0 ? std::sqrt(disc) : -std::sqrt(disc));
+        double e0 = b, e1 = lam - a;
+        if (std::fabs(e0) + std::fabs(e1) == 0.0) { e0 = lam - d; e1 = c; }
+        const double r = std::hypot(e0, e1);
+        const double cs = e0 / r, sn = e1 / r;
+        // Rotation G = [[cs, -sn], [sn, cs]] on rows/columns i, i+1: T <- G^T T G, Q <- Q G.
+        for (int j = 0; j < n; ++j) {
+            const double h0 = at(i, j), h1 = at(i + 1, j);
+            at(i, j) = cs * h0 + sn * h1;
+            at(i + 1, j) = -sn * h0 + cs * h1;
+        }
+        for (int j = 0; j < n; ++j) {
+            const double h0 = at(j, i), h1 = at(j, i + 1);
+            at(j, i) = cs * h0 + sn * h1;
+            at(j, i + 1) = -sn * h0 + cs * h1;
+            const double q0 = Q[(size_t)j * n + i], q1 = Q[(size_t)j * n + i + 1];
+            Q[(size_t)j * n + i] = cs * q0 + sn * q1;
+            Q[(size_t)j * n + i + 1] = -sn * q0 + cs * q1;
+        }
+        at(i + 1, i) = 0.0;
+        ++i;
+    }
+    *Qo = Q;
+    *To = H;
+    return true;
+}
+
+// Values at the fine interior points x = p h (p = 1..M-1) of the not-a-knot
+// cubic spline through the knots 0, H, .., 1 with zero end values and value 1
+// at interior knot m (R10): W is (M-1) x (mc-1), row-major.
+std::vector<double> spline_value_operator(int mc, int n) {
+    const int M = mc * n, Nc = mc - 1, Nf = M - 1;
+    const double H = 1.0 / mc;
+    const std::vector<double> Sm = spline_moment_operator(mc);       // (mc+1) x (mc-1)
+    std::vector<double> W((size_t)Nf * Nc, 0.0);
+    for (int m = 0; m < Nc; ++m) {
+        for (int p = 1; p <= Nf; ++p) {
+            const int i = std::min(p / n, mc - 1);                      // knot interval [i H, (i+1) H]
+            const double x = (double)p / M, xi = i * H, xj = (i + 1) * H;
+            const double yi = (i == m + 1) ? 1.0 : 0.0, yj = (i + 1 == m + 1) ? 1.0 : 0.0;
+            const double Mi = Sm[(size_t)i * Nc + m], Mj = Sm[(size_t)(i + 1) * Nc + m];
+            const double a = xj - x, b = x - xi;
+            W[(size_t)(p - 1) * Nc + m] = Mi * a * a * a / (6.0 * H) + Mj * b * b * b / (6.0 * H)
+                                        + (yi - Mi * H * H / 6.0) * a / H + (yj - Mj * H * H / 6.0) * b / H;
+        }
+    }
+    return W;
+}
+
+}  // namespace asdsm
