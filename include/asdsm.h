@@ -26,6 +26,19 @@
  * 2^q - 1 unknowns per axis and a hole's factors fit in shared memory.
  * Other sizes return ASDSM_ERR_INVALID.
  *
+ * The 3D extension (Section 3.5; asdsm_desc.d = 3): the unit cube, N x N x N
+ * grids (element (i, j, l) at offset (l*N + j)*N + i, boundary included),
+ * the 7-point operator with alpha_i, beta_i per axis x, y, z.  Sizes: N - 1
+ * and mc powers of two with N <= 257, 2 <= mc <= 32 and
+ * 2 <= (N - 1)/mc <= 16.  ASDSM iterates over the three plane families
+ * Omega^{H,h,h}, Omega^{h,H,h}, Omega^{h,h,H}; the initial guess also solves
+ * the line families and the coarse mesh to extrapolate the intersection
+ * points.  asdsm_setup, asdsm_set_opts, asdsm_solve, asdsm_initial_guess,
+ * asdsm_residual (rel_norm only; r must be NULL), asdsm_submesh_solve,
+ * asdsm_history and asdsm_destroy accept 3D handles; the other entry points
+ * that take a handle return ASDSM_ERR_INVALID for them.  The mixed path keeps
+ * the iterate, the residual and the accumulation in FP64 (not fixed point).
+ *
  * Errors: every int-returning function returns ASDSM_OK (0) or a negative
  * code (see asdsm_strerror).  The library never aborts or traps; after an
  * error the handle stays valid and may be destroyed or reused.
@@ -60,9 +73,10 @@ extern "C" {
                             accumulation exact to FP64 level (64-bit fixed-point u, FP32-pair
                             arithmetic for the residual) */
 
-/* Problem description: one instance of eq. (1.1) on the unit square (d = 2). */
+/* Problem description: one instance of eq. (1.1) on the unit square (d = 2)
+ * or the unit cube (d = 3). */
 typedef struct {
-    int32_t d;          /* space dimension; 2 */
+    int32_t d;          /* space dimension: 2, or 3 for the 3D extension of Section 3.5 */
     int32_t n;          /* grid points per axis including the boundary (N) */
     int32_t mc;         /* coarse intervals per axis (N_c + 1 in eq. 2.1) */
     int32_t pad_;
@@ -218,7 +232,13 @@ int asdsm_residual(asdsm_handle* h, const double* s, const double* u, double* r,
  *       points of out are left untouched.  For n = 16 on the mixed path this
  *       is the tensor-core Filler unless the tuned state selects the block
  *       cyclic reduction kernel.
- * in/out: device FP64 arrays; they may not alias. */
+ * in/out: device FP64 arrays; they may not alias.
+ * For a 3D handle: mesh 0..2 = the plane family coarse in x, y, z, arrays
+ * [k][q][p] (k the coarse plane, (p, q) the two other axes in increasing
+ * order, p fastest); 3..5 = the line family fine in x, y, z, arrays
+ * [f][cq][cp] (f the fine coordinate, cp/cq the coarse coordinates of the
+ * other two axes); 6 = the coarse mesh [cz][cy][cx]; 7 = the cube holes:
+ * N^3 grids, only hole points read and written. */
 int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out);
 
 /* Relative residual after each completed sweep of the last asdsm_solve

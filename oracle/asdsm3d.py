@@ -59,7 +59,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 from scipy.interpolate import CubicSpline
 
-from .asdsm2d import L_matrix, D_matrix, splitmix64, _GOLDEN_GAMMA, _MASK64
+from .asdsm2d import L_matrix, D_matrix, splitmix64, _GOLDEN_GAMMA, _MASK64, hole_fix_due
 
 FAMILIES = ("x", "y", "z")          # plane family P_a: coordinate a on the coarse knots
 
@@ -341,17 +341,20 @@ class Discretisation3D:
 
 
 def asdsm(disc: Discretisation3D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, seed=0,
-          stagnation_window=10, stagnation_factor=1e-3, u0=None):
-    """Algorithm 4 in 3D (readings R13-R15 of the 2D oracle; R18's hole
-    correction is not needed at these sizes and is left out).
+          stagnation_window=10, stagnation_factor=1e-3, hole_fix_ratio=0.25, hole_fix_growth=4.0, u0=None):
+    """Algorithm 4 in 3D with the readings R13-R15 and R18 of the 2D oracle
+    (R18: a Filler pass on the cube holes replaces a sweep when rounding has
+    left a hole residual above hole_fix_ratio of the whole residual and above
+    hole_fix_growth times its size after the previous pass).
 
     b = (b_ff, b_plane, b_line, b_cc) from Discretisation3D.rhs."""
     b_ff, b_p, b_l, b_c = b
     sk = disc.P_skel
     u = disc.initial_guess(b_ff, b_p, b_l, b_c) if u0 is None else np.array(u0, dtype=np.float64)
     nb = np.linalg.norm(b_ff)
-    hist, steps, choices = [], [], []
+    hist, steps, choices, kinds = [], [], [], []
     Z, Q = [], []
+    hole_ref = 0.0
     status = "max_sweeps"
     k = 0
     while True:
@@ -367,6 +370,16 @@ def asdsm(disc: Discretisation3D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
                 hist[-1] > (1 - stagnation_factor) * hist[-1 - stagnation_window]):
             status = "stagnated"
             break
+        if hole_fix_due(np.linalg.norm(disc.P_holes @ r), np.linalg.norm(r), hole_ref, hole_fix_ratio,
+                        hole_fix_growth):
+            u = disc.filler(u, b_ff)
+            hole_ref = np.linalg.norm(disc.P_holes @ disc.residual(b_ff, u))
+            Z, Q = [], []
+            kinds.append("hole_fix")
+            choices.append(-1)
+            steps.append(1.0)
+            k += 1
+            continue
         ch = choice3(seed, k)
         # the correction: Algorithm 1 on the error equations of the plane meshes
         r_p = {f: disc.P_plane[f] @ r for f in FAMILIES}
@@ -396,8 +409,9 @@ def asdsm(disc: Discretisation3D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
             if len(Z) >= accel_m:
                 Z, Q = [], []
         choices.append(ch)
+        kinds.append("sweep")
         k += 1
-    return u, {"hist": hist, "steps": steps, "choices": choices, "status": status, "sweeps": k}
+    return u, {"hist": hist, "steps": steps, "choices": choices, "kinds": kinds, "status": status, "sweeps": k}
 
 
 # ---------------------------------------------------------------------------

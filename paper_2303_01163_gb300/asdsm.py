@@ -31,6 +31,8 @@ FP64 = 0
 MIXED = 1
 
 MESH_FC, MESH_CF, MESH_CC, MESH_HOLES, MESH_HOLES_HOMOGENEOUS = 0, 1, 2, 3, 4
+# 3D (asdsm_submesh_solve with d = 3): plane families, line families, coarse mesh, cube holes.
+MESH3_PLANE, MESH3_LINE, MESH3_COARSE, MESH3_HOLES = 0, 3, 6, 7
 
 
 class Desc(ctypes.Structure):
@@ -256,7 +258,9 @@ class SolveResult:
 
 
 class Solver:
-    """One problem of eq. (1.1) on an N x N grid (the handle of asdsm_setup)."""
+    """One problem of eq. (1.1) on an N x N grid (the handle of asdsm_setup),
+    or, with three alpha and beta values, on an N x N x N grid (the 3D
+    extension, Section 3.5)."""
 
     def __init__(self, N: int, mc: int, alpha, beta, *, precision: int = MIXED, tol: float = 1e-10,
                  max_sweeps: int = 500, accel_m: int = 8, seed: int = 0, stream=None, **opt_overrides):
@@ -265,10 +269,13 @@ class Solver:
         self._lib = lib
         self.N, self.mc = int(N), int(mc)
         d = Desc()
-        d.d = 2
+        self.dim = len(alpha)
+        if self.dim not in (2, 3) or len(beta) != self.dim:
+            raise ValueError("alpha and beta need 2 (2D) or 3 (3D) values each")
+        d.d = self.dim
         d.n = self.N
         d.mc = self.mc
-        for q in range(2):
+        for q in range(self.dim):
             d.alpha[q] = float(alpha[q])
             d.beta[q] = float(beta[q])
         o = default_opts()

@@ -24,6 +24,7 @@
 #include <vector>
 #include <algorithm>
 #include <functional>
+#include "solve3d.h"
 
 using namespace asdsm;
 
@@ -63,6 +64,7 @@ bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 
 struct asdsm_handle {
     asdsm_desc desc{};
+    asdsm::Solver3D* s3 = nullptr;   // d = 3: the 3D extension's solver; the 2D members stay unused
     asdsm_opts opts{};
     cudaStream_t st = nullptr;
     int num_sms = 152;
@@ -1435,6 +1437,11 @@ int solve_impl(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) 
 
 }  // namespace
 
+namespace asdsm {
+int report_cuda_error(cudaError_t e) { return set_cuda_error(e); }
+void report_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace asdsm
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -1476,6 +1483,19 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if (!out) return ASDSM_ERR_INVALID;
     *out = nullptr;
     if (!desc) return ASDSM_ERR_INVALID;
+    if (desc->d == 3) {
+        asdsm_opts o3;
+        if (opts) o3 = *opts; else asdsm_default_opts(&o3);
+        Solver3D* s3 = nullptr;
+        if (int rc = s3_create(desc, &o3, (cudaStream_t)stream, &s3)) return rc;
+        asdsm_handle* h = new asdsm_handle();
+        h->desc = *desc;
+        h->opts = o3;
+        h->st = (cudaStream_t)stream;
+        h->s3 = s3;
+        *out = h;
+        return ASDSM_OK;
+    }
     if (desc->d != 2) return ASDSM_ERR_INVALID;
     const long long N = desc->n, mc = desc->mc;
     if (N < 5 || !is_pow2(N - 1) || mc < 2 || !is_pow2(mc) || (N - 1) % mc != 0) return ASDSM_ERR_INVALID;
@@ -1582,6 +1602,7 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
 
 int asdsm_autotune(asdsm_handle* h, int precision) {
     if (!h) return ASDSM_ERR_INVALID;
+    if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
     int rc;
     if (precision == ASDSM_FP64) rc = autotune_impl<double>(h);
     else if (precision == ASDSM_MIXED) rc = autotune_impl<float>(h);
@@ -1596,6 +1617,7 @@ constexpr int kTuneInts = 2 * (4 * kMaxLevels + 1);
 
 int asdsm_tune_get(const asdsm_handle* h, int32_t* out, int cap) {
     if (!h || !out || cap < kTuneInts) return ASDSM_ERR_INVALID;
+    if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
     int q = 0;
     for (int pi = 0; pi < 2; ++pi) {
         for (int d = 0; d < 2; ++d)
@@ -1627,6 +1649,7 @@ int asdsm_tune_check(const int32_t* in, int n) {
 
 int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n) {
     if (!h) return ASDSM_ERR_INVALID;
+    if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
     if (int rc = asdsm_tune_check(in, n)) return rc;
     int q = 0;
     for (int pi = 0; pi < 2; ++pi) {
@@ -1644,6 +1667,7 @@ int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n) {
 
 int asdsm_attach_cnn(asdsm_handle* h, asdsm_cnn* net) {
     if (!h) return ASDSM_ERR_INVALID;
+    if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
     if (h->cnn_x) { cudaFree(h->cnn_x); h->cnn_x = nullptr; }
     if (h->cnn_y) { cudaFree(h->cnn_y); h->cnn_y = nullptr; }
     h->cnn = nullptr;
@@ -1659,6 +1683,7 @@ int asdsm_cnn_directions(const asdsm_handle* h) { return h ? h->cnn_dirs : ASDSM
 
 int asdsm_correction(asdsm_handle* h, const double* s, const double* u, float* r_out, float* e_out, int k) {
     if (!h || !s || !u || !r_out || !e_out || k < 0) return ASDSM_ERR_INVALID;
+    if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
     if (int rc = ensure_work<double>(h, 0, 1)) return rc;
     if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(h->g), 4096))) return rc;
     auto& w = h->w[0];
@@ -1701,12 +1726,14 @@ int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts) {
     if (!h || !opts) return ASDSM_ERR_INVALID;
     if (opts->accel_m < 1 || opts->accel_m > kMaxM) return ASDSM_ERR_INVALID;
     if (opts->precision != ASDSM_FP64 && opts->precision != ASDSM_MIXED) return ASDSM_ERR_INVALID;
+    if (h->s3) { h->opts = *opts; return s3_set_opts(h->s3, opts); }
     h->opts = *opts;
     return ASDSM_OK;
 }
 
 int asdsm_solve(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats) {
     if (!h || !s || !u) return ASDSM_ERR_INVALID;
+    if (h->s3) return s3_solve(h->s3, s, u, stats);
     if (h->opts.precision == ASDSM_FP64) return solve_impl<double>(h, s, u, stats);
     if (h->opts.precision == ASDSM_MIXED) return solve_impl<float>(h, s, u, stats);
     return ASDSM_ERR_INVALID;
@@ -1714,6 +1741,7 @@ int asdsm_solve(asdsm_handle* h, const double* s, double* u, asdsm_stats* stats)
 
 int asdsm_initial_guess(asdsm_handle* h, const double* s, double* u) {
     if (!h || !s || !u) return ASDSM_ERR_INVALID;
+    if (h->s3) return s3_initial_guess(h->s3, s, u);
     int rc;
     if (h->opts.precision == ASDSM_FP64) {
         if ((rc = ensure_work<double>(h, 0))) return rc;
@@ -1736,6 +1764,10 @@ int asdsm_initial_guess(asdsm_handle* h, const double* s, double* u) {
 
 int asdsm_residual(asdsm_handle* h, const double* s, const double* u, double* r, double* rel_norm) {
     if (!h || !s || !u) return ASDSM_ERR_INVALID;
+    if (h->s3) {
+        if (r) { g_last_error = "3D: r is not returned (use asdsm_residual_noalloc)"; return ASDSM_ERR_INVALID; }
+        return s3_residual(h->s3, s, u, r, rel_norm);
+    }
     const Geometry& g = h->g;
     double b2 = 0.0;
     int rc;
@@ -1755,6 +1787,7 @@ int asdsm_residual(asdsm_handle* h, const double* s, const double* u, double* r,
 
 int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out) {
     if (!h || !in || !out || in == out) return ASDSM_ERR_INVALID;
+    if (h->s3) return s3_submesh_solve(h->s3, mesh, in, out);
     const Geometry& g = h->g;
     const bool fp64 = h->opts.precision == ASDSM_FP64;
     const int pi = fp64 ? 0 : 1;
@@ -1864,6 +1897,7 @@ int asdsm_real_schur(int n, const double* A, double* Q, double* T) {
 
 int asdsm_selftest_wait_timeout(asdsm_handle* h, long long limit_ns) {
     if (!h || limit_ns <= 0 || limit_ns > 2000000000LL) return ASDSM_ERR_INVALID;
+    if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
     CK(wait_selftest(h->dtcerr, limit_ns, h->st));
     return tc_status(h, h->st);
 }
@@ -1898,6 +1932,7 @@ int asdsm_hole_extension_operator_3d(int N, int mc, const double* alpha, const d
 
 int asdsm_history(asdsm_handle* h, double* hist, int cap) {
     if (!h || (!hist && cap > 0)) return ASDSM_ERR_INVALID;
+    if (h->s3) return s3_history(h->s3, hist, cap);
     const int n = std::min<int>(cap, (int)h->hist.size());
     for (int q = 0; q < n; ++q) hist[q] = h->hist[q];
     return n;
@@ -1905,6 +1940,7 @@ int asdsm_history(asdsm_handle* h, double* hist, int cap) {
 
 int asdsm_profile(asdsm_handle* h, int enable) {
     if (!h) return ASDSM_ERR_INVALID;
+    if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
     h->prof = enable != 0;
     std::memset(h->pc, 0, sizeof(h->pc));
     for (int c = 0; c < PC_COUNT; ++c) std::snprintf(h->pc[c].name, sizeof(h->pc[c].name), "%s", kProfNames[c]);
@@ -2079,6 +2115,11 @@ int asdsm_batch_history(const asdsm_batch* b, int index, double* out, int cap) {
 
 void asdsm_destroy(asdsm_handle* h) {
     if (!h) return;
+    if (h->s3) {
+        s3_destroy(h->s3);
+        delete h;
+        return;
+    }
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
     auto fr = [](void* p) { if (p) cudaFree(p); };
     for (int p = 0; p < 2; ++p) {

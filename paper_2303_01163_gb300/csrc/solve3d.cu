@@ -1,0 +1,1383 @@
+// The 3D extension of ASDSM (Section 3.5) on the GPU.
+//
+// Meshes of the unit cube with N points per axis and mc coarse intervals
+// (N_f = N - 2 fine and N_c = mc - 1 coarse interior points per axis):
+//   plane family P_a (a = x, y, z): coarse in axis a, fine in the other two;
+//   line family L_a: fine in axis a only (needed by the extrapolation of the
+//   initial guess, R21); the coarse mesh C; the cube holes of n - 1 points
+//   per side between the coarse planes.
+//
+// Every submesh operator is a Kronecker sum of 1D three-point operators
+// (Section 2.3 with each axis' own spacing), so every system is solved
+// exactly by block cyclic reduction (the kernels of kernels_solve.cu) with
+// factors computed once on the host in FP64:
+//   * L_a, C and the holes: BCR along one axis with the dense Kronecker-sum
+//     block of the two others (N_c^2 or (n-1)^2 columns; all holes at once);
+//   * P_a: the coarse-axis operator T_H (N_c x N_c) is brought to real Schur
+//     form T_H = Q S Q^T (host).  In the basis of Q the plane system becomes a
+//     back-substitution over S's diagonal blocks, each a shifted 2D fine-plane
+//     system (A_2D + S_kk I) y_k = g_k - sum_{j>k} S_kj y_j solved by 2D BCR;
+//     a 2 x 2 block (a complex eigenvalue pair) is one real system with two
+//     components per point (2 N_f columns).
+//
+// Merge (Algorithm 2 in 3D): the value u_hat on every line point (where two
+// or three plane families meet) by the combination technique (R21) or the
+// random choice (R22); each plane moved onto u_hat by the Boolean sum of
+// not-a-knot splines of its mismatch (R23); the union of the planes, a point
+// shared by several families taken from the last of x, y, z.  Filler
+// (Algorithm 3): every cube hole solved with Dirichlet data from the
+// skeleton.  Sweeps (Algorithm 4): FP64 fine residual with the previous
+// update fused in, the correction above, least squares on the skeleton rows
+// (the clamped optimal scaling, or GCR(m), R15), the hole-residual pass R18.
+//
+// Precision: ASDSM_FP64 does everything in FP64.  ASDSM_MIXED solves, merges
+// and fills in FP32 and keeps the iterate, the residual and the accumulation
+// in FP64.
+#include "asdsm.h"
+#include "asdsm_internal.h"
+#include "solve3d.h"
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace asdsm {
+
+// ---------------------------------------------------------------------------
+// Geometry and stencil
+// ---------------------------------------------------------------------------
+struct Geo3 {
+    int N, M, Nf, mc, Nc, n, hc;     // hc = n - 1 points per hole side
+    long long NN;                    // N^3
+    long long skel;                  // skeleton points: Nf^3 - (Nf - Nc)^3
+    long long plane;                 // Nf^2: points of one plane
+};
+
+// 7-point operator: A u = cc u + cw u_{x-1} + ce u_{x+1} + cs u_{y-1} + cn u_{y+1} + cd u_{z-1} + cu u_{z+1}.
+struct Sten3 {
+    double cc, cw, ce, cs, cn, cd, cu;
+};
+
+// Compact skeleton index of interior point (i, j, l) on the skeleton
+// (at least one coordinate a multiple of n): z slabs in order; a coarse z
+// slab holds its whole N_f x N_f plane, a fine one the 2D skeleton of its
+// plane (coarse rows whole, fine rows only at the coarse columns).
+__device__ __forceinline__ long long skel3_index(int i, int j, int l, const Geo3& g) {
+    const long long P = g.plane;
+    const long long S2 = (long long)g.Nc * g.Nf + (long long)(g.Nf - g.Nc) * g.Nc;
+    const int cz = (l - 1) / g.n;
+    long long off = (long long)cz * P + (long long)(l - 1 - cz) * S2;
+    if (l % g.n == 0) return off + (long long)(j - 1) * g.Nf + (i - 1);
+    const int cy = (j - 1) / g.n;
+    off += (long long)cy * g.Nf + (long long)(j - 1 - cy) * g.Nc;
+    if (j % g.n == 0) return off + (i - 1);
+    return off + (i / g.n - 1);
+}
+
+__device__ __forceinline__ bool on_skel3(int i, int j, int l, int n) {
+    return i % n == 0 || j % n == 0 || l % n == 0;
+}
+
+namespace {
+unsigned grid_rows(long long rows) {
+    long long b = rows < 1 ? 1 : rows;
+    return (unsigned)(b > 152LL * 32 ? 152LL * 32 : b);
+}
+}  // namespace
+
+constexpr int T3 = 256;    // threads per CTA of the grid kernels
+
+// Block sums of two values into partials[2 * block].
+__device__ __forceinline__ void block_sum_pair(double a, double b, double* partials) {
+    __shared__ double red[2][T3 / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { red[0][w] = a; red[1][w] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int q = 0; q < T3 / 32; ++q) { x += red[0][q]; y += red[1][q]; }
+        partials[2 * blockIdx.x] = x;
+        partials[2 * blockIdx.x + 1] = y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The update of Algorithm 4, u_out = u_in + sum_j c_j z_j over the interior
+// (FP64 accumulation of the T directions), and the fine residual r = s - A u
+// (FP64) with the sums of r^2 over the interior and over the holes and r
+// gathered onto the compact skeleton and into the three plane families'
+// right-hand sides ([k][q][p], (p, q) the two other axes in increasing order).
+// One CTA per (y, z) row, threads along x.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(T3)
+update3_kernel(const double* __restrict__ u_in, double* __restrict__ u_out, UpdateTerms up, Geo3 g) {
+    const int N = g.N, Nf = g.Nf;
+    for (long long row = blockIdx.x; row < (long long)Nf * Nf; row += gridDim.x) {
+        const int j = (int)(row % Nf) + 1, l = (int)(row / Nf) + 1;
+        const long long base = ((long long)l * N + j) * N;
+        for (int i = 1 + threadIdx.x; i <= N - 2; i += T3) {
+            const long long idx = base + i;
+            double v = u_in[idx];
+            for (int t = 0; t < up.count; ++t) v += up.coef[t] * (double)reinterpret_cast<const T*>(up.z[t])[idx];
+            u_out[idx] = v;
+        }
+    }
+}
+
+template <typename T>
+struct Resid3Out {
+    T* rskel;            // [skel]
+    T* rp[3];            // plane right-hand sides per family
+    double* partials;    // [grid][2]
+};
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+resid3_kernel(const double* __restrict__ s, const double* __restrict__ u, Geo3 g, Sten3 c, Resid3Out<T> o) {
+    const int N = g.N, Nf = g.Nf, n = g.n;
+    const long long NN2 = (long long)N * N;
+    double sr = 0.0, sh = 0.0;
+    for (long long row = blockIdx.x; row < (long long)Nf * Nf; row += gridDim.x) {
+        const int j = (int)(row % Nf) + 1, l = (int)(row / Nf) + 1;
+        const long long base = ((long long)l * N + j) * N;
+        for (int i = 1 + threadIdx.x; i <= N - 2; i += T3) {
+            const long long idx = base + i;
+            const double Au = c.cc * u[idx] + c.cw * u[idx - 1] + c.ce * u[idx + 1] + c.cs * u[idx - N]
+                            + c.cn * u[idx + N] + c.cd * u[idx - NN2] + c.cu * u[idx + NN2];
+            const double r = s[idx] - Au;
+            sr += r * r;
+            const bool ci = i % n == 0, cj = j % n == 0, cl = l % n == 0;
+            if (!(ci || cj || cl)) { sh += r * r; continue; }
+            const T rt = (T)r;
+            if (o.rskel) o.rskel[skel3_index(i, j, l, g)] = rt;
+            const long long P = g.plane;
+            if (ci && o.rp[0]) o.rp[0][(long long)(i / n - 1) * P + (long long)(l - 1) * Nf + (j - 1)] = rt;
+            if (cj && o.rp[1]) o.rp[1][(long long)(j / n - 1) * P + (long long)(l - 1) * Nf + (i - 1)] = rt;
+            if (cl && o.rp[2]) o.rp[2][(long long)(l / n - 1) * P + (long long)(j - 1) * Nf + (i - 1)] = rt;
+        }
+    }
+    block_sum_pair(sr, sh, o.partials);
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand sides of the submesh systems with the Dirichlet lifting (R5):
+// samples of s plus, along each axis, the moved stencil coefficient (with
+// that mesh's spacing on that axis) times g where a neighbour falls on the
+// boundary.  kind 0..2: plane family a, [k][q][p]; 3..5: line family a,
+// [f][cq][cp]; 6: the coarse mesh, [cz][cy][cx].
+// ---------------------------------------------------------------------------
+struct Lift3 {
+    double lo[3][2], hi[3][2];    // [axis][0: fine step, 1: coarse step]
+};
+
+__device__ __forceinline__ void other_axes(int a, int& pa, int& qa) {
+    pa = a == 0 ? 1 : 0;
+    qa = a == 2 ? 1 : 2;
+}
+
+// Grid coordinates (x, y, z) of entry e of a submesh array of the given kind.
+__device__ __forceinline__ void submesh_coords(int kind, long long e, const Geo3& g, int c[3], bool coarse[3]) {
+    const int Nf = g.Nf, Nc = g.Nc, n = g.n;
+    if (kind < 3) {
+        const int a = kind;
+        int pa, qa;
+        other_axes(a, pa, qa);
+        const int p = (int)(e % Nf), q = (int)((e / Nf) % Nf), k = (int)(e / ((long long)Nf * Nf));
+        c[a] = (k + 1) * n; c[pa] = p + 1; c[qa] = q + 1;
+        coarse[a] = true; coarse[pa] = false; coarse[qa] = false;
+    } else if (kind < 6) {
+        const int a = kind - 3;
+        int pa, qa;
+        other_axes(a, pa, qa);
+        const int cp = (int)(e % Nc), cq = (int)((e / Nc) % Nc), f = (int)(e / ((long long)Nc * Nc));
+        c[a] = f + 1; c[pa] = (cp + 1) * n; c[qa] = (cq + 1) * n;
+        coarse[a] = false; coarse[pa] = true; coarse[qa] = true;
+    } else {
+        c[0] = (int)(e % Nc + 1) * n; c[1] = (int)((e / Nc) % Nc + 1) * n; c[2] = (int)(e / ((long long)Nc * Nc) + 1) * n;
+        coarse[0] = coarse[1] = coarse[2] = true;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+rhs3_kernel(const double* __restrict__ s, const double* __restrict__ u, Geo3 g, int kind, long long count, Lift3 lf,
+            T* __restrict__ out) {
+    const int N = g.N, M = g.M;
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < count; e += (long long)gridDim.x * T3) {
+        int c[3];
+        bool co[3];
+        submesh_coords(kind, e, g, c, co);
+        auto at = [&](int x, int y, int z) { return u[((long long)z * N + y) * N + x]; };
+        double b = s[((long long)c[2] * N + c[1]) * N + c[0]];
+        for (int a = 0; a < 3; ++a) {
+            const int st = co[a] ? g.n : 1;
+            int lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
+            lo[a] = 0;
+            hi[a] = M;
+            if (c[a] - st == 0) b += lf.lo[a][co[a] ? 1 : 0] * at(lo[0], lo[1], lo[2]);
+            if (c[a] + st == M) b += lf.hi[a][co[a] ? 1 : 0] * at(hi[0], hi[1], hi[2]);
+        }
+        out[e] = (T)b;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plane-family solve in the Schur basis of the coarse-axis operator:
+//   right-hand side of block k (size bs = 1 or 2):
+//     v_i = sum_j Q[j][k+i] F_j - sum_{j >= k+bs} S[k+i][j] Y_j   (i < bs),
+//   written plainly (bs = 1) or interleaved per point (bs = 2, column 2 e + i);
+//   back-transform U_j = sum_k Q[j][k] Y_k with the partial sums of U^2.
+// ---------------------------------------------------------------------------
+constexpr int kMaxNc3 = 31;     // coarse points per axis (mc <= 32)
+
+struct SchurStep {
+    double q[2][kMaxNc3];       // Q[j][k+i]
+    double s[2][kMaxNc3];       // S[k+i][j] (zero for j < k + bs)
+    int k, bs, Nc;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+schur_rhs_kernel(const T* __restrict__ F, const T* __restrict__ Y, long long P, SchurStep ss, T* __restrict__ X) {
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < P; e += (long long)gridDim.x * T3) {
+        double v[2] = {0.0, 0.0};
+        for (int j = 0; j < ss.Nc; ++j) {
+            const double f = (double)F[(long long)j * P + e];
+            v[0] += ss.q[0][j] * f;
+            if (ss.bs == 2) v[1] += ss.q[1][j] * f;
+        }
+        for (int j = ss.k + ss.bs; j < ss.Nc; ++j) {
+            const double y = (double)Y[(long long)j * P + e];
+            v[0] -= ss.s[0][j] * y;
+            if (ss.bs == 2) v[1] -= ss.s[1][j] * y;
+        }
+        if (ss.bs == 1) {
+            X[e] = (T)v[0];
+        } else {
+            X[2 * e] = (T)v[0];
+            X[2 * e + 1] = (T)v[1];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+deinterleave_kernel(const T* __restrict__ Z, long long P, T* __restrict__ Y0, T* __restrict__ Y1) {
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < P; e += (long long)gridDim.x * T3) {
+        Y0[e] = Z[2 * e];
+        Y1[e] = Z[2 * e + 1];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+schur_back_kernel(const T* __restrict__ Y, const T* __restrict__ Q, int Nc, long long P, T* __restrict__ U,
+                  double* partials) {
+    __shared__ double Qs[kMaxNc3 * kMaxNc3];
+    for (int t = threadIdx.x; t < Nc * Nc; t += T3) Qs[t] = (double)Q[t];
+    __syncthreads();
+    double s2 = 0.0;
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < P; e += (long long)gridDim.x * T3) {
+        double y[kMaxNc3];
+        for (int k = 0; k < Nc; ++k) y[k] = (double)Y[(long long)k * P + e];
+        for (int j = 0; j < Nc; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < Nc; ++k) v += Qs[j * Nc + k] * y[k];
+            const T vt = (T)v;
+            U[(long long)j * P + e] = vt;
+            s2 += (double)vt * (double)vt;
+        }
+    }
+    block_sum_pair(s2, 0.0, partials);
+}
+
+// ---------------------------------------------------------------------------
+// Merge, part 1: u_hat on every line point (a point where two or three plane
+// families meet).  Enumeration: for each family a the points of L_a that are
+// not knots (coordinate a fine and not a multiple of n), then the knots.
+//   initial guess (lines and coarse given, R21):
+//     on L_a (not a knot):  u_hat = U_pa + U_qa - L_a,
+//     knots:                u_hat = U_x + U_y + U_z - L_x - L_y - L_z + C;
+//   a sweep's correction (R22): the value of the drawn family if its planes
+//   contain the point, else of the next family in the order x -> y -> z -> x.
+// Plane values are scaled by 1/||U_a|| when norms are given (R24).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Merge3Args {
+    const T* U[3];          // plane solutions [k][q][p]
+    const double* nrm2;     // ||U_a||^2 at nrm2[2 a] (sweep correction) or null
+    const T* Lf[3];         // line solutions [f][cq][cp] (initial guess) or null
+    const T* Cc;            // coarse solution [cz][cy][cx] (initial guess) or null
+    int choice;             // drawn family (sweep correction)
+    T* uh;                  // full grid: u_hat on the line points
+    const T* W;             // spline values [N_f][N_c]
+    T* z;                   // full grid: receives the merged skeleton
+};
+
+__device__ __forceinline__ double plane_scale(const double* nrm2, int a) {
+    if (!nrm2) return 1.0;
+    const double v = nrm2[2 * a];
+    return v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+}
+
+template <typename T>
+__device__ __forceinline__ double plane_at(const Merge3Args<T>& m, const Geo3& g, int a, const int c[3], double sc) {
+    int pa, qa;
+    other_axes(a, pa, qa);
+    const long long e = ((long long)(c[a] / g.n - 1) * g.Nf + (c[qa] - 1)) * g.Nf + (c[pa] - 1);
+    return sc * (double)m.U[a][e];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T3) uhat3_kernel(Merge3Args<T> m, Geo3 g) {
+    const int n = g.n, Nc = g.Nc, N = g.N;
+    const long long per = (long long)(g.Nf - Nc) * Nc * Nc, count = 3 * per + (long long)Nc * Nc * Nc;
+    double sc[3];
+    for (int a = 0; a < 3; ++a) sc[a] = plane_scale(m.nrm2, a);
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < count; e += (long long)gridDim.x * T3) {
+        int c[3];
+        int a = -1;                       // the line family (fine axis), -1 for a knot
+        if (e < 3 * per) {
+            a = (int)(e / per);
+            const long long r = e % per;
+            int pa, qa;
+            other_axes(a, pa, qa);
+            const int cp = (int)(r % Nc), cq = (int)((r / Nc) % Nc), t = (int)(r / ((long long)Nc * Nc));
+            c[a] = t + 1 + t / (n - 1);   // the t-th fine coordinate that is not a multiple of n
+            c[pa] = (cp + 1) * n;
+            c[qa] = (cq + 1) * n;
+        } else {
+            const long long r = e - 3 * per;
+            c[0] = (int)(r % Nc + 1) * n; c[1] = (int)((r / Nc) % Nc + 1) * n; c[2] = (int)(r / ((long long)Nc * Nc) + 1) * n;
+        }
+        double v;
+        if (m.Lf[0]) {
+            auto line_at = [&](int b) {
+                int pb, qb;
+                other_axes(b, pb, qb);
+                return (double)m.Lf[b][((long long)(c[b] - 1) * Nc + (c[qb] / n - 1)) * Nc + (c[pb] / n - 1)];
+            };
+            if (a >= 0) {
+                int pa, qa;
+                other_axes(a, pa, qa);
+                v = plane_at(m, g, pa, c, sc[pa]) + plane_at(m, g, qa, c, sc[qa]) - line_at(a);
+            } else {
+                v = plane_at(m, g, 0, c, sc[0]) + plane_at(m, g, 1, c, sc[1]) + plane_at(m, g, 2, c, sc[2])
+                  - line_at(0) - line_at(1) - line_at(2)
+                  + (double)m.Cc[((long long)(c[2] / n - 1) * Nc + (c[1] / n - 1)) * Nc + (c[0] / n - 1)];
+            }
+        } else {
+            int f = m.choice;
+            if (a >= 0 && f == a) f = (f + 1) % 3;          // the drawn family does not contain this line
+            v = plane_at(m, g, f, c, sc[f]);
+        }
+        m.uh[((long long)c[2] * N + c[1]) * N + c[0]] = (T)v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Merge, part 2: every plane of every family moved onto u_hat (R23).  On the
+// plane of family a at coordinate (k+1) n, with its fine axes p < q and the
+// mismatch E = u_hat - U_a on the plane's lines,
+//   corr(p, q) = sum_m W[p][m] E(knot m, q) + sum_m W[q][m] E(p, knot m)
+//              - sum_m W[p][m] sum_m' W[q][m'] E(knot m, knot m'),
+// the Boolean sum S_p E + S_q E - S_p S_q E of the not-a-knot splines.  The
+// value U_a + corr is written where family a is the last of x, y, z whose
+// planes contain the point.  One CTA per 32 x 8 tile of one plane.
+// ---------------------------------------------------------------------------
+constexpr int MP = 32, MQ = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(MP * MQ) plane_corr_kernel(Merge3Args<T> m, Geo3 g) {
+    __shared__ double Wp[MP][kMaxNc3], Wq[MQ][kMaxNc3], Ekk[kMaxNc3][kMaxNc3];
+    __shared__ double Eq[kMaxNc3][MQ], Ep[MP][kMaxNc3], Tm[kMaxNc3][MQ];
+    const int Nf = g.Nf, Nc = g.Nc, n = g.n, N = g.N;
+    const int a = blockIdx.z / Nc, k = blockIdx.z % Nc;
+    int pa, qa;
+    other_axes(a, pa, qa);
+    const int p0 = blockIdx.x * MP, q0 = blockIdx.y * MQ, tid = threadIdx.x;
+    const double sc = plane_scale(m.nrm2, a);
+    const T* U = m.U[a];
+    const long long P = g.plane;
+    // E at plane point (pi, qi) (0-based fine indices), a line point of this plane.
+    auto E = [&](int pi, int qi) -> double {
+        int c[3];
+        c[a] = (k + 1) * n; c[pa] = pi + 1; c[qa] = qi + 1;
+        return (double)m.uh[((long long)c[2] * N + c[1]) * N + c[0]]
+             - sc * (double)U[(long long)k * P + (long long)qi * Nf + pi];
+    };
+    for (int t = tid; t < MP * Nc; t += MP * MQ) {
+        const int r = t / Nc, mm = t % Nc, pi = p0 + r;
+        Wp[r][mm] = pi < Nf ? (double)m.W[(long long)pi * Nc + mm] : 0.0;
+        Ep[r][mm] = pi < Nf ? E(pi, (mm + 1) * n - 1) : 0.0;
+    }
+    for (int t = tid; t < MQ * Nc; t += MP * MQ) {
+        const int r = t / Nc, mm = t % Nc, qi = q0 + r;
+        Wq[r][mm] = qi < Nf ? (double)m.W[(long long)qi * Nc + mm] : 0.0;
+        Eq[mm][r] = qi < Nf ? E((mm + 1) * n - 1, qi) : 0.0;
+    }
+    for (int t = tid; t < Nc * Nc; t += MP * MQ) {
+        const int r = t / Nc, mm = t % Nc;
+        Ekk[r][mm] = E((r + 1) * n - 1, (mm + 1) * n - 1);
+    }
+    __syncthreads();
+    for (int t = tid; t < Nc * MQ; t += MP * MQ) {
+        const int mm = t / MQ, r = t % MQ;
+        double v = 0.0;
+        for (int m2 = 0; m2 < Nc; ++m2) v += Wq[r][m2] * Ekk[mm][m2];
+        Tm[mm][r] = v;
+    }
+    __syncthreads();
+    const int tp = tid % MP, tq = tid / MP, pi = p0 + tp, qi = q0 + tq;
+    if (pi >= Nf || qi >= Nf) return;
+    double corr = 0.0;
+    for (int mm = 0; mm < Nc; ++mm) corr += Wp[tp][mm] * (Eq[mm][tq] - Tm[mm][tq]) + Wq[tq][mm] * Ep[tp][mm];
+    int c[3];
+    c[a] = (k + 1) * n; c[pa] = pi + 1; c[qa] = qi + 1;
+    int owner = a;
+    if (c[pa] % n == 0 && pa > owner) owner = pa;
+    if (c[qa] % n == 0 && qa > owner) owner = qa;
+    if (owner != a) return;
+    m.z[((long long)c[2] * N + c[1]) * N + c[0]] = (T)(sc * (double)U[(long long)k * P + (long long)qi * Nf + pi] + corr);
+}
+
+// ---------------------------------------------------------------------------
+// Filler (Algorithm 3) on the cube holes as one batched block cyclic
+// reduction: right-hand sides [hole][lz][ly (n-1) + lx] and the scatter back.
+//   mode 0: s - (stencil terms reaching outside the hole) . z   (z: skeleton and g on the ring)
+//   mode 1: -(stencil terms reaching outside the hole) . z     (zero source)
+//   mode 2: s - A u at the hole point (FP64), the hole part of the residual;
+//           the scatter then adds the solution to u (R18);
+//   mode 3: the values of the FP64 grid s at the hole points; the scatter
+//           writes the solution into the FP64 grid u (single-solve checks).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void hole_point(long long e, const Geo3& g, int& i, int& j, int& l, int& lx, int& ly,
+                                           int& lz) {
+    const int hc = g.hc, mc = g.mc;
+    const long long h3 = (long long)hc * hc * hc;
+    const long long hole = e / h3, loc = e % h3;
+    lx = (int)(loc % hc); ly = (int)((loc / hc) % hc); lz = (int)(loc / ((long long)hc * hc));
+    const int hx = (int)(hole % mc), hy = (int)((hole / mc) % mc), hz = (int)(hole / ((long long)mc * mc));
+    i = hx * g.n + 1 + lx; j = hy * g.n + 1 + ly; l = hz * g.n + 1 + lz;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+hole_rhs3_kernel(int mode, const T* __restrict__ z, const double* __restrict__ s, const double* __restrict__ u, Geo3 g,
+                 Sten3 c, T* __restrict__ X) {
+    const long long count = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
+    const int N = g.N, hc = g.hc;
+    const long long NN2 = (long long)N * N;
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < count; e += (long long)gridDim.x * T3) {
+        int i, j, l, lx, ly, lz;
+        hole_point(e, g, i, j, l, lx, ly, lz);
+        const long long idx = ((long long)l * N + j) * N + i;
+        double r;
+        if (mode == 3) {
+            r = s[idx];
+        } else if (mode == 2) {
+            r = s[idx] - (c.cc * u[idx] + c.cw * u[idx - 1] + c.ce * u[idx + 1] + c.cs * u[idx - N] + c.cn * u[idx + N]
+                          + c.cd * u[idx - NN2] + c.cu * u[idx + NN2]);
+        } else {
+            r = mode == 0 ? s[idx] : 0.0;
+            if (lx == 0) r -= c.cw * (double)z[idx - 1];
+            if (lx == hc - 1) r -= c.ce * (double)z[idx + 1];
+            if (ly == 0) r -= c.cs * (double)z[idx - N];
+            if (ly == hc - 1) r -= c.cn * (double)z[idx + N];
+            if (lz == 0) r -= c.cd * (double)z[idx - NN2];
+            if (lz == hc - 1) r -= c.cu * (double)z[idx + NN2];
+        }
+        X[e] = (T)r;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+hole_scatter3_kernel(int mode, const T* __restrict__ Y, Geo3 g, T* __restrict__ z, double* __restrict__ u) {
+    const long long count = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
+    const int N = g.N;
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < count; e += (long long)gridDim.x * T3) {
+        int i, j, l, lx, ly, lz;
+        hole_point(e, g, i, j, l, lx, ly, lz);
+        const long long idx = ((long long)l * N + j) * N + i;
+        if (mode == 2) u[idx] += (double)Y[e];
+        else if (mode == 3) u[idx] = (double)Y[e];
+        else z[idx] = Y[e];
+    }
+}
+
+// q = A z on the compact skeleton (T arithmetic).
+template <typename T>
+__global__ void __launch_bounds__(T3)
+skel_apply3_kernel(const T* __restrict__ z, Geo3 g, Sten3 c, T* __restrict__ q) {
+    const int N = g.N, Nf = g.Nf, n = g.n;
+    const long long NN2 = (long long)N * N;
+    const T cc = (T)c.cc, cw = (T)c.cw, ce = (T)c.ce, cs = (T)c.cs, cn = (T)c.cn, cd = (T)c.cd, cu = (T)c.cu;
+    for (long long row = blockIdx.x; row < (long long)Nf * Nf; row += gridDim.x) {
+        const int j = (int)(row % Nf) + 1, l = (int)(row / Nf) + 1;
+        const bool row_coarse = j % n == 0 || l % n == 0;
+        const long long base = ((long long)l * N + j) * N;
+        for (int i = 1 + threadIdx.x; i <= N - 2; i += T3) {
+            if (!row_coarse && i % n != 0) continue;
+            const long long idx = base + i;
+            q[skel3_index(i, j, l, g)] = cc * z[idx] + cw * z[idx - 1] + ce * z[idx + 1] + cs * z[idx - N]
+                                        + cn * z[idx + N] + cd * z[idx - NN2] + cu * z[idx + NN2];
+        }
+    }
+}
+
+// z (T grid): its ring from u's ring (g) or zero, its interior zero.
+template <typename T>
+__global__ void __launch_bounds__(T3) ring3_kernel(const double* __restrict__ u, Geo3 g, T* __restrict__ z) {
+    const int N = g.N;
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < g.NN; e += (long long)gridDim.x * T3) {
+        const int i = (int)(e % N), j = (int)((e / N) % N), l = (int)(e / ((long long)N * N));
+        const bool ring = i == 0 || j == 0 || l == 0 || i == N - 1 || j == N - 1 || l == N - 1;
+        z[e] = ring && u ? (T)u[e] : (T)0;
+    }
+}
+
+// u interior = z interior (converted), ring untouched.
+template <typename T>
+__global__ void __launch_bounds__(T3) interior3_kernel(const T* __restrict__ z, Geo3 g, double* __restrict__ u) {
+    const int N = g.N, Nf = g.Nf;
+    for (long long row = blockIdx.x; row < (long long)Nf * Nf; row += gridDim.x) {
+        const int j = (int)(row % Nf) + 1, l = (int)(row / Nf) + 1;
+        const long long base = ((long long)l * N + j) * N;
+        for (int i = 1 + threadIdx.x; i <= N - 2; i += T3) u[base + i] = (double)z[base + i];
+    }
+}
+
+// Plain copies (FP64 -> T) of submesh arrays, for single-solve checks.
+template <typename Ts, typename Td>
+__global__ void __launch_bounds__(T3) convert3_kernel(const Ts* __restrict__ a, long long n, Td* __restrict__ b) {
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < n; e += (long long)gridDim.x * T3) b[e] = (Td)a[e];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+#define CK3(...)                                          \
+    do {                                                  \
+        cudaError_t e__ = (__VA_ARGS__);                  \
+        if (e__ != cudaSuccess) return report_cuda_error(e__); \
+    } while (0)
+
+// BCR factors on the device in one precision.
+struct Fac {
+    void* Mt = nullptr; void* Bt = nullptr;
+    double wl[kMaxLevels] = {}, wr[kMaxLevels] = {};
+    int R = 0, C = 0, L = 0;
+};
+
+template <typename T>
+int upload_fac(const BcrFactors& f, Fac* d) {
+    const size_t n = f.Mt.size();
+    std::vector<T> tmp(n);
+    void** dst[2] = {&d->Mt, &d->Bt};
+    const std::vector<double>* src[2] = {&f.Mt, &f.Bt};
+    for (int q = 0; q < 2; ++q) {
+        CK3(cudaMalloc(dst[q], n * sizeof(T)));
+        for (size_t e = 0; e < n; ++e) tmp[e] = (T)(*src[q])[e];
+        CK3(cudaMemcpy(*dst[q], tmp.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    for (int l = 0; l < f.L; ++l) { d->wl[l] = f.wl[l]; d->wr[l] = f.wr[l]; }
+    d->R = f.R; d->C = f.C; d->L = f.L;
+    return ASDSM_OK;
+}
+
+void free_fac(Fac& d) {
+    if (d.Mt) cudaFree(d.Mt);
+    if (d.Bt) cudaFree(d.Bt);
+    d.Mt = d.Bt = nullptr;
+}
+
+template <typename T>
+BcrSys<T> sys3(const Fac& d, void* X, void* Y, int nsys = 1) {
+    BcrSys<T> s{};
+    s.X = (T*)X; s.Y = (T*)Y;
+    s.Mt = (const T*)d.Mt; s.Bt = (const T*)d.Bt;
+    for (int l = 0; l < d.L; ++l) { s.wl[l] = (T)d.wl[l]; s.wr[l] = (T)d.wr[l]; }
+    s.R = d.R; s.C = d.C; s.L = d.L; s.nsys = nsys;
+    s.stride = (long long)d.R * d.C;
+    return s;
+}
+
+// 1D three-point operator of axis a on spacing sp: (lower, diagonal, upper).
+struct Op1 { double lo, di, up; };
+Op1 op1(double alpha, double beta, double sp) {
+    return {-alpha / (sp * sp) - beta / (2 * sp), 2 * alpha / (sp * sp), -alpha / (sp * sp) + beta / (2 * sp)};
+}
+
+// Dense Kronecker sum  T_q (x) I + I (x) T_p + d I  on a [q][p] grid (p fastest).
+std::vector<double> kron_sum2(int nq, Op1 tq, int np, Op1 tp, double d) {
+    const int C = nq * np;
+    std::vector<double> K((size_t)C * C, 0.0);
+    for (int q = 0; q < nq; ++q)
+        for (int p = 0; p < np; ++p) {
+            const size_t r = (size_t)q * np + p;
+            K[r * C + r] = tq.di + tp.di + d;
+            if (p > 0) K[r * C + r - 1] = tp.lo;
+            if (p + 1 < np) K[r * C + r + 1] = tp.up;
+            if (q > 0) K[r * C + r - np] = tq.lo;
+            if (q + 1 < nq) K[r * C + r + np] = tq.up;
+        }
+    return K;
+}
+
+struct PlaneFam {
+    std::vector<int> bk, bs;             // Schur blocks: first index, size (1 or 2), in back-substitution order
+    std::vector<double> Q, S;            // N_c x N_c
+    std::vector<Fac> fac[2];             // per precision, per block
+    void* Qd[2] = {nullptr, nullptr};    // Q on the device [j][k] (T)
+};
+
+template <typename T>
+int upload_vec3(const std::vector<double>& v, void** d) {
+    std::vector<T> tmp(v.begin(), v.end());
+    CK3(cudaMalloc(d, std::max<size_t>(1, tmp.size()) * sizeof(T)));
+    if (!tmp.empty()) CK3(cudaMemcpy(*d, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ASDSM_OK;
+}
+
+}  // namespace
+
+struct Solver3D {
+    asdsm_desc desc{};
+    asdsm_opts opts{};
+    cudaStream_t st = nullptr;
+    int num_sms = 152;
+    Geo3 g{};
+    Sten3 sten{};
+    Lift3 lift{};
+    PlaneFam plane[3];
+    Fac line[2][3], coarse[2], hole[2];
+    void* W[2] = {nullptr, nullptr};       // spline values [N_f][N_c]
+    struct Work {
+        bool ready = false;
+        void* F[3] = {}; void* Y[3] = {}; void* U[3] = {};
+        void* Xb = nullptr; void* Yb = nullptr;
+        void* Xl[3] = {}; void* Yl[3] = {};
+        void* Xc = nullptr; void* Yc = nullptr;
+        void* Xh = nullptr; void* Yh = nullptr;
+        void* uh = nullptr;
+        void* z[16] = {};
+        void* rskel = nullptr; void* q = nullptr; void* qp[16] = {};
+    } w[2];
+    double* u_work = nullptr;
+    double* partials = nullptr;
+    int partials_cap = 0;
+    double* dsmall = nullptr;
+    double* hsmall = nullptr;
+    std::vector<double> hist;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+};
+
+namespace {
+
+// Host FP64 factors of every 3D system, computed in parallel threads.
+int build_factors(Solver3D* S) {
+    const Geo3& g = S->g;
+    const double h = 1.0 / g.M, H = 1.0 / g.mc;
+    const double* al = S->desc.alpha;
+    const double* be = S->desc.beta;
+    Op1 fine[3], crs[3];
+    for (int a = 0; a < 3; ++a) { fine[a] = op1(al[a], be[a], h); crs[a] = op1(al[a], be[a], H); }
+    struct Job { int kind, a, blk; BcrFactors f; bool ok = false; };
+    std::vector<Job> jobs;
+    // Plane families: Schur form of the coarse-axis operator, then one system per block.
+    for (int a = 0; a < 3; ++a) {
+        PlaneFam& pf = S->plane[a];
+        std::vector<double> T((size_t)g.Nc * g.Nc, 0.0);
+        for (int k = 0; k < g.Nc; ++k) {
+            T[(size_t)k * g.Nc + k] = crs[a].di;
+            if (k > 0) T[(size_t)k * g.Nc + k - 1] = crs[a].lo;
+            if (k + 1 < g.Nc) T[(size_t)k * g.Nc + k + 1] = crs[a].up;
+        }
+        if (!real_schur(g.Nc, T, &pf.Q, &pf.S)) { report_error("3D: Schur form of a coarse-axis operator failed"); return ASDSM_ERR_INVALID; }
+        std::vector<int> starts, sizes;
+        for (int k = 0; k < g.Nc;) {
+            const int bs = (k + 1 < g.Nc && pf.S[(size_t)(k + 1) * g.Nc + k] != 0.0) ? 2 : 1;
+            starts.push_back(k); sizes.push_back(bs);
+            k += bs;
+        }
+        pf.bk.assign(starts.rbegin(), starts.rend());     // back-substitution: last block first
+        pf.bs.assign(sizes.rbegin(), sizes.rend());
+        for (size_t b = 0; b < pf.bk.size(); ++b) jobs.push_back({0, a, (int)b, {}, false});
+    }
+    for (int a = 0; a < 3; ++a) jobs.push_back({1, a, 0, {}, false});
+    jobs.push_back({2, 0, 0, {}, false});
+    jobs.push_back({3, 0, 0, {}, false});
+    auto run = [&](Job& jb) {
+        int pa, qa;
+        pa = jb.a == 0 ? 1 : 0;
+        qa = jb.a == 2 ? 1 : 2;
+        if (jb.kind == 0) {
+            // Shifted 2D fine-plane system: rows along q, columns along p (and the pair's two components).
+            const PlaneFam& pf = S->plane[jb.a];
+            const int k = pf.bk[jb.blk], bs = pf.bs[jb.blk], Nc = g.Nc, Nf = g.Nf;
+            if (bs == 1) {
+                const double sig = pf.S[(size_t)k * Nc + k];
+                std::vector<double> K((size_t)Nf * Nf, 0.0);
+                for (int p = 0; p < Nf; ++p) {
+                    K[(size_t)p * Nf + p] = fine[pa].di + fine[qa].di + sig;
+                    if (p > 0) K[(size_t)p * Nf + p - 1] = fine[pa].lo;
+                    if (p + 1 < Nf) K[(size_t)p * Nf + p + 1] = fine[pa].up;
+                }
+                jb.ok = make_bcr_dense(Nf, fine[qa].lo, fine[qa].up, Nf, K, &jb.f);
+            } else {
+                const int C = 2 * Nf;
+                std::vector<double> K((size_t)C * C, 0.0);
+                for (int p = 0; p < Nf; ++p)
+                    for (int i = 0; i < 2; ++i) {
+                        const size_t r = (size_t)p * 2 + i;
+                        K[r * C + r] += fine[pa].di + fine[qa].di;
+                        if (p > 0) K[r * C + r - 2] = fine[pa].lo;
+                        if (p + 1 < Nf) K[r * C + r + 2] = fine[pa].up;
+                        for (int j = 0; j < 2; ++j) K[r * C + (size_t)p * 2 + j] += pf.S[(size_t)(k + i) * Nc + k + j];
+                    }
+                jb.ok = make_bcr_dense(Nf, fine[qa].lo, fine[qa].up, C, K, &jb.f);
+            }
+        } else if (jb.kind == 1) {
+            // Line family: rows along the fine axis a, columns (cq, cp) coarse.
+            jb.ok = make_bcr_dense(g.Nf, fine[jb.a].lo, fine[jb.a].up, g.Nc * g.Nc,
+                                   kron_sum2(g.Nc, crs[qa], g.Nc, crs[pa], fine[jb.a].di), &jb.f);
+        } else if (jb.kind == 2) {
+            // Coarse mesh: rows along z, columns (y, x).
+            jb.ok = make_bcr_dense(g.Nc, crs[2].lo, crs[2].up, g.Nc * g.Nc,
+                                   kron_sum2(g.Nc, crs[1], g.Nc, crs[0], crs[2].di), &jb.f);
+        } else {
+            // Cube holes: rows along z, columns (y, x), all fine.
+            jb.ok = make_bcr_dense(g.hc, fine[2].lo, fine[2].up, g.hc * g.hc,
+                                   kron_sum2(g.hc, fine[1], g.hc, fine[0], fine[2].di), &jb.f);
+        }
+    };
+    const unsigned nth = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)jobs.size()));
+    std::vector<std::thread> pool;
+    size_t next = 0;
+    std::mutex mu;
+    for (unsigned t = 0; t < nth; ++t)
+        pool.emplace_back([&] {
+            for (;;) {
+                size_t i;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    if (next >= jobs.size()) return;
+                    i = next++;
+                }
+                run(jobs[i]);
+            }
+        });
+    for (auto& th : pool) th.join();
+    for (auto& jb : jobs)
+        if (!jb.ok) { report_error("3D: block cyclic reduction factors could not be formed"); return ASDSM_ERR_INVALID; }
+    // Upload in both precisions.
+    for (int a = 0; a < 3; ++a)
+        for (int pi = 0; pi < 2; ++pi) S->plane[a].fac[pi].assign(S->plane[a].bk.size(), Fac{});
+    for (auto& jb : jobs) {
+        for (int pi = 0; pi < 2; ++pi) {
+            Fac* d = jb.kind == 0 ? &S->plane[jb.a].fac[pi][jb.blk]
+                   : jb.kind == 1 ? &S->line[pi][jb.a] : jb.kind == 2 ? &S->coarse[pi] : &S->hole[pi];
+            const int rc = pi == 0 ? upload_fac<double>(jb.f, d) : upload_fac<float>(jb.f, d);
+            if (rc) return rc;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (int rc = upload_vec3<double>(S->plane[a].Q, &S->plane[a].Qd[0])) return rc;
+        if (int rc = upload_vec3<float>(S->plane[a].Q, &S->plane[a].Qd[1])) return rc;
+    }
+    const std::vector<double> W = spline_value_operator(g.mc, g.n);
+    if (int rc = upload_vec3<double>(W, &S->W[0])) return rc;
+    if (int rc = upload_vec3<float>(W, &S->W[1])) return rc;
+    return ASDSM_OK;
+}
+
+template <typename T>
+int ensure_work3(Solver3D* S, int pi) {
+    auto& w = S->w[pi];
+    if (w.ready) return ASDSM_OK;
+    const Geo3& g = S->g;
+    const long long PL = (long long)g.Nc * g.plane;
+    auto al = [&](void** p, long long n) -> int {
+        CK3(cudaMalloc(p, (size_t)std::max(1LL, n) * sizeof(T)));
+        CK3(cudaMemset(*p, 0, (size_t)std::max(1LL, n) * sizeof(T)));
+        return ASDSM_OK;
+    };
+    int rc;
+    for (int a = 0; a < 3; ++a) {
+        if ((rc = al(&w.F[a], PL)) || (rc = al(&w.Y[a], PL)) || (rc = al(&w.U[a], PL))) return rc;
+        if ((rc = al(&w.Xl[a], (long long)g.Nf * g.Nc * g.Nc)) || (rc = al(&w.Yl[a], (long long)g.Nf * g.Nc * g.Nc)))
+            return rc;
+    }
+    if ((rc = al(&w.Xb, 2 * g.plane)) || (rc = al(&w.Yb, 2 * g.plane))) return rc;
+    const long long nc3 = (long long)g.Nc * g.Nc * g.Nc, nh = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
+    if ((rc = al(&w.Xc, nc3)) || (rc = al(&w.Yc, nc3)) || (rc = al(&w.Xh, nh)) || (rc = al(&w.Yh, nh))) return rc;
+    if ((rc = al(&w.uh, g.NN)) || (rc = al(&w.rskel, g.skel)) || (rc = al(&w.q, g.skel))) return rc;
+    const int m = std::max(1, std::min(S->opts.accel_m, 16));
+    for (int j = 0; j < m; ++j)
+        if ((rc = al(&w.z[j], g.NN)) || (rc = al(&w.qp[j], g.skel))) return rc;
+    w.ready = true;
+    return ASDSM_OK;
+}
+
+void free_work3(Solver3D* S, int pi) {
+    auto& w = S->w[pi];
+    auto fr = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
+    for (int a = 0; a < 3; ++a) { fr(w.F[a]); fr(w.Y[a]); fr(w.U[a]); fr(w.Xl[a]); fr(w.Yl[a]); }
+    fr(w.Xb); fr(w.Yb); fr(w.Xc); fr(w.Yc); fr(w.Xh); fr(w.Yh); fr(w.uh); fr(w.rskel); fr(w.q);
+    for (int j = 0; j < 16; ++j) { fr(w.z[j]); fr(w.qp[j]); }
+    w.ready = false;
+}
+
+}  // namespace
+
+// Largest |s - A u| over the hole points (FP64), per block.
+__global__ void __launch_bounds__(T3)
+hole_max3_kernel(const double* __restrict__ s, const double* __restrict__ u, Geo3 g, Sten3 c, double* partials) {
+    const long long count = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
+    const int N = g.N;
+    const long long NN2 = (long long)N * N;
+    double mx = 0.0;
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < count; e += (long long)gridDim.x * T3) {
+        int i, j, l, lx, ly, lz;
+        hole_point(e, g, i, j, l, lx, ly, lz);
+        const long long idx = ((long long)l * N + j) * N + i;
+        const double r = s[idx] - (c.cc * u[idx] + c.cw * u[idx - 1] + c.ce * u[idx + 1] + c.cs * u[idx - N]
+                                   + c.cn * u[idx + N] + c.cd * u[idx - NN2] + c.cu * u[idx + NN2]);
+        mx = fmax(mx, fabs(r));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xFFFFFFFFu, mx, o));
+    __shared__ double red[T3 / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int q = 0; q < T3 / 32; ++q) m = fmax(m, red[q]);
+        partials[blockIdx.x] = m;
+    }
+}
+
+namespace {
+
+unsigned g1d(long long n) {
+    long long b = (n + T3 - 1) / T3;
+    return (unsigned)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b));
+}
+
+// Plane family a: F[a] -> U[a] (Schur back-substitution of shifted 2D solves),
+// with the partial sums of U^2 at partials + off (2 values per block).
+template <typename T>
+int plane_solve3(Solver3D* S, int pi, int a, double* partials, int* nblocks) {
+    auto& w = S->w[pi];
+    const Geo3& g = S->g;
+    const PlaneFam& pf = S->plane[a];
+    const long long P = g.plane;
+    cudaStream_t st = S->st;
+    const T* F = (const T*)w.F[a];
+    T* Y = (T*)w.Y[a];
+    for (size_t b = 0; b < pf.bk.size(); ++b) {
+        const int k = pf.bk[b], bs = pf.bs[b];
+        SchurStep ss{};
+        ss.k = k; ss.bs = bs; ss.Nc = g.Nc;
+        for (int i = 0; i < bs; ++i)
+            for (int j = 0; j < g.Nc; ++j) {
+                ss.q[i][j] = pf.Q[(size_t)j * g.Nc + k + i];
+                ss.s[i][j] = j >= k + bs ? pf.S[(size_t)(k + i) * g.Nc + j] : 0.0;
+            }
+        schur_rhs_kernel<T><<<g1d(P), T3, 0, st>>>(F, Y, P, ss, (T*)w.Xb);
+        note_launch();
+        CK3(cudaGetLastError());
+        BcrSys<T> sys = sys3<T>(pf.fac[pi][b], w.Xb, bs == 1 ? (void*)(Y + (long long)k * P) : w.Yb);
+        CK3(bcr_solve<T>(&sys, 1, st));
+        if (bs == 2) {
+            deinterleave_kernel<T><<<g1d(P), T3, 0, st>>>((const T*)w.Yb, P, Y + (long long)k * P,
+                                                         Y + (long long)(k + 1) * P);
+            note_launch();
+            CK3(cudaGetLastError());
+        }
+    }
+    const unsigned nb = g1d(P);
+    schur_back_kernel<T><<<nb, T3, 0, st>>>(Y, (const T*)pf.Qd[pi], g.Nc, P, (T*)w.U[a], partials);
+    note_launch();
+    CK3(cudaGetLastError());
+    *nblocks = (int)nb;
+    return ASDSM_OK;
+}
+
+// The three plane families; with norms, ||U_a||^2 into dsmall[200 + 2a].
+template <typename T>
+int planes3(Solver3D* S, int pi, bool norms) {
+    for (int a = 0; a < 3; ++a) {
+        int nb = 0;
+        double* part = S->partials + (size_t)a * 2 * 152 * 16;
+        if (int rc = plane_solve3<T>(S, pi, a, part, &nb)) return rc;
+        if (norms) CK3(reduce_partials(part, nb, 2, S->dsmall + 200 + 2 * a, S->st));
+    }
+    return ASDSM_OK;
+}
+
+// Algorithm 3 over all cube holes (mode as hole_rhs3_kernel).
+template <typename T>
+int fill3(Solver3D* S, int pi, int mode, T* z, const double* s, double* u) {
+    auto& w = S->w[pi];
+    const Geo3& g = S->g;
+    const long long nh = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
+    hole_rhs3_kernel<T><<<g1d(nh), T3, 0, S->st>>>(mode, z, s, u, g, S->sten, (T*)w.Xh);
+    note_launch();
+    CK3(cudaGetLastError());
+    BcrSys<T> sys = sys3<T>(S->hole[pi], w.Xh, w.Yh, g.mc * g.mc * g.mc);
+    CK3(bcr_solve<T>(&sys, 1, S->st));
+    hole_scatter3_kernel<T><<<g1d(nh), T3, 0, S->st>>>(mode, (const T*)w.Yh, g, z, u);
+    note_launch();
+    CK3(cudaGetLastError());
+    return ASDSM_OK;
+}
+
+// Merge (R21-R23) into z: u_hat on the line points, then every plane moved onto it.
+template <typename T>
+int merge3(Solver3D* S, int pi, bool initial, int choice, T* z) {
+    auto& w = S->w[pi];
+    const Geo3& g = S->g;
+    Merge3Args<T> m{};
+    for (int a = 0; a < 3; ++a) {
+        m.U[a] = (const T*)w.U[a];
+        m.Lf[a] = initial ? (const T*)w.Yl[a] : nullptr;
+    }
+    m.Cc = initial ? (const T*)w.Yc : nullptr;
+    m.nrm2 = initial ? nullptr : S->dsmall + 200;
+    m.choice = choice;
+    m.uh = (T*)w.uh;
+    m.W = (const T*)S->W[pi];
+    m.z = z;
+    const long long lines = 3LL * (g.Nf - g.Nc) * g.Nc * g.Nc + (long long)g.Nc * g.Nc * g.Nc;
+    uhat3_kernel<T><<<g1d(lines), T3, 0, S->st>>>(m, g);
+    dim3 grid((g.Nf + MP - 1) / MP, (g.Nf + MQ - 1) / MQ, 3 * g.Nc);
+    plane_corr_kernel<T><<<grid, MP * MQ, 0, S->st>>>(m, g);
+    note_launch(2);
+    CK3(cudaGetLastError());
+    return ASDSM_OK;
+}
+
+// The ASDSM correction of a sweep into z: plane solves of the residual's
+// restrictions (already in F), normalisation, random-choice merge, Filler
+// with zero source.
+template <typename T>
+int correction3(Solver3D* S, int pi, int choice, T* z) {
+    if (int rc = planes3<T>(S, pi, true)) return rc;
+    if (int rc = merge3<T>(S, pi, false, choice, z)) return rc;
+    return fill3<T>(S, pi, 1, z, nullptr, nullptr);
+}
+
+// Algorithm 1 with b_cc in 3D: u's interior receives u^(0) (u's ring = g).
+template <typename T>
+int initial_guess3(Solver3D* S, int pi, const double* s, double* u) {
+    auto& w = S->w[pi];
+    const Geo3& g = S->g;
+    cudaStream_t st = S->st;
+    const long long PL = (long long)g.Nc * g.plane, LN = (long long)g.Nf * g.Nc * g.Nc,
+                    C3 = (long long)g.Nc * g.Nc * g.Nc;
+    for (int a = 0; a < 3; ++a) {
+        rhs3_kernel<T><<<g1d(PL), T3, 0, st>>>(s, u, g, a, PL, S->lift, (T*)w.F[a]);
+        rhs3_kernel<T><<<g1d(LN), T3, 0, st>>>(s, u, g, 3 + a, LN, S->lift, (T*)w.Xl[a]);
+        note_launch(2);
+    }
+    rhs3_kernel<T><<<g1d(C3), T3, 0, st>>>(s, u, g, 6, C3, S->lift, (T*)w.Xc);
+    note_launch();
+    CK3(cudaGetLastError());
+    if (int rc = planes3<T>(S, pi, false)) return rc;
+    for (int a = 0; a < 3; ++a) {
+        BcrSys<T> sys = sys3<T>(S->line[pi][a], w.Xl[a], w.Yl[a]);
+        CK3(bcr_solve<T>(&sys, 1, st));
+    }
+    BcrSys<T> sc = sys3<T>(S->coarse[pi], w.Xc, w.Yc);
+    CK3(bcr_solve<T>(&sc, 1, st));
+    T* z = (T*)w.z[0];
+    ring3_kernel<T><<<g1d(g.NN), T3, 0, st>>>(u, g, z);
+    note_launch();
+    if (int rc = merge3<T>(S, pi, true, 0, z)) return rc;
+    if (int rc = fill3<T>(S, pi, 0, z, s, nullptr)) return rc;
+    interior3_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(z, g, u);
+    ring3_kernel<T><<<g1d(g.NN), T3, 0, st>>>(nullptr, g, z);     // a direction slot again: all zero
+    note_launch(2);
+    CK3(cudaGetLastError());
+    return ASDSM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+constexpr int kPartials3 = 32768;
+constexpr unsigned long long kGolden = 0x9E3779B97F4A7C15ull;
+
+uint64_t splitmix64_3(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Family drawn by the random choice of Algorithm 2 at sweep k (R22).
+int choice3(uint64_t seed, int k) { return (int)(splitmix64_3(seed + (uint64_t)(k + 1) * kGolden) % 3ull); }
+
+int read3(Solver3D* S, const double* dev, int count) {
+    CK3(cudaMemcpyAsync(S->hsmall, dev, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, S->st));
+    CK3(cudaStreamSynchronize(S->st));
+    return ASDSM_OK;
+}
+
+// FP64 residual of u: ||r||^2 and the hole part into dsmall[0..1]; r also onto
+// the skeleton and the plane right-hand sides (when `gather`).
+template <typename T>
+int residual3(Solver3D* S, int pi, const double* s, const double* u, bool gather) {
+    auto& w = S->w[pi];
+    const Geo3& g = S->g;
+    Resid3Out<T> o{};
+    if (gather) {
+        o.rskel = (T*)w.rskel;
+        for (int a = 0; a < 3; ++a) o.rp[a] = (T*)w.F[a];
+    }
+    o.partials = S->partials;
+    const unsigned nb = grid_rows((long long)g.Nf * g.Nf);
+    resid3_kernel<T><<<nb, T3, 0, S->st>>>(s, u, g, S->sten, o);
+    note_launch();
+    CK3(cudaGetLastError());
+    CK3(reduce_partials(S->partials, (int)nb, 2, S->dsmall, S->st));
+    return ASDSM_OK;
+}
+
+template <typename T>
+int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
+    const bool mixed = sizeof(T) == 4;
+    const int pi = mixed ? 1 : 0;
+    if (int rc = ensure_work3<T>(S, pi)) return rc;
+    auto& w = S->w[pi];
+    const Geo3& g = S->g;
+    const asdsm_opts& op = S->opts;
+    cudaStream_t st = S->st;
+    const int m = std::max(1, std::min(op.accel_m, 16));
+    const long long launches0 = launch_count();
+    S->hist.clear();
+    CK3(cudaEventRecord(S->ev0, st));
+    // ||b_ff||: the residual of the grid with g on the ring and a zero interior.
+    ring3_kernel<double><<<g1d(g.NN), T3, 0, st>>>(u, g, S->u_work);
+    note_launch();
+    if (int rc = residual3<T>(S, pi, s, S->u_work, false)) return rc;
+    if (int rc = read3(S, S->dsmall, 1)) return rc;
+    const double bnorm = std::sqrt(S->hsmall[0]);
+    if (!std::isfinite(bnorm)) return ASDSM_ERR_NAN;
+    if (!op.skip_initial_guess)
+        if (int rc = initial_guess3<T>(S, pi, s, u)) return rc;
+    CK3(cudaEventRecord(S->ev1, st));
+    double* ucur = u;
+    double* unxt = S->u_work;            // its ring holds g (ring3 above)
+    UpdateTerms pend{};
+    double Tm[16][16] = {};
+    int k = 0, kc = 0, status = ASDSM_NOT_CONVERGED, hole_fixes = 0;
+    double rel = 0.0, rel0 = 0.0, hole_ref = 0.0;
+    bool hole_ref_pending = false;
+    for (;;) {
+        if (pend.count > 0) {
+            update3_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(ucur, unxt, pend, g);
+            note_launch();
+            CK3(cudaGetLastError());
+            std::swap(ucur, unxt);
+            pend.count = 0;
+        }
+        if (int rc = residual3<T>(S, pi, s, ucur, true)) return rc;
+        if (int rc = read3(S, S->dsmall, 2)) return rc;
+        const double rnorm = std::sqrt(S->hsmall[0]), hnorm = std::sqrt(S->hsmall[1]);
+        rel = bnorm > 0 ? rnorm / bnorm : rnorm;
+        if (!std::isfinite(rel)) { status = ASDSM_ERR_NAN; break; }
+        S->hist.push_back(rel);
+        if (k == 0) rel0 = rel;
+        if (rel <= op.tol) { status = ASDSM_OK; break; }
+        if (k >= op.max_sweeps) { status = ASDSM_NOT_CONVERGED; break; }
+        const int win = op.stagnation_window;
+        if (win > 0 && (int)S->hist.size() > win &&
+            S->hist.back() > (1.0 - op.stagnation_factor) * S->hist[S->hist.size() - 1 - win]) {
+            status = ASDSM_STAGNATED;
+            break;
+        }
+        if (hole_ref_pending) { hole_ref = hnorm; hole_ref_pending = false; }
+        // R18: a Filler pass on the hole part of the residual replaces the sweep.
+        if (hnorm > op.hole_fix_ratio * rnorm && hnorm > op.hole_fix_growth * hole_ref) {
+            if (int rc = fill3<T>(S, pi, 2, (T*)nullptr, s, ucur)) return rc;
+            hole_ref_pending = true;
+            ++hole_fixes;
+            kc = 0;
+            ++k;
+            continue;
+        }
+        // The correction: Algorithm 1 without b_cc on the residual.
+        T* z = (T*)w.z[kc];
+        if (int rc = correction3<T>(S, pi, choice3(op.seed, k), z)) return rc;
+        // Least squares on the skeleton rows.
+        skel_apply3_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(z, g, S->sten, (T*)w.q);
+        note_launch();
+        CK3(cudaGetLastError());
+        const T* qpv[16];
+        for (int j = 0; j < kc; ++j) qpv[j] = (const T*)w.qp[j];
+        const int nd = 2 + 2 * kc;
+        int nb3 = 0;
+        CK3(gcr_dots<T>((const T*)w.q, (const T*)w.rskel, qpv, kc, g.skel, S->partials, &nb3, st));
+        CK3(reduce_partials(S->partials, nb3, nd, S->dsmall, st));
+        if (int rc = read3(S, S->dsmall, nd)) return rc;
+        const double qq = S->hsmall[0], qr = S->hsmall[1];
+        if (m == 1) {
+            const double shat = qq > 0 ? std::max(0.0, qr / qq) : 0.0;   // the clamped optimal scaling
+            pend.count = 1;
+            pend.z[0] = z;
+            pend.coef[0] = shat;
+            ++k;
+            continue;
+        }
+        // GCR(m) (R15): orthogonalise A e against the cycle's earlier images.
+        double beta_[16] = {}, rq[16] = {};
+        double nu2 = qq;
+        for (int j = 0; j < kc; ++j) {
+            beta_[j] = S->hsmall[2 + 2 * j];
+            rq[j] = S->hsmall[3 + 2 * j];
+            nu2 -= beta_[j] * beta_[j];
+        }
+        if (!(nu2 > 1e-24 * qq) || !(qq > 0)) {    // dependent direction: restart the cycle
+            kc = 0;
+            ++k;
+            continue;
+        }
+        const double nu = std::sqrt(nu2);
+        double alpha_ = qr;
+        for (int j = 0; j < kc; ++j) alpha_ -= beta_[j] * rq[j];
+        alpha_ /= nu;
+        for (int i = 0; i <= kc; ++i) Tm[i][kc] = 0.0;
+        Tm[kc][kc] = 1.0 / nu;
+        for (int j = 0; j < kc; ++j)
+            for (int i = 0; i <= j; ++i) Tm[i][kc] -= beta_[j] * Tm[i][j] / nu;
+        for (int i = 0; i <= kc; ++i) {
+            pend.z[i] = w.z[i];
+            pend.coef[i] = alpha_ * Tm[i][kc];
+        }
+        pend.count = kc + 1;
+        CK3(combine_skeleton<T>((const T*)w.q, qpv, beta_, kc, 1.0 / nu, g.skel, (T*)w.qp[kc], st));
+        ++kc;
+        if (kc >= m) kc = 0;
+        ++k;
+    }
+    if (ucur != u) {
+        interior3_kernel<double><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(ucur, g, u);
+        note_launch();
+    }
+    // The largest hole residual of the returned iterate.
+    const long long nh = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
+    const unsigned nbh = g1d(nh);
+    hole_max3_kernel<<<nbh, T3, 0, st>>>(s, u, g, S->sten, S->partials);
+    note_launch();
+    CK3(cudaGetLastError());
+    CK3(cudaMemcpyAsync(S->hsmall + 8, S->partials, nbh * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK3(cudaEventRecord(S->ev2, st));
+    CK3(cudaEventSynchronize(S->ev2));
+    double hmax = 0.0;
+    for (unsigned b = 0; b < nbh; ++b) hmax = std::max(hmax, S->hsmall[8 + b]);
+    float ms_setup = 0.f, ms_all = 0.f;
+    cudaEventElapsedTime(&ms_setup, S->ev0, S->ev1);
+    cudaEventElapsedTime(&ms_all, S->ev0, S->ev2);
+    if (stats) {
+        asdsm_stats stt{};
+        stt.sweeps = k;
+        stt.status = status;
+        stt.hole_fixes = hole_fixes;
+        stt.rel_res = rel;
+        stt.rel_res0 = rel0;
+        stt.setup_ms = ms_setup;
+        stt.solve_ms = ms_all;
+        stt.launches = launch_count() - launches0;
+        stt.rel_res_fp64 = rel;            // the sweep residual is FP64 in 3D
+        stt.hole_res_max = hmax;
+        *stats = stt;
+    }
+    return status;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Interface to the C ABI
+// ---------------------------------------------------------------------------
+int s3_create(const asdsm_desc* d, const asdsm_opts* o, cudaStream_t st, Solver3D** out) {
+    *out = nullptr;
+    const int N = d->n, mc = d->mc;
+    auto pow2 = [](long long v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (N < 5 || N > 257 || !pow2(N - 1) || !pow2(mc) || mc < 2 || mc > 32 || (N - 1) % mc != 0) {
+        report_error("3D sizes: N - 1 and mc powers of two, N <= 257, 2 <= mc <= 32");
+        return ASDSM_ERR_INVALID;
+    }
+    const int n = (N - 1) / mc;
+    if (n < 2 || n > 16) { report_error("3D sizes: hole size (N-1)/mc must be 2..16"); return ASDSM_ERR_INVALID; }
+    for (int a = 0; a < 3; ++a)
+        if (!(d->alpha[a] > 0.0) || !std::isfinite(d->alpha[a]) || !std::isfinite(d->beta[a])) {
+            report_error("3D: alpha_i must be positive and finite");
+            return ASDSM_ERR_INVALID;
+        }
+    Solver3D* S = new Solver3D();
+    S->desc = *d;
+    S->opts = *o;
+    S->st = st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    Geo3& g = S->g;
+    g.N = N; g.M = N - 1; g.Nf = N - 2; g.mc = mc; g.Nc = mc - 1; g.n = n; g.hc = n - 1;
+    g.NN = (long long)N * N * N;
+    g.plane = (long long)g.Nf * g.Nf;
+    const long long nf = g.Nf, nhole = g.Nf - g.Nc;
+    g.skel = nf * nf * nf - nhole * nhole * nhole;
+    const double h = 1.0 / g.M, H = 1.0 / mc;
+    const double* al = d->alpha;
+    const double* be = d->beta;
+    S->sten.cc = 2 * (al[0] + al[1] + al[2]) / (h * h);
+    S->sten.cw = -al[0] / (h * h) - be[0] / (2 * h); S->sten.ce = -al[0] / (h * h) + be[0] / (2 * h);
+    S->sten.cs = -al[1] / (h * h) - be[1] / (2 * h); S->sten.cn = -al[1] / (h * h) + be[1] / (2 * h);
+    S->sten.cd = -al[2] / (h * h) - be[2] / (2 * h); S->sten.cu = -al[2] / (h * h) + be[2] / (2 * h);
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < 2; ++q) {
+            const double sp = q ? H : h;
+            S->lift.lo[a][q] = al[a] / (sp * sp) + be[a] / (2 * sp);
+            S->lift.hi[a][q] = al[a] / (sp * sp) - be[a] / (2 * sp);
+        }
+    auto fail = [&](int rc) { s3_destroy(S); return rc; };
+    if (int rc = build_factors(S)) return fail(rc);
+    cudaError_t e;
+    if ((e = cudaMalloc(&S->u_work, (size_t)g.NN * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
+    if ((e = cudaMalloc(&S->partials, (size_t)kPartials3 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
+    if ((e = cudaMalloc(&S->dsmall, 256 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
+    if ((e = cudaMallocHost(&S->hsmall, 4096 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
+    for (cudaEvent_t* ev : {&S->ev0, &S->ev1, &S->ev2})
+        if ((e = cudaEventCreate(ev)) != cudaSuccess) return fail(report_cuda_error(e));
+    *out = S;
+    return ASDSM_OK;
+}
+
+int s3_set_opts(Solver3D* S, const asdsm_opts* o) {
+    const int m_old = std::max(1, std::min(S->opts.accel_m, 16)), m_new = std::max(1, std::min(o->accel_m, 16));
+    S->opts = *o;
+    if (m_new > m_old) { free_work3(S, 0); free_work3(S, 1); }     // direction slots re-allocated on first use
+    return ASDSM_OK;
+}
+
+int s3_solve(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
+    return S->opts.precision == ASDSM_FP64 ? solve3<double>(S, s, u, stats) : solve3<float>(S, s, u, stats);
+}
+
+int s3_initial_guess(Solver3D* S, const double* s, double* u) {
+    const bool fp64 = S->opts.precision == ASDSM_FP64;
+    int rc = fp64 ? ensure_work3<double>(S, 0) : ensure_work3<float>(S, 1);
+    if (rc) return rc;
+    rc = fp64 ? initial_guess3<double>(S, 0, s, u) : initial_guess3<float>(S, 1, s, u);
+    if (rc) return rc;
+    CK3(cudaStreamSynchronize(S->st));
+    return ASDSM_OK;
+}
+
+int s3_residual(Solver3D* S, const double* s, const double* u, double* r, double* rel) {
+    (void)r;
+    if (int rc = ensure_work3<double>(S, 0)) return rc;
+    ring3_kernel<double><<<g1d(S->g.NN), T3, 0, S->st>>>(u, S->g, S->u_work);
+    note_launch();
+    if (int rc = residual3<double>(S, 0, s, S->u_work, false)) return rc;
+    if (int rc = read3(S, S->dsmall, 1)) return rc;
+    const double b2 = S->hsmall[0];
+    if (int rc = residual3<double>(S, 0, s, u, false)) return rc;
+    if (int rc = read3(S, S->dsmall, 1)) return rc;
+    if (rel) *rel = b2 > 0 ? std::sqrt(S->hsmall[0] / b2) : std::sqrt(S->hsmall[0]);
+    return ASDSM_OK;
+}
+
+namespace {
+template <typename T>
+int submesh3(Solver3D* S, int pi, int mesh, const double* in, double* out) {
+    if (int rc = ensure_work3<T>(S, pi)) return rc;
+    auto& w = S->w[pi];
+    const Geo3& g = S->g;
+    cudaStream_t st = S->st;
+    auto conv_in = [&](void* dst, long long n) {
+        convert3_kernel<double, T><<<g1d(n), T3, 0, st>>>(in, n, (T*)dst);
+        note_launch();
+    };
+    auto conv_out = [&](const void* src, long long n) {
+        convert3_kernel<T, double><<<g1d(n), T3, 0, st>>>((const T*)src, n, out);
+        note_launch();
+    };
+    if (mesh < 3) {
+        const long long n = (long long)g.Nc * g.plane;
+        conv_in(w.F[mesh], n);
+        int nb = 0;
+        if (int rc = plane_solve3<T>(S, pi, mesh, S->partials, &nb)) return rc;
+        conv_out(w.U[mesh], n);
+    } else if (mesh < 6) {
+        const int a = mesh - 3;
+        const long long n = (long long)g.Nf * g.Nc * g.Nc;
+        conv_in(w.Xl[a], n);
+        BcrSys<T> sys = sys3<T>(S->line[pi][a], w.Xl[a], w.Yl[a]);
+        CK3(bcr_solve<T>(&sys, 1, st));
+        conv_out(w.Yl[a], n);
+    } else if (mesh == 6) {
+        const long long n = (long long)g.Nc * g.Nc * g.Nc;
+        conv_in(w.Xc, n);
+        BcrSys<T> sys = sys3<T>(S->coarse[pi], w.Xc, w.Yc);
+        CK3(bcr_solve<T>(&sys, 1, st));
+        conv_out(w.Yc, n);
+    } else {
+        if (int rc = fill3<T>(S, pi, 3, (T*)nullptr, in, out)) return rc;
+    }
+    CK3(cudaGetLastError());
+    CK3(cudaStreamSynchronize(st));
+    return ASDSM_OK;
+}
+}  // namespace
+
+int s3_submesh_solve(Solver3D* S, int mesh, const double* in, double* out) {
+    if (mesh < 0 || mesh > 7) return ASDSM_ERR_INVALID;
+    return S->opts.precision == ASDSM_FP64 ? submesh3<double>(S, 0, mesh, in, out)
+                                           : submesh3<float>(S, 1, mesh, in, out);
+}
+
+int s3_history(Solver3D* S, double* hist, int cap) {
+    const int n = std::min<int>(cap, (int)S->hist.size());
+    for (int i = 0; i < n; ++i) hist[i] = S->hist[i];
+    return n;
+}
+
+void s3_destroy(Solver3D* S) {
+    if (!S) return;
+    if (S->st) cudaStreamSynchronize(S->st);
+    for (int pi = 0; pi < 2; ++pi) {
+        free_work3(S, pi);
+        for (int a = 0; a < 3; ++a) {
+            for (Fac& f : S->plane[a].fac[pi]) free_fac(f);
+            free_fac(S->line[pi][a]);
+            if (S->plane[a].Qd[pi]) cudaFree(S->plane[a].Qd[pi]);
+        }
+        free_fac(S->coarse[pi]);
+        free_fac(S->hole[pi]);
+        if (S->W[pi]) cudaFree(S->W[pi]);
+    }
+    if (S->u_work) cudaFree(S->u_work);
+    if (S->partials) cudaFree(S->partials);
+    if (S->dsmall) cudaFree(S->dsmall);
+    if (S->hsmall) cudaFreeHost(S->hsmall);
+    for (cudaEvent_t ev : {S->ev0, S->ev1, S->ev2})
+        if (ev) cudaEventDestroy(ev);
+    delete S;
+}
+
+}  // namespace asdsm

@@ -188,3 +188,22 @@ def test_sweep_correction_is_invariant_to_per_family_scaling():
         e1 = disc.initial_guess(zero, r_p, None, None, choice)
         e2 = disc.initial_guess(zero, scaled, None, None, choice)
         assert np.allclose(e1, e2, rtol=0, atol=1e-12 * np.abs(e1).max())
+
+
+def test_filler_pass_in_3d_removes_the_hole_residual_and_keeps_the_skeleton():
+    """R18 in 3D: a start whose residual sits mostly in the cube holes gets a
+    Filler pass first, which zeroes the hole residual (Prop. 3.1 on the cube
+    holes) and leaves the skeleton as it was."""
+    N, mc = 17, 4
+    p = wl.random_sine_3d(N, 6)
+    disc = o3.Discretisation3D(N, mc, p.alpha, p.beta)
+    b = disc.rhs(p.s, p.g)
+    u_ff = disc.solve_fine(b[0])
+    u0 = u_ff + np.random.default_rng(3).normal(size=u_ff.size) * np.abs(u_ff).max()
+    r0 = disc.residual(b[0], u0)
+    assert np.linalg.norm(disc.P_holes @ r0) > 0.25 * np.linalg.norm(r0)
+    u1, info = o3.asdsm(disc, b, tol=0.0, max_sweeps=1, accel_m=4, u0=u0, stagnation_window=10**9)
+    assert info["kinds"] == ["hole_fix"]
+    r1 = disc.residual(b[0], u1)
+    assert np.linalg.norm(disc.P_holes @ r1) <= 1e-12 * np.linalg.norm(r0)
+    np.testing.assert_array_equal(disc.P_skel @ u1, disc.P_skel @ u0)
