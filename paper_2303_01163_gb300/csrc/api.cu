@@ -1724,9 +1724,13 @@ int asdsm_correction(asdsm_handle* h, const double* s, const double* u, float* r
 
 int asdsm_set_opts(asdsm_handle* h, const asdsm_opts* opts) {
     if (!h || !opts) return ASDSM_ERR_INVALID;
-    if (opts->accel_m < 1 || opts->accel_m > kMaxM) return ASDSM_ERR_INVALID;
     if (opts->precision != ASDSM_FP64 && opts->precision != ASDSM_MIXED) return ASDSM_ERR_INVALID;
-    if (h->s3) { h->opts = *opts; return s3_set_opts(h->s3, opts); }
+    if (h->s3) {
+        if (int rc = s3_set_opts(h->s3, opts)) return rc;
+        h->opts = *opts;
+        return ASDSM_OK;
+    }
+    if (opts->accel_m < 1 || opts->accel_m > kMaxM) return ASDSM_ERR_INVALID;
     h->opts = *opts;
     return ASDSM_OK;
 }

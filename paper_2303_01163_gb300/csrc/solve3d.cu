@@ -135,7 +135,7 @@ update3_kernel(const double* __restrict__ u_in, double* __restrict__ u_out, Upda
 
 template <typename T>
 struct Resid3Out {
-    T* rskel;            // [skel]
+    double* rskel;       // [skel], FP64
     T* rp[3];            // plane right-hand sides per family
     double* partials;    // [grid][2]
 };
@@ -158,7 +158,7 @@ resid3_kernel(const double* __restrict__ s, const double* __restrict__ u, Geo3 g
             const bool ci = i % n == 0, cj = j % n == 0, cl = l % n == 0;
             if (!(ci || cj || cl)) { sh += r * r; continue; }
             const T rt = (T)r;
-            if (o.rskel) o.rskel[skel3_index(i, j, l, g)] = rt;
+            if (o.rskel) o.rskel[skel3_index(i, j, l, g)] = r;
             const long long P = g.plane;
             if (ci && o.rp[0]) o.rp[0][(long long)(i / n - 1) * P + (long long)(l - 1) * Nf + (j - 1)] = rt;
             if (cj && o.rp[1]) o.rp[1][(long long)(j / n - 1) * P + (long long)(l - 1) * Nf + (i - 1)] = rt;
@@ -238,6 +238,8 @@ rhs3_kernel(const double* __restrict__ s, const double* __restrict__ u, Geo3 g, 
 //   back-transform U_j = sum_k Q[j][k] Y_k with the partial sums of U^2.
 // ---------------------------------------------------------------------------
 constexpr int kMaxNc3 = 31;     // coarse points per axis (mc <= 32)
+constexpr int kMaxM3 = 1024;    // directions kept by the 3D GCR (restart length)
+constexpr int kCheck3 = 16;     // sweeps between true residuals (hole-residual checks, R18)
 
 struct SchurStep {
     double q[2][kMaxNc3];       // Q[j][k+i]
@@ -564,6 +566,128 @@ __global__ void __launch_bounds__(T3) convert3_kernel(const Ts* __restrict__ a, 
 }
 
 // ---------------------------------------------------------------------------
+// GCR with a long memory on the skeleton (R15 with the residual tracked on the
+// skeleton rows between true residuals; by Prop. 3.1 A e vanishes in the holes).
+//   dots:    for the new image q and the tracked residual r (FP64):
+//            out = [<q,q>, <q,r>, <r,r>, <q,V_j> (j < k), <r,V_j> (j < k)]
+//            partials [column][chunk], then summed per column in chunk order;
+//   combine: V_k = (q - sum_j beta_j V_j) * inv_nu,  r -= alpha V_k, with the
+//            partial sums of the new r^2;
+//   planes:  the plane families' right-hand sides from the tracked residual;
+//   update:  u += sum_j c_j Z_j over the interior (FP64 accumulation).
+// ---------------------------------------------------------------------------
+constexpr int DK_CHUNKS = 64;      // skeleton chunks of the many-vector dots
+constexpr int DK_VEC = 8;          // vectors per CTA
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+dots_many_kernel(const T* __restrict__ q, const double* __restrict__ r, const T* __restrict__ V, long long n,
+                 long long vstride, int k, double* __restrict__ partials) {
+    __shared__ double red[T3 / 32][2 * DK_VEC + 3];
+    const int chunk = blockIdx.x, j0 = blockIdx.y * DK_VEC;
+    const long long len = (n + DK_CHUNKS - 1) / DK_CHUNKS, e0 = chunk * len, e1 = min(n, e0 + len);
+    const int nv = min(DK_VEC, k - j0);
+    double acc[2 * DK_VEC + 3];
+#pragma unroll
+    for (int t = 0; t < 2 * DK_VEC + 3; ++t) acc[t] = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += T3) {
+        const double qv = (double)q[e], rv = r[e];
+        if (blockIdx.y == 0) { acc[0] += qv * qv; acc[1] += qv * rv; acc[2] += rv * rv; }
+#pragma unroll
+        for (int t = 0; t < DK_VEC; ++t)
+            if (t < nv) {
+                const double v = (double)V[(long long)(j0 + t) * vstride + e];
+                acc[3 + t] += qv * v;
+                acc[3 + DK_VEC + t] += rv * v;
+            }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 2 * DK_VEC + 3; ++t) {
+        double v = acc[t];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0) red[w][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * DK_VEC + 3) {
+        const int t = threadIdx.x;
+        double v = 0.0;
+        for (int q2 = 0; q2 < T3 / 32; ++q2) v += red[q2][t];
+        // column layout: 0, 1, 2 then <q,V_j> at 3 + j, <r,V_j> at 3 + k + j
+        int col = -1;
+        if (t < 3) col = blockIdx.y == 0 ? t : -1;
+        else if (t < 3 + DK_VEC) col = (t - 3 < nv) ? 3 + j0 + (t - 3) : -1;
+        else col = (t - 3 - DK_VEC < nv) ? 3 + k + j0 + (t - 3 - DK_VEC) : -1;
+        if (col >= 0) partials[(long long)col * DK_CHUNKS + chunk] = v;
+    }
+}
+
+__global__ void __launch_bounds__(32) sum_chunks_kernel(const double* __restrict__ partials, int ncols,
+                                                        double* __restrict__ out) {
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    if (col >= ncols) return;
+    double v = 0.0;
+    for (int c = 0; c < DK_CHUNKS; ++c) v += partials[(long long)col * DK_CHUNKS + c];
+    out[col] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+combine_many_kernel(const T* __restrict__ q, T* __restrict__ V, long long n, long long vstride, int k,
+                    const double* __restrict__ beta, double inv_nu, double alpha, double* __restrict__ r,
+                    double* __restrict__ partials) {
+    double rr = 0.0;
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < n; e += (long long)gridDim.x * T3) {
+        double v = (double)q[e];
+        for (int j = 0; j < k; ++j) v -= beta[j] * (double)V[(long long)j * vstride + e];
+        const T vk = (T)(v * inv_nu);
+        V[(long long)k * vstride + e] = vk;
+        const double rn = r[e] - alpha * (double)vk;
+        r[e] = rn;
+        rr += rn * rn;
+    }
+    block_sum_pair(rr, 0.0, partials);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T3) planes_from_skel_kernel(const double* __restrict__ rs, Geo3 g, T* F0, T* F1,
+                                                              T* F2) {
+    const int Nf = g.Nf, n = g.n;
+    const long long P = g.plane;
+    for (long long row = blockIdx.x; row < (long long)Nf * Nf; row += gridDim.x) {
+        const int j = (int)(row % Nf) + 1, l = (int)(row / Nf) + 1;
+        const bool row_coarse = j % n == 0 || l % n == 0;
+        for (int i = 1 + threadIdx.x; i <= Nf; i += T3) {
+            if (!row_coarse && i % n != 0) continue;
+            const T rt = (T)rs[skel3_index(i, j, l, g)];
+            if (i % n == 0) F0[(long long)(i / n - 1) * P + (long long)(l - 1) * Nf + (j - 1)] = rt;
+            if (j % n == 0) F1[(long long)(j / n - 1) * P + (long long)(l - 1) * Nf + (i - 1)] = rt;
+            if (l % n == 0) F2[(long long)(l / n - 1) * P + (long long)(j - 1) * Nf + (i - 1)] = rt;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T3)
+update_many_kernel(double* __restrict__ u, const T* __restrict__ Z, long long zstride, int k,
+                   const double* __restrict__ c, Geo3 g) {
+    __shared__ double cs[1024];
+    for (int j = threadIdx.x; j < k && j < 1024; j += T3) cs[j] = c[j];
+    __syncthreads();
+    const int N = g.N, Nf = g.Nf;
+    for (long long row = blockIdx.x; row < (long long)Nf * Nf; row += gridDim.x) {
+        const int j = (int)(row % Nf) + 1, l = (int)(row / Nf) + 1;
+        const long long base = ((long long)l * N + j) * N;
+        for (int i = 1 + threadIdx.x; i <= N - 2; i += T3) {
+            const long long idx = base + i;
+            double v = 0.0;
+            for (int t = 0; t < k; ++t) v += cs[t] * (double)Z[(long long)t * zstride + idx];
+            u[idx] += v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -672,9 +796,15 @@ struct Solver3D {
         void* Xc = nullptr; void* Yc = nullptr;
         void* Xh = nullptr; void* Yh = nullptr;
         void* uh = nullptr;
-        void* z[16] = {};
-        void* rskel = nullptr; void* q = nullptr; void* qp[16] = {};
+        void* Z = nullptr;               // m directions, [m][N^3] (ring zero)
+        void* V = nullptr;               // their orthonormalised skeleton images, [m][skel]
+        void* q = nullptr;               // the new image A e on the skeleton [skel]
+        double* rs = nullptr;            // tracked residual on the skeleton [skel], FP64
+        int m = 0;
     } w[2];
+    double* dcoef = nullptr;             // [1024] step coefficients / Gram-Schmidt weights
+    double* dsum = nullptr;              // [2*1024 + 3] many-vector dot results
+    double* dpart = nullptr;             // many-vector dot partials [(2*1024 + 3)][DK_CHUNKS]
     double* u_work = nullptr;
     double* partials = nullptr;
     int partials_cap = 0;
@@ -823,10 +953,11 @@ int ensure_work3(Solver3D* S, int pi) {
     if ((rc = al(&w.Xb, 2 * g.plane)) || (rc = al(&w.Yb, 2 * g.plane))) return rc;
     const long long nc3 = (long long)g.Nc * g.Nc * g.Nc, nh = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
     if ((rc = al(&w.Xc, nc3)) || (rc = al(&w.Yc, nc3)) || (rc = al(&w.Xh, nh)) || (rc = al(&w.Yh, nh))) return rc;
-    if ((rc = al(&w.uh, g.NN)) || (rc = al(&w.rskel, g.skel)) || (rc = al(&w.q, g.skel))) return rc;
-    const int m = std::max(1, std::min(S->opts.accel_m, 16));
-    for (int j = 0; j < m; ++j)
-        if ((rc = al(&w.z[j], g.NN)) || (rc = al(&w.qp[j], g.skel))) return rc;
+    const int m = std::max(1, std::min(S->opts.accel_m, kMaxM3));
+    if ((rc = al(&w.uh, g.NN)) || (rc = al(&w.q, g.skel)) || (rc = al(&w.Z, m * g.NN)) || (rc = al(&w.V, m * g.skel)))
+        return rc;
+    CK3(cudaMalloc(&w.rs, (size_t)g.skel * sizeof(double)));
+    w.m = m;
     w.ready = true;
     return ASDSM_OK;
 }
@@ -835,8 +966,9 @@ void free_work3(Solver3D* S, int pi) {
     auto& w = S->w[pi];
     auto fr = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
     for (int a = 0; a < 3; ++a) { fr(w.F[a]); fr(w.Y[a]); fr(w.U[a]); fr(w.Xl[a]); fr(w.Yl[a]); }
-    fr(w.Xb); fr(w.Yb); fr(w.Xc); fr(w.Yc); fr(w.Xh); fr(w.Yh); fr(w.uh); fr(w.rskel); fr(w.q);
-    for (int j = 0; j < 16; ++j) { fr(w.z[j]); fr(w.qp[j]); }
+    fr(w.Xb); fr(w.Yb); fr(w.Xc); fr(w.Yc); fr(w.Xh); fr(w.Yh); fr(w.uh); fr(w.q); fr(w.Z); fr(w.V);
+    if (w.rs) cudaFree(w.rs);
+    w.rs = nullptr;
     w.ready = false;
 }
 
@@ -1002,7 +1134,7 @@ int initial_guess3(Solver3D* S, int pi, const double* s, double* u) {
     }
     BcrSys<T> sc = sys3<T>(S->coarse[pi], w.Xc, w.Yc);
     CK3(bcr_solve<T>(&sc, 1, st));
-    T* z = (T*)w.z[0];
+    T* z = (T*)w.Z;
     ring3_kernel<T><<<g1d(g.NN), T3, 0, st>>>(u, g, z);
     note_launch();
     if (int rc = merge3<T>(S, pi, true, 0, z)) return rc;
@@ -1044,7 +1176,7 @@ int residual3(Solver3D* S, int pi, const double* s, const double* u, bool gather
     const Geo3& g = S->g;
     Resid3Out<T> o{};
     if (gather) {
-        o.rskel = (T*)w.rskel;
+        o.rskel = w.rs;
         for (int a = 0; a < 3; ++a) o.rp[a] = (T*)w.F[a];
     }
     o.partials = S->partials;
@@ -1065,7 +1197,7 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
     const Geo3& g = S->g;
     const asdsm_opts& op = S->opts;
     cudaStream_t st = S->st;
-    const int m = std::max(1, std::min(op.accel_m, 16));
+    const int m = w.m;
     const long long launches0 = launch_count();
     S->hist.clear();
     CK3(cudaEventRecord(S->ev0, st));
@@ -1079,103 +1211,140 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
     if (!op.skip_initial_guess)
         if (int rc = initial_guess3<T>(S, pi, s, u)) return rc;
     CK3(cudaEventRecord(S->ev1, st));
-    double* ucur = u;
-    double* unxt = S->u_work;            // its ring holds g (ring3 above)
-    UpdateTerms pend{};
-    double Tm[16][16] = {};
+    T* Z = (T*)w.Z;
+    T* V = (T*)w.V;
+    std::vector<double> Tm((size_t)m * m, 0.0), c(m, 0.0), c_app(m, 0.0), dc(m, 0.0), beta(m, 0.0), rq(m, 0.0);
+    auto rel_of = [&](double r2) { return bnorm > 0 ? std::sqrt(std::max(r2, 0.0)) / bnorm : std::sqrt(std::max(r2, 0.0)); };
     int k = 0, kc = 0, status = ASDSM_NOT_CONVERGED, hole_fixes = 0;
-    double rel = 0.0, rel0 = 0.0, hole_ref = 0.0;
-    bool hole_ref_pending = false;
+    double rel = 0.0, rel0 = 0.0, hole_ref = 0.0, rh2 = 0.0;
+    bool hole_ref_pending = false, need_true = true;
+    bool last_tracked = false;           // the last history entry is a tracked value of the current iterate
+    bool restart = true;                 // the next true residual starts a new cycle
+    int since_check = 0;                 // sweeps since the last true residual
     for (;;) {
-        if (pend.count > 0) {
-            update3_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(ucur, unxt, pend, g);
-            note_launch();
-            CK3(cudaGetLastError());
-            std::swap(ucur, unxt);
-            pend.count = 0;
+        if (need_true) {
+            // Checkpoint: u receives the part of the cycle's update not applied yet,
+            // then the true FP64 residual replaces the tracked one.
+            if (kc > 0) {
+                for (int i = 0; i < kc; ++i) { dc[i] = c[i] - c_app[i]; c_app[i] = c[i]; }
+                CK3(cudaMemcpyAsync(S->dcoef, dc.data(), (size_t)kc * sizeof(double), cudaMemcpyHostToDevice, st));
+                update_many_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(u, Z, g.NN, kc, S->dcoef, g);
+                note_launch();
+                CK3(cudaGetLastError());
+                CK3(cudaStreamSynchronize(st));      // dcoef is rewritten before the next launch that reads it
+            }
+            if (int rc = residual3<T>(S, pi, s, u, true)) return rc;
+            if (int rc = read3(S, S->dsmall, 2)) return rc;
+            const double rr = S->hsmall[0];
+            rh2 = S->hsmall[1];
+            rel = rel_of(rr);
+            if (last_tracked) S->hist.back() = rel;      // replaces the tracked value of this iterate
+            else S->hist.push_back(rel);
+            last_tracked = false;
+            if (restart) {
+                kc = 0;
+                std::fill(c.begin(), c.end(), 0.0);
+                std::fill(c_app.begin(), c_app.end(), 0.0);
+                restart = false;
+            }
+            since_check = 0;
+            need_true = false;
+            if (!std::isfinite(rel)) { status = ASDSM_ERR_NAN; break; }
+            if (k == 0) rel0 = rel;
+            if (rel <= op.tol) { status = ASDSM_OK; break; }
+            if (k >= op.max_sweeps) { status = ASDSM_NOT_CONVERGED; break; }
+            const int win = op.stagnation_window;
+            if (win > 0 && (int)S->hist.size() > win &&
+                S->hist.back() > (1.0 - op.stagnation_factor) * S->hist[S->hist.size() - 1 - win]) {
+                status = ASDSM_STAGNATED;
+                break;
+            }
+            const double hnorm = std::sqrt(rh2), rnorm = std::sqrt(rr);
+            if (hole_ref_pending) { hole_ref = hnorm; hole_ref_pending = false; }
+            // R18: a Filler pass on the hole part of the residual replaces the sweep.
+            if (hnorm > op.hole_fix_ratio * rnorm && hnorm > op.hole_fix_growth * hole_ref) {
+                if (int rc = fill3<T>(S, pi, 2, (T*)nullptr, s, u)) return rc;
+                hole_ref_pending = true;
+                ++hole_fixes;
+                ++k;
+                need_true = true;
+                restart = true;                      // u moved outside the cycle's directions
+                continue;
+            }
         }
-        if (int rc = residual3<T>(S, pi, s, ucur, true)) return rc;
-        if (int rc = read3(S, S->dsmall, 2)) return rc;
-        const double rnorm = std::sqrt(S->hsmall[0]), hnorm = std::sqrt(S->hsmall[1]);
-        rel = bnorm > 0 ? rnorm / bnorm : rnorm;
-        if (!std::isfinite(rel)) { status = ASDSM_ERR_NAN; break; }
-        S->hist.push_back(rel);
-        if (k == 0) rel0 = rel;
-        if (rel <= op.tol) { status = ASDSM_OK; break; }
-        if (k >= op.max_sweeps) { status = ASDSM_NOT_CONVERGED; break; }
-        const int win = op.stagnation_window;
-        if (win > 0 && (int)S->hist.size() > win &&
-            S->hist.back() > (1.0 - op.stagnation_factor) * S->hist[S->hist.size() - 1 - win]) {
-            status = ASDSM_STAGNATED;
-            break;
-        }
-        if (hole_ref_pending) { hole_ref = hnorm; hole_ref_pending = false; }
-        // R18: a Filler pass on the hole part of the residual replaces the sweep.
-        if (hnorm > op.hole_fix_ratio * rnorm && hnorm > op.hole_fix_growth * hole_ref) {
-            if (int rc = fill3<T>(S, pi, 2, (T*)nullptr, s, ucur)) return rc;
-            hole_ref_pending = true;
-            ++hole_fixes;
-            kc = 0;
-            ++k;
-            continue;
-        }
-        // The correction: Algorithm 1 without b_cc on the residual.
-        T* z = (T*)w.z[kc];
+        // The correction: Algorithm 1 without b_cc on the (tracked) residual.
+        T* z = Z + (long long)kc * g.NN;
         if (int rc = correction3<T>(S, pi, choice3(op.seed, k), z)) return rc;
-        // Least squares on the skeleton rows.
+        ++k;
+        // Least squares on the skeleton rows: A e there and its products with the
+        // tracked residual and the cycle's orthonormal images.
         skel_apply3_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(z, g, S->sten, (T*)w.q);
-        note_launch();
+        const dim3 dgrid(DK_CHUNKS, std::max(1, (kc + DK_VEC - 1) / DK_VEC));
+        dots_many_kernel<T><<<dgrid, T3, 0, st>>>((const T*)w.q, w.rs, V, g.skel, g.skel, kc, S->dpart);
+        const int ncol = 3 + 2 * kc;
+        sum_chunks_kernel<<<(ncol + 31) / 32, 32, 0, st>>>(S->dpart, ncol, S->dsum);
+        note_launch(3);
         CK3(cudaGetLastError());
-        const T* qpv[16];
-        for (int j = 0; j < kc; ++j) qpv[j] = (const T*)w.qp[j];
-        const int nd = 2 + 2 * kc;
-        int nb3 = 0;
-        CK3(gcr_dots<T>((const T*)w.q, (const T*)w.rskel, qpv, kc, g.skel, S->partials, &nb3, st));
-        CK3(reduce_partials(S->partials, nb3, nd, S->dsmall, st));
-        if (int rc = read3(S, S->dsmall, nd)) return rc;
-        const double qq = S->hsmall[0], qr = S->hsmall[1];
+        if (int rc = read3(S, S->dsum, ncol)) return rc;
+        const double qq = S->hsmall[0], qr = S->hsmall[1], rr = S->hsmall[2];
         if (m == 1) {
-            const double shat = qq > 0 ? std::max(0.0, qr / qq) : 0.0;   // the clamped optimal scaling
-            pend.count = 1;
-            pend.z[0] = z;
-            pend.coef[0] = shat;
-            ++k;
+            // The paper's clamped optimal scaling: s_hat = argmin_{s >= 0} ||r - s A e||.
+            const double shat = qq > 0 ? std::max(0.0, qr / qq) : 0.0;
+            c[0] = shat;
+            kc = 1;
+            S->hist.push_back(rel_of(rr - 2 * shat * qr + shat * shat * qq + rh2));
+            last_tracked = true;
+            need_true = true;
+            restart = true;
             continue;
         }
-        // GCR(m) (R15): orthogonalise A e against the cycle's earlier images.
-        double beta_[16] = {}, rq[16] = {};
+        // GCR (R15): orthogonalise A e against the cycle's earlier images.
         double nu2 = qq;
         for (int j = 0; j < kc; ++j) {
-            beta_[j] = S->hsmall[2 + 2 * j];
-            rq[j] = S->hsmall[3 + 2 * j];
-            nu2 -= beta_[j] * beta_[j];
+            beta[j] = S->hsmall[3 + j];
+            rq[j] = S->hsmall[3 + kc + j];
+            nu2 -= beta[j] * beta[j];
         }
-        if (!(nu2 > 1e-24 * qq) || !(qq > 0)) {    // dependent direction: restart the cycle
-            kc = 0;
-            ++k;
+        if (!(nu2 > 1e-24 * qq) || !(qq > 0)) {      // a dependent direction ends the cycle
+            S->hist.push_back(S->hist.back());
+            last_tracked = true;
+            need_true = true;
+            restart = true;
             continue;
         }
         const double nu = std::sqrt(nu2);
         double alpha_ = qr;
-        for (int j = 0; j < kc; ++j) alpha_ -= beta_[j] * rq[j];
+        for (int j = 0; j < kc; ++j) alpha_ -= beta[j] * rq[j];
         alpha_ /= nu;
-        for (int i = 0; i <= kc; ++i) Tm[i][kc] = 0.0;
-        Tm[kc][kc] = 1.0 / nu;
+        // Column kc of T: V_kc = sum_i T[i][kc] Z_i; the cycle's update is sum_i c_i Z_i.
+        for (int i = 0; i <= kc; ++i) Tm[(size_t)i * m + kc] = 0.0;
+        Tm[(size_t)kc * m + kc] = 1.0 / nu;
         for (int j = 0; j < kc; ++j)
-            for (int i = 0; i <= j; ++i) Tm[i][kc] -= beta_[j] * Tm[i][j] / nu;
-        for (int i = 0; i <= kc; ++i) {
-            pend.z[i] = w.z[i];
-            pend.coef[i] = alpha_ * Tm[i][kc];
-        }
-        pend.count = kc + 1;
-        CK3(combine_skeleton<T>((const T*)w.q, qpv, beta_, kc, 1.0 / nu, g.skel, (T*)w.qp[kc], st));
-        ++kc;
-        if (kc >= m) kc = 0;
-        ++k;
-    }
-    if (ucur != u) {
-        interior3_kernel<double><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(ucur, g, u);
+            for (int i = 0; i <= j; ++i) Tm[(size_t)i * m + kc] -= beta[j] * Tm[(size_t)i * m + j] / nu;
+        for (int i = 0; i <= kc; ++i) c[i] += alpha_ * Tm[(size_t)i * m + kc];
+        if (kc > 0) CK3(cudaMemcpyAsync(S->dcoef, beta.data(), (size_t)kc * sizeof(double), cudaMemcpyHostToDevice, st));
+        combine_many_kernel<T><<<g1d(g.skel), T3, 0, st>>>((const T*)w.q, V, g.skel, g.skel, kc, S->dcoef, 1.0 / nu,
+                                                         alpha_, w.rs, S->partials);
         note_launch();
+        CK3(cudaGetLastError());
+        ++kc;
+        // ||r - alpha V_kc||^2 = ||r||^2 - alpha^2 for the orthonormal V_kc with alpha = <r, V_kc>.
+        const double rel_t = rel_of(rr - alpha_ * alpha_ + rh2);
+        S->hist.push_back(rel_t);
+        last_tracked = true;
+        ++since_check;
+        if (kc >= m) restart = true;
+        if (rel_t <= op.tol || kc >= m || k >= op.max_sweeps || since_check >= kCheck3) { need_true = true; continue; }
+        const int win = op.stagnation_window;
+        if (win > 0 && (int)S->hist.size() > win &&
+            S->hist.back() > (1.0 - op.stagnation_factor) * S->hist[S->hist.size() - 1 - win]) {
+            need_true = true;
+            continue;
+        }
+        planes_from_skel_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(w.rs, g, (T*)w.F[0], (T*)w.F[1],
+                                                                                   (T*)w.F[2]);
+        note_launch();
+        CK3(cudaGetLastError());
     }
     // The largest hole residual of the returned iterate.
     const long long nh = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
@@ -1223,6 +1392,10 @@ int s3_create(const asdsm_desc* d, const asdsm_opts* o, cudaStream_t st, Solver3
     }
     const int n = (N - 1) / mc;
     if (n < 2 || n > 16) { report_error("3D sizes: hole size (N-1)/mc must be 2..16"); return ASDSM_ERR_INVALID; }
+    if (o->accel_m < 1 || o->accel_m > kMaxM3 || (o->precision != ASDSM_FP64 && o->precision != ASDSM_MIXED)) {
+        report_error("3D options: accel_m in 1..1024, precision ASDSM_FP64 or ASDSM_MIXED");
+        return ASDSM_ERR_INVALID;
+    }
     for (int a = 0; a < 3; ++a)
         if (!(d->alpha[a] > 0.0) || !std::isfinite(d->alpha[a]) || !std::isfinite(d->beta[a])) {
             report_error("3D: alpha_i must be positive and finite");
@@ -1261,6 +1434,10 @@ int s3_create(const asdsm_desc* d, const asdsm_opts* o, cudaStream_t st, Solver3
     if ((e = cudaMalloc(&S->partials, (size_t)kPartials3 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
     if ((e = cudaMalloc(&S->dsmall, 256 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
     if ((e = cudaMallocHost(&S->hsmall, 4096 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
+    if ((e = cudaMalloc(&S->dcoef, kMaxM3 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
+    if ((e = cudaMalloc(&S->dsum, (2 * kMaxM3 + 3) * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
+    if ((e = cudaMalloc(&S->dpart, (size_t)(2 * kMaxM3 + 3) * DK_CHUNKS * sizeof(double))) != cudaSuccess)
+        return fail(report_cuda_error(e));
     for (cudaEvent_t* ev : {&S->ev0, &S->ev1, &S->ev2})
         if ((e = cudaEventCreate(ev)) != cudaSuccess) return fail(report_cuda_error(e));
     *out = S;
@@ -1268,9 +1445,10 @@ int s3_create(const asdsm_desc* d, const asdsm_opts* o, cudaStream_t st, Solver3
 }
 
 int s3_set_opts(Solver3D* S, const asdsm_opts* o) {
-    const int m_old = std::max(1, std::min(S->opts.accel_m, 16)), m_new = std::max(1, std::min(o->accel_m, 16));
+    if (o->accel_m < 1 || o->accel_m > kMaxM3) return ASDSM_ERR_INVALID;
+    const int m_old = S->opts.accel_m;
     S->opts = *o;
-    if (m_new > m_old) { free_work3(S, 0); free_work3(S, 1); }     // direction slots re-allocated on first use
+    if (o->accel_m != m_old) { free_work3(S, 0); free_work3(S, 1); }     // direction slots re-allocated on first use
     return ASDSM_OK;
 }
 
@@ -1375,6 +1553,8 @@ void s3_destroy(Solver3D* S) {
     if (S->partials) cudaFree(S->partials);
     if (S->dsmall) cudaFree(S->dsmall);
     if (S->hsmall) cudaFreeHost(S->hsmall);
+    for (double* p : {S->dcoef, S->dsum, S->dpart})
+        if (p) cudaFree(p);
     for (cudaEvent_t ev : {S->ev0, S->ev1, S->ev2})
         if (ev) cudaEventDestroy(ev);
     delete S;

@@ -135,14 +135,14 @@ def test_3d_fp64_iterates_match_oracle(lib, name, make, mc, m):
         np.testing.assert_allclose(res.history, info["hist"], rtol=1e-6, atol=1e-11)
 
 
-@pytest.mark.parametrize("N,mc,seed", [(33, 8, 2), (33, 4, 3), (65, 8, 4)])
+@pytest.mark.parametrize("N,mc,seed,m", [(33, 8, 2, 16), (33, 4, 3, 64), (65, 8, 4, 256)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_3d_solve_reaches_the_fine_solution(lib, N, mc, seed, precision):
+def test_3d_solve_reaches_the_fine_solution(lib, N, mc, seed, m, precision):
     p = wl.random_sine_3d(N, seed)
     disc = o3.Discretisation3D(N, mc, p.alpha, p.beta)
     b = disc.rhs(p.s, p.g)
     prec = lib.FP64 if precision == "fp64" else lib.MIXED
-    with lib.Solver(N, mc, p.alpha, p.beta, precision=prec, tol=1e-10, max_sweeps=800, accel_m=16) as sv:
+    with lib.Solver(N, mc, p.alpha, p.beta, precision=prec, tol=1e-10, max_sweeps=800, accel_m=m) as sv:
         u = _dev(p.g)
         res = sv.solve(_dev(p.s), u)
         rel_lib = sv.residual(_dev(p.s), u)
@@ -152,9 +152,10 @@ def test_3d_solve_reaches_the_fine_solution(lib, N, mc, seed, precision):
     assert rel <= 1.01e-10, rel
     assert abs(rel_lib - rel) <= 1e-3 * rel
     assert abs(res.stats["rel_res_fp64"] - rel) <= 1e-3 * rel
-    u_ff = disc.solve_fine(b[0])
-    kappa = 4.0 / (np.pi**2 / (N - 1) ** 2) * max(p.alpha) / min(p.alpha)
-    assert _rel(got, u_ff) <= kappa * rel
+    if N <= 33:       # a direct sparse solve of the 3D fine system is cheap only on small grids
+        u_ff = disc.solve_fine(b[0])
+        kappa = 4.0 / (np.pi**2 / (N - 1) ** 2) * max(p.alpha) / min(p.alpha)
+        assert _rel(got, u_ff) <= kappa * rel
     print(f"3D {precision} N={N} mc={mc}: {res.stats['sweeps']} sweeps, oracle residual {rel:.2e}")
 
 
