@@ -468,6 +468,9 @@ def run_ours(args):
                              "hole n = min(32, (N-1)/16), per-instance alpha/beta as the 2D workload"}
         bsv.close()
 
+    # The 3D extension (Section 3.5) on its configuration: 257^3, mc = 16.
+    leg3d = bench_3d(asdsm, wl, dev, stream) if (args.bench3d and rank == 0) else None
+
     if rank != 0:
         return
 
@@ -507,11 +510,64 @@ def run_ours(args):
             "roofline_fill": roof_fill, "roofline_merge": roof_merge,
             "kernel_shares": shares, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "sweeps_per_solve": sweeps, "rel_res": max(rels), "rel_res_fp64": rel_res_fp64, "fp64_gpu": fp64,
-            "setup_excluded": {"autotune_ms": tune_ms}, "batch": batch}
+            "setup_excluded": {"autotune_ms": tune_ms}, "batch": batch, "solve_3d": leg3d}
     print(json.dumps(line), flush=True)
     solver.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+N3D, MC3D, ACCEL_M3D = 257, 16, 256
+
+
+def bench_3d(asdsm, wl, dev, stream, N=N3D, mc=MC3D, reps=2):
+    """The 3D leg: u = prod sin(pi x_i) on the unit cube, alpha_i log-uniform in
+    [1e-2, 1], beta_i in [-5, 5] (seed 0), N^3 grid, mc coarse intervals,
+    mixed precision, GCR with up to ACCEL_M3D directions, tol 1e-10; CUDA
+    events around `reps` complete solves (setup excluded), one more solve
+    with per-family timing for the shares."""
+    import torch
+    p = wl.random_sine_3d(N, 0)
+    t0 = time.time()
+    sv = asdsm.Solver(N, mc, p.alpha, p.beta, precision=asdsm.MIXED, tol=TOL, max_sweeps=3000, accel_m=ACCEL_M3D)
+    setup_s = time.time() - t0
+    s = torch.tensor(p.s, dtype=torch.float64, device=dev)
+    g = torch.tensor(p.g, dtype=torch.float64, device=dev)
+    u = g.clone()
+    sv.solve(s, u)                                  # warm-up (allocates the direction store)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    results = []
+    for _ in range(reps):
+        u.copy_(g)
+        results.append(sv.solve(s, u))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    for r in results:
+        if r.status != asdsm.OK or not r.stats["rel_res_fp64"] <= TOL:
+            raise RuntimeError(f"3D solve did not reach {TOL:g}: {r.stats}")
+    err = float((u - torch.tensor(p.u_exact, device=dev)).abs().max())
+    sv.profile(True)
+    u.copy_(g)
+    sv.solve(s, u)
+    torch.cuda.synchronize()
+    prof = sv.profile_read()
+    sv.profile(False)
+    sv.close()
+    total = sum(v["ms"] for v in prof.values()) or 1.0
+    unknowns = (N - 2) ** 3
+    return {"value": unknowns / (ms * 1e-3), "unit": UNIT, "ms_per_solve": ms, "unknowns": unknowns,
+            "sweeps": results[-1].stats["sweeps"], "rel_res_fp64": max(r.stats["rel_res_fp64"] for r in results),
+            "hole_fixes": results[-1].stats["hole_fixes"], "max_error_vs_manufactured": err,
+            "launches_per_solve": results[-1].stats["launches"], "setup_s": setup_s,
+            "kernel_shares": {k: round(v["ms"] / total, 4) for k, v in prof.items() if v["ms"] > 0},
+            "families": {k: {"ms": v["ms"], "launches": v["launches"], "GB/s": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
+                             "TFLOP/s": v["flops"] / (v["ms"] * 1e-3) / 1e12} for k, v in prof.items() if v["ms"] > 0},
+            "workload": f"3D extension: {N}^3 grid, mc {mc} (holes 15^3), alpha_i log-uniform [1e-2,1], "
+                        f"beta_i in [-5,5], u = prod sin(pi x_i), seed 0; FP32 solves/merge/fill, FP64 residual "
+                        f"and accumulation, GCR with up to {ACCEL_M3D} directions"}
 
 
 def main():
@@ -525,6 +581,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the 64-problem batch measurement")
+    ap.add_argument("--no-3d", dest="bench3d", action="store_false", help="skip the 3D leg (257^3)")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of tuned launch shapes: written after autotuning, read instead of tuning if present")
     ap.add_argument("--host-sweeps", action="store_true",

@@ -238,7 +238,10 @@ int asdsm_residual(asdsm_handle* h, const double* s, const double* u, double* r,
  * order, p fastest); 3..5 = the line family fine in x, y, z, arrays
  * [f][cq][cp] (f the fine coordinate, cp/cq the coarse coordinates of the
  * other two axes); 6 = the coarse mesh [cz][cy][cx]; 7 = the cube holes:
- * N^3 grids, only hole points read and written. */
+ * N^3 grids, only hole points read and written; 8 = Algorithm 3 with zero
+ * source as the sweeps apply it (in: N^3 grid whose skeleton values are the
+ * Dirichlet data; out: its hole points receive the fill; on the mixed path
+ * this is the FP32 product with the hole extension operator). */
 int asdsm_submesh_solve(asdsm_handle* h, int mesh, const double* in, double* out);
 
 /* Relative residual after each completed sweep of the last asdsm_solve

@@ -32,7 +32,7 @@ MIXED = 1
 
 MESH_FC, MESH_CF, MESH_CC, MESH_HOLES, MESH_HOLES_HOMOGENEOUS = 0, 1, 2, 3, 4
 # 3D (asdsm_submesh_solve with d = 3): plane families, line families, coarse mesh, cube holes.
-MESH3_PLANE, MESH3_LINE, MESH3_COARSE, MESH3_HOLES = 0, 3, 6, 7
+MESH3_PLANE, MESH3_LINE, MESH3_COARSE, MESH3_HOLES, MESH3_FILL = 0, 3, 6, 7, 8
 
 
 class Desc(ctypes.Structure):

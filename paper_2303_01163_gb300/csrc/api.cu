@@ -1944,7 +1944,7 @@ int asdsm_history(asdsm_handle* h, double* hist, int cap) {
 
 int asdsm_profile(asdsm_handle* h, int enable) {
     if (!h) return ASDSM_ERR_INVALID;
-    if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
+    if (h->s3) return s3_profile(h->s3, enable);
     h->prof = enable != 0;
     std::memset(h->pc, 0, sizeof(h->pc));
     for (int c = 0; c < PC_COUNT; ++c) std::snprintf(h->pc[c].name, sizeof(h->pc[c].name), "%s", kProfNames[c]);
@@ -1955,6 +1955,7 @@ int asdsm_profile(asdsm_handle* h, int enable) {
 
 int asdsm_profile_read(asdsm_handle* h, asdsm_kprof* out, int cap) {
     if (!h || (!out && cap > 0)) return ASDSM_ERR_INVALID;
+    if (h->s3) return s3_profile_read(h->s3, out, cap);
     const int n = std::min<int>(cap, PC_COUNT);
     for (int c = 0; c < n; ++c) out[c] = h->pc[c];
     return n;

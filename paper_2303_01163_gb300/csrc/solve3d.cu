@@ -517,6 +517,19 @@ hole_scatter3_kernel(int mode, const T* __restrict__ Y, Geo3 g, T* __restrict__ 
     }
 }
 
+// out (FP64 grid) = z at the hole points.
+template <typename T>
+__global__ void __launch_bounds__(T3) hole_copy3_kernel(const T* __restrict__ z, Geo3 g, double* __restrict__ out) {
+    const long long count = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
+    const int N = g.N;
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < count; e += (long long)gridDim.x * T3) {
+        int i, j, l, lx, ly, lz;
+        hole_point(e, g, i, j, l, lx, ly, lz);
+        const long long idx = ((long long)l * N + j) * N + i;
+        out[idx] = (double)z[idx];
+    }
+}
+
 // q = A z on the compact skeleton (T arithmetic).
 template <typename T>
 __global__ void __launch_bounds__(T3)
@@ -688,6 +701,225 @@ update_many_kernel(double* __restrict__ u, const T* __restrict__ Z, long long zs
 }
 
 // ---------------------------------------------------------------------------
+// The same three operations for FP32 directions, without the FP64 pipe in the
+// inner loops (on GB300 it runs at 1/64 of the FP32 rate): every product is
+// made exact by the FMA-based TwoProd and accumulated as an unevaluated pair
+// (hi, lo) by TwoSum (Knuth), the compensated dot product "Dot2" of Ogita,
+// Rump and Oishi (2005), accurate as if computed in twice the working
+// precision.  FP64 coefficients enter as float pairs (hi, lo); an FP64
+// operand (the tracked residual) is split into a float pair once per element.
+// ---------------------------------------------------------------------------
+struct F2 { float h, l; };
+
+__device__ __forceinline__ void acc_prod(F2& s, float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);                 // a b = p + e exactly
+    const float t = s.h + p;
+    const float z = t - s.h;
+    s.l += ((s.h - (t - z)) + (p - z)) + e;          // TwoSum error of s.h + p, plus e
+    s.h = t;
+}
+
+__device__ __forceinline__ double f2_value(const F2& s) { return (double)s.h + (double)s.l; }
+
+__global__ void __launch_bounds__(T3)
+dots_many_f32_kernel(const float* __restrict__ q, const double* __restrict__ r, const float* __restrict__ V, long long n,
+                     long long vstride, int k, double* __restrict__ partials) {
+    __shared__ double red[T3 / 32][2 * DK_VEC + 3];
+    const int chunk = blockIdx.x, j0 = blockIdx.y * DK_VEC;
+    const long long len = (n + DK_CHUNKS - 1) / DK_CHUNKS, e0 = chunk * len, e1 = min(n, e0 + len);
+    const int nv = min(DK_VEC, k - j0);
+    F2 aq[DK_VEC], ar[DK_VEC], a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+    double a2 = 0.0;
+#pragma unroll
+    for (int t = 0; t < DK_VEC; ++t) { aq[t] = {0.f, 0.f}; ar[t] = {0.f, 0.f}; }
+    for (long long e = e0 + threadIdx.x; e < e1; e += T3) {
+        const float qv = q[e];
+        const double rd = r[e];
+        const float rh = (float)rd, rl = (float)(rd - (double)rh);
+        if (blockIdx.y == 0) {
+            acc_prod(a0, qv, qv);
+            acc_prod(a1, qv, rh);
+            a1.l = fmaf(qv, rl, a1.l);
+            a2 = fma(rd, rd, a2);
+        }
+#pragma unroll
+        for (int t = 0; t < DK_VEC; ++t)
+            if (t < nv) {
+                const float v = V[(long long)(j0 + t) * vstride + e];
+                acc_prod(aq[t], qv, v);
+                acc_prod(ar[t], rh, v);
+                ar[t].l = fmaf(rl, v, ar[t].l);
+            }
+    }
+    double acc[2 * DK_VEC + 3];
+    acc[0] = f2_value(a0); acc[1] = f2_value(a1); acc[2] = a2;
+#pragma unroll
+    for (int t = 0; t < DK_VEC; ++t) { acc[3 + t] = f2_value(aq[t]); acc[3 + DK_VEC + t] = f2_value(ar[t]); }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 2 * DK_VEC + 3; ++t) {
+        double v = acc[t];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0) red[w][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * DK_VEC + 3) {
+        const int t = threadIdx.x;
+        double v = 0.0;
+        for (int q2 = 0; q2 < T3 / 32; ++q2) v += red[q2][t];
+        int col = -1;
+        if (t < 3) col = blockIdx.y == 0 ? t : -1;
+        else if (t < 3 + DK_VEC) col = (t - 3 < nv) ? 3 + j0 + (t - 3) : -1;
+        else col = (t - 3 - DK_VEC < nv) ? 3 + k + j0 + (t - 3 - DK_VEC) : -1;
+        if (col >= 0) partials[(long long)col * DK_CHUNKS + chunk] = v;
+    }
+}
+
+// V_k = (q - sum_j beta_j V_j) * inv_nu (beta as float pairs), r -= alpha V_k.
+__global__ void __launch_bounds__(T3)
+combine_many_f32_kernel(const float* __restrict__ q, float* __restrict__ V, long long n, long long vstride, int k,
+                        const float2* __restrict__ beta, double inv_nu, double alpha, double* __restrict__ r) {
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < n; e += (long long)gridDim.x * T3) {
+        F2 acc = {q[e], 0.f};
+        for (int j = 0; j < k; ++j) {
+            const float v = V[(long long)j * vstride + e];
+            const float2 b = beta[j];
+            acc_prod(acc, -b.x, v);
+            acc.l = fmaf(-b.y, v, acc.l);
+        }
+        const float vk = (float)(f2_value(acc) * inv_nu);
+        V[(long long)k * vstride + e] = vk;
+        r[e] = fma(-alpha, (double)vk, r[e]);
+    }
+}
+
+// u += sum_j c_j Z_j over the interior (c as float pairs), one FP64 add per point.
+__global__ void __launch_bounds__(T3)
+update_many_f32_kernel(double* __restrict__ u, const float* __restrict__ Z, long long zstride, int k,
+                       const float2* __restrict__ c, Geo3 g) {
+    __shared__ float2 cs[1024];
+    for (int j = threadIdx.x; j < k && j < 1024; j += T3) cs[j] = c[j];
+    __syncthreads();
+    const int N = g.N, Nf = g.Nf;
+    for (long long row = blockIdx.x; row < (long long)Nf * Nf; row += gridDim.x) {
+        const int j = (int)(row % Nf) + 1, l = (int)(row / Nf) + 1;
+        const long long base = ((long long)l * N + j) * N;
+        for (int i = 1 + threadIdx.x; i <= N - 2; i += T3) {
+            const long long idx = base + i;
+            F2 acc = {0.f, 0.f};
+            for (int t = 0; t < k; ++t) {
+                const float z = Z[(long long)t * zstride + idx];
+                acc_prod(acc, cs[t].x, z);
+                acc.l = fmaf(cs[t].y, z, acc.l);
+            }
+            u[idx] += f2_value(acc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Homogeneous cube-hole Filler of the sweeps (Algorithm 3 with zero source) as
+// one GEMM: the hole values are G f for the 6 C^2 face values f of the hole,
+// G = -A_hh^{-1} A_hs (C^3 x 6 C^2, host FP64, FP32 here), for all holes at
+// once: Out[p][h] = sum_k G[p][k] F[k][h], F gathered from the skeleton, Out
+// written straight into the grid.  Faces: west, east (x = 0, C+1), south,
+// north, down, up, each C x C with its second axis slowest.
+// ---------------------------------------------------------------------------
+constexpr int GB_M = 128, GB_N = 128, GB_K = 16, GB_T = 256;
+
+__device__ __forceinline__ void hole_origin(int h, const Geo3& g, int& x0, int& y0, int& z0) {
+    const int mc = g.mc;
+    x0 = (h % mc) * g.n; y0 = ((h / mc) % mc) * g.n; z0 = (h / (mc * mc)) * g.n;
+}
+
+__global__ void __launch_bounds__(T3) faces3_kernel(const float* __restrict__ z, Geo3 g, float* __restrict__ F) {
+    const int C = g.hc, C2 = C * C, N = g.N, n = g.n;
+    const long long H = (long long)g.mc * g.mc * g.mc, K = 6LL * C2;
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < K * H; e += (long long)gridDim.x * T3) {
+        const int k = (int)(e / H), h = (int)(e % H);
+        const int face = k / C2, r = k % C2, a = r % C + 1, b = r / C + 1;
+        int x0, y0, z0;
+        hole_origin(h, g, x0, y0, z0);
+        int x, y, zz;
+        if (face < 2) { x = x0 + (face == 0 ? 0 : n); y = y0 + a; zz = z0 + b; }
+        else if (face < 4) { y = y0 + (face == 2 ? 0 : n); x = x0 + a; zz = z0 + b; }
+        else { zz = z0 + (face == 4 ? 0 : n); x = x0 + a; y = y0 + b; }
+        F[e] = z[((long long)zz * N + y) * N + x];
+    }
+}
+
+__global__ void __launch_bounds__(GB_T)
+fill_g3_kernel(const float* __restrict__ G, int KP, const float* __restrict__ F, int P, int K, int H, Geo3 g,
+               float* __restrict__ z) {
+    __shared__ __align__(16) float As[GB_K][GB_M + 4];
+    __shared__ __align__(16) float Bs[GB_K][GB_N];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int p0 = blockIdx.y * GB_M, h0 = blockIdx.x * GB_N;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    // Register staging of the next tiles: A 128 x 16 (8 per thread), B 16 x 128 (8 per thread).
+    const int ap = tid >> 1, ak = (tid & 1) * 8;
+    const int bk = tid >> 4, bh = (tid & 15) * 8;
+    float av[8], bv[8];
+    auto load = [&](int k0) {
+        const int p = p0 + ap;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int k = k0 + ak + t;
+            av[t] = (p < P && k < K) ? G[(long long)p * KP + k] : 0.f;
+        }
+        const int k = k0 + bk;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int h = h0 + bh + t;
+            bv[t] = (k < K && h < H) ? F[(long long)k * H + h] : 0.f;
+        }
+    };
+    load(0);
+    for (int k0 = 0; k0 < K; k0 += GB_K) {
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 8; ++t) As[ak + t][ap] = av[t];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) Bs[bk][bh + t] = bv[t];
+        __syncthreads();
+        if (k0 + GB_K < K) load(k0 + GB_K);
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
+            const float a_[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b_[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a_[i], b_[j], acc[i][j]);
+        }
+    }
+    const int C = g.hc, N = g.N;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int h = h0 + tx * 8 + j;
+        if (h >= H) continue;
+        int x0, y0, z0;
+        hole_origin(h, g, x0, y0, z0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int p = p0 + ty * 8 + i;
+            if (p >= P) continue;
+            const int x = x0 + 1 + p % C, y = y0 + 1 + (p / C) % C, zz = z0 + 1 + p / (C * C);
+            z[((long long)zz * N + y) * N + x] = acc[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -788,10 +1020,17 @@ struct Solver3D {
     PlaneFam plane[3];
     Fac line[2][3], coarse[2], hole[2];
     void* W[2] = {nullptr, nullptr};       // spline values [N_f][N_c]
+    float* G3 = nullptr;                   // hole extension operator, FP32 [C^3][KP] (rows padded to KP)
+    int G3_KP = 0;
+    float* faces = nullptr;                // [6 C^2][holes]
+    cudaStream_t fork[2] = {nullptr, nullptr};   // the second and third plane family's streams
+    cudaStream_t cap = nullptr;                  // capture stream of the plane-solve graph
+    cudaEvent_t evf[3] = {nullptr, nullptr, nullptr};
+    struct PlaneGraph { cudaGraphExec_t exec = nullptr; long long launches = 0; int runs = 0; } pgraph[2][2];
     struct Work {
         bool ready = false;
         void* F[3] = {}; void* Y[3] = {}; void* U[3] = {};
-        void* Xb = nullptr; void* Yb = nullptr;
+        void* Xb[3] = {}; void* Yb[3] = {};   // per plane family, so the three can run concurrently
         void* Xl[3] = {}; void* Yl[3] = {};
         void* Xc = nullptr; void* Yc = nullptr;
         void* Xh = nullptr; void* Yh = nullptr;
@@ -803,11 +1042,19 @@ struct Solver3D {
         int m = 0;
     } w[2];
     double* dcoef = nullptr;             // [1024] step coefficients / Gram-Schmidt weights
+    float2* dcoef2 = nullptr;            // [1024] the same as float pairs (hi, lo) for the FP32 kernels
     double* dsum = nullptr;              // [2*1024 + 3] many-vector dot results
     double* dpart = nullptr;             // many-vector dot partials [(2*1024 + 3)][DK_CHUNKS]
     double* u_work = nullptr;
     double* partials = nullptr;
     int partials_cap = 0;
+    // Per-family CUDA-event timing (asdsm_profile) with algorithmic bytes and flops.
+    bool prof = false;
+    asdsm_kprof pc[8] = {};
+    std::vector<cudaEvent_t> evpool;
+    struct Mark { int a, b, cat; long long launches; double bytes, flops; };
+    std::vector<Mark> marks;
+    int evnext = 0;
     double* dsmall = nullptr;
     double* hsmall = nullptr;
     std::vector<double> hist;
@@ -930,6 +1177,21 @@ int build_factors(Solver3D* S) {
     const std::vector<double> W = spline_value_operator(g.mc, g.n);
     if (int rc = upload_vec3<double>(W, &S->W[0])) return rc;
     if (int rc = upload_vec3<float>(W, &S->W[1])) return rc;
+    // The hole extension operator of the sweeps' Filler (FP32 path).
+    {
+        const double sten7[7] = {S->sten.cc, S->sten.cw, S->sten.ce, S->sten.cs, S->sten.cn, S->sten.cd, S->sten.cu};
+        std::vector<double> G;
+        if (!hole_extension_operator_3d(g.hc, sten7, &G)) { report_error("3D: hole extension operator failed"); return ASDSM_ERR_INVALID; }
+        const int P = g.hc * g.hc * g.hc, K = 6 * g.hc * g.hc, KP = (K + 3) / 4 * 4;
+        std::vector<float> img((size_t)P * KP, 0.0f);
+        for (int p = 0; p < P; ++p)
+            for (int k = 0; k < K; ++k) img[(size_t)p * KP + k] = (float)G[(size_t)p * K + k];
+        CK3(cudaMalloc(&S->G3, img.size() * sizeof(float)));
+        CK3(cudaMemcpy(S->G3, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice));
+        S->G3_KP = KP;
+        const long long H = (long long)g.mc * g.mc * g.mc;
+        CK3(cudaMalloc(&S->faces, (size_t)K * H * sizeof(float)));
+    }
     return ASDSM_OK;
 }
 
@@ -950,7 +1212,8 @@ int ensure_work3(Solver3D* S, int pi) {
         if ((rc = al(&w.Xl[a], (long long)g.Nf * g.Nc * g.Nc)) || (rc = al(&w.Yl[a], (long long)g.Nf * g.Nc * g.Nc)))
             return rc;
     }
-    if ((rc = al(&w.Xb, 2 * g.plane)) || (rc = al(&w.Yb, 2 * g.plane))) return rc;
+    for (int a = 0; a < 3; ++a)
+        if ((rc = al(&w.Xb[a], 2 * g.plane)) || (rc = al(&w.Yb[a], 2 * g.plane))) return rc;
     const long long nc3 = (long long)g.Nc * g.Nc * g.Nc, nh = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
     if ((rc = al(&w.Xc, nc3)) || (rc = al(&w.Yc, nc3)) || (rc = al(&w.Xh, nh)) || (rc = al(&w.Yh, nh))) return rc;
     const int m = std::max(1, std::min(S->opts.accel_m, kMaxM3));
@@ -963,10 +1226,15 @@ int ensure_work3(Solver3D* S, int pi) {
 }
 
 void free_work3(Solver3D* S, int pi) {
+    for (auto& pg : S->pgraph[pi]) {
+        if (pg.exec) cudaGraphExecDestroy(pg.exec);
+        pg = Solver3D::PlaneGraph{};
+    }
     auto& w = S->w[pi];
     auto fr = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
     for (int a = 0; a < 3; ++a) { fr(w.F[a]); fr(w.Y[a]); fr(w.U[a]); fr(w.Xl[a]); fr(w.Yl[a]); }
-    fr(w.Xb); fr(w.Yb); fr(w.Xc); fr(w.Yc); fr(w.Xh); fr(w.Yh); fr(w.uh); fr(w.q); fr(w.Z); fr(w.V);
+    for (int a = 0; a < 3; ++a) { fr(w.Xb[a]); fr(w.Yb[a]); }
+    fr(w.Xc); fr(w.Yc); fr(w.Xh); fr(w.Yh); fr(w.uh); fr(w.q); fr(w.Z); fr(w.V);
     if (w.rs) cudaFree(w.rs);
     w.rs = nullptr;
     w.ready = false;
@@ -1002,6 +1270,63 @@ hole_max3_kernel(const double* __restrict__ s, const double* __restrict__ u, Geo
 
 namespace {
 
+// Kernel families of the 3D sweep for asdsm_profile.
+enum Prof3 : int { P3_PLANES = 0, P3_MERGE, P3_FILL, P3_RESID, P3_GCR, P3_UPDATE, P3_HOLEFIX, P3_GUESS, P3_COUNT };
+const char* const kProf3Names[P3_COUNT] = {"plane_solves", "merge3", "fill3", "residual3", "gcr3", "update3",
+                                           "hole_fix3", "initial_guess3"};
+
+struct PMark3 { int ev = -1; long long launches = 0; };
+
+PMark3 prof3_begin(Solver3D* S) {
+    PMark3 m;
+    if (!S->prof) return m;
+    if (S->evnext + 2 > (int)S->evpool.size()) {
+        cudaEvent_t e;
+        for (int t = 0; t < 64; ++t)
+            if (cudaEventCreate(&e) == cudaSuccess) S->evpool.push_back(e);
+    }
+    if (S->evnext + 2 > (int)S->evpool.size()) return m;
+    m.ev = S->evnext;
+    S->evnext += 2;
+    m.launches = launch_count();
+    cudaEventRecord(S->evpool[m.ev], S->st);
+    return m;
+}
+
+void prof3_end(Solver3D* S, const PMark3& m, int cat, double bytes, double flops) {
+    if (m.ev < 0) return;
+    cudaEventRecord(S->evpool[m.ev + 1], S->st);
+    S->marks.push_back({m.ev, m.ev + 1, cat, launch_count() - m.launches, bytes, flops});
+}
+
+void prof3_resolve(Solver3D* S) {
+    if (!S->prof) return;
+    for (const auto& mk : S->marks) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, S->evpool[mk.a], S->evpool[mk.b]);
+        asdsm_kprof& r = S->pc[mk.cat];
+        r.launches += mk.launches;
+        r.calls += 1;
+        r.ms += ms;
+        r.bytes += mk.bytes;
+        r.flops += mk.flops;
+    }
+    S->marks.clear();
+    S->evnext = 0;
+}
+
+// Multiply-adds of one block cyclic reduction: 2 C^2 per reduced row, 3 C^2 per solved row.
+double bcr_macs3(int R, int C, int L) {
+    const double c2 = (double)C * C;
+    double macs = 0.0;
+    for (int l = 0; l + 1 < L; ++l) macs += (double)(((R + 1) >> (l + 1)) - 1) * 2.0 * c2;
+    for (int l = 0; l < L; ++l) {
+        const double rb = (double)((R + 1) >> (l + 1));
+        macs += rb * c2 + 2.0 * (rb - 1.0) * c2;
+    }
+    return macs;
+}
+
 unsigned g1d(long long n) {
     long long b = (n + T3 - 1) / T3;
     return (unsigned)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b));
@@ -1010,12 +1335,11 @@ unsigned g1d(long long n) {
 // Plane family a: F[a] -> U[a] (Schur back-substitution of shifted 2D solves),
 // with the partial sums of U^2 at partials + off (2 values per block).
 template <typename T>
-int plane_solve3(Solver3D* S, int pi, int a, double* partials, int* nblocks) {
+int plane_solve3(Solver3D* S, int pi, int a, double* partials, int* nblocks, cudaStream_t st) {
     auto& w = S->w[pi];
     const Geo3& g = S->g;
     const PlaneFam& pf = S->plane[a];
     const long long P = g.plane;
-    cudaStream_t st = S->st;
     const T* F = (const T*)w.F[a];
     T* Y = (T*)w.Y[a];
     for (size_t b = 0; b < pf.bk.size(); ++b) {
@@ -1027,13 +1351,13 @@ int plane_solve3(Solver3D* S, int pi, int a, double* partials, int* nblocks) {
                 ss.q[i][j] = pf.Q[(size_t)j * g.Nc + k + i];
                 ss.s[i][j] = j >= k + bs ? pf.S[(size_t)(k + i) * g.Nc + j] : 0.0;
             }
-        schur_rhs_kernel<T><<<g1d(P), T3, 0, st>>>(F, Y, P, ss, (T*)w.Xb);
+        schur_rhs_kernel<T><<<g1d(P), T3, 0, st>>>(F, Y, P, ss, (T*)w.Xb[a]);
         note_launch();
         CK3(cudaGetLastError());
-        BcrSys<T> sys = sys3<T>(pf.fac[pi][b], w.Xb, bs == 1 ? (void*)(Y + (long long)k * P) : w.Yb);
+        BcrSys<T> sys = sys3<T>(pf.fac[pi][b], w.Xb[a], bs == 1 ? (void*)(Y + (long long)k * P) : w.Yb[a]);
         CK3(bcr_solve<T>(&sys, 1, st));
         if (bs == 2) {
-            deinterleave_kernel<T><<<g1d(P), T3, 0, st>>>((const T*)w.Yb, P, Y + (long long)k * P,
+            deinterleave_kernel<T><<<g1d(P), T3, 0, st>>>((const T*)w.Yb[a], P, Y + (long long)k * P,
                                                          Y + (long long)(k + 1) * P);
             note_launch();
             CK3(cudaGetLastError());
@@ -1047,15 +1371,62 @@ int plane_solve3(Solver3D* S, int pi, int a, double* partials, int* nblocks) {
     return ASDSM_OK;
 }
 
-// The three plane families; with norms, ||U_a||^2 into dsmall[200 + 2a].
+// The three plane families, each on its own stream (forked from and joined
+// back to the handle's stream); with norms, ||U_a||^2 into dsmall[200 + 2a].
 template <typename T>
-int planes3(Solver3D* S, int pi, bool norms) {
+int planes3_enqueue(Solver3D* S, int pi, bool norms, cudaStream_t st) {
+    CK3(cudaEventRecord(S->evf[0], st));
+    for (int q = 0; q < 2; ++q) CK3(cudaStreamWaitEvent(S->fork[q], S->evf[0], 0));
     for (int a = 0; a < 3; ++a) {
+        cudaStream_t sa = a == 0 ? st : S->fork[a - 1];
         int nb = 0;
         double* part = S->partials + (size_t)a * 2 * 152 * 16;
-        if (int rc = plane_solve3<T>(S, pi, a, part, &nb)) return rc;
-        if (norms) CK3(reduce_partials(part, nb, 2, S->dsmall + 200 + 2 * a, S->st));
+        if (int rc = plane_solve3<T>(S, pi, a, part, &nb, sa)) return rc;
+        if (norms) CK3(reduce_partials(part, nb, 2, S->dsmall + 200 + 2 * a, sa));
     }
+    for (int q = 0; q < 2; ++q) {
+        CK3(cudaEventRecord(S->evf[1 + q], S->fork[q]));
+        CK3(cudaStreamWaitEvent(st, S->evf[1 + q], 0));
+    }
+    return ASDSM_OK;
+}
+
+// The plane-family solves are the same launches every sweep (fixed buffers),
+// so after one plain run they are captured once as a CUDA graph and replayed
+// (not while profiling, whose event records would be captured too).
+template <typename T>
+int planes3(Solver3D* S, int pi, bool norms) {
+    const PMark3 pm = prof3_begin(S);
+    double flops = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (const Fac& f : S->plane[a].fac[pi]) flops += 2.0 * bcr_macs3(f.R, f.C, f.L);
+    const double P = (double)S->g.plane, Nc = S->g.Nc;
+    struct End { Solver3D* S; PMark3 pm; double b, f; ~End() { prof3_end(S, pm, P3_PLANES, b, f); } }
+        end{S, pm, sizeof(T) * 3.0 * (2.0 * Nc * P), flops + 3.0 * 2.0 * 2.0 * Nc * Nc * P};
+    auto& pg = S->pgraph[pi][norms ? 1 : 0];
+    if (pg.exec && !S->prof) {
+        CK3(cudaGraphLaunch(pg.exec, S->st));
+        note_launch(pg.launches);
+        return ASDSM_OK;
+    }
+    if (S->prof || pg.runs == 0) {
+        ++pg.runs;
+        return planes3_enqueue<T>(S, pi, norms, S->st);
+    }
+    // Captured on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); replayed on the caller's stream.
+    const long long l0 = launch_count();
+    cudaGraph_t graph = nullptr;
+    CK3(cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = planes3_enqueue<T>(S, pi, norms, S->cap);
+    const cudaError_t e = cudaStreamEndCapture(S->cap, &graph);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) return report_cuda_error(e);
+    const cudaError_t e2 = cudaGraphInstantiate(&pg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) { pg.exec = nullptr; return report_cuda_error(e2); }
+    pg.launches = launch_count() - l0;
+    CK3(cudaGraphLaunch(pg.exec, S->st));
     return ASDSM_OK;
 }
 
@@ -1065,6 +1436,10 @@ int fill3(Solver3D* S, int pi, int mode, T* z, const double* s, double* u) {
     auto& w = S->w[pi];
     const Geo3& g = S->g;
     const long long nh = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
+    const PMark3 pm = prof3_begin(S);
+    struct End { Solver3D* S; PMark3 pm; int cat; double b, f; ~End() { prof3_end(S, pm, cat, b, f); } }
+        end{S, pm, mode == 2 ? P3_HOLEFIX : P3_FILL, (double)nh * sizeof(T) * 2.0,
+            2.0 * (double)g.mc * g.mc * g.mc * bcr_macs3(S->hole[pi].R, S->hole[pi].C, S->hole[pi].L)};
     hole_rhs3_kernel<T><<<g1d(nh), T3, 0, S->st>>>(mode, z, s, u, g, S->sten, (T*)w.Xh);
     note_launch();
     CK3(cudaGetLastError());
@@ -1073,6 +1448,20 @@ int fill3(Solver3D* S, int pi, int mode, T* z, const double* s, double* u) {
     hole_scatter3_kernel<T><<<g1d(nh), T3, 0, S->st>>>(mode, (const T*)w.Yh, g, z, u);
     note_launch();
     CK3(cudaGetLastError());
+    return ASDSM_OK;
+}
+
+// Algorithm 3 with zero source on all cube holes of the FP32 grid z: v = G f per hole.
+int fill_g3(Solver3D* S, float* z) {
+    const Geo3& g = S->g;
+    const int P = g.hc * g.hc * g.hc, K = 6 * g.hc * g.hc, H = g.mc * g.mc * g.mc;
+    const PMark3 pm = prof3_begin(S);
+    faces3_kernel<<<g1d((long long)K * H), T3, 0, S->st>>>(z, g, S->faces);
+    const dim3 grid((H + GB_N - 1) / GB_N, (P + GB_M - 1) / GB_M);
+    fill_g3_kernel<<<grid, GB_T, 0, S->st>>>(S->G3, S->G3_KP, S->faces, P, K, H, g, z);
+    note_launch(2);
+    CK3(cudaGetLastError());
+    prof3_end(S, pm, P3_FILL, 4.0 * ((double)K * H * 2.0 + (double)P * H + (double)P * K), 2.0 * P * (double)K * H);
     return ASDSM_OK;
 }
 
@@ -1093,6 +1482,10 @@ int merge3(Solver3D* S, int pi, bool initial, int choice, T* z) {
     m.W = (const T*)S->W[pi];
     m.z = z;
     const long long lines = 3LL * (g.Nf - g.Nc) * g.Nc * g.Nc + (long long)g.Nc * g.Nc * g.Nc;
+    const PMark3 pm = prof3_begin(S);
+    struct End { Solver3D* S; PMark3 pm; double b, f; ~End() { prof3_end(S, pm, P3_MERGE, b, f); } }
+        end{S, pm, sizeof(T) * (3.0 * g.Nc * g.plane + (double)g.skel + 2.0 * lines),
+            2.0 * 3.0 * g.Nc * g.plane * 3.0 * g.Nc};
     uhat3_kernel<T><<<g1d(lines), T3, 0, S->st>>>(m, g);
     dim3 grid((g.Nf + MP - 1) / MP, (g.Nf + MQ - 1) / MQ, 3 * g.Nc);
     plane_corr_kernel<T><<<grid, MP * MQ, 0, S->st>>>(m, g);
@@ -1108,7 +1501,8 @@ template <typename T>
 int correction3(Solver3D* S, int pi, int choice, T* z) {
     if (int rc = planes3<T>(S, pi, true)) return rc;
     if (int rc = merge3<T>(S, pi, false, choice, z)) return rc;
-    return fill3<T>(S, pi, 1, z, nullptr, nullptr);
+    if constexpr (sizeof(T) == 4) return fill_g3(S, z);
+    else return fill3<T>(S, pi, 1, z, nullptr, nullptr);
 }
 
 // Algorithm 1 with b_cc in 3D: u's interior receives u^(0) (u's ring = g).
@@ -1161,6 +1555,18 @@ uint64_t splitmix64_3(uint64_t z) {
 
 // Family drawn by the random choice of Algorithm 2 at sweep k (R22).
 int choice3(uint64_t seed, int k) { return (int)(splitmix64_3(seed + (uint64_t)(k + 1) * kGolden) % 3ull); }
+
+// FP64 coefficients as float pairs (hi, lo = rounding of the remainder) on the device.
+int upload_pairs(Solver3D* S, const double* v, int n) {
+    static thread_local std::vector<float2> tmp;
+    tmp.resize((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const float hi = (float)v[i];
+        tmp[(size_t)i] = make_float2(hi, (float)(v[i] - (double)hi));
+    }
+    CK3(cudaMemcpyAsync(S->dcoef2, tmp.data(), (size_t)n * sizeof(float2), cudaMemcpyHostToDevice, S->st));
+    return ASDSM_OK;
+}
 
 int read3(Solver3D* S, const double* dev, int count) {
     CK3(cudaMemcpyAsync(S->hsmall, dev, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, S->st));
@@ -1225,15 +1631,27 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
         if (need_true) {
             // Checkpoint: u receives the part of the cycle's update not applied yet,
             // then the true FP64 residual replaces the tracked one.
+            const double nf3 = (double)g.Nf * g.Nf * g.Nf;
             if (kc > 0) {
                 for (int i = 0; i < kc; ++i) { dc[i] = c[i] - c_app[i]; c_app[i] = c[i]; }
-                CK3(cudaMemcpyAsync(S->dcoef, dc.data(), (size_t)kc * sizeof(double), cudaMemcpyHostToDevice, st));
-                update_many_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(u, Z, g.NN, kc, S->dcoef, g);
+                const PMark3 pm = prof3_begin(S);
+                if constexpr (sizeof(T) == 4) {
+                    if (int rc = upload_pairs(S, dc.data(), kc)) return rc;
+                    update_many_f32_kernel<<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(u, Z, g.NN, kc, S->dcoef2, g);
+                } else {
+                    CK3(cudaMemcpyAsync(S->dcoef, dc.data(), (size_t)kc * sizeof(double), cudaMemcpyHostToDevice, st));
+                    update_many_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(u, Z, g.NN, kc, S->dcoef, g);
+                }
                 note_launch();
                 CK3(cudaGetLastError());
+                prof3_end(S, pm, P3_UPDATE, nf3 * (16.0 + sizeof(T) * kc), 2.0 * kc * nf3);
                 CK3(cudaStreamSynchronize(st));      // dcoef is rewritten before the next launch that reads it
             }
-            if (int rc = residual3<T>(S, pi, s, u, true)) return rc;
+            {
+                const PMark3 pm = prof3_begin(S);
+                if (int rc = residual3<T>(S, pi, s, u, true)) return rc;
+                prof3_end(S, pm, P3_RESID, nf3 * 16.0 + 8.0 * g.skel + sizeof(T) * 3.0 * g.Nc * g.plane, 14.0 * nf3);
+            }
             if (int rc = read3(S, S->dsmall, 2)) return rc;
             const double rr = S->hsmall[0];
             rh2 = S->hsmall[1];
@@ -1278,14 +1696,21 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
         ++k;
         // Least squares on the skeleton rows: A e there and its products with the
         // tracked residual and the cycle's orthonormal images.
+        const PMark3 pm_gcr = prof3_begin(S);
+        const double gcr_bytes = (double)g.skel * (sizeof(T) * (3.0 + 2.0 * kc) + 16.0);
+        const double gcr_flops = (double)g.skel * (14.0 + 6.0 * kc + 6.0);
         skel_apply3_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(z, g, S->sten, (T*)w.q);
         const dim3 dgrid(DK_CHUNKS, std::max(1, (kc + DK_VEC - 1) / DK_VEC));
-        dots_many_kernel<T><<<dgrid, T3, 0, st>>>((const T*)w.q, w.rs, V, g.skel, g.skel, kc, S->dpart);
+        if constexpr (sizeof(T) == 4)
+            dots_many_f32_kernel<<<dgrid, T3, 0, st>>>((const float*)w.q, w.rs, V, g.skel, g.skel, kc, S->dpart);
+        else
+            dots_many_kernel<T><<<dgrid, T3, 0, st>>>((const T*)w.q, w.rs, V, g.skel, g.skel, kc, S->dpart);
         const int ncol = 3 + 2 * kc;
         sum_chunks_kernel<<<(ncol + 31) / 32, 32, 0, st>>>(S->dpart, ncol, S->dsum);
         note_launch(3);
         CK3(cudaGetLastError());
         if (int rc = read3(S, S->dsum, ncol)) return rc;
+        prof3_end(S, pm_gcr, P3_GCR, gcr_bytes, gcr_flops);
         const double qq = S->hsmall[0], qr = S->hsmall[1], rr = S->hsmall[2];
         if (m == 1) {
             // The paper's clamped optimal scaling: s_hat = argmin_{s >= 0} ||r - s A e||.
@@ -1322,11 +1747,23 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
         for (int j = 0; j < kc; ++j)
             for (int i = 0; i <= j; ++i) Tm[(size_t)i * m + kc] -= beta[j] * Tm[(size_t)i * m + j] / nu;
         for (int i = 0; i <= kc; ++i) c[i] += alpha_ * Tm[(size_t)i * m + kc];
-        if (kc > 0) CK3(cudaMemcpyAsync(S->dcoef, beta.data(), (size_t)kc * sizeof(double), cudaMemcpyHostToDevice, st));
-        combine_many_kernel<T><<<g1d(g.skel), T3, 0, st>>>((const T*)w.q, V, g.skel, g.skel, kc, S->dcoef, 1.0 / nu,
-                                                         alpha_, w.rs, S->partials);
-        note_launch();
-        CK3(cudaGetLastError());
+        {
+            const PMark3 pm = prof3_begin(S);
+            if constexpr (sizeof(T) == 4) {
+                if (kc > 0)
+                    if (int rc = upload_pairs(S, beta.data(), kc)) return rc;
+                combine_many_f32_kernel<<<g1d(g.skel), T3, 0, st>>>((const float*)w.q, V, g.skel, g.skel, kc, S->dcoef2,
+                                                                   1.0 / nu, alpha_, w.rs);
+            } else {
+                if (kc > 0)
+                    CK3(cudaMemcpyAsync(S->dcoef, beta.data(), (size_t)kc * sizeof(double), cudaMemcpyHostToDevice, st));
+                combine_many_kernel<T><<<g1d(g.skel), T3, 0, st>>>((const T*)w.q, V, g.skel, g.skel, kc, S->dcoef,
+                                                                 1.0 / nu, alpha_, w.rs, S->partials);
+            }
+            note_launch();
+            CK3(cudaGetLastError());
+            prof3_end(S, pm, P3_GCR, (double)g.skel * (sizeof(T) * (2.0 + kc) + 16.0), (double)g.skel * 2.0 * (kc + 2));
+        }
         ++kc;
         // ||r - alpha V_kc||^2 = ||r||^2 - alpha^2 for the orthonormal V_kc with alpha = <r, V_kc>.
         const double rel_t = rel_of(rr - alpha_ * alpha_ + rh2);
@@ -1341,10 +1778,12 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
             need_true = true;
             continue;
         }
+        const PMark3 pm_pl = prof3_begin(S);
         planes_from_skel_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(w.rs, g, (T*)w.F[0], (T*)w.F[1],
                                                                                    (T*)w.F[2]);
         note_launch();
         CK3(cudaGetLastError());
+        prof3_end(S, pm_pl, P3_GCR, 8.0 * g.skel + sizeof(T) * 3.0 * g.Nc * g.plane, 0.0);
     }
     // The largest hole residual of the returned iterate.
     const long long nh = (long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc;
@@ -1360,6 +1799,7 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
     float ms_setup = 0.f, ms_all = 0.f;
     cudaEventElapsedTime(&ms_setup, S->ev0, S->ev1);
     cudaEventElapsedTime(&ms_all, S->ev0, S->ev2);
+    prof3_resolve(S);
     if (stats) {
         asdsm_stats stt{};
         stt.sweeps = k;
@@ -1435,11 +1875,16 @@ int s3_create(const asdsm_desc* d, const asdsm_opts* o, cudaStream_t st, Solver3
     if ((e = cudaMalloc(&S->dsmall, 256 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
     if ((e = cudaMallocHost(&S->hsmall, 4096 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
     if ((e = cudaMalloc(&S->dcoef, kMaxM3 * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
+    if ((e = cudaMalloc(&S->dcoef2, kMaxM3 * sizeof(float2))) != cudaSuccess) return fail(report_cuda_error(e));
     if ((e = cudaMalloc(&S->dsum, (2 * kMaxM3 + 3) * sizeof(double))) != cudaSuccess) return fail(report_cuda_error(e));
     if ((e = cudaMalloc(&S->dpart, (size_t)(2 * kMaxM3 + 3) * DK_CHUNKS * sizeof(double))) != cudaSuccess)
         return fail(report_cuda_error(e));
     for (cudaEvent_t* ev : {&S->ev0, &S->ev1, &S->ev2})
         if ((e = cudaEventCreate(ev)) != cudaSuccess) return fail(report_cuda_error(e));
+    for (cudaEvent_t* ev : {&S->evf[0], &S->evf[1], &S->evf[2]})
+        if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return fail(report_cuda_error(e));
+    for (cudaStream_t* fs : {&S->fork[0], &S->fork[1], &S->cap})
+        if ((e = cudaStreamCreateWithFlags(fs, cudaStreamNonBlocking)) != cudaSuccess) return fail(report_cuda_error(e));
     *out = S;
     return ASDSM_OK;
 }
@@ -1499,7 +1944,7 @@ int submesh3(Solver3D* S, int pi, int mesh, const double* in, double* out) {
         const long long n = (long long)g.Nc * g.plane;
         conv_in(w.F[mesh], n);
         int nb = 0;
-        if (int rc = plane_solve3<T>(S, pi, mesh, S->partials, &nb)) return rc;
+        if (int rc = plane_solve3<T>(S, pi, mesh, S->partials, &nb, st)) return rc;
         conv_out(w.U[mesh], n);
     } else if (mesh < 6) {
         const int a = mesh - 3;
@@ -1514,8 +1959,19 @@ int submesh3(Solver3D* S, int pi, int mesh, const double* in, double* out) {
         BcrSys<T> sys = sys3<T>(S->coarse[pi], w.Xc, w.Yc);
         CK3(bcr_solve<T>(&sys, 1, st));
         conv_out(w.Yc, n);
-    } else {
+    } else if (mesh == 7) {
         if (int rc = fill3<T>(S, pi, 3, (T*)nullptr, in, out)) return rc;
+    } else {
+        // Algorithm 3 with zero source: in's skeleton values as Dirichlet data, out's hole points receive the fill.
+        T* z = (T*)w.uh;
+        conv_in(z, g.NN);
+        if constexpr (sizeof(T) == 4) {
+            if (int rc = fill_g3(S, z)) return rc;
+        } else {
+            if (int rc = fill3<T>(S, pi, 1, z, nullptr, nullptr)) return rc;
+        }
+        hole_copy3_kernel<T><<<g1d((long long)g.mc * g.mc * g.mc * g.hc * g.hc * g.hc), T3, 0, st>>>(z, g, out);
+        note_launch();
     }
     CK3(cudaGetLastError());
     CK3(cudaStreamSynchronize(st));
@@ -1524,9 +1980,24 @@ int submesh3(Solver3D* S, int pi, int mesh, const double* in, double* out) {
 }  // namespace
 
 int s3_submesh_solve(Solver3D* S, int mesh, const double* in, double* out) {
-    if (mesh < 0 || mesh > 7) return ASDSM_ERR_INVALID;
+    if (mesh < 0 || mesh > 8) return ASDSM_ERR_INVALID;
     return S->opts.precision == ASDSM_FP64 ? submesh3<double>(S, 0, mesh, in, out)
                                            : submesh3<float>(S, 1, mesh, in, out);
+}
+
+int s3_profile(Solver3D* S, int enable) {
+    S->prof = enable != 0;
+    std::memset(S->pc, 0, sizeof(S->pc));
+    for (int c = 0; c < P3_COUNT; ++c) std::strncpy(S->pc[c].name, kProf3Names[c], sizeof(S->pc[c].name) - 1);
+    S->marks.clear();
+    S->evnext = 0;
+    return ASDSM_OK;
+}
+
+int s3_profile_read(Solver3D* S, asdsm_kprof* out, int cap) {
+    const int n = std::min<int>(cap, P3_COUNT);
+    for (int c = 0; c < n; ++c) out[c] = S->pc[c];
+    return n;
 }
 
 int s3_history(Solver3D* S, double* hist, int cap) {
@@ -1555,6 +2026,17 @@ void s3_destroy(Solver3D* S) {
     if (S->hsmall) cudaFreeHost(S->hsmall);
     for (double* p : {S->dcoef, S->dsum, S->dpart})
         if (p) cudaFree(p);
+    if (S->dcoef2) cudaFree(S->dcoef2);
+    for (auto& row : S->pgraph)
+        for (auto& pg : row)
+            if (pg.exec) cudaGraphExecDestroy(pg.exec);
+    for (cudaEvent_t e : S->evf)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t fs : {S->fork[0], S->fork[1], S->cap})
+        if (fs) cudaStreamDestroy(fs);
+    if (S->G3) cudaFree(S->G3);
+    if (S->faces) cudaFree(S->faces);
+    for (cudaEvent_t e : S->evpool) cudaEventDestroy(e);
     for (cudaEvent_t ev : {S->ev0, S->ev1, S->ev2})
         if (ev) cudaEventDestroy(ev);
     delete S;

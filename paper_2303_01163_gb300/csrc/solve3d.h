@@ -17,6 +17,8 @@ int s3_initial_guess(Solver3D* S, const double* s, double* u);
 int s3_residual(Solver3D* S, const double* s, const double* u, double* r, double* rel);
 int s3_submesh_solve(Solver3D* S, int mesh, const double* in, double* out);
 int s3_history(Solver3D* S, double* hist, int cap);
+int s3_profile(Solver3D* S, int enable);
+int s3_profile_read(Solver3D* S, asdsm_kprof* out, int cap);
 void s3_destroy(Solver3D* S);
 
 // Error reporting shared with api.cu (asdsm_last_error).

@@ -166,3 +166,26 @@ def test_3d_sizes_are_checked(lib):
         lib.Solver(65, 2, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0))            # holes of 31 points per side
     with pytest.raises(lib.AsdsmError):
         lib.Solver(33, 4, (1.0, -1.0, 1.0), (0.0, 0.0, 0.0))           # alpha <= 0
+
+
+@pytest.mark.parametrize("name,make,mc", CASES[:4] + [("rand65_mc4", lambda: wl.random_sine_3d(65, 8), 4)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_3d_homogeneous_fill_matches_oracle(lib, name, make, mc, precision):
+    """Algorithm 3 with zero source as the sweeps apply it (FP32: the product
+    with the hole extension operator; FP64: block cyclic reduction per hole)."""
+    import torch
+    p = make()
+    disc = o3.Discretisation3D(p.N, mc, p.alpha, p.beta)
+    rng = np.random.default_rng(11)
+    Z = np.zeros((p.N,) * 3)
+    Z[1:-1, 1:-1, 1:-1] = rng.normal(size=(disc.m.Nf,) * 3)
+    skel = disc.P_skel.T @ (disc.P_skel @ o3.interior(Z))            # skeleton values, zero holes
+    want = disc.P_holes @ disc.filler(skel, np.zeros_like(skel))
+    prec = lib.FP64 if precision == "fp64" else lib.MIXED
+    with lib.Solver(p.N, mc, p.alpha, p.beta, precision=prec) as sv:
+        out = _dev(np.full((p.N,) * 3, 7.0))
+        sv.submesh_solve(lib.MESH3_FILL, _dev(o3.to_grid(skel, np.zeros((p.N,) * 3))), out)
+        got = out.cpu().numpy()
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    assert _rel(disc.P_holes @ o3.interior(got), want) <= tol
+    assert np.all(disc.P_skel @ o3.interior(got) == 7.0)
