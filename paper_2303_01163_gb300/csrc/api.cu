@@ -648,7 +648,11 @@ int enqueue_sweep_body(asdsm_handle* h, int kc, int m, cudaStream_t st) {
     CK(gcr_dots<T>((const T*)w.q, (const T*)w.rskel, qpv, kc, g.skel, h->partials, &nb3, st));
     CK(reduce_partials(h->partials, nb3, 2 + 2 * kc, h->dsmall, st));
     CK(ctl_after_dots(h->dctl, h->dsmall, st));
-    if (m > 1) CK(combine_skeleton_dyn<T>((const T*)w.q, qpv, kc, &h->dctl->comb, g.skel, (T*)w.qp[kc], st));
+    if (m > 1) {
+        CK(combine_skeleton_dyn<T>((const T*)w.q, qpv, kc, &h->dctl->comb, g.skel, (T*)w.qp[kc], st));
+        // Inside a deferred cycle: the tracked residual and the next sweep's submesh right-hand sides.
+        CK(track_skeleton<T>((T*)w.rskel, (const T*)w.qp[kc], 0.0, &h->dctl->comb, g, (T*)w.Xfc, (T*)w.Xcf, st));
+    }
     return ASDSM_OK;
 }
 
@@ -777,11 +781,14 @@ int graph_start(asdsm_handle* h, SolveRun& r) {
     c.max_sweeps = op.max_sweeps; c.window = op.stagnation_window; c.m = m; c.mixed = sizeof(T) == 4;
     c.hist_cap = h->hist_cap;
     c.upd.live = 1;
+    c.defer = m > 1 && !h->cnn ? 1 : 0;
     CK(cudaMemcpyAsync(h->dctl, &c, sizeof(c), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->dflag, 0, sizeof(int), st));
-    // At most max_sweeps / kSweepsPerGraph + 2 launches: every replayed sweep
-    // either advances k or finds the solve ended, and k = max_sweeps ends it.
-    r.max_q = op.max_sweeps / kSweepsPerGraph + 2;
+    // A bounded number of launches: every replayed sweep advances k, ends a
+    // deferred GCR cycle early (at most once per cycle, and a cycle holds at
+    // least one sweep that advances k) or finds the solve ended, and
+    // k = max_sweeps ends it.
+    r.max_q = (2 * op.max_sweeps + 2) / kSweepsPerGraph + 3;
     r.q = 0;
     r.in_flight = 0;
     r.done = false;
@@ -1024,11 +1031,44 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
     // GCR bookkeeping (host, FP64).
     double Tm[kMaxM][kMaxM] = {};
     int kc = 0;                  // directions in the current cycle
-    UpdateTerms pend{};          // the previous sweep's update, applied by the next residual kernel
+    UpdateTerms pend{};          // the update the next residual kernel applies
     double hole_ref = 0.0;       // hole residual right after the last correction (0 before the first)
     bool hole_ref_pending = false;
     const bool trace = std::getenv("ASDSM_TRACE") != nullptr;
+    // GCR(m > 1) with a deferred update: a cycle's steps accumulate in cacc (in
+    // the basis of its raw directions) and reach u through the residual kernel
+    // of the cycle's next true residual; in between the residual is tracked on
+    // the skeleton (||r||^2 = rr_skel + rh2, the hole part of the cycle's first
+    // residual).  Not with a learned direction, whose features need the full residual.
+    // Deferral stops for the rest of the solve near the tolerance, or when a
+    // cycle's true residual exceeds twice its tracked value (rounding of the
+    // FP32 directions in the holes); the stagnation test then holds for a window.
+    bool defer = m > 1 && !h->cnn;
+    bool tracked = false, cycle_ended = false;
+    int stag_hold = 0;
+    double cacc[kMaxM] = {};
+    double rr_skel = 0.0, rh2c = 0.0;
+    auto end_cycle = [&](int count) {
+        pend.count = count;
+        for (int i = 0; i < count; ++i) { pend.z[i] = w.z[i]; pend.coef[i] = cacc[i]; cacc[i] = 0.0; }
+        tracked = false;
+        cycle_ended = count > 0;
+        kc = 0;
+    };
     for (;;) {
+      if (tracked) {
+        rel = bnorm > 0 ? std::sqrt(std::max(rr_skel, 0.0) + rh2c) / bnorm : std::sqrt(std::max(rr_skel, 0.0) + rh2c);
+        const int win = op.stagnation_window;
+        const bool stag = win > 0 && (int)rhist.size() > win &&
+                          rel > (1.0 - op.stagnation_factor) * rhist[rhist.size() - 1 - win];
+        if (!(rel > op.tol) || k >= op.max_sweeps || stag) {
+            end_cycle(kc);               // the next true residual decides
+            continue;
+        }
+        if (!std::isfinite(rel)) { status = ASDSM_ERR_NAN; break; }
+        rhist.push_back(rel);
+        if (k == 0) rel0 = rel;
+      } else {
         // ---- fine residual (with the pending update fused) ----
         ResidOut o{};
         o.rfc = w.Xfc; o.rcf = w.Xcf; o.rskel = w.rskel; o.partials = h->partials;
@@ -1064,14 +1104,25 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
         }
         const double rnorm = std::sqrt(r2), hnorm = std::sqrt(rh2);
         rel = bnorm > 0 ? rnorm / bnorm : rnorm;
+        const int win = op.stagnation_window;
+        if (defer && cycle_ended) {
+            const double p2 = std::max(rr_skel, 0.0) + rh2c;
+            const double pred = bnorm > 0 ? std::sqrt(p2) / bnorm : std::sqrt(p2);
+            if (rel > 2.0 * pred) { defer = false; stag_hold = win; }
+        }
+        if (defer && rel < 100.0 * op.tol) defer = false;
+        cycle_ended = false;
+        rr_skel = r2 - rh2;
+        rh2c = rh2;
         if (!std::isfinite(rel)) { status = ASDSM_ERR_NAN; break; }
         rhist.push_back(rel);
         if (k == 0) rel0 = rel;
         if (rel <= op.tol) { status = ASDSM_OK; break; }
         if (k >= op.max_sweeps) { status = ASDSM_NOT_CONVERGED; break; }
-        const int win = op.stagnation_window;
-        if (win > 0 && (int)rhist.size() > win &&
-            rhist.back() > (1.0 - op.stagnation_factor) * rhist[rhist.size() - 1 - win]) {
+        if (stag_hold > 0) {
+            --stag_hold;
+        } else if (win > 0 && (int)rhist.size() > win &&
+                   rhist.back() > (1.0 - op.stagnation_factor) * rhist[rhist.size() - 1 - win]) {
             status = ASDSM_STAGNATED;
             break;
         }
@@ -1103,6 +1154,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
             ++k;
             continue;
         }
+      }
         // ---- the correction: Algorithm 1 without b_cc on the residual ----
         const int bit = choice_bit(op.seed, k);
         BcrSys<T> sys[2] = {sys_of<T>(h->fc[pi], w.Xfc, w.Yfc), sys_of<T>(h->cf[pi], w.Xcf, w.Ycf)};
@@ -1192,14 +1244,27 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
             Tm[kc][kc] = 1.0 / nu;
             for (int j = 0; j < kc; ++j)
                 for (int i = 0; i <= j; ++i) Tm[i][kc] -= beta_[j] * Tm[i][j] / nu;
+            const T* qps[kMaxM];
+            for (int j = 0; j < kc; ++j) qps[j] = (const T*)w.qp[j];
+            CK(combine_skeleton<T>((const T*)w.q, qps, beta_, kc, 1.0 / nu, g.skel, (T*)w.qp[kc], st));
+            if (defer) {
+                for (int i = 0; i <= kc; ++i) cacc[i] += alpha_ * Tm[i][kc];
+                rr_skel -= alpha_ * alpha_;
+                if (kc + 1 >= m) {
+                    end_cycle(kc + 1);
+                } else {
+                    CK(track_skeleton<T>((T*)w.rskel, (const T*)w.qp[kc], alpha_, nullptr, g, (T*)w.Xfc, (T*)w.Xcf,
+                                         st));
+                    tracked = true;
+                    ++kc;
+                }
+                return 0;
+            }
             for (int i = 0; i <= kc; ++i) {
                 pend.z[i] = w.z[i];
                 pend.coef[i] = (add && i < pend.count ? pend.coef[i] : 0.0) + alpha_ * Tm[i][kc];
             }
             pend.count = kc + 1;
-            const T* qps[kMaxM];
-            for (int j = 0; j < kc; ++j) qps[j] = (const T*)w.qp[j];
-            CK(combine_skeleton<T>((const T*)w.q, qps, beta_, kc, 1.0 / nu, g.skel, (T*)w.qp[kc], st));
             ++kc;
             if (kc >= m) kc = 0;
             return 0;
@@ -1207,7 +1272,8 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
         const int dep = gcr_step(z, false);
         if (dep < 0) return dep;
         if (dep == 1) {
-            kc = 0;                           // dependent direction: restart the cycle
+            if (defer) end_cycle(kc);         // dependent direction: restart the cycle
+            kc = 0;
             ++k;
             continue;
         }
@@ -1215,7 +1281,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
         // whose slots the pending update still reads).
         if (mixed && h->cnn && m > 1 && kc != 0) {
             T* zc = (T*)w.z[kc];
-            if (int rc = cnn_direction(h, r2, (const float*)z, (float*)zc)) return rc;
+            if (int rc = cnn_direction(h, rr_skel + rh2c, (const float*)z, (float*)zc)) return rc;
             CK(fill_homogeneous<T>(h, pi, zc, st));
             const int dep2 = gcr_step(zc, true);
             if (dep2 < 0) return dep2;

@@ -223,7 +223,8 @@ struct DynUpdate {
     int live;           // 0 once the solve has ended: the residual kernel returns at once
     int count;          // pending directions: u += sum_j coef_j z_j, j < count
     int par;            // current iterate: buffer 0 (par = 0) or buffer 1
-    int pad;
+    int skip;           // 1: a sweep inside a GCR cycle, the residual is tracked on the skeleton
+                        //    and the residual kernel returns at once
     double coef[16];    // step lengths (FP64 path)
     float cf[16];       // step lengths times 2^S, rounded to FP32 (mixed path)
 };
@@ -302,13 +303,21 @@ cudaError_t combine_skeleton(const T* q, const T* const* Qp, const double* beta,
 // Device-held GCR combination: qp = (q - sum beta_j Qp_j) * inv_nu when run != 0.
 struct CtlCombine {
     int run;
-    int pad;
+    int track;          // 1: then r_skel -= alpha qp (the tracked residual) and the submesh
+                        //    right-hand sides are gathered from it for the next sweep
     double beta[16];
     double inv_nu;
+    double alpha;
 };
 template <typename T>
 cudaError_t combine_skeleton_dyn(const T* q, const T* const* Qp, int k, const CtlCombine* c,
                                  long long n, T* out, cudaStream_t st);
+// The tracked residual of a deferred GCR cycle: r_skel -= alpha qp on the compact
+// skeleton and r_fc, r_cf (the submesh right-hand sides, BCR layouts) gathered
+// from it; with track = 0 (from the device control when c is given) nothing is done.
+template <typename T>
+cudaError_t track_skeleton(T* rskel, const T* qp, double alpha, const CtlCombine* c, const Geometry& g, T* rfc,
+                           T* rcf, cudaStream_t st);
 
 // Sweep control on the device (control.cu) ---------------------------------------
 // The decisions of Algorithm 4 that the host loop takes between sweeps
@@ -325,6 +334,17 @@ struct SweepCtl {
     int runs[20];                 // executions of each branch (sweep bodies 0..m-1, hole fixes m, m+1)
     double hole_ref, rel0, rel;
     double Tm[16][16];
+    // GCR cycles with a deferred update (m > 1): the cycle's step coefficients
+    // in the basis of its raw directions, applied by the residual kernel of the
+    // cycle's next true residual; in between, ||r||^2 is tracked on the skeleton
+    // (rr_skel) plus the hole part of the cycle's first residual (rh2).
+    double cacc[16];
+    double rr_skel, rh2;
+    int defer;          // deferred cycles in use (m > 1); cleared for the rest of the solve near the
+                        // tolerance or when a cycle's true residual exceeds twice its tracked value
+    int cycle_ended;    // the residual about to be computed closes a deferred cycle
+    int stag_hold;      // sweeps without the stagnation test (after a tracked value was replaced)
+    int pad3;
     DynUpdate upd;
     int choice;
     int pad2;

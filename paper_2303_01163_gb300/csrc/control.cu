@@ -46,33 +46,76 @@ __global__ void ctl_after_residual_kernel(SweepCtl* c, const double* __restrict_
         cudaGraphSetConditional(sw, (unsigned)(c->m + 2));
         return;
     }
-    // The residual kernel has applied the pending update into the other buffer.
-    if (c->upd.count > 0) c->upd.par ^= 1;
-    c->upd.count = 0;
     c->comb.run = 0;
-    if (c->mixed) {
-        const int ovf = *overflow;
-        *overflow = 0;
-        if (ovf) { finish(c, ASDSM_ERR_RANGE, sw); return; }
+    c->comb.track = 0;
+    const bool tracked = c->upd.skip != 0;
+    double rel, rnorm = 0.0, hnorm = 0.0;
+    if (!tracked) {
+        // The residual kernel has applied the pending update into the other buffer.
+        if (c->upd.count > 0) c->upd.par ^= 1;
+        c->upd.count = 0;
+        if (c->mixed) {
+            const int ovf = *overflow;
+            *overflow = 0;
+            if (ovf) { finish(c, ASDSM_ERR_RANGE, sw); return; }
+        }
+        rnorm = sqrt(sums[0]);
+        hnorm = sqrt(sums[1]);
+        rel = c->bnorm > 0 ? rnorm / c->bnorm : rnorm;
+        if (c->defer && c->cycle_ended) {
+            // The cycle's tracked prediction of this residual against the true one.
+            const double p2 = fmax(c->rr_skel, 0.0) + c->rh2;
+            const double pred = c->bnorm > 0 ? sqrt(p2) / c->bnorm : sqrt(p2);
+            if (rel > 2.0 * pred) { c->defer = 0; c->stag_hold = c->window; }
+        }
+        if (c->defer && rel < 100.0 * c->tol) c->defer = 0;
+        c->cycle_ended = 0;
+        c->rr_skel = sums[0] - sums[1];
+        c->rh2 = sums[1];
+    } else {
+        // Inside a deferred GCR cycle: the residual of the virtual iterate, tracked.
+        const double r2 = fmax(c->rr_skel, 0.0) + c->rh2;
+        rel = c->bnorm > 0 ? sqrt(r2) / c->bnorm : sqrt(r2);
+        const int win = c->window;
+        const bool stag = win > 0 && c->nhist > win && c->nhist <= c->hist_cap &&
+                          rel > (1.0 - c->stagnation_factor) * hist[c->nhist - 1 - win];
+        if (!(rel > c->tol) || c->k >= c->max_sweeps || stag) {
+            // End the cycle here: its update is applied by the next residual kernel,
+            // whose true residual (replacing this tracked value) takes the decision.
+            c->upd.count = c->kc;
+            for (int i = 0; i < c->kc; ++i) {
+                c->upd.coef[i] = c->cacc[i];
+                c->upd.cf[i] = (float)(c->cacc[i] * c->scale);
+                c->cacc[i] = 0.0;
+            }
+            c->upd.skip = 0;
+            c->cycle_ended = c->kc > 0;
+            c->kc = 0;
+            c->branch = c->m + 2;
+            cudaGraphSetConditional(sw, (unsigned)(c->m + 2));
+            return;
+        }
     }
-    const double rnorm = sqrt(sums[0]), hnorm = sqrt(sums[1]);
-    const double rel = c->bnorm > 0 ? rnorm / c->bnorm : rnorm;
     c->rel = rel;
     if (!isfinite(rel)) { finish(c, ASDSM_ERR_NAN, sw); return; }
     if (c->nhist < c->hist_cap) hist[c->nhist] = rel;
     c->nhist += 1;
     if (c->k == 0) c->rel0 = rel;
-    if (rel <= c->tol) { finish(c, ASDSM_OK, sw); return; }
-    if (c->k >= c->max_sweeps) { finish(c, ASDSM_NOT_CONVERGED, sw); return; }
-    const int win = c->window;
-    if (win > 0 && c->nhist > win && c->nhist <= c->hist_cap &&
-        rel > (1.0 - c->stagnation_factor) * hist[c->nhist - 1 - win]) {
-        finish(c, ASDSM_STAGNATED, sw);
-        return;
+    if (!tracked) {
+        if (rel <= c->tol) { finish(c, ASDSM_OK, sw); return; }
+        if (c->k >= c->max_sweeps) { finish(c, ASDSM_NOT_CONVERGED, sw); return; }
+        const int win = c->window;
+        if (c->stag_hold > 0) {
+            c->stag_hold -= 1;
+        } else if (win > 0 && c->nhist > win && c->nhist <= c->hist_cap &&
+                   rel > (1.0 - c->stagnation_factor) * hist[c->nhist - 1 - win]) {
+            finish(c, ASDSM_STAGNATED, sw);
+            return;
+        }
+        if (c->hole_ref_pending) { c->hole_ref = hnorm; c->hole_ref_pending = 0; }
     }
-    if (c->hole_ref_pending) { c->hole_ref = hnorm; c->hole_ref_pending = 0; }
     int branch;
-    if (hnorm > c->hole_fix_ratio * rnorm && hnorm > c->hole_fix_growth * c->hole_ref) {
+    if (!tracked && hnorm > c->hole_fix_ratio * rnorm && hnorm > c->hole_fix_growth * c->hole_ref) {
         branch = c->m + c->upd.par;      // hole correction on the current iterate buffer
         c->hole_fixes += 1;
         c->kc = 0;
@@ -109,8 +152,21 @@ __global__ void ctl_after_dots_kernel(SweepCtl* c, const double* __restrict__ do
         rq[j] = dots[3 + 2 * j];
         nu2 -= beta[j] * beta[j];
     }
+    // The cycle's update so far goes to the next residual kernel.
+    auto end_cycle = [&](int count) {
+        c->upd.count = count;
+        for (int i = 0; i < count; ++i) {
+            c->upd.coef[i] = c->cacc[i];
+            c->upd.cf[i] = (float)(c->cacc[i] * c->scale);
+            c->cacc[i] = 0.0;
+        }
+        c->upd.skip = 0;
+        c->cycle_ended = count > 0;
+        c->kc = 0;
+    };
     if (!(nu2 > 1e-24 * qq) || !(qq > 0)) {
-        c->kc = 0;                       // dependent direction: restart the cycle
+        if (c->defer) end_cycle(kc);     // dependent direction: restart the cycle
+        c->kc = 0;
         c->k += 1;
         return;
     }
@@ -118,22 +174,39 @@ __global__ void ctl_after_dots_kernel(SweepCtl* c, const double* __restrict__ do
     double alpha = qr;
     for (int j = 0; j < kc; ++j) alpha -= beta[j] * rq[j];
     alpha /= nu;
-    // Column kc of T: z'_kc = sum_i T[i][kc] z_i.
+    // Column kc of T: z'_kc = sum_i T[i][kc] z_i; the cycle's update is
+    // sum_k alpha_k z'_k = sum_i cacc_i z_i, applied when the cycle ends.
     for (int i = 0; i <= kc; ++i) c->Tm[i][kc] = 0.0;
     c->Tm[kc][kc] = 1.0 / nu;
     for (int j = 0; j < kc; ++j)
         for (int i = 0; i <= j; ++i) c->Tm[i][kc] -= beta[j] * c->Tm[i][j] / nu;
-    c->upd.count = kc + 1;
-    for (int i = 0; i <= kc; ++i) {
-        const double v = alpha * c->Tm[i][kc];
-        c->upd.coef[i] = v;
-        c->upd.cf[i] = (float)(v * c->scale);
-    }
     c->comb.run = 1;
     for (int j = 0; j < kc; ++j) c->comb.beta[j] = beta[j];
     c->comb.inv_nu = 1.0 / nu;
-    c->kc = kc + 1 >= m ? 0 : kc + 1;
+    c->comb.alpha = alpha;
     c->k += 1;
+    if (!c->defer) {
+        // The step goes to u at the next residual kernel; the cycle continues.
+        c->upd.count = kc + 1;
+        for (int i = 0; i <= kc; ++i) {
+            const double v = alpha * c->Tm[i][kc];
+            c->upd.coef[i] = v;
+            c->upd.cf[i] = (float)(v * c->scale);
+        }
+        c->upd.skip = 0;
+        c->kc = kc + 1 >= m ? 0 : kc + 1;
+        return;
+    }
+    for (int i = 0; i <= kc; ++i) c->cacc[i] += alpha * c->Tm[i][kc];
+    c->rr_skel -= alpha * alpha;         // ||r - alpha z'||^2 for the orthonormal image of z'
+    if (kc + 1 >= m) {
+        end_cycle(kc + 1);
+    } else {
+        c->upd.count = 0;
+        c->upd.skip = 1;
+        c->comb.track = 1;
+        c->kc = kc + 1;
+    }
 }
 
 }  // namespace

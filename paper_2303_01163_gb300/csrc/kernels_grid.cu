@@ -90,7 +90,7 @@ residual_fp64_kernel(const double* __restrict__ s, const double* u_in, double* u
     const double* ucur = u_in;
     double* unxt = u_out;
     if (up.dyn) {
-        if (!up.dyn->live) return;
+        if (!up.dyn->live || up.dyn->skip) return;
         count = up.dyn->count;
         if (up.dyn->par) { ucur = u_out; unxt = const_cast<double*>(u_in); }
     }
@@ -312,7 +312,7 @@ residual_mixed_kernel(const float* __restrict__ s_hi, const float* __restrict__ 
     const long long* U_in = U_in0;
     long long* U_out = U_out0;
     if (up.dyn) {
-        if (!up.dyn->live) return;
+        if (!up.dyn->live || up.dyn->skip) return;
         up.count = up.dyn->count;
 #pragma unroll
         for (int q = 0; q < 16; ++q) up.c[q] = up.dyn->cf[q];
@@ -1009,6 +1009,39 @@ cudaError_t skeleton_apply(const T* z, const Geometry& g, const Stencil& s, T* q
     return cudaGetLastError();
 }
 
+// The tracked residual of a deferred GCR cycle on the compact skeleton, and the
+// submesh right-hand sides gathered from it (fc lines [x][line], cf columns [y][column]).
+template <typename T>
+__global__ void track_skeleton_kernel(T* __restrict__ r, const T* __restrict__ qp, double alpha_h,
+                                      const CtlCombine* __restrict__ ctl, Geometry g, T* __restrict__ rfc,
+                                      T* __restrict__ rcf) {
+    if (ctl && !ctl->track) return;
+    const T a = (T)(ctl ? ctl->alpha : alpha_h);
+    const int n = g.n, Nf = g.Nf, Nc = g.Nc;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.skel; e += (long long)gridDim.x * blockDim.x) {
+        const T v = r[e] - a * qp[e];
+        r[e] = v;
+        if (e < (long long)Nc * Nf) {                        // fc line l, fine x (cross points included)
+            const int i = (int)(e % Nf) + 1, l = (int)(e / Nf);
+            rfc[(long long)(i - 1) * Nc + l] = v;
+            if (i % n == 0) rcf[(long long)((l + 1) * n - 1) * Nc + (i / n - 1)] = v;
+        } else {                                             // cf column point off the fc lines
+            const long long f = e - (long long)Nc * Nf;
+            const int yr = (int)(f / Nc), k = (int)(f % Nc);
+            const int j = yr + yr / (n - 1) + 1;
+            rcf[(long long)(j - 1) * Nc + k] = v;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t track_skeleton(T* rskel, const T* qp, double alpha, const CtlCombine* c, const Geometry& g, T* rfc,
+                           T* rcf, cudaStream_t st) {
+    track_skeleton_kernel<T><<<grid_for(g.skel), 256, 0, st>>>(rskel, qp, alpha, c, g, rfc, rcf);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t combine_skeleton(const T* q, const T* const* Qp, const double* beta, int k, double inv_nu,
                              long long n, T* out, cudaStream_t st) {
@@ -1142,6 +1175,7 @@ cudaError_t convert_array(const Ts* in, Td* out, long long n, cudaStream_t st) {
     template cudaError_t skeleton_apply<T>(const T*, const Geometry&, const Stencil&, T*, cudaStream_t); \
     template cudaError_t combine_skeleton<T>(const T*, const T* const*, const double*, int, double, long long, T*, cudaStream_t); \
     template cudaError_t combine_skeleton_dyn<T>(const T*, const T* const*, int, const CtlCombine*, long long, T*, cudaStream_t); \
+    template cudaError_t track_skeleton<T>(T*, const T*, double, const CtlCombine*, const Geometry&, T*, T*, cudaStream_t); \
     template cudaError_t fill_value<T>(T*, long long, T, cudaStream_t); \
     template cudaError_t ring_from<T>(const double*, T*, const Geometry&, int, cudaStream_t); \
     template cudaError_t maxabs<T>(const T*, long long, double*, int*, cudaStream_t);
