@@ -176,8 +176,8 @@ int asdsm_autotune(asdsm_handle* h, int precision);
  * the coarse system (2 x 16), then the Filler.  A level entry is
  * (TM << 8) | KS: TM = 16 or 64 rows per CTA on the FMA pipes with KS = 1, 2,
  * 4 or 8 CTAs per cluster splitting the reduction; TM = 32 the mma.sync
- * tensor-core kernel, TM = 128 the tcgen05 kernel (FP32 only, KS = 1); 0 the
- * built-in choice.  The Filler entry is 16 for the tensor-core kernel, 1..8
+ * tensor-core kernel (KS = 1), TM = 128 the tcgen05 kernel (FP32 only, KS =
+ * 1, 2 or 4 CTAs per cluster splitting the reduction); 0 the built-in choice.  The Filler entry is 16 for the tensor-core kernel, 1..8
  * for the block cyclic reduction kernel's warps per CTA, 0 for the default.  get returns the count written
  * (cap >= 130) or ASDSM_ERR_INVALID. */
 int asdsm_tune_get(const asdsm_handle* h, int32_t* out, int cap);
@@ -188,8 +188,8 @@ int asdsm_tune_set(asdsm_handle* h, const int32_t* in, int n);
 /* Check a saved tuning (n = 130 entries, layout as above) against the
  * encoding without a handle or any device work: every level entry 0,
  * (TM << 8) | KS with TM in {16, 64} and KS in {1, 2, 4, 8}, or - FP32 half
- * only - TM in {32, 128} with KS = 1; every Filler entry 0..8, or 16 in the
- * FP32 half.  Returns ASDSM_OK or ASDSM_ERR_INVALID. */
+ * only - TM = 32 with KS = 1 or TM = 128 with KS in {1, 2, 4}; every Filler
+ * entry 0..8, or 16 in the FP32 half.  Returns ASDSM_OK or ASDSM_ERR_INVALID. */
 int asdsm_tune_check(const int32_t* in, int n);
 
 /* Algorithm 4 (ASDSM).  The initial guess (Algorithm 1) has FP64 quality in

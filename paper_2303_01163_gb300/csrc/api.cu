@@ -908,7 +908,7 @@ int tune_bcr(asdsm_handle* h, const BcrSys<T>* sys, int ngroups, BcrTune* tune, 
                 if (tm == 32 && (sizeof(T) != 4 || !sys[0].Mw)) continue;
                 if (tm == 128 && (sizeof(T) != 4 || !sys[0].Ti)) continue;
                 for (int ks : {1, 2, 4, 8}) {
-                    if ((tm == 32 || tm == 128) && ks != 1) continue;
+                    if ((tm == 32 && ks != 1) || (tm == 128 && ks == 8)) continue;
                     tune->cfg[dir][l] = (tm << 8) | ks;
                     float ms = 0.f;
                     if (int rc = time_ms<T>(h, a, b, 5, &ms, [&]() -> int {
@@ -1704,7 +1704,7 @@ int asdsm_tune_check(const int32_t* in, int n) {
             if (v == 0) continue;
             const int tm = v >> 8, ks = v & 0xFF;
             const bool split_k = (tm == 16 || tm == 64) && (ks == 1 || ks == 2 || ks == 4 || ks == 8);
-            const bool tensor = pi == 1 && (tm == 32 || tm == 128) && ks == 1;
+            const bool tensor = pi == 1 && ((tm == 32 && ks == 1) || (tm == 128 && (ks == 1 || ks == 2 || ks == 4)));
             if (v < 0 || !(split_k || tensor)) return ASDSM_ERR_INVALID;
         }
         const int f = in[q++];

@@ -162,9 +162,10 @@ template <typename T>
 size_t fill_smem_bytes(int n, int L);
 
 // Tensor-core BCR level kernel (bcr_tc.cu), FP32 systems: the image of the
-// factors (BcrSys::Ti, TKC, TCB) and one level for 1 or 2 groups.
+// factors (BcrSys::Ti, TKC, TCB) and one level for 1 or 2 groups, the
+// reduction of each output tile split over ks (1, 2 or 4) CTAs of a cluster.
 void bcr_tc_image(const BcrFactors& f, std::vector<float>* img, int* KC, int* CB);
-cudaError_t bcr_tc_level(const BcrSys<float>& g0, const BcrSys<float>& g1, int ngroups, int level, bool backward,
+cudaError_t bcr_tc_level(const BcrSys<float>& g0, const BcrSys<float>& g1, int ngroups, int level, bool backward, int ks,
                          int maxRows, int nsys, cudaStream_t st);
 
 // Discrete harmonic extension of a C x C hole (Algorithm 3 with zero source,

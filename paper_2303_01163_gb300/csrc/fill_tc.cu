@@ -23,9 +23,9 @@
 // (the skeleton column of every hole row), so that each row is written whole.
 //
 // Precision: FP32 results from TF32 tensor-core products by splitting both
-// operands, x = hi + lo with hi = x with its 13 low mantissa bits cleared:
-// G z ~ G_lo z_hi + G_hi z_lo + G_hi z_hi (the G_lo z_lo term is ~2^-22
-// relative), accumulated in FP32 in tensor memory.
+// operands, x ~ hi + lo with hi and lo = x - hi both rounded to nearest TF32
+// (|x - hi - lo| <= 2^-22 |x|): G z ~ G_lo z_hi + G_hi z_lo + G_hi z_hi (the
+// G_lo z_lo term is of the same order), accumulated in FP32 in tensor memory.
 //
 // Every wait on an mbarrier is bounded (1 s by %globaltimer); on a timeout the
 // kernel sets *err, stops, and frees its tensor memory.
@@ -212,10 +212,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) fill_tc_kernel(FillTcArgs a) {
             unsigned char* pb = pB + st * TC_B_STAGE;
 #pragma unroll
             for (int kk = 0; kk < 32; ++kk) {
-                const float hi = tf32_hi(zr[kk]);
+                float hi, lo;
+                tf32_split(zr[kk], hi, lo);
                 const int off = half * TC_BBLK + swz_offset(h, kk);
                 *reinterpret_cast<float*>(pb + off) = hi;
-                *reinterpret_cast<float*>(pb + 2 * TC_BBLK + off) = zr[kk] - hi;
+                *reinterpret_cast<float*>(pb + 2 * TC_BBLK + off) = lo;
             }
             fence_async_smem();
             mbar_arrive(smem_u32(&bfull[st]));
@@ -326,8 +327,8 @@ void fill_tc_image(const std::vector<double>& G, std::vector<float>* img) {
             const int hp = y * TC_C + (x - 1);         // hole point (y+1, x) in row-major order
             for (int k = 0; k < TC_RING; ++k) {
                 const double gv = G[(size_t)hp * TC_RING + k];
-                const float hi = tc::tf32_hi((float)gv);
-                const float lo = (float)(gv - (double)hi);
+                const float hi = tc::tf32_rn((float)gv);
+                const float lo = tc::tf32_rn((float)(gv - (double)hi));
                 const int off = tc_offset(r, k);
                 std::memcpy(base + (size_t)(0 * TC_MT + mt) * 2 * TC_BLK + off, &hi, 4);
                 std::memcpy(base + (size_t)(1 * TC_MT + mt) * 2 * TC_BLK + off, &lo, 4);

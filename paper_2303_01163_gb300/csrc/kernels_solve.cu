@@ -567,7 +567,7 @@ cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, const 
         cudaError_t e = cudaSuccess;
         if constexpr (sizeof(T) == 4) {
             e = bcr_tc_level(reinterpret_cast<const BcrSys<float>&>(groups[0]), reinterpret_cast<const BcrSys<float>&>(g1),
-                             ngroups, level, kBackward, maxRows, nsys, st);
+                             ngroups, level, kBackward, ks == 2 || ks == 4 ? ks : 1, maxRows, nsys, st);
         }
         note_launch();
         if (e != cudaSuccess) return e;

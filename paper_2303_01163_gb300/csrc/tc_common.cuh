@@ -153,18 +153,26 @@ __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// TF32 split: hi keeps the 10 explicit mantissa bits of x, lo = x - hi (exact).
-__host__ __device__ __forceinline__ float tf32_hi(float x) {
+// TF32 rounding to nearest (ties away from zero) of a finite x: the 10
+// explicit mantissa bits kept, the 13 below them rounded off.
+__host__ __device__ __forceinline__ float tf32_rn(float x) {
 #ifdef __CUDA_ARCH__
-    return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 #else
     uint32_t b;
     __builtin_memcpy(&b, &x, 4);
-    b &= 0xFFFFE000u;
+    b = (b + 0x1000u) & 0xFFFFE000u;
     float r;
     __builtin_memcpy(&r, &b, 4);
     return r;
 #endif
+}
+
+// x ~ hi + lo with hi = tf32_rn(x) and lo = tf32_rn(x - hi) (x - hi is exact in
+// FP32): both parts exact TF32 operands, |x - hi - lo| <= 2^-22 |x|.
+__host__ __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+    hi = tf32_rn(x);
+    lo = tf32_rn(x - hi);
 }
 
 }  // namespace tc

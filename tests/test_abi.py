@@ -92,11 +92,15 @@ def test_saved_tuning_passes_the_check_and_bad_entries_fail(lib):
     assert _tune_check(lib, saved) == 0
     assert _tune_check(lib, [0] * 130) == 0
     assert _tune_check(lib, saved[:129]) == -1                      # wrong count
+    good = list(saved)
+    good[65], good[66] = (128 << 8) | 2, (128 << 8) | 4               # tcgen05 kernel split 2 and 4 ways
+    assert _tune_check(lib, good) == 0
     for index, value in [(0, (48 << 8) | 1),       # rows per CTA not in {16, 64}
                          (1, (16 << 8) | 3),       # split factor not a power of two up to 8
                          (2, (128 << 8) | 1),      # tcgen05 kernel in the FP64 half
                          (3, (32 << 8) | 1),       # mma.sync kernel in the FP64 half
-                         (65, (128 << 8) | 2),     # tcgen05 kernel split
+                         (65, (128 << 8) | 8),     # tcgen05 kernel split 8 ways (1, 2 or 4 only)
+                         (66, (32 << 8) | 2),      # mma.sync kernel split
                          (64, 16),                 # tensor-core Filler in the FP64 half
                          (129, 9),                 # Filler warps above 8
                          (70, -1)]:

@@ -283,14 +283,15 @@ def test_resume_from_a_zero_interior_rescales_the_accumulator(lib):
     assert abs(res.stats["rel_res_fp64"] - rel) <= 1e-3 * rel
 
 
-@pytest.mark.parametrize("tm", [32, 128])
+@pytest.mark.parametrize("tm,ks", [(32, 1), (128, 1), (128, 2), (128, 4)])
 @pytest.mark.parametrize("name,make,mc", CASES[:3] + [("fourier257", lambda: wl.random_fourier_2d(257, 5), 8),
                                                       ("fourier513_c255", lambda: wl.random_fourier_2d(513, 6), 256)])
-def test_tensor_core_level_kernels_match_oracle(lib, name, make, mc, tm):
+def test_tensor_core_level_kernels_match_oracle(lib, name, make, mc, tm, ks):
     """Every level of the FP32 submesh solves forced onto a tensor-core kernel
     (TF32 split products; tm = 32: the mma.sync kernel for A_fc and A_cf,
-    tm = 128: the tcgen05 kernel for A_fc, A_cf and A_cc): the solves within
-    the FP32 bar, and a mixed solve still reaches the fine solution."""
+    tm = 128: the tcgen05 kernel for A_fc, A_cf and A_cc, its reduction split
+    over ks CTAs of a cluster): the solves within the FP32 bar, and a mixed
+    solve still reaches the fine solution."""
     import torch
     p = make()
     disc = orc.Discretisation2D(p.N, mc, p.alpha, p.beta)
@@ -301,7 +302,7 @@ def test_tensor_core_level_kernels_match_oracle(lib, name, make, mc, tm):
         # layout: per precision [aniso fwd 16, aniso bwd 16, cc fwd 16, cc bwd 16, fill]; FP32 second
         base = 4 * 16 + 1
         for q in range(64 if tm == 128 else 32):
-            state[base + q] = (tm << 8) | 1
+            state[base + q] = (tm << 8) | ks
         sv.set_tune_state(state)
         meshes = [(lib.MESH_FC, m.Nc * m.Nf, disc.lu_fc), (lib.MESH_CF, m.Nc * m.Nf, disc.lu_cf)]
         if tm == 128:
