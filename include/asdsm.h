@@ -23,8 +23,9 @@
  * Sizes: N - 1 must be a power of two (N = 2^p + 1, p >= 2) and mc (coarse
  * intervals per axis, the N_c + 1 of eq. 2.1) a power of two with
  * 2 <= (N - 1)/mc <= 32, so every line, submesh and hole system has
- * 2^q - 1 unknowns per axis and a hole's factors fit in shared memory.
- * Other sizes return ASDSM_ERR_INVALID.
+ * 2^q - 1 unknowns per axis and a hole's factors fit in shared memory, and
+ * N <= 32769 (grid offsets fit 32-bit integers).  Other sizes return
+ * ASDSM_ERR_INVALID.
  *
  * The 3D extension (Section 3.5; asdsm_desc.d = 3): the unit cube, N x N x N
  * grids (element (i, j, l) at offset (l*N + j)*N + i, boundary included),

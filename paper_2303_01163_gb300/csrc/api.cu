@@ -417,7 +417,7 @@ int bnorm2(asdsm_handle* h, const double* s, const double* u, double* out) {
     const Geometry& g = h->g;
     CK(ring_from<double>(u, h->u_work, g, 1, h->st));
     int nb = 0;
-    const int need = 2 * residual_grid_blocks(g);
+    const int need = std::max(2 * residual_grid_blocks(g), kDotPartials);
     if (int rc = ensure_partials(h, need)) return rc;
     ResidOut o{};
     o.partials = h->partials;
@@ -1304,7 +1304,7 @@ int run_begin(asdsm_handle* h, SolveRun& r) {
     const long long NN = (long long)g.N * g.N;
     const double* s = r.s;
     double* u = r.u;
-    if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), 4096))) return rc;
+    if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), kDotPartials))) return rc;
     h->hist.clear();
     h->pend_ev.clear();
     h->evnext = 0;
@@ -1532,7 +1532,7 @@ void asdsm_default_opts(asdsm_opts* o) {
 const char* asdsm_strerror(int code) {
     switch (code) {
         case ASDSM_OK: return "ok";
-        case ASDSM_ERR_INVALID: return "invalid argument (sizes must satisfy eq. 2.1 with N-1 and mc powers of two, 2 <= mc, (N-1)/mc in [2, 32]; alpha > 0)";
+        case ASDSM_ERR_INVALID: return "invalid argument (sizes must satisfy eq. 2.1 with N-1 and mc powers of two, 2 <= mc, (N-1)/mc in [2, 32], N <= 32769; alpha > 0)";
         case ASDSM_ERR_CUDA: return "CUDA runtime error";
         case ASDSM_ERR_OOM: return "device allocation failed";
         case ASDSM_ERR_NAN: return "NaN or Inf in the residual";
@@ -1564,7 +1564,8 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     }
     if (desc->d != 2) return ASDSM_ERR_INVALID;
     const long long N = desc->n, mc = desc->mc;
-    if (N < 5 || !is_pow2(N - 1) || mc < 2 || !is_pow2(mc) || (N - 1) % mc != 0) return ASDSM_ERR_INVALID;
+    if (N < 5 || N > 32769 || !is_pow2(N - 1) || mc < 2 || !is_pow2(mc) || (N - 1) % mc != 0)
+        return ASDSM_ERR_INVALID;
     const long long n = (N - 1) / mc;
     if (n < 2 || n > 32) return ASDSM_ERR_INVALID;
     if (!(desc->alpha[0] > 0) || !(desc->alpha[1] > 0)) return ASDSM_ERR_INVALID;
@@ -1660,7 +1661,7 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if ((e = cudaMallocHost(&h->hdone, 2 * sizeof(int))) != cudaSuccess) return fail(set_cuda_error(e));
     for (int q = 0; q < 2; ++q)
         if ((e = cudaEventCreateWithFlags(&h->evc[q], cudaEventDisableTiming)) != cudaSuccess) return fail(set_cuda_error(e));
-    if ((rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), 4096)))) return fail(rc);
+    if ((rc = ensure_partials(h, std::max(2 * residual_grid_blocks(g), kDotPartials)))) return fail(rc);
     asdsm_profile(h, 0);
     *out = h;
     return ASDSM_OK;
@@ -1751,7 +1752,7 @@ int asdsm_correction(asdsm_handle* h, const double* s, const double* u, float* r
     if (!h || !s || !u || !r_out || !e_out || k < 0) return ASDSM_ERR_INVALID;
     if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
     if (int rc = ensure_work<double>(h, 0, 1)) return rc;
-    if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(h->g), 4096))) return rc;
+    if (int rc = ensure_partials(h, std::max(2 * residual_grid_blocks(h->g), kDotPartials))) return rc;
     auto& w = h->w[0];
     const Geometry& g = h->g;
     cudaStream_t st = h->st;
@@ -1822,7 +1823,7 @@ int asdsm_initial_guess(asdsm_handle* h, const double* s, double* u) {
         // The solver's mixed-path initial guess: FP32 solves refined to FP64 quality.
         CK(split_source(s, h->s_hi, h->s_lo, (long long)h->g.N * h->g.N, h->st));
         if ((rc = ensure_work<float>(h, 1))) return rc;
-        if ((rc = ensure_partials(h, std::max(2 * residual_grid_blocks(h->g), 4096)))) return rc;
+        if ((rc = ensure_partials(h, std::max(2 * residual_grid_blocks(h->g), kDotPartials)))) return rc;
         if ((rc = initial_guess_refined(h, s, u))) return rc;
         CK(copy_interior<double, double>((const double*)h->w[0].z[0], u, h->g, h->st));
         CK(ring_from<double>(nullptr, (double*)h->w[0].z[0], h->g, 0, h->st));

@@ -263,7 +263,11 @@ cudaError_t final_check(const double* s, const double* u, const Geometry& g, con
 // Reductions ----------------------------------------------------------------
 // out[j] = sum over blocks of partials[b][j]  (fixed order, 1 CTA), j < ncols
 cudaError_t reduce_partials(const double* partials, int nblocks, int ncols, double* out, cudaStream_t st);
-// Multi-dot: out partials for dots <a_i, b_i>, i < ndots over length n vectors.
+// The dot kernels run at most kDotBlocks CTAs and at most kMaxDots dots, so
+// kDotPartials doubles hold their partials; every reduction scratch is at
+// least that large.
+constexpr int kDotBlocks = 152 * 4, kMaxDots = 40, kDotPartials = kDotBlocks * kMaxDots;
+// Multi-dot: out partials for dots <a_i, b_i>, i < ndots <= kMaxDots over length n vectors.
 template <typename T>
 cudaError_t multi_dot(const T* const* a, const T* const* b, int ndots, long long n,
                       double* partials, int* nblocks, cudaStream_t st);
@@ -309,6 +313,9 @@ struct CtlCombine {
     double beta[16];
     double inv_nu;
     double alpha;
+    float beta_f[16];   // the same rounded to FP32, for the FP32 kernels (no FP64 work per element)
+    float inv_nu_f;
+    float alpha_f;
 };
 template <typename T>
 cudaError_t combine_skeleton_dyn(const T* q, const T* const* Qp, int k, const CtlCombine* c,

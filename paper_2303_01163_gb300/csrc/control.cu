@@ -181,9 +181,14 @@ __global__ void ctl_after_dots_kernel(SweepCtl* c, const double* __restrict__ do
     for (int j = 0; j < kc; ++j)
         for (int i = 0; i <= j; ++i) c->Tm[i][kc] -= beta[j] * c->Tm[i][j] / nu;
     c->comb.run = 1;
-    for (int j = 0; j < kc; ++j) c->comb.beta[j] = beta[j];
+    for (int j = 0; j < kc; ++j) {
+        c->comb.beta[j] = beta[j];
+        c->comb.beta_f[j] = (float)beta[j];
+    }
     c->comb.inv_nu = 1.0 / nu;
     c->comb.alpha = alpha;
+    c->comb.inv_nu_f = (float)c->comb.inv_nu;
+    c->comb.alpha_f = (float)alpha;
     c->k += 1;
     if (!c->defer) {
         // The step goes to u at the next residual kernel; the cycle continues.

@@ -39,6 +39,18 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// Compensated FP32 sum over a warp of the pairs (hi, lo): the additions of the
+// hi parts are exact through TwoSum (Knuth), their errors collect in lo, so the
+// warp's sum costs no FP64 work (the FP64 pipe of this part runs at 1/64 of FP32).
+__device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = hi + h2, bp = s - hi;
+        const float err = (hi - (s - bp)) + (h2 - bp);
+        hi = s;
+        lo = lo + l2 + err;
+    }
+}
 __device__ __forceinline__ double warp_max(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
@@ -427,8 +439,9 @@ __device__ __forceinline__ void inv_norms(const MergeArgs<T>& a, T* inv1, T* inv
 // with the cross-point errors of Algorithm 2 formed on the fly from the cross points.  A CTA
 // owns MK_L lines x MK_R moments and walks the knots in chunks of MK_Q staged
 // in shared memory (Sm is stored transposed, [knot q][moment r], so the staging
-// reads are coalesced); the next chunk is loaded into registers while the
-// current one is multiplied.  The CTAs of the first moment block also store e.
+// reads are coalesced); a group of chunks is loaded into registers at once and
+// the chunks are multiplied in order.  The CTAs of the first moment block also
+// store e.
 constexpr int MK_L = 16, MK_R = 32, MK_Q = 32, MK_THREADS = 128;
 
 template <typename T>
@@ -452,8 +465,10 @@ __global__ void __launch_bounds__(MK_THREADS) merge_knots_kernel(MergeArgs<T> a)
     const bool store_e = blockIdx.y == 0;
     __shared__ T Es[MK_Q][MK_L + 1];
     __shared__ __align__(16) T Ss[MK_Q][MK_R];
-    T inv1, inv2;
-    inv_norms(a, &inv1, &inv2);
+    __shared__ T inv_s[2];                       // the families' norm scales, once per block
+    if (threadIdx.x == 0) inv_norms(a, &inv_s[0], &inv_s[1]);
+    __syncthreads();
+    const T inv1 = inv_s[0], inv2 = inv_s[1];
     const int choice = a.choice_dev ? *a.choice_dev : a.choice;
     const int tid = threadIdx.x;
     const int tl = tid / (MK_R / 2), tr = tid % (MK_R / 2);   // 2 lines x 2 moments per thread
@@ -477,33 +492,50 @@ __global__ void __launch_bounds__(MK_THREADS) merge_knots_kernel(MergeArgs<T> a)
         }
     };
     T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
-    load_chunk(0);
-    for (int q0 = 0; q0 < Nc; q0 += MK_Q) {
-        __syncthreads();                         // previous chunk consumed
+    // Up to MK_G chunks of knots are loaded into registers at once (one memory
+    // latency for all of them), then staged and multiplied one after another.
+    constexpr int MK_G = 8;
+    for (int g0 = 0; g0 < Nc; g0 += MK_G * MK_Q) {
+        T evg[MK_G][EPT], svg[MK_G][SPT];
 #pragma unroll
-        for (int j = 0; j < EPT; ++j) {
-            const int e = tid + j * MK_THREADS;
-            const int li = e / MK_Q, qq = e % MK_Q;
-            Es[qq][li] = ev[j];
-            const int line = l0 + li, q = q0 + qq;
-            if (store_e && line < Nc && q < Nc) {
-                if (fam == 0) a.E1[(long long)line * Nc + q] = ev[j];      // E1[l][k]
-                else a.E2[(long long)q * Nc + line] = ev[j];               // E2[l][k]
+        for (int c = 0; c < MK_G; ++c) {
+            if (g0 + c * MK_Q < Nc) {
+                load_chunk(g0 + c * MK_Q);
+#pragma unroll
+                for (int j = 0; j < EPT; ++j) evg[c][j] = ev[j];
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) svg[c][j] = sv[j];
             }
         }
 #pragma unroll
-        for (int j = 0; j < SPT; ++j) {
-            const int e = tid + j * MK_THREADS;
-            Ss[e / MK_R][e % MK_R] = sv[j];
-        }
-        __syncthreads();
-        if (q0 + MK_Q < Nc) load_chunk(q0 + MK_Q);
+        for (int c = 0; c < MK_G; ++c) {
+            const int q0 = g0 + c * MK_Q;
+            if (q0 >= Nc) break;
+            __syncthreads();                     // previous chunk consumed
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const int e = tid + j * MK_THREADS;
+                const int li = e / MK_Q, qq = e % MK_Q;
+                Es[qq][li] = evg[c][j];
+                const int line = l0 + li, q = q0 + qq;
+                if (store_e && line < Nc && q < Nc) {
+                    if (fam == 0) a.E1[(long long)line * Nc + q] = evg[c][j];      // E1[l][k]
+                    else a.E2[(long long)q * Nc + line] = evg[c][j];               // E2[l][k]
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < SPT; ++j) {
+                const int e = tid + j * MK_THREADS;
+                Ss[e / MK_R][e % MK_R] = svg[c][j];
+            }
+            __syncthreads();
 #pragma unroll 8
-        for (int qq = 0; qq < MK_Q; ++qq) {
-            const T e0 = Es[qq][2 * tl], e1 = Es[qq][2 * tl + 1];
-            const T s0 = Ss[qq][2 * tr], s1 = Ss[qq][2 * tr + 1];
-            acc[0][0] += s0 * e0; acc[0][1] += s1 * e0;
-            acc[1][0] += s0 * e1; acc[1][1] += s1 * e1;
+            for (int qq = 0; qq < MK_Q; ++qq) {
+                const T e0 = Es[qq][2 * tl], e1 = Es[qq][2 * tl + 1];
+                const T s0 = Ss[qq][2 * tr], s1 = Ss[qq][2 * tr + 1];
+                acc[0][0] += s0 * e0; acc[0][1] += s1 * e0;
+                acc[1][0] += s0 * e1; acc[1][1] += s1 * e1;
+            }
         }
     }
 #pragma unroll
@@ -532,21 +564,35 @@ __device__ __forceinline__ void spline_weights(int p, int n, T H, T* w) {
     w[3] = t / H;
 }
 
+// fc lines in tiles of MW_T lines x MW_T fine x through shared memory (Yfc is
+// [x][line]: read along lines, written along x, both coalesced); cf points in
+// a grid-stride loop after the tiles' blocks.
+constexpr int MW_T = 32, MW_THREADS = 256;
+
 template <typename T>
-__global__ void merge_write_kernel(MergeArgs<T> a) {
+__global__ void __launch_bounds__(MW_THREADS) merge_write_kernel(MergeArgs<T> a, int nft) {
     const Geometry& g = a.g;
     const int Nf = g.Nf, Nc = g.Nc, n = g.n, N = g.N, K = g.mc + 1;
     const T H = T(1) / (T)g.mc;
     __shared__ T sw[33][4];                     // spline weights per fine offset p = 0..n (n <= 32)
+    __shared__ T tile[MW_T][MW_T + 1];          // [x][line]
+    __shared__ T inv_s[2];                      // the families' norm scales, once per block
     for (int p = threadIdx.x; p <= n; p += blockDim.x) spline_weights<T>(p, n, H, sw[p]);
-    __syncthreads();
-    T inv1, inv2;
-    inv_norms(a, &inv1, &inv2);
-    const long long total = 2LL * Nf * Nc;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        if (e < (long long)Nf * Nc) {
-            // fc line l, fine x: u_fc/||u_fc|| + Spline(e1); cross points too (written from fc).
-            const int l = (int)(e / Nf), x = (int)(e % Nf);
+    if (threadIdx.x == 0) inv_norms(a, &inv_s[0], &inv_s[1]);
+    const int tx = threadIdx.x % MW_T, ty = threadIdx.x / MW_T;
+    if ((int)blockIdx.x < nft) {
+        // fc line l, fine x: u_fc/||u_fc|| + Spline(e1); cross points too (written from fc).
+        const int nxt = (Nf + MW_T - 1) / MW_T;
+        const int l0 = ((int)blockIdx.x / nxt) * MW_T, x0 = ((int)blockIdx.x % nxt) * MW_T;
+        for (int xx = ty; xx < MW_T; xx += MW_THREADS / MW_T) {
+            const int x = x0 + xx, l = l0 + tx;
+            tile[xx][tx] = (x < Nf && l < Nc) ? a.Yfc[(long long)x * Nc + l] : T(0);
+        }
+        __syncthreads();
+        const T inv1 = inv_s[0];
+        for (int ll = ty; ll < MW_T; ll += MW_THREADS / MW_T) {
+            const int l = l0 + ll, x = x0 + tx;
+            if (l >= Nc || x >= Nf) continue;
             const int i = x + 1, ki = i / n, p = i % n;
             T corr;
             const T yk = ki == 0 ? T(0) : a.E1[(long long)l * Nc + ki - 1];
@@ -557,49 +603,59 @@ __global__ void merge_write_kernel(MergeArgs<T> a) {
                 const T yk1 = ki + 1 >= g.mc ? T(0) : a.E1[(long long)l * Nc + ki];
                 corr = sw[p][0] * Mv[ki] + sw[p][1] * Mv[ki + 1] + sw[p][2] * yk + sw[p][3] * yk1;
             }
-            a.z[(long long)((l + 1) * n) * N + i] = a.Yfc[(long long)x * Nc + l] * inv1 + corr;
-        } else {
-            // cf points, ordered [y][column] so that consecutive threads read Ycf contiguously;
-            // cross points are skipped: they keep the fc value.
-            const long long f = e - (long long)Nf * Nc;
-            const int y = (int)(f / Nc), k = (int)(f % Nc);
-            const int j = y + 1;
-            if (j % n == 0) continue;
-            const int ki = j / n, p = j % n;
-            const T* Mv = a.M2 + (long long)k * K;
-            const T yk = ki == 0 ? T(0) : a.E2[(long long)(ki - 1) * Nc + k];
-            const T yk1 = ki + 1 >= g.mc ? T(0) : a.E2[(long long)ki * Nc + k];
-            const T corr = sw[p][0] * Mv[ki] + sw[p][1] * Mv[ki + 1] + sw[p][2] * yk + sw[p][3] * yk1;
-            const T val = a.Ycf[(long long)y * Nc + k] * inv2 + corr;
-            if (a.zv) a.zv[(long long)j * (g.mc + 1) + k + 1] = val;
-            else a.z[(long long)j * N + (k + 1) * n] = val;
+            a.z[(long long)((l + 1) * n) * N + i] = tile[tx][ll] * inv1 + corr;
         }
+        return;
+    }
+    __syncthreads();
+    const T inv2 = inv_s[1];
+    const int total = Nf * Nc;
+    const int nb = (int)gridDim.x - nft;
+    for (int f = ((int)blockIdx.x - nft) * blockDim.x + threadIdx.x; f < total; f += nb * blockDim.x) {
+        // cf points, ordered [y][column] so that consecutive threads read Ycf contiguously;
+        // cross points are skipped: they keep the fc value.
+        const int y = f / Nc, k = f % Nc;
+        const int j = y + 1;
+        if (j % n == 0) continue;
+        const int ki = j / n, p = j % n;
+        const T* Mv = a.M2 + (long long)k * K;
+        const T yk = ki == 0 ? T(0) : a.E2[(long long)(ki - 1) * Nc + k];
+        const T yk1 = ki + 1 >= g.mc ? T(0) : a.E2[(long long)ki * Nc + k];
+        const T corr = sw[p][0] * Mv[ki] + sw[p][1] * Mv[ki + 1] + sw[p][2] * yk + sw[p][3] * yk1;
+        const T val = a.Ycf[(long long)y * Nc + k] * inv2 + corr;
+        if (a.zv) a.zv[(long long)j * (g.mc + 1) + k + 1] = val;
+        else a.z[(long long)j * N + (k + 1) * n] = val;
     }
 }
 
-// q = A z at compact skeleton rows (z: full grid, zero ring).
+// Stencil weights in the vectors' precision (rounded on the host: no FP64 work per element).
 template <typename T>
-__global__ void skeleton_apply_kernel(const T* __restrict__ z, Geometry g, Stencil c, T* __restrict__ q) {
+struct StencilT { T cc, cw, ce, cs, cn; };
+
+// q = A z at compact skeleton rows (z: full grid, zero ring).  Grids are at most
+// 8193^2 points: 32-bit indices.
+template <typename T>
+__global__ void skeleton_apply_kernel(const T* __restrict__ z, Geometry g, StencilT<T> c, T* __restrict__ q) {
     const int N = g.N, n = g.n, Nf = g.Nf, Nc = g.Nc;
-    const T cc = (T)c.cc, cw = (T)c.cw, ce = (T)c.ce, cs = (T)c.cs, cn = (T)c.cn;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.skel; e += (long long)gridDim.x * blockDim.x) {
+    const int nfc = Nc * Nf, skel = (int)g.skel;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < skel; e += gridDim.x * blockDim.x) {
         int i, j;
-        if (e < (long long)Nc * Nf) {
-            i = (int)(e % Nf) + 1;
-            j = ((int)(e / Nf) + 1) * n;
+        if (e < nfc) {
+            i = e % Nf + 1;
+            j = (e / Nf + 1) * n;
         } else {
-            const long long f = e - (long long)Nc * Nf;
-            const int yr = (int)(f / Nc), k = (int)(f % Nc);
+            const int f = e - nfc;
+            const int yr = f / Nc, k = f % Nc;
             j = yr + yr / (n - 1) + 1;
             i = (k + 1) * n;
         }
-        const long long idx = (long long)j * N + i;
-        q[e] = cc * z[idx] + cw * z[idx - 1] + ce * z[idx + 1] + cs * z[idx - N] + cn * z[idx + N];
+        const int idx = j * N + i;
+        q[e] = c.cc * z[idx] + c.cw * z[idx - 1] + c.ce * z[idx + 1] + c.cs * z[idx - N] + c.cn * z[idx + N];
     }
 }
 
 template <typename T>
-struct CombineArgs { const T* Qp[16]; double beta[16]; };
+struct CombineArgs { const T* Qp[16]; T beta[16]; };
 
 // out = (q - sum_j beta_j Qp_j) * inv_nu on a grid-strided range, in the
 // vectors' own precision and in the same order per element; FP32 vectors are
@@ -614,15 +670,19 @@ __device__ __forceinline__ void combine_range(const T* __restrict__ q, const Com
     if constexpr (sizeof(T) == 4) {
         const long long n4 = n >> 2;
         for (long long e = tid; e < n4; e += stride) {
+            // Every load of the element is issued before the first use.
             float4 v = __ldg(reinterpret_cast<const float4*>(q) + e);
+            float4 p[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                p[j] = j < k ? __ldg(reinterpret_cast<const float4*>(c.Qp[j]) + e) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 if (j < k) {
-                    const float4 p = __ldg(reinterpret_cast<const float4*>(c.Qp[j]) + e);
-                    v.x -= beta[j] * p.x;
-                    v.y -= beta[j] * p.y;
-                    v.z -= beta[j] * p.z;
-                    v.w -= beta[j] * p.w;
+                    v.x -= beta[j] * p[j].x;
+                    v.y -= beta[j] * p[j].y;
+                    v.z -= beta[j] * p[j].z;
+                    v.w -= beta[j] * p[j].w;
                 }
             }
             v.x *= inu; v.y *= inu; v.z *= inu; v.w *= inu;
@@ -641,11 +701,11 @@ __device__ __forceinline__ void combine_range(const T* __restrict__ q, const Com
 
 template <typename T>
 __global__ void combine_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
-                               double inv_nu, long long n, T* __restrict__ out) {
+                               T inv_nu, long long n, T* __restrict__ out) {
     T beta[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)c.beta[j] : T(0);
-    combine_range<T>(q, c, k, beta, (T)inv_nu, n, out);
+    for (int j = 0; j < 16; ++j) beta[j] = j < k ? c.beta[j] : T(0);
+    combine_range<T>(q, c, k, beta, inv_nu, n, out);
 }
 
 template <typename T>
@@ -653,14 +713,20 @@ __global__ void combine_dyn_kernel(const T* __restrict__ q, CombineArgs<T> c, in
                                    const CtlCombine* __restrict__ ctl, long long n, T* __restrict__ out) {
     if (!ctl->run) return;
     T beta[16];
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)ctl->beta[j] : T(0);
-    combine_range<T>(q, c, k, beta, (T)ctl->inv_nu, n, out);
+        for (int j = 0; j < 16; ++j) beta[j] = j < k ? ctl->beta_f[j] : T(0);
+        combine_range<T>(q, c, k, beta, ctl->inv_nu_f, n, out);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)ctl->beta[j] : T(0);
+        combine_range<T>(q, c, k, beta, (T)ctl->inv_nu, n, out);
+    }
 }
 
 // Multi-dot partials: blockDim 256, partials[block][ndots].
 constexpr int DOT_THREADS = 256;
-constexpr int MAX_DOTS = 40;
+constexpr int MAX_DOTS = kMaxDots;
 template <typename T>
 struct DotArgs { const T* a[MAX_DOTS]; const T* b[MAX_DOTS]; };
 
@@ -668,19 +734,45 @@ template <typename T>
 __global__ void __launch_bounds__(DOT_THREADS)
 multi_dot_kernel(DotArgs<T> d, int ndots, long long n, double* partials) {
     __shared__ double red[DOT_THREADS / 32];
+    const long long tid = blockIdx.x * (long long)DOT_THREADS + threadIdx.x, stride = (long long)gridDim.x * DOT_THREADS;
     for (int q = 0; q < ndots; ++q) {
         T acct = T(0);
         const T* a = d.a[q];
         const T* b = d.b[q];
-        for (long long e = blockIdx.x * (long long)DOT_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * DOT_THREADS)
-            acct += a[e] * b[e];
-        double acc = warp_sum((double)acct);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double v = threadIdx.x < DOT_THREADS / 32 ? red[threadIdx.x] : 0.0;
-            v = warp_sum(v);
-            if (threadIdx.x == 0) partials[(long long)blockIdx.x * ndots + q] = v;
+        long long done = 0;
+        if constexpr (sizeof(T) == 4) {
+            // 16-byte aligned vectors: four at a time, the tail one by one.
+            if (((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0) {
+                const long long n4 = n >> 2;
+                for (long long e = tid; e < n4; e += stride) {
+                    const float4 x = __ldg(reinterpret_cast<const float4*>(a) + e);
+                    const float4 y = __ldg(reinterpret_cast<const float4*>(b) + e);
+                    acct += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+                }
+                done = n4 << 2;
+            }
+        }
+        for (long long e = done + tid; e < n; e += stride) acct += a[e] * b[e];
+        if constexpr (sizeof(T) == 4) {
+            // Compensated FP32 warp sums; the block's sum in FP64 by one thread.
+            float hi = acct, lo = 0.0f;
+            warp_sum_pair(hi, lo);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)hi + (double)lo;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double v = 0.0;
+                for (int ww = 0; ww < DOT_THREADS / 32; ++ww) v += red[ww];
+                partials[(long long)blockIdx.x * ndots + q] = v;
+            }
+        } else {
+            double acc = warp_sum((double)acct);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                double v = threadIdx.x < DOT_THREADS / 32 ? red[threadIdx.x] : 0.0;
+                v = warp_sum(v);
+                if (threadIdx.x == 0) partials[(long long)blockIdx.x * ndots + q] = v;
+            }
         }
         __syncthreads();
     }
@@ -699,7 +791,29 @@ gcr_dots_kernel(const T* __restrict__ q, const T* __restrict__ r, GcrDotArgs<T> 
     T acc[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) acc[d] = T(0);
-    for (long long e = blockIdx.x * (long long)DOT_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * DOT_THREADS) {
+    const long long tid = blockIdx.x * (long long)DOT_THREADS + threadIdx.x, stride = (long long)gridDim.x * DOT_THREADS;
+    long long done = 0;
+    if constexpr (sizeof(T) == 4) {
+        // The skeleton vectors are 16-byte aligned: four elements at a time, every
+        // load of an element group issued before the first use; the tail one by one.
+        const long long n4 = n >> 2;
+        for (long long e = tid; e < n4; e += stride) {
+            const float4 qv = __ldg(reinterpret_cast<const float4*>(q) + e);
+            const float4 rv = __ldg(reinterpret_cast<const float4*>(r) + e);
+            float4 pv[K > 0 ? K : 1];
+#pragma unroll
+            for (int j = 0; j < K; ++j) pv[j] = __ldg(reinterpret_cast<const float4*>(P.p[j]) + e);
+            acc[0] += qv.x * qv.x + qv.y * qv.y + qv.z * qv.z + qv.w * qv.w;
+            acc[1] += qv.x * rv.x + qv.y * rv.y + qv.z * rv.z + qv.w * rv.w;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                acc[2 + 2 * j] += qv.x * pv[j].x + qv.y * pv[j].y + qv.z * pv[j].z + qv.w * pv[j].w;
+                acc[3 + 2 * j] += rv.x * pv[j].x + rv.y * pv[j].y + rv.z * pv[j].z + rv.w * pv[j].w;
+            }
+        }
+        done = n4 << 2;
+    }
+    for (long long e = done + tid; e < n; e += stride) {
         const T qv = q[e], rv = r[e];
         acc[0] += qv * qv;
         acc[1] += qv * rv;
@@ -710,18 +824,35 @@ gcr_dots_kernel(const T* __restrict__ q, const T* __restrict__ r, GcrDotArgs<T> 
             acc[3 + 2 * j] += rv * pv;
         }
     }
-    __shared__ double red[DOT_THREADS / 32][ND];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (sizeof(T) == 4) {
+        // Warp sums as compensated FP32 pairs; the block's sum in FP64, once per dot.
+        __shared__ float redh[DOT_THREADS / 32][ND], redl[DOT_THREADS / 32][ND];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        const double v = warp_sum((double)acc[d]);
-        if (lane == 0) red[w][d] = v;
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < ND; d += DOT_THREADS) {
-        double v = 0.0;
-        for (int ww = 0; ww < DOT_THREADS / 32; ++ww) v += red[ww][d];
-        partials[(long long)blockIdx.x * ND + d] = v;
+        for (int d = 0; d < ND; ++d) {
+            float hi = acc[d], lo = 0.0f;
+            warp_sum_pair(hi, lo);
+            if (lane == 0) { redh[w][d] = hi; redl[w][d] = lo; }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < ND; d += DOT_THREADS) {
+            double v = 0.0;
+            for (int ww = 0; ww < DOT_THREADS / 32; ++ww) v += (double)redh[ww][d] + (double)redl[ww][d];
+            partials[(long long)blockIdx.x * ND + d] = v;
+        }
+    } else {
+        __shared__ double red[DOT_THREADS / 32][ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const double v = warp_sum((double)acc[d]);
+            if (lane == 0) red[w][d] = v;
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < ND; d += DOT_THREADS) {
+            double v = 0.0;
+            for (int ww = 0; ww < DOT_THREADS / 32; ++ww) v += red[ww][d];
+            partials[(long long)blockIdx.x * ND + d] = v;
+        }
     }
 }
 
@@ -943,7 +1074,7 @@ cudaError_t multi_dot(const T* const* a, const T* const* b, int ndots, long long
     if (ndots > MAX_DOTS) return cudaErrorInvalidValue;
     DotArgs<T> d{};
     for (int q = 0; q < ndots; ++q) { d.a[q] = a[q]; d.b[q] = b[q]; }
-    unsigned grid = grid_for(n, DOT_THREADS, 152LL * 2);
+    unsigned grid = grid_for(n, DOT_THREADS, kDotBlocks);
     *nblocks = (int)grid;
     multi_dot_kernel<T><<<grid, DOT_THREADS, 0, st>>>(d, ndots, n, partials);
     note_launch();
@@ -963,7 +1094,7 @@ cudaError_t gcr_dots(const T* q, const T* r, const T* const* p, int k, long long
                      double* partials, int* nblocks, cudaStream_t st) {
     GcrDotArgs<T> P{};
     for (int j = 0; j < k && j < 16; ++j) P.p[j] = p[j];
-    const unsigned grid = grid_for(n, DOT_THREADS, 152LL * 2);
+    const unsigned grid = grid_for(n, DOT_THREADS, kDotBlocks);
     *nblocks = (int)grid;
     switch (k) {
         case 0: return gcr_dots_launch<T, 0>(q, r, P, n, partials, grid, st);
@@ -997,14 +1128,17 @@ cudaError_t merge_knots(const MergeArgs<T>& a, cudaStream_t st) {
 
 template <typename T>
 cudaError_t merge_write(const MergeArgs<T>& a, cudaStream_t st) {
-    merge_write_kernel<T><<<grid_for(2LL * a.g.Nf * a.g.Nc), 256, 0, st>>>(a);
+    const int nft = ((a.g.Nc + MW_T - 1) / MW_T) * ((a.g.Nf + MW_T - 1) / MW_T);
+    const unsigned ncf = grid_for((long long)a.g.Nf * a.g.Nc, MW_THREADS);
+    merge_write_kernel<T><<<nft + ncf, MW_THREADS, 0, st>>>(a, nft);
     note_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t skeleton_apply(const T* z, const Geometry& g, const Stencil& s, T* q, cudaStream_t st) {
-    skeleton_apply_kernel<T><<<grid_for(g.skel), 256, 0, st>>>(z, g, s, q);
+    const StencilT<T> c{(T)s.cc, (T)s.cw, (T)s.ce, (T)s.cs, (T)s.cn};
+    skeleton_apply_kernel<T><<<grid_for(g.skel), 256, 0, st>>>(z, g, c, q);
     note_launch();
     return cudaGetLastError();
 }
@@ -1012,32 +1146,60 @@ cudaError_t skeleton_apply(const T* z, const Geometry& g, const Stencil& s, T* q
 // The tracked residual of a deferred GCR cycle on the compact skeleton, and the
 // submesh right-hand sides gathered from it (fc lines [x][line], cf columns [y][column]).
 template <typename T>
-__global__ void track_skeleton_kernel(T* __restrict__ r, const T* __restrict__ qp, double alpha_h,
-                                      const CtlCombine* __restrict__ ctl, Geometry g, T* __restrict__ rfc,
-                                      T* __restrict__ rcf) {
+__global__ void __launch_bounds__(MW_THREADS) track_skeleton_kernel(T* __restrict__ r, const T* __restrict__ qp,
+                                                                    T alpha_h, const CtlCombine* __restrict__ ctl,
+                                                                    Geometry g, T* __restrict__ rfc,
+                                                                    T* __restrict__ rcf, int nft) {
     if (ctl && !ctl->track) return;
-    const T a = (T)(ctl ? ctl->alpha : alpha_h);
+    T a = alpha_h;
+    if (ctl) {
+        if constexpr (sizeof(T) == 4) a = ctl->alpha_f;
+        else a = (T)ctl->alpha;
+    }
     const int n = g.n, Nf = g.Nf, Nc = g.Nc;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.skel; e += (long long)gridDim.x * blockDim.x) {
+    if ((int)blockIdx.x < nft) {
+        // fc line points (cross points included) in tiles of MW_T lines x MW_T
+        // fine x: r updated along x, r_fc ([x][line]) written along lines.
+        __shared__ T tile[MW_T][MW_T + 1];       // [x][line]
+        const int tx = threadIdx.x % MW_T, ty = threadIdx.x / MW_T;
+        const int nxt = (Nf + MW_T - 1) / MW_T;
+        const int l0 = ((int)blockIdx.x / nxt) * MW_T, x0 = ((int)blockIdx.x % nxt) * MW_T;
+        for (int ll = ty; ll < MW_T; ll += MW_THREADS / MW_T) {
+            const int l = l0 + ll, x = x0 + tx;
+            if (l >= Nc || x >= Nf) continue;
+            const long long e = (long long)l * Nf + x;
+            const T v = r[e] - a * qp[e];
+            r[e] = v;
+            tile[tx][ll] = v;
+            const int i = x + 1;
+            if (i % n == 0) rcf[(long long)((l + 1) * n - 1) * Nc + (i / n - 1)] = v;
+        }
+        __syncthreads();
+        for (int xx = ty; xx < MW_T; xx += MW_THREADS / MW_T) {
+            const int x = x0 + xx, l = l0 + tx;
+            if (x < Nf && l < Nc) rfc[(long long)x * Nc + l] = tile[xx][tx];
+        }
+        return;
+    }
+    const int nfc = Nc * Nf, total = (int)g.skel - nfc;
+    const int nb = (int)gridDim.x - nft;
+    for (int f = ((int)blockIdx.x - nft) * blockDim.x + threadIdx.x; f < total; f += nb * blockDim.x) {
+        // cf column point off the fc lines
+        const int e = nfc + f;
         const T v = r[e] - a * qp[e];
         r[e] = v;
-        if (e < (long long)Nc * Nf) {                        // fc line l, fine x (cross points included)
-            const int i = (int)(e % Nf) + 1, l = (int)(e / Nf);
-            rfc[(long long)(i - 1) * Nc + l] = v;
-            if (i % n == 0) rcf[(long long)((l + 1) * n - 1) * Nc + (i / n - 1)] = v;
-        } else {                                             // cf column point off the fc lines
-            const long long f = e - (long long)Nc * Nf;
-            const int yr = (int)(f / Nc), k = (int)(f % Nc);
-            const int j = yr + yr / (n - 1) + 1;
-            rcf[(long long)(j - 1) * Nc + k] = v;
-        }
+        const int yr = f / Nc, k = f % Nc;
+        const int j = yr + yr / (n - 1) + 1;
+        rcf[(j - 1) * Nc + k] = v;
     }
 }
 
 template <typename T>
 cudaError_t track_skeleton(T* rskel, const T* qp, double alpha, const CtlCombine* c, const Geometry& g, T* rfc,
                            T* rcf, cudaStream_t st) {
-    track_skeleton_kernel<T><<<grid_for(g.skel), 256, 0, st>>>(rskel, qp, alpha, c, g, rfc, rcf);
+    const int nft = ((g.Nc + MW_T - 1) / MW_T) * ((g.Nf + MW_T - 1) / MW_T);
+    const unsigned ncf = grid_for(g.skel - (long long)g.Nc * g.Nf, MW_THREADS);
+    track_skeleton_kernel<T><<<nft + ncf, MW_THREADS, 0, st>>>(rskel, qp, (T)alpha, c, g, rfc, rcf, nft);
     note_launch();
     return cudaGetLastError();
 }
@@ -1047,8 +1209,8 @@ cudaError_t combine_skeleton(const T* q, const T* const* Qp, const double* beta,
                              long long n, T* out, cudaStream_t st) {
     if (k > 16) return cudaErrorInvalidValue;
     CombineArgs<T> c{};
-    for (int j = 0; j < k; ++j) { c.Qp[j] = Qp[j]; c.beta[j] = beta[j]; }
-    combine_kernel<T><<<grid_for(sizeof(T) == 4 ? (n + 3) / 4 : n), 256, 0, st>>>(q, c, k, inv_nu, n, out);
+    for (int j = 0; j < k; ++j) { c.Qp[j] = Qp[j]; c.beta[j] = (T)beta[j]; }
+    combine_kernel<T><<<grid_for(sizeof(T) == 4 ? (n + 3) / 4 : n), 256, 0, st>>>(q, c, k, (T)inv_nu, n, out);
     note_launch();
     return cudaGetLastError();
 }

@@ -66,7 +66,9 @@ def test_null_arguments_are_rejected_without_touching_the_gpu(lib):
     assert lib.asdsm_setup(ctypes.byref(d), None, None, ctypes.byref(h)) == asdsm.ERR_INVALID
     d.n, d.mc = 65, 3                      # mc not a power of two
     assert lib.asdsm_setup(ctypes.byref(d), None, None, ctypes.byref(h)) == asdsm.ERR_INVALID
-    d.mc = 8
+    d.n, d.mc = 65537, 4096                # N above 32769 (grid offsets beyond 32 bits)
+    assert lib.asdsm_setup(ctypes.byref(d), None, None, ctypes.byref(h)) == asdsm.ERR_INVALID
+    d.n, d.mc = 65, 8
     d.alpha[0] = 0.0                       # alpha must be positive
     assert lib.asdsm_setup(ctypes.byref(d), None, None, ctypes.byref(h)) == asdsm.ERR_INVALID
     assert lib.asdsm_solve(None, None, None, None) == asdsm.ERR_INVALID
