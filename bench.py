@@ -46,7 +46,7 @@ N_GRID = 4097
 MC = 256
 TOL = 1e-10
 ACCEL_M = 8
-ACCEL_M_BATCH = 8
+ACCEL_M_BATCH = 16
 STAG_WINDOW_BATCH = 30
 MAX_SWEEPS = 1000
 FP32_LANES_PER_SM = 128

@@ -288,7 +288,8 @@ struct MergeArgs {
     const int* choice_dev;    // non-null: the choice is read from the device instead
     const T* Sm;              // spline moment operator, transposed: [Nc knots][mc+1 moments]
     T* E1; T* E2;             // [Nc][Nc] knot errors (fc lines: E1[l][k]; cf columns: E2[l][k])
-    T* M1; T* M2;             // moments: M1[l][mc+1], M2[k][mc+1]
+    T* M1; T* M2;             // moments: M1[l][mc+1] (fc line l), M2[mc+1][Nc] (moment-major: the
+                              // cf points of one row read consecutive columns k)
     T* z;                     // full grid output (skeleton written)
     T* zv;                    // non-null: the points of the lines x = k n (k = 1..mc-1) between knots go
                               // here, [N][mc+1] (column k), instead of into z

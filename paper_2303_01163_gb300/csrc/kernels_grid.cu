@@ -542,11 +542,12 @@ __global__ void __launch_bounds__(MK_THREADS) merge_knots_kernel(MergeArgs<T> a)
     for (int i = 0; i < 2; ++i) {
         const int line = l0 + 2 * tl + i;
         if (line >= Nc) continue;
-        T* Mout = (fam == 0 ? a.M1 : a.M2) + (long long)line * K;
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
             const int r = r0 + 2 * tr + jj;
-            if (r < K) Mout[r] = acc[i][jj];
+            if (r >= K) continue;
+            if (fam == 0) a.M1[(long long)line * K + r] = acc[i][jj];
+            else a.M2[(long long)r * Nc + line] = acc[i][jj];
         }
     }
 }
@@ -618,10 +619,10 @@ __global__ void __launch_bounds__(MW_THREADS) merge_write_kernel(MergeArgs<T> a,
         const int j = y + 1;
         if (j % n == 0) continue;
         const int ki = j / n, p = j % n;
-        const T* Mv = a.M2 + (long long)k * K;
-        const T yk = ki == 0 ? T(0) : a.E2[(long long)(ki - 1) * Nc + k];
-        const T yk1 = ki + 1 >= g.mc ? T(0) : a.E2[(long long)ki * Nc + k];
-        const T corr = sw[p][0] * Mv[ki] + sw[p][1] * Mv[ki + 1] + sw[p][2] * yk + sw[p][3] * yk1;
+        const T yk = ki == 0 ? T(0) : a.E2[(ki - 1) * Nc + k];
+        const T yk1 = ki + 1 >= g.mc ? T(0) : a.E2[ki * Nc + k];
+        const T corr = sw[p][0] * a.M2[ki * Nc + k] + sw[p][1] * a.M2[(ki + 1) * Nc + k] + sw[p][2] * yk +
+                       sw[p][3] * yk1;
         const T val = a.Ycf[(long long)y * Nc + k] * inv2 + corr;
         if (a.zv) a.zv[(long long)j * (g.mc + 1) + k + 1] = val;
         else a.z[(long long)j * N + (k + 1) * n] = val;
@@ -660,9 +661,10 @@ struct CombineArgs { const T* Qp[16]; T beta[16]; };
 // out = (q - sum_j beta_j Qp_j) * inv_nu on a grid-strided range, in the
 // vectors' own precision and in the same order per element; FP32 vectors are
 // read and written four at a time (the arrays are 16-byte aligned), the tail
-// one by one.
-template <typename T>
-__device__ __forceinline__ void combine_range(const T* __restrict__ q, const CombineArgs<T>& c, int k, const T* beta,
+// one by one.  K (the directions, <= 15) is a template parameter: no branch
+// per direction and every load of an element issued before the first use.
+template <typename T, int K>
+__device__ __forceinline__ void combine_range(const T* __restrict__ q, const CombineArgs<T>& c, const T* beta,
                                               T inu, long long n, T* __restrict__ out) {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -670,20 +672,16 @@ __device__ __forceinline__ void combine_range(const T* __restrict__ q, const Com
     if constexpr (sizeof(T) == 4) {
         const long long n4 = n >> 2;
         for (long long e = tid; e < n4; e += stride) {
-            // Every load of the element is issued before the first use.
             float4 v = __ldg(reinterpret_cast<const float4*>(q) + e);
-            float4 p[16];
+            float4 p[K > 0 ? K : 1];
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                p[j] = j < k ? __ldg(reinterpret_cast<const float4*>(c.Qp[j]) + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < K; ++j) p[j] = __ldg(reinterpret_cast<const float4*>(c.Qp[j]) + e);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                if (j < k) {
-                    v.x -= beta[j] * p[j].x;
-                    v.y -= beta[j] * p[j].y;
-                    v.z -= beta[j] * p[j].z;
-                    v.w -= beta[j] * p[j].w;
-                }
+            for (int j = 0; j < K; ++j) {
+                v.x -= beta[j] * p[j].x;
+                v.y -= beta[j] * p[j].y;
+                v.z -= beta[j] * p[j].z;
+                v.w -= beta[j] * p[j].w;
             }
             v.x *= inu; v.y *= inu; v.z *= inu; v.w *= inu;
             reinterpret_cast<float4*>(out)[e] = v;
@@ -693,34 +691,32 @@ __device__ __forceinline__ void combine_range(const T* __restrict__ q, const Com
     for (long long e = done + tid; e < n; e += stride) {
         T v = q[e];
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-            if (j < k) v -= beta[j] * __ldg(c.Qp[j] + e);
+        for (int j = 0; j < K; ++j) v -= beta[j] * __ldg(c.Qp[j] + e);
         out[e] = v * inu;
     }
 }
 
-template <typename T>
-__global__ void combine_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
-                               T inv_nu, long long n, T* __restrict__ out) {
-    T beta[16];
+template <typename T, int K>
+__global__ void combine_kernel(const T* __restrict__ q, CombineArgs<T> c, T inv_nu, long long n, T* __restrict__ out) {
+    T beta[K > 0 ? K : 1];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) beta[j] = j < k ? c.beta[j] : T(0);
-    combine_range<T>(q, c, k, beta, inv_nu, n, out);
+    for (int j = 0; j < K; ++j) beta[j] = c.beta[j];
+    combine_range<T, K>(q, c, beta, inv_nu, n, out);
 }
 
-template <typename T>
-__global__ void combine_dyn_kernel(const T* __restrict__ q, CombineArgs<T> c, int k,
-                                   const CtlCombine* __restrict__ ctl, long long n, T* __restrict__ out) {
+template <typename T, int K>
+__global__ void combine_dyn_kernel(const T* __restrict__ q, CombineArgs<T> c, const CtlCombine* __restrict__ ctl,
+                                   long long n, T* __restrict__ out) {
     if (!ctl->run) return;
-    T beta[16];
+    T beta[K > 0 ? K : 1];
     if constexpr (sizeof(T) == 4) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) beta[j] = j < k ? ctl->beta_f[j] : T(0);
-        combine_range<T>(q, c, k, beta, ctl->inv_nu_f, n, out);
+        for (int j = 0; j < K; ++j) beta[j] = ctl->beta_f[j];
+        combine_range<T, K>(q, c, beta, ctl->inv_nu_f, n, out);
     } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) beta[j] = j < k ? (T)ctl->beta[j] : T(0);
-        combine_range<T>(q, c, k, beta, (T)ctl->inv_nu, n, out);
+        for (int j = 0; j < K; ++j) beta[j] = (T)ctl->beta[j];
+        combine_range<T, K>(q, c, beta, (T)ctl->inv_nu, n, out);
     }
 }
 
@@ -1204,26 +1200,48 @@ cudaError_t track_skeleton(T* rskel, const T* qp, double alpha, const CtlCombine
     return cudaGetLastError();
 }
 
+// Launch of the combination with K directions as a template argument.
+template <typename T, bool kDyn, int K>
+cudaError_t combine_launch(const T* q, const CombineArgs<T>& c, T inv_nu, const CtlCombine* ctl, long long n, T* out,
+                           cudaStream_t st) {
+    const unsigned grid = grid_for(sizeof(T) == 4 ? (n + 3) / 4 : n);
+    if constexpr (kDyn) combine_dyn_kernel<T, K><<<grid, 256, 0, st>>>(q, c, ctl, n, out);
+    else combine_kernel<T, K><<<grid, 256, 0, st>>>(q, c, inv_nu, n, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T, bool kDyn>
+cudaError_t combine_switch(int k, const T* q, const CombineArgs<T>& c, T inv_nu, const CtlCombine* ctl, long long n,
+                           T* out, cudaStream_t st) {
+    switch (k) {
+#define ASDSM_COMBINE_CASE(K) \
+        case K: return combine_launch<T, kDyn, K>(q, c, inv_nu, ctl, n, out, st);
+        ASDSM_COMBINE_CASE(0) ASDSM_COMBINE_CASE(1) ASDSM_COMBINE_CASE(2) ASDSM_COMBINE_CASE(3)
+        ASDSM_COMBINE_CASE(4) ASDSM_COMBINE_CASE(5) ASDSM_COMBINE_CASE(6) ASDSM_COMBINE_CASE(7)
+        ASDSM_COMBINE_CASE(8) ASDSM_COMBINE_CASE(9) ASDSM_COMBINE_CASE(10) ASDSM_COMBINE_CASE(11)
+        ASDSM_COMBINE_CASE(12) ASDSM_COMBINE_CASE(13) ASDSM_COMBINE_CASE(14) ASDSM_COMBINE_CASE(15)
+#undef ASDSM_COMBINE_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename T>
 cudaError_t combine_skeleton(const T* q, const T* const* Qp, const double* beta, int k, double inv_nu,
                              long long n, T* out, cudaStream_t st) {
-    if (k > 16) return cudaErrorInvalidValue;
+    if (k < 0 || k > 15) return cudaErrorInvalidValue;
     CombineArgs<T> c{};
     for (int j = 0; j < k; ++j) { c.Qp[j] = Qp[j]; c.beta[j] = (T)beta[j]; }
-    combine_kernel<T><<<grid_for(sizeof(T) == 4 ? (n + 3) / 4 : n), 256, 0, st>>>(q, c, k, (T)inv_nu, n, out);
-    note_launch();
-    return cudaGetLastError();
+    return combine_switch<T, false>(k, q, c, (T)inv_nu, nullptr, n, out, st);
 }
 
 template <typename T>
 cudaError_t combine_skeleton_dyn(const T* q, const T* const* Qp, int k, const CtlCombine* ctl,
                                  long long n, T* out, cudaStream_t st) {
-    if (k > 16) return cudaErrorInvalidValue;
+    if (k < 0 || k > 15) return cudaErrorInvalidValue;
     CombineArgs<T> c{};
     for (int j = 0; j < k; ++j) c.Qp[j] = Qp[j];
-    combine_dyn_kernel<T><<<grid_for(sizeof(T) == 4 ? (n + 3) / 4 : n), 256, 0, st>>>(q, c, k, ctl, n, out);
-    note_launch();
-    return cudaGetLastError();
+    return combine_switch<T, true>(k, q, c, T(0), ctl, n, out, st);
 }
 
 // Input channels of the learned correction on the full N x N grid:

@@ -117,3 +117,26 @@ def test_batch_autotune_per_size_class(lib):
     for p, u in zip(probs, us):
         r, bb = orc.residual_grid(p.N, p.alpha, p.beta, p.s, u.cpu().numpy())
         assert np.linalg.norm(r) / np.linalg.norm(bb) <= 1e-10 * 1.01
+
+
+def test_batch_with_sixteen_directions_and_a_large_instance(lib):
+    """GCR(16) in a batch with a 1025^2 instance: the GCR products of 16
+    directions over its skeleton take the dot kernels' widest partial layout,
+    which the reduction scratch must hold.  Both instances reach the fine
+    solution (oracle residual) and equal their single solves bit for bit."""
+    sizes = [1025, 129]
+    probs, mcs = [wl.random_fourier_2d(N, 300 + i) for i, N in enumerate(sizes)], [64, 8]
+    kw = dict(precision=lib.MIXED, tol=1e-10, max_sweeps=600, accel_m=16)
+    with lib.BatchSolver([(p.N, mc, p.alpha, p.beta) for p, mc in zip(probs, mcs)], **kw) as bs:
+        us = [_dev(p.g) for p in probs]
+        rc, stats = bs.solve([_dev(p.s) for p in probs], us)
+        got = [u.cpu().numpy() for u in us]
+    assert rc == lib.OK, stats
+    for i, (p, mc) in enumerate(zip(probs, mcs)):
+        r, b = orc.residual_grid(p.N, p.alpha, p.beta, p.s, got[i])
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-10, i
+        with lib.Solver(p.N, mc, p.alpha, p.beta, **kw) as sv:
+            u = _dev(p.g)
+            res = sv.solve(_dev(p.s), u)
+        assert res.status == lib.OK
+        assert np.array_equal(got[i], u.cpu().numpy()), i
