@@ -245,18 +245,13 @@ def job_throughput(world: int, unknowns_per_rank: int, steps: int, ms: float) ->
 
 def family_roofline(fname, frec, peaks, peak_src, num_sms, sm_max):
     """Roofline entry of one kernel family from its profile record (launches, ms,
-    algorithmic bytes and flops): the tensor-core Filler against the TF32 dense
-    peak (measured bf16 burst x the nominal TF32/BF16 ratio 1.1/2.25), the block
-    cyclic reductions and the reduction Filler against the derived FP32 FMA peak,
-    every other family against the measured HBM bandwidth."""
+    algorithmic bytes and flops): the block cyclic reductions and the reduction
+    Filler against the derived FP32 FMA peak, every other family - the
+    tensor-core Filler included - against the measured HBM bandwidth.  The
+    tensor-core Filler moves 4 (225 + 60) bytes per hole for 2 x 225 x 60 flops,
+    about 24 flop/byte, far below the TF32 ridge (~140 flop/byte): HBM bounds it;
+    its tensor rate is given beside."""
     avg_ms = frec["ms"] / max(1, frec["launches"])
-    if fname == "fill_tc" and frec["flops"] > 0:
-        achieved = frec["flops"] / (frec["ms"] * 1e-3) / 1e12
-        peak = float(peaks["bf16_tflops"]) * 1.1 / 2.25
-        return {"kernel": fname, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{peak_src} bf16_tflops x 1.1/2.25 (nominal TF32/BF16 dense)",
-                "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
     if frec["flops"] > 0 and fname in ("bcr_aniso", "fill_holes"):
         achieved = frec["flops"] / (frec["ms"] * 1e-3) / 1e12
         peak = num_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -266,9 +261,15 @@ def family_roofline(fname, frec, peaks, peak_src, num_sms, sm_max):
                 "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
     achieved = frec["bytes"] / (frec["ms"] * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
-    return {"kernel": fname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
-            "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
+    out = {"kernel": fname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "traffic": None, "peak_source": f"{peak_src} hbm_gbs",
+           "avg_launch_us": avg_ms * 1e3, "launches": frec["launches"]}
+    if fname == "fill_tc" and frec["flops"] > 0:
+        tf = frec["flops"] / (frec["ms"] * 1e-3) / 1e12
+        tpeak = float(peaks["bf16_tflops"]) * 1.1 / 2.25
+        out["tensor"] = {"achieved_tflops": tf, "peak_tflops": tpeak, "frac": tf / tpeak,
+                         "peak_source": f"{peak_src} bf16_tflops x 1.1/2.25 (nominal TF32/BF16 dense)"}
+    return out
 
 
 def run_reference(args):

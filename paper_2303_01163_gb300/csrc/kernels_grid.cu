@@ -1,12 +1,14 @@
 // Grid-wide kernels of the ASDSM sweep on sm_103a: the fine residual of
-// The fine residual of Algorithm 4 (with the previous sweep's update fused in), the
-// right-hand sides of eq. (2.4), the merge of Algorithm 2, the skeleton
-// operator for the least-squares step length, reductions and conversions.
+// Algorithm 4 (with the previous sweep's update fused in), the right-hand
+// sides of eq. (2.4), the merge of Algorithm 2, the skeleton operator for the
+// least-squares step length, reductions and conversions.
 #include "asdsm_internal.h"
 #include <cuda_runtime.h>
+#include <cooperative_groups.h>
 #include <atomic>
 
 namespace asdsm {
+namespace cg = cooperative_groups;
 
 static std::atomic<long long> g_launches{0};
 void note_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -347,20 +349,19 @@ residual_mixed_kernel(const float* __restrict__ s_hi, const float* __restrict__ 
     }
     if (ovf) atomicOr(overflow, 1);
     // Block reduction of the two norms (8 warps).
+    // Warp sums as compensated FP32 pairs; the block's sum in FP64 by one thread.
     __shared__ double red[2][MS_WARPS];
-    double a = warp_sum((double)srf), b = warp_sum((double)shf);
-    if (lane == 0) { red[0][warp] = a; red[1][warp] = b; }
+    float ah = srf, al = 0.0f, bh = shf, bl = 0.0f;
+    warp_sum_pair(ah, al);
+    warp_sum_pair(bh, bl);
+    if (lane == 0) { red[0][warp] = (double)ah + (double)al; red[1][warp] = (double)bh + (double)bl; }
     __syncthreads();
-    if (warp == 0) {
-        a = lane < MS_WARPS ? red[0][lane] : 0.0;
-        b = lane < MS_WARPS ? red[1][lane] : 0.0;
-        a = warp_sum(a);
-        b = warp_sum(b);
-        if (lane == 0) {
-            const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-            o.partials[2 * blk] = a;
-            o.partials[2 * blk + 1] = b;
-        }
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < MS_WARPS; ++w) { a += red[0][w]; b += red[1][w]; }
+        const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+        o.partials[2 * blk] = a;
+        o.partials[2 * blk + 1] = b;
     }
 }
 
@@ -408,17 +409,6 @@ __global__ void submesh_rhs_kernel(const double* __restrict__ s, const double* _
 // merge_write: every skeleton point gets its anisotropic value plus the spline
 // correction and the merged skeleton is stored.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T cross_t1(const MergeArgs<T>& a, T inv1, int l, int k) {
-    // t1[l][k] = u_fc at (x = (k+1)n, line l)
-    return a.Yfc[(long long)((k + 1) * a.g.n - 1) * a.g.Nc + l] * inv1;
-}
-template <typename T>
-__device__ __forceinline__ T cross_t2(const MergeArgs<T>& a, T inv2, int l, int k) {
-    // t2[l][k] = u_cf at (y = (l+1)n, column k)
-    return a.Ycf[(long long)((l + 1) * a.g.n - 1) * a.g.Nc + k] * inv2;
-}
-
 // 1/||u|| of the normalisation of Algorithm 1 (FP32 reciprocal square root on the mixed path:
 // a single scale factor, and FP64 division and square root are slow on this part).
 template <typename T>
@@ -436,120 +426,131 @@ __device__ __forceinline__ void inv_norms(const MergeArgs<T>& a, T* inv1, T* inv
 
 // Knot errors and spline moments as one small GEMM per family:
 //   M[line][r] = sum_q Sm[r][q] e[line][q]
-// with the cross-point errors of Algorithm 2 formed on the fly from the cross points.  A CTA
-// owns MK_L lines x MK_R moments and walks the knots in chunks of MK_Q staged
-// in shared memory (Sm is stored transposed, [knot q][moment r], so the staging
-// reads are coalesced); a group of chunks is loaded into registers at once and
-// the chunks are multiplied in order.  The CTAs of the first moment block also
-// store e.
-constexpr int MK_L = 16, MK_R = 32, MK_Q = 32, MK_THREADS = 128;
-
-template <typename T>
-__device__ __forceinline__ T knot_error(const MergeArgs<T>& a, int fam, int line, int q, T inv1, T inv2, int choice) {
-    const int l = fam == 0 ? line : q;       // fc line l: knots along x (k = q)
-    const int k = fam == 0 ? q : line;       // cf column k: knots along y (l = q)
-    const T t1 = cross_t1(a, inv1, l, k), t2 = cross_t2(a, inv2, l, k);
-    T uh;
-    if (a.re_mode) uh = t1 + t2 - a.Ycc[(long long)l * a.g.Nc + k];   // Richardson extrapolation (combination)
-    else uh = choice ? t2 : t1;                                        // random choice
-    return fam == 0 ? uh - t1 : uh - t2;                               // cross-point error
-}
+// with the cross-point errors of Algorithm 2 formed from the cross points.  A
+// cluster of MK_KS CTAs owns MK_L lines x MK_R moments; CTA rank k takes the
+// k-th quarter of the knots, in chunks of MK_Q (half that for FP64).  Per chunk the cross values
+// t1 (u_fc, [x][line] in Yfc) and t2 (u_cf, [y][column] in Ycf) are read as two
+// tiles, each along its contiguous index, the errors formed in shared memory,
+// and Sm (stored transposed, [knot q][moment r]) staged beside them; a thread
+// accumulates 2 lines x 4 moments.  The partial tiles are summed in rank order
+// through distributed shared memory.  The CTAs of the first moment block also
+// store e.  One cluster wave covers the 4097^2 case (320 CTAs).
+constexpr int MK_L = 32, MK_R = 64, MK_Q = 64, MK_KS = 4, MK_THREADS = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(MK_THREADS) merge_knots_kernel(MergeArgs<T> a) {
-    const int Nc = a.g.Nc, K = a.g.mc + 1;
+    constexpr int MQ = sizeof(T) == 4 ? MK_Q : MK_Q / 2;   // knots per chunk (static shared memory <= 48 KB)
+    cg::cluster_group cluster = cg::this_cluster();
+    const int Nc = a.g.Nc, K = a.g.mc + 1, n = a.g.n;
     const int nlb = (Nc + MK_L - 1) / MK_L;
-    const int fam = blockIdx.x / nlb;            // 0: fc lines, 1: cf columns
-    const int l0 = (blockIdx.x % nlb) * MK_L;
+    const int rank = (int)(blockIdx.x % MK_KS), tile = (int)(blockIdx.x / MK_KS);
+    const int fam = tile / nlb;                  // 0: fc lines, 1: cf columns
+    const int l0 = (tile % nlb) * MK_L;
     const int r0 = blockIdx.y * MK_R;
     const bool store_e = blockIdx.y == 0;
-    __shared__ T Es[MK_Q][MK_L + 1];
-    __shared__ __align__(16) T Ss[MK_Q][MK_R];
+    const int qs = (Nc + MK_KS - 1) / MK_KS;     // knots per rank
+    const int qb = rank * qs, qe = min(Nc, qb + qs);
+    // Ta: the cross value contiguous along the lines (fam 0: t1, fam 1: t2), then the
+    // errors; Tb: the one contiguous along the knots; Tc: u_cc (Richardson mode only).
+    // After the knot loop the buffer of Tb, Tc holds the partial tile.
+    __shared__ T Ta[MQ][MK_L + 1];
+    __shared__ __align__(16) T Tbc[2 * MQ * (MK_L + 1)];
+    __shared__ __align__(16) T Ss[MQ][MK_R];
     __shared__ T inv_s[2];                       // the families' norm scales, once per block
-    if (threadIdx.x == 0) inv_norms(a, &inv_s[0], &inv_s[1]);
-    __syncthreads();
-    const T inv1 = inv_s[0], inv2 = inv_s[1];
-    const int choice = a.choice_dev ? *a.choice_dev : a.choice;
+    static_assert(MK_L * MK_R <= 2 * MQ * (MK_L + 1), "the partial tile fits the Tb, Tc buffer");
+    T (*Tb)[MK_L + 1] = reinterpret_cast<T (*)[MK_L + 1]>(Tbc);
+    T (*Tc)[MK_L + 1] = reinterpret_cast<T (*)[MK_L + 1]>(Tbc + MQ * (MK_L + 1));
+    T (*Part)[MK_R] = reinterpret_cast<T (*)[MK_R]>(Tbc);
     const int tid = threadIdx.x;
-    const int tl = tid / (MK_R / 2), tr = tid % (MK_R / 2);   // 2 lines x 2 moments per thread
-    constexpr int EPT = MK_L * MK_Q / MK_THREADS;             // 4
-    constexpr int SPT = MK_Q * MK_R / MK_THREADS;             // 8
-    T ev[EPT], sv[SPT];
-    auto load_chunk = [&](int q0) {
+    if (tid == 0) inv_norms(a, &inv_s[0], &inv_s[1]);
+    const int choice = a.choice_dev ? *a.choice_dev : a.choice;
+    const T* along_lines = fam == 0 ? a.Yfc : a.Ycf;   // [(q+1)n-1][line]
+    const T* along_knots = fam == 0 ? a.Ycf : a.Yfc;   // [(line+1)n-1][q]
+    const int tl = tid / (MK_R / 4), tr = tid % (MK_R / 4);   // lines 2 tl, 2 tl + 1; moments 4 tr .. + 3
+    T acc[2][4];
 #pragma unroll
-        for (int j = 0; j < EPT; ++j) {
-            const int e = tid + j * MK_THREADS;
-            const int li = e / MK_Q, qq = e % MK_Q;
-            const int line = l0 + li, q = q0 + qq;
-            ev[j] = (line < Nc && q < Nc) ? knot_error(a, fam, line, q, inv1, inv2, choice) : T(0);
-        }
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < SPT; ++j) {
-            const int e = tid + j * MK_THREADS;
-            const int qq = e / MK_R, rr = e % MK_R;
-            const int q = q0 + qq, r = r0 + rr;
-            sv[j] = (q < Nc && r < K) ? __ldg(a.Sm + (long long)q * K + r) : T(0);
-        }
-    };
-    T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
-    // Up to MK_G chunks of knots are loaded into registers at once (one memory
-    // latency for all of them), then staged and multiplied one after another.
-    constexpr int MK_G = 8;
-    for (int g0 = 0; g0 < Nc; g0 += MK_G * MK_Q) {
-        T evg[MK_G][EPT], svg[MK_G][SPT];
-#pragma unroll
-        for (int c = 0; c < MK_G; ++c) {
-            if (g0 + c * MK_Q < Nc) {
-                load_chunk(g0 + c * MK_Q);
-#pragma unroll
-                for (int j = 0; j < EPT; ++j) evg[c][j] = ev[j];
-#pragma unroll
-                for (int j = 0; j < SPT; ++j) svg[c][j] = sv[j];
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = T(0);
+    for (int q0 = qb; q0 < qe; q0 += MQ) {
+        __syncthreads();                         // previous chunk consumed (and inv_s written)
+        for (int e = tid; e < MQ * MK_L; e += MK_THREADS) {
+            {
+                const int qq = e / MK_L, li = e % MK_L, q = q0 + qq, line = l0 + li;
+                const bool ok = q < qe && line < Nc;
+                Ta[qq][li] = ok ? along_lines[((long long)(q + 1) * n - 1) * Nc + line] : T(0);
+                // u_cc at (l, k): fam 0 (l = line, k = q) along the knots, fam 1 (l = q, k = line) here
+                if (a.re_mode && fam == 1) Tc[qq][li] = ok ? a.Ycc[(long long)q * Nc + line] : T(0);
+            }
+            {
+                const int li = e / MQ, qq = e % MQ, q = q0 + qq, line = l0 + li;
+                const bool ok = q < qe && line < Nc;
+                Tb[qq][li] = ok ? along_knots[((long long)(line + 1) * n - 1) * Nc + q] : T(0);
+                if (a.re_mode && fam == 0) Tc[qq][li] = ok ? a.Ycc[(long long)line * Nc + q] : T(0);
             }
         }
-#pragma unroll
-        for (int c = 0; c < MK_G; ++c) {
-            const int q0 = g0 + c * MK_Q;
-            if (q0 >= Nc) break;
-            __syncthreads();                     // previous chunk consumed
-#pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                const int e = tid + j * MK_THREADS;
-                const int li = e / MK_Q, qq = e % MK_Q;
-                Es[qq][li] = evg[c][j];
-                const int line = l0 + li, q = q0 + qq;
-                if (store_e && line < Nc && q < Nc) {
-                    if (fam == 0) a.E1[(long long)line * Nc + q] = evg[c][j];      // E1[l][k]
-                    else a.E2[(long long)q * Nc + line] = evg[c][j];               // E2[l][k]
-                }
+        for (int e = tid; e < MQ * MK_R; e += MK_THREADS) {
+            const int qq = e / MK_R, rr = e % MK_R, q = q0 + qq, r = r0 + rr;
+            Ss[qq][rr] = (q < qe && r < K) ? __ldg(a.Sm + (long long)q * K + r) : T(0);
+        }
+        __syncthreads();
+        const T inv1 = inv_s[0], inv2 = inv_s[1];
+        for (int e = tid; e < MQ * MK_L; e += MK_THREADS) {
+            const int qq = e / MK_L, li = e % MK_L, q = q0 + qq, line = l0 + li;
+            const T A = Ta[qq][li], B = Tb[qq][li];
+            const T t1 = (fam == 0 ? A : B) * inv1, t2 = (fam == 0 ? B : A) * inv2;
+            T uh;
+            if (a.re_mode) uh = t1 + t2 - Tc[qq][li];   // Richardson extrapolation (combination)
+            else uh = choice ? t2 : t1;                 // random choice
+            const T ev = fam == 0 ? uh - t1 : uh - t2;  // cross-point error (0 outside the ranges)
+            Ta[qq][li] = ev;
+            if (store_e && q < qe && line < Nc) {
+                if (fam == 0) a.E1[(long long)line * Nc + q] = ev;      // E1[l][k]
+                else a.E2[(long long)q * Nc + line] = ev;               // E2[l][k]
             }
-#pragma unroll
-            for (int j = 0; j < SPT; ++j) {
-                const int e = tid + j * MK_THREADS;
-                Ss[e / MK_R][e % MK_R] = svg[c][j];
-            }
-            __syncthreads();
+        }
+        __syncthreads();
 #pragma unroll 8
-            for (int qq = 0; qq < MK_Q; ++qq) {
-                const T e0 = Es[qq][2 * tl], e1 = Es[qq][2 * tl + 1];
-                const T s0 = Ss[qq][2 * tr], s1 = Ss[qq][2 * tr + 1];
-                acc[0][0] += s0 * e0; acc[0][1] += s1 * e0;
-                acc[1][0] += s0 * e1; acc[1][1] += s1 * e1;
+        for (int qq = 0; qq < MQ; ++qq) {
+            const T e0 = Ta[qq][2 * tl], e1 = Ta[qq][2 * tl + 1];
+            T sv4[4];
+            if constexpr (sizeof(T) == 4) {
+                const float4 v = *reinterpret_cast<const float4*>(&Ss[qq][4 * tr]);
+                sv4[0] = v.x; sv4[1] = v.y; sv4[2] = v.z; sv4[3] = v.w;
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) sv4[jj] = Ss[qq][4 * tr + jj];
+            }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                acc[0][jj] += sv4[jj] * e0;
+                acc[1][jj] += sv4[jj] * e1;
             }
         }
     }
+    __syncthreads();                             // the Tb, Tc buffer becomes the partial tile
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int line = l0 + 2 * tl + i;
-        if (line >= Nc) continue;
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            const int r = r0 + 2 * tr + jj;
-            if (r >= K) continue;
-            if (fam == 0) a.M1[(long long)line * K + r] = acc[i][jj];
-            else a.M2[(long long)r * Nc + line] = acc[i][jj];
+        for (int jj = 0; jj < 4; ++jj) Part[2 * tl + i][4 * tr + jj] = acc[i][jj];
+    cluster.sync();                              // every rank's partial tile is complete
+    // Rank k sums lines [k MK_L / MK_KS, (k + 1) MK_L / MK_KS) over the ranks, in rank order.
+    constexpr int LPR = MK_L / MK_KS;
+    const T* P[MK_KS];
+#pragma unroll
+    for (int j = 0; j < MK_KS; ++j) P[j] = cluster.map_shared_rank(&Part[0][0], j);
+    for (int e = tid; e < LPR * MK_R; e += MK_THREADS) {
+        const int li = rank * LPR + e / MK_R, rr = e % MK_R;
+        T v = T(0);
+#pragma unroll
+        for (int j = 0; j < MK_KS; ++j) v += P[j][li * MK_R + rr];
+        const int line = l0 + li, r = r0 + rr;
+        if (line < Nc && r < K) {
+            if (fam == 0) a.M1[(long long)line * K + r] = v;
+            else a.M2[(long long)r * Nc + line] = v;
         }
     }
+    cluster.sync();                              // no CTA leaves while its tile is read
 }
 
 // Weights of the not-a-knot spline with moments M and knot values (0, e.., 0) at
@@ -565,10 +566,12 @@ __device__ __forceinline__ void spline_weights(int p, int n, T H, T* w) {
     w[3] = t / H;
 }
 
-// fc lines in tiles of MW_T lines x MW_T fine x through shared memory (Yfc is
-// [x][line]: read along lines, written along x, both coalesced); cf points in
-// a grid-stride loop after the tiles' blocks.
-constexpr int MW_T = 32, MW_THREADS = 256;
+// fc lines in tiles of MW_T lines x MW_X MW_T fine x through shared memory (Yfc
+// is [x][line]: read along lines, written along x, both coalesced); then blocks
+// of MW_Y cf rows (columns along the threads).  A thread's loads are issued
+// before the block waits for the spline weights and norm scales, so that about
+// one wave of blocks covers the skeleton.
+constexpr int MW_T = 32, MW_X = 4, MW_Y = 8, MW_THREADS = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(MW_THREADS) merge_write_kernel(MergeArgs<T> a, int nft) {
@@ -576,56 +579,71 @@ __global__ void __launch_bounds__(MW_THREADS) merge_write_kernel(MergeArgs<T> a,
     const int Nf = g.Nf, Nc = g.Nc, n = g.n, N = g.N, K = g.mc + 1;
     const T H = T(1) / (T)g.mc;
     __shared__ T sw[33][4];                     // spline weights per fine offset p = 0..n (n <= 32)
-    __shared__ T tile[MW_T][MW_T + 1];          // [x][line]
+    __shared__ T tile[MW_X][MW_T][MW_T + 1];    // [x][line]
     __shared__ T inv_s[2];                      // the families' norm scales, once per block
     for (int p = threadIdx.x; p <= n; p += blockDim.x) spline_weights<T>(p, n, H, sw[p]);
     if (threadIdx.x == 0) inv_norms(a, &inv_s[0], &inv_s[1]);
     const int tx = threadIdx.x % MW_T, ty = threadIdx.x / MW_T;
     if ((int)blockIdx.x < nft) {
         // fc line l, fine x: u_fc/||u_fc|| + Spline(e1); cross points too (written from fc).
-        const int nxt = (Nf + MW_T - 1) / MW_T;
-        const int l0 = ((int)blockIdx.x / nxt) * MW_T, x0 = ((int)blockIdx.x % nxt) * MW_T;
-        for (int xx = ty; xx < MW_T; xx += MW_THREADS / MW_T) {
-            const int x = x0 + xx, l = l0 + tx;
-            tile[xx][tx] = (x < Nf && l < Nc) ? a.Yfc[(long long)x * Nc + l] : T(0);
-        }
+        const int nxt = (Nf + MW_T * MW_X - 1) / (MW_T * MW_X);
+        const int l0 = ((int)blockIdx.x / nxt) * MW_T, x0 = ((int)blockIdx.x % nxt) * MW_T * MW_X;
+#pragma unroll
+        for (int c = 0; c < MW_X; ++c)
+#pragma unroll
+            for (int xx = ty; xx < MW_T; xx += MW_THREADS / MW_T) {
+                const int x = x0 + c * MW_T + xx, l = l0 + tx;
+                tile[c][xx][tx] = (x < Nf && l < Nc) ? a.Yfc[(long long)x * Nc + l] : T(0);
+            }
         __syncthreads();
         const T inv1 = inv_s[0];
-        for (int ll = ty; ll < MW_T; ll += MW_THREADS / MW_T) {
-            const int l = l0 + ll, x = x0 + tx;
-            if (l >= Nc || x >= Nf) continue;
-            const int i = x + 1, ki = i / n, p = i % n;
-            T corr;
-            const T yk = ki == 0 ? T(0) : a.E1[(long long)l * Nc + ki - 1];
-            if (p == 0) {
-                corr = yk;                       // at a knot the spline interpolates exactly
-            } else {
-                const T* Mv = a.M1 + (long long)l * K;
-                const T yk1 = ki + 1 >= g.mc ? T(0) : a.E1[(long long)l * Nc + ki];
-                corr = sw[p][0] * Mv[ki] + sw[p][1] * Mv[ki + 1] + sw[p][2] * yk + sw[p][3] * yk1;
+#pragma unroll
+        for (int c = 0; c < MW_X; ++c)
+            for (int ll = ty; ll < MW_T; ll += MW_THREADS / MW_T) {
+                const int l = l0 + ll, x = x0 + c * MW_T + tx;
+                if (l >= Nc || x >= Nf) continue;
+                const int i = x + 1, ki = i >> g.ln, p = i & (n - 1);
+                T corr;
+                const T yk = ki == 0 ? T(0) : a.E1[(long long)l * Nc + ki - 1];
+                if (p == 0) {
+                    corr = yk;                   // at a knot the spline interpolates exactly
+                } else {
+                    const T* Mv = a.M1 + (long long)l * K;
+                    const T yk1 = ki + 1 >= g.mc ? T(0) : a.E1[(long long)l * Nc + ki];
+                    corr = sw[p][0] * Mv[ki] + sw[p][1] * Mv[ki + 1] + sw[p][2] * yk + sw[p][3] * yk1;
+                }
+                a.z[(long long)((l + 1) * n) * N + i] = tile[c][tx][ll] * inv1 + corr;
             }
-            a.z[(long long)((l + 1) * n) * N + i] = tile[tx][ll] * inv1 + corr;
-        }
         return;
     }
-    __syncthreads();
-    const T inv2 = inv_s[1];
-    const int total = Nf * Nc;
-    const int nb = (int)gridDim.x - nft;
-    for (int f = ((int)blockIdx.x - nft) * blockDim.x + threadIdx.x; f < total; f += nb * blockDim.x) {
-        // cf points, ordered [y][column] so that consecutive threads read Ycf contiguously;
-        // cross points are skipped: they keep the fc value.
-        const int y = f / Nc, k = f % Nc;
-        const int j = y + 1;
-        if (j % n == 0) continue;
-        const int ki = j / n, p = j % n;
-        const T yk = ki == 0 ? T(0) : a.E2[(ki - 1) * Nc + k];
-        const T yk1 = ki + 1 >= g.mc ? T(0) : a.E2[ki * Nc + k];
-        const T corr = sw[p][0] * a.M2[ki * Nc + k] + sw[p][1] * a.M2[(ki + 1) * Nc + k] + sw[p][2] * yk +
-                       sw[p][3] * yk1;
-        const T val = a.Ycf[(long long)y * Nc + k] * inv2 + corr;
-        if (a.zv) a.zv[(long long)j * (g.mc + 1) + k + 1] = val;
-        else a.z[(long long)j * N + (k + 1) * n] = val;
+    // cf points, MW_Y fine rows per block; the cross rows are skipped, their points
+    // keep the fc value.  Columns k along the threads, in chunks of MW_THREADS.
+    const int y0 = ((int)blockIdx.x - nft) * MW_Y;
+    const int nkc = (Nc + MW_THREADS - 1) / MW_THREADS;
+    for (int kc = 0; kc < nkc; ++kc) {
+        const int k = kc * MW_THREADS + threadIdx.x;
+        T yv[MW_Y], e0[MW_Y], e1[MW_Y], m0[MW_Y], m1[MW_Y];
+#pragma unroll
+        for (int u = 0; u < MW_Y; ++u) {
+            const int y = y0 + u, j = y + 1, ki = j >> g.ln;
+            const bool ok = y < Nf && k < Nc && (j & (n - 1)) != 0;
+            yv[u] = ok ? a.Ycf[(long long)y * Nc + k] : T(0);
+            e0[u] = ok && ki > 0 ? a.E2[(ki - 1) * Nc + k] : T(0);
+            e1[u] = ok && ki + 1 < g.mc ? a.E2[ki * Nc + k] : T(0);
+            m0[u] = ok ? a.M2[ki * Nc + k] : T(0);
+            m1[u] = ok ? a.M2[(ki + 1) * Nc + k] : T(0);
+        }
+        if (kc == 0) __syncthreads();           // spline weights and norm scales ready
+        const T inv2 = inv_s[1];
+#pragma unroll
+        for (int u = 0; u < MW_Y; ++u) {
+            const int y = y0 + u, j = y + 1, p = j & (n - 1);
+            if (y >= Nf || k >= Nc || p == 0) continue;
+            const T corr = sw[p][0] * m0[u] + sw[p][1] * m1[u] + sw[p][2] * e0[u] + sw[p][3] * e1[u];
+            const T val = yv[u] * inv2 + corr;
+            if (a.zv) a.zv[(long long)j * (g.mc + 1) + k + 1] = val;
+            else a.z[(long long)j * N + (k + 1) * n] = val;
+        }
     }
 }
 
@@ -633,10 +651,51 @@ __global__ void __launch_bounds__(MW_THREADS) merge_write_kernel(MergeArgs<T> a,
 template <typename T>
 struct StencilT { T cc, cw, ce, cs, cn; };
 
-// q = A z at compact skeleton rows (z: full grid, zero ring).  Grids are at most
-// 8193^2 points: 32-bit indices.
+// q = A z at compact skeleton rows (z: full grid, zero ring).  A thread computes
+// SA_E points with every load issued before the first use, so that about one
+// wave of blocks covers the skeleton: fc lines in chunks of 256 SA_E points
+// (consecutive threads, consecutive x), then blocks of SA_E cf rows off the fc
+// lines (one row per step, columns along the threads).  Grid offsets fit 32-bit
+// integers (N <= 32769).
+constexpr int SA_E = 8;
+
 template <typename T>
-__global__ void skeleton_apply_kernel(const T* __restrict__ z, Geometry g, StencilT<T> c, T* __restrict__ q) {
+__global__ void __launch_bounds__(256) skeleton_apply_kernel(const T* __restrict__ z, Geometry g, StencilT<T> c,
+                                                            T* __restrict__ q, int nxb) {
+    const int N = g.N, n = g.n, Nf = g.Nf, Nc = g.Nc;
+    const int b = (int)blockIdx.x, nfb = Nc * nxb;
+    T v[SA_E][5];
+    int out[SA_E];
+    if (b < nfb) {
+        const int l = b / nxb, x0 = (b % nxb) * 256 * SA_E + threadIdx.x;
+        const int row = ((l + 1) * n) * N + 1;
+#pragma unroll
+        for (int u = 0; u < SA_E; ++u) {
+            const int x = x0 + 256 * u;
+            out[u] = x < Nf ? l * Nf + x : -1;
+            const int idx = row + (x < Nf ? x : 0);
+            v[u][0] = z[idx]; v[u][1] = z[idx - 1]; v[u][2] = z[idx + 1]; v[u][3] = z[idx - N]; v[u][4] = z[idx + N];
+        }
+    } else {
+        const int yr0 = (b - nfb) * SA_E, nyr = Nf - Nc;
+#pragma unroll
+        for (int u = 0; u < SA_E; ++u) {
+            const int yr = yr0 + u, k = threadIdx.x;
+            const bool ok = yr < nyr && k < Nc;
+            out[u] = ok ? Nc * Nf + yr * Nc + k : -1;
+            const int j = ok ? yr + yr / (n - 1) + 1 : n + 1;
+            const int idx = j * N + ((ok ? k : 0) + 1) * n;
+            v[u][0] = z[idx]; v[u][1] = z[idx - 1]; v[u][2] = z[idx + 1]; v[u][3] = z[idx - N]; v[u][4] = z[idx + N];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < SA_E; ++u)
+        if (out[u] >= 0) q[out[u]] = c.cc * v[u][0] + c.cw * v[u][1] + c.ce * v[u][2] + c.cs * v[u][3] + c.cn * v[u][4];
+}
+
+// The same for any N_c: one point per thread, grid-strided.
+template <typename T>
+__global__ void skeleton_apply_generic_kernel(const T* __restrict__ z, Geometry g, StencilT<T> c, T* __restrict__ q) {
     const int N = g.N, n = g.n, Nf = g.Nf, Nc = g.Nc;
     const int nfc = Nc * Nf, skel = (int)g.skel;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < skel; e += gridDim.x * blockDim.x) {
@@ -774,6 +833,42 @@ multi_dot_kernel(DotArgs<T> d, int ndots, long long n, double* partials) {
     }
 }
 
+// The block's partial sums of ND per-thread accumulators into partials[block][ND]:
+// FP32 accumulators as compensated warp sums with FP64 once per dot and block.
+template <typename T, int ND>
+__device__ __forceinline__ void dots_block_reduce(const T* acc, double* partials) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (sizeof(T) == 4) {
+        // Warp sums as compensated FP32 pairs; the block's sum in FP64, once per dot.
+        __shared__ float redh[DOT_THREADS / 32][ND], redl[DOT_THREADS / 32][ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            float hi = acc[d], lo = 0.0f;
+            warp_sum_pair(hi, lo);
+            if (lane == 0) { redh[w][d] = hi; redl[w][d] = lo; }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < ND; d += DOT_THREADS) {
+            double v = 0.0;
+            for (int ww = 0; ww < DOT_THREADS / 32; ++ww) v += (double)redh[ww][d] + (double)redl[ww][d];
+            partials[(long long)blockIdx.x * ND + d] = v;
+        }
+    } else {
+        __shared__ double red[DOT_THREADS / 32][ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const double v = warp_sum((double)acc[d]);
+            if (lane == 0) red[w][d] = v;
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < ND; d += DOT_THREADS) {
+            double v = 0.0;
+            for (int ww = 0; ww < DOT_THREADS / 32; ++ww) v += red[ww][d];
+            partials[(long long)blockIdx.x * ND + d] = v;
+        }
+    }
+}
+
 // Inner products of the GCR step in one pass over the skeleton vectors:
 // out partials [block][2 + 2k]: <q,q>, <q,r>, then <q,p_j>, <r,p_j> for j < k.
 template <typename T>
@@ -820,36 +915,7 @@ gcr_dots_kernel(const T* __restrict__ q, const T* __restrict__ r, GcrDotArgs<T> 
             acc[3 + 2 * j] += rv * pv;
         }
     }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if constexpr (sizeof(T) == 4) {
-        // Warp sums as compensated FP32 pairs; the block's sum in FP64, once per dot.
-        __shared__ float redh[DOT_THREADS / 32][ND], redl[DOT_THREADS / 32][ND];
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            float hi = acc[d], lo = 0.0f;
-            warp_sum_pair(hi, lo);
-            if (lane == 0) { redh[w][d] = hi; redl[w][d] = lo; }
-        }
-        __syncthreads();
-        for (int d = threadIdx.x; d < ND; d += DOT_THREADS) {
-            double v = 0.0;
-            for (int ww = 0; ww < DOT_THREADS / 32; ++ww) v += (double)redh[ww][d] + (double)redl[ww][d];
-            partials[(long long)blockIdx.x * ND + d] = v;
-        }
-    } else {
-        __shared__ double red[DOT_THREADS / 32][ND];
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            const double v = warp_sum((double)acc[d]);
-            if (lane == 0) red[w][d] = v;
-        }
-        __syncthreads();
-        for (int d = threadIdx.x; d < ND; d += DOT_THREADS) {
-            double v = 0.0;
-            for (int ww = 0; ww < DOT_THREADS / 32; ++ww) v += red[ww][d];
-            partials[(long long)blockIdx.x * ND + d] = v;
-        }
-    }
+    dots_block_reduce<T, ND>(acc, partials);
 }
 
 // One CTA per column q: out[q] = sum over blocks of partials[b][q], in a fixed
@@ -1117,16 +1183,27 @@ template <typename T>
 cudaError_t merge_knots(const MergeArgs<T>& a, cudaStream_t st) {
     const int nlb = (a.g.Nc + MK_L - 1) / MK_L;
     const int nrb = (a.g.mc + 1 + MK_R - 1) / MK_R;
-    merge_knots_kernel<T><<<dim3(2 * nlb, nrb), MK_THREADS, 0, st>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * nlb * MK_KS, nrb);
+    cfg.blockDim = dim3(MK_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = MK_KS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, merge_knots_kernel<T>, a);
     note_launch();
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t merge_write(const MergeArgs<T>& a, cudaStream_t st) {
-    const int nft = ((a.g.Nc + MW_T - 1) / MW_T) * ((a.g.Nf + MW_T - 1) / MW_T);
-    const unsigned ncf = grid_for((long long)a.g.Nf * a.g.Nc, MW_THREADS);
-    merge_write_kernel<T><<<nft + ncf, MW_THREADS, 0, st>>>(a, nft);
+    const int nft = ((a.g.Nc + MW_T - 1) / MW_T) * ((a.g.Nf + MW_T * MW_X - 1) / (MW_T * MW_X));
+    merge_write_kernel<T><<<nft + (a.g.Nf + MW_Y - 1) / MW_Y, MW_THREADS, 0, st>>>(a, nft);
     note_launch();
     return cudaGetLastError();
 }
@@ -1134,7 +1211,15 @@ cudaError_t merge_write(const MergeArgs<T>& a, cudaStream_t st) {
 template <typename T>
 cudaError_t skeleton_apply(const T* z, const Geometry& g, const Stencil& s, T* q, cudaStream_t st) {
     const StencilT<T> c{(T)s.cc, (T)s.cw, (T)s.ce, (T)s.cs, (T)s.cn};
-    skeleton_apply_kernel<T><<<grid_for(g.skel), 256, 0, st>>>(z, g, c, q);
+    if (g.Nc > 256) {
+        // wider cf rows than one block: the generic per-point kernel
+        skeleton_apply_generic_kernel<T><<<grid_for(g.skel), 256, 0, st>>>(z, g, c, q);
+        note_launch();
+        return cudaGetLastError();
+    }
+    const int nxb = (g.Nf + 256 * SA_E - 1) / (256 * SA_E);
+    const int ncf = (int)((g.skel - (long long)g.Nc * g.Nf) / g.Nc);     // cf rows off the fc lines
+    skeleton_apply_kernel<T><<<g.Nc * nxb + (ncf + SA_E - 1) / SA_E, 256, 0, st>>>(z, g, c, q, nxb);
     note_launch();
     return cudaGetLastError();
 }
@@ -1154,48 +1239,73 @@ __global__ void __launch_bounds__(MW_THREADS) track_skeleton_kernel(T* __restric
     }
     const int n = g.n, Nf = g.Nf, Nc = g.Nc;
     if ((int)blockIdx.x < nft) {
-        // fc line points (cross points included) in tiles of MW_T lines x MW_T
+        // fc line points (cross points included) in tiles of MW_T lines x MW_X MW_T
         // fine x: r updated along x, r_fc ([x][line]) written along lines.
-        __shared__ T tile[MW_T][MW_T + 1];       // [x][line]
+        __shared__ T tile[MW_X][MW_T][MW_T + 1];   // [x][line]
         const int tx = threadIdx.x % MW_T, ty = threadIdx.x / MW_T;
-        const int nxt = (Nf + MW_T - 1) / MW_T;
-        const int l0 = ((int)blockIdx.x / nxt) * MW_T, x0 = ((int)blockIdx.x % nxt) * MW_T;
-        for (int ll = ty; ll < MW_T; ll += MW_THREADS / MW_T) {
-            const int l = l0 + ll, x = x0 + tx;
+        const int nxt = (Nf + MW_T * MW_X - 1) / (MW_T * MW_X);
+        const int l0 = ((int)blockIdx.x / nxt) * MW_T, x0 = ((int)blockIdx.x % nxt) * MW_T * MW_X;
+        constexpr int PT = MW_X * MW_T / (MW_THREADS / MW_T);   // points per thread
+        T rv[PT], qv[PT];
+#pragma unroll
+        for (int u = 0; u < PT; ++u) {
+            const int c = u / (MW_T / (MW_THREADS / MW_T)), ll = ty + (MW_THREADS / MW_T) * (u % (MW_T / (MW_THREADS / MW_T)));
+            const int l = l0 + ll, x = x0 + c * MW_T + tx;
+            const bool ok = l < Nc && x < Nf;
+            const long long e = ok ? (long long)l * Nf + x : 0;
+            rv[u] = ok ? r[e] : T(0);
+            qv[u] = ok ? qp[e] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < PT; ++u) {
+            const int c = u / (MW_T / (MW_THREADS / MW_T)), ll = ty + (MW_THREADS / MW_T) * (u % (MW_T / (MW_THREADS / MW_T)));
+            const int l = l0 + ll, x = x0 + c * MW_T + tx;
             if (l >= Nc || x >= Nf) continue;
-            const long long e = (long long)l * Nf + x;
-            const T v = r[e] - a * qp[e];
-            r[e] = v;
-            tile[tx][ll] = v;
+            const T v = rv[u] - a * qv[u];
+            r[(long long)l * Nf + x] = v;
+            tile[c][tx][ll] = v;
             const int i = x + 1;
-            if (i % n == 0) rcf[(long long)((l + 1) * n - 1) * Nc + (i / n - 1)] = v;
+            if ((i & (n - 1)) == 0) rcf[(long long)((l + 1) * n - 1) * Nc + ((i >> g.ln) - 1)] = v;
         }
         __syncthreads();
-        for (int xx = ty; xx < MW_T; xx += MW_THREADS / MW_T) {
-            const int x = x0 + xx, l = l0 + tx;
-            if (x < Nf && l < Nc) rfc[(long long)x * Nc + l] = tile[xx][tx];
-        }
+#pragma unroll
+        for (int c = 0; c < MW_X; ++c)
+            for (int xx = ty; xx < MW_T; xx += MW_THREADS / MW_T) {
+                const int x = x0 + c * MW_T + xx, l = l0 + tx;
+                if (x < Nf && l < Nc) rfc[(long long)x * Nc + l] = tile[c][xx][tx];
+            }
         return;
     }
-    const int nfc = Nc * Nf, total = (int)g.skel - nfc;
-    const int nb = (int)gridDim.x - nft;
-    for (int f = ((int)blockIdx.x - nft) * blockDim.x + threadIdx.x; f < total; f += nb * blockDim.x) {
-        // cf column point off the fc lines
-        const int e = nfc + f;
-        const T v = r[e] - a * qp[e];
-        r[e] = v;
-        const int yr = f / Nc, k = f % Nc;
-        const int j = yr + yr / (n - 1) + 1;
-        rcf[(j - 1) * Nc + k] = v;
+    // cf column points off the fc lines: MW_Y such rows yr per block (columns along the threads).
+    const int yr0 = ((int)blockIdx.x - nft) * MW_Y, nyr = Nf - Nc;
+    for (int k = threadIdx.x; k < Nc; k += blockDim.x) {
+        T rv[MW_Y], qv[MW_Y];
+#pragma unroll
+        for (int u = 0; u < MW_Y; ++u) {
+            const int yr = yr0 + u;
+            const int e = Nc * Nf + (yr < nyr ? yr : 0) * Nc + k;
+            rv[u] = yr < nyr ? r[e] : T(0);
+            qv[u] = yr < nyr ? qp[e] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < MW_Y; ++u) {
+            const int yr = yr0 + u;
+            if (yr >= nyr) continue;
+            const T v = rv[u] - a * qv[u];
+            r[Nc * Nf + yr * Nc + k] = v;
+            const int j = yr + yr / (n - 1) + 1;
+            rcf[(j - 1) * Nc + k] = v;
+        }
     }
 }
 
 template <typename T>
 cudaError_t track_skeleton(T* rskel, const T* qp, double alpha, const CtlCombine* c, const Geometry& g, T* rfc,
                            T* rcf, cudaStream_t st) {
-    const int nft = ((g.Nc + MW_T - 1) / MW_T) * ((g.Nf + MW_T - 1) / MW_T);
-    const unsigned ncf = grid_for(g.skel - (long long)g.Nc * g.Nf, MW_THREADS);
-    track_skeleton_kernel<T><<<nft + ncf, MW_THREADS, 0, st>>>(rskel, qp, (T)alpha, c, g, rfc, rcf, nft);
+    const int nft = ((g.Nc + MW_T - 1) / MW_T) * ((g.Nf + MW_T * MW_X - 1) / (MW_T * MW_X));
+    const int ncf = (int)((g.skel - (long long)g.Nc * g.Nf) / g.Nc);     // cf rows off the fc lines
+    track_skeleton_kernel<T><<<nft + (ncf + MW_Y - 1) / MW_Y, MW_THREADS, 0, st>>>(rskel, qp, (T)alpha, c, g, rfc,
+                                                                                  rcf, nft);
     note_launch();
     return cudaGetLastError();
 }
