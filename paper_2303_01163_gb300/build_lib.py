@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libasdsm.so")
 
-SOURCES = ["host_math.cu", "kernels_solve.cu", "kernels_grid.cu", "control.cu", "api.cu", "noalloc.cu", "cnn.cu", "fill_tc.cu", "bcr_tc.cu", "solve3d.cu"]
+SOURCES = ["host_math.cu", "kernels_solve.cu", "kernels_grid.cu", "control.cu", "api.cu", "noalloc.cu", "cnn.cu", "fill_tc.cu", "bcr_tc.cu", "fill3_tc.cu", "solve3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -36,6 +36,7 @@
 #include "asdsm.h"
 #include "asdsm_internal.h"
 #include "solve3d.h"
+#include "fill3_tc.h"
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cmath>
@@ -819,107 +820,6 @@ update_many_f32_kernel(double* __restrict__ u, const float* __restrict__ Z, long
 }
 
 // ---------------------------------------------------------------------------
-// Homogeneous cube-hole Filler of the sweeps (Algorithm 3 with zero source) as
-// one GEMM: the hole values are G f for the 6 C^2 face values f of the hole,
-// G = -A_hh^{-1} A_hs (C^3 x 6 C^2, host FP64, FP32 here), for all holes at
-// once: Out[p][h] = sum_k G[p][k] F[k][h], F gathered from the skeleton, Out
-// written straight into the grid.  Faces: west, east (x = 0, C+1), south,
-// north, down, up, each C x C with its second axis slowest.
-// ---------------------------------------------------------------------------
-constexpr int GB_M = 128, GB_N = 128, GB_K = 16, GB_T = 256;
-
-__device__ __forceinline__ void hole_origin(int h, const Geo3& g, int& x0, int& y0, int& z0) {
-    const int mc = g.mc;
-    x0 = (h % mc) * g.n; y0 = ((h / mc) % mc) * g.n; z0 = (h / (mc * mc)) * g.n;
-}
-
-__global__ void __launch_bounds__(T3) faces3_kernel(const float* __restrict__ z, Geo3 g, float* __restrict__ F) {
-    const int C = g.hc, C2 = C * C, N = g.N, n = g.n;
-    const long long H = (long long)g.mc * g.mc * g.mc, K = 6LL * C2;
-    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < K * H; e += (long long)gridDim.x * T3) {
-        const int k = (int)(e / H), h = (int)(e % H);
-        const int face = k / C2, r = k % C2, a = r % C + 1, b = r / C + 1;
-        int x0, y0, z0;
-        hole_origin(h, g, x0, y0, z0);
-        int x, y, zz;
-        if (face < 2) { x = x0 + (face == 0 ? 0 : n); y = y0 + a; zz = z0 + b; }
-        else if (face < 4) { y = y0 + (face == 2 ? 0 : n); x = x0 + a; zz = z0 + b; }
-        else { zz = z0 + (face == 4 ? 0 : n); x = x0 + a; y = y0 + b; }
-        F[e] = z[((long long)zz * N + y) * N + x];
-    }
-}
-
-__global__ void __launch_bounds__(GB_T)
-fill_g3_kernel(const float* __restrict__ G, int KP, const float* __restrict__ F, int P, int K, int H, Geo3 g,
-               float* __restrict__ z) {
-    __shared__ __align__(16) float As[GB_K][GB_M + 4];
-    __shared__ __align__(16) float Bs[GB_K][GB_N];
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    const int p0 = blockIdx.y * GB_M, h0 = blockIdx.x * GB_N;
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    // Register staging of the next tiles: A 128 x 16 (8 per thread), B 16 x 128 (8 per thread).
-    const int ap = tid >> 1, ak = (tid & 1) * 8;
-    const int bk = tid >> 4, bh = (tid & 15) * 8;
-    float av[8], bv[8];
-    auto load = [&](int k0) {
-        const int p = p0 + ap;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int k = k0 + ak + t;
-            av[t] = (p < P && k < K) ? G[(long long)p * KP + k] : 0.f;
-        }
-        const int k = k0 + bk;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int h = h0 + bh + t;
-            bv[t] = (k < K && h < H) ? F[(long long)k * H + h] : 0.f;
-        }
-    };
-    load(0);
-    for (int k0 = 0; k0 < K; k0 += GB_K) {
-        __syncthreads();
-#pragma unroll
-        for (int t = 0; t < 8; ++t) As[ak + t][ap] = av[t];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) Bs[bk][bh + t] = bv[t];
-        __syncthreads();
-        if (k0 + GB_K < K) load(k0 + GB_K);
-#pragma unroll
-        for (int kk = 0; kk < GB_K; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
-            const float a_[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b_[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a_[i], b_[j], acc[i][j]);
-        }
-    }
-    const int C = g.hc, N = g.N;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int h = h0 + tx * 8 + j;
-        if (h >= H) continue;
-        int x0, y0, z0;
-        hole_origin(h, g, x0, y0, z0);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int p = p0 + ty * 8 + i;
-            if (p >= P) continue;
-            const int x = x0 + 1 + p % C, y = y0 + 1 + (p / C) % C, zz = z0 + 1 + p / (C * C);
-            z[((long long)zz * N + y) * N + x] = acc[i][j];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -1020,9 +920,9 @@ struct Solver3D {
     PlaneFam plane[3];
     Fac line[2][3], coarse[2], hole[2];
     void* W[2] = {nullptr, nullptr};       // spline values [N_f][N_c]
-    float* G3 = nullptr;                   // hole extension operator, FP32 [C^3][KP] (rows padded to KP)
-    int G3_KP = 0;
-    float* faces = nullptr;                // [6 C^2][holes]
+    float* g3img = nullptr;                // hole extension operator G^T as the tensor-core operand image
+    float* a3img = nullptr;                // the sweeps' face values as the tensor-core operand image
+    int* tc3err = nullptr;                 // set by the tensor-core Filler when a wait timed out
     cudaStream_t fork[2] = {nullptr, nullptr};   // the second and third plane family's streams
     cudaStream_t cap = nullptr;                  // capture stream of the plane-solve graph
     cudaEvent_t evf[3] = {nullptr, nullptr, nullptr};
@@ -1182,15 +1082,16 @@ int build_factors(Solver3D* S) {
         const double sten7[7] = {S->sten.cc, S->sten.cw, S->sten.ce, S->sten.cs, S->sten.cn, S->sten.cd, S->sten.cu};
         std::vector<double> G;
         if (!hole_extension_operator_3d(g.hc, sten7, &G)) { report_error("3D: hole extension operator failed"); return ASDSM_ERR_INVALID; }
-        const int P = g.hc * g.hc * g.hc, K = 6 * g.hc * g.hc, KP = (K + 3) / 4 * 4;
-        std::vector<float> img((size_t)P * KP, 0.0f);
-        for (int p = 0; p < P; ++p)
-            for (int k = 0; k < K; ++k) img[(size_t)p * KP + k] = (float)G[(size_t)p * K + k];
-        CK3(cudaMalloc(&S->G3, img.size() * sizeof(float)));
-        CK3(cudaMemcpy(S->G3, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice));
-        S->G3_KP = KP;
-        const long long H = (long long)g.mc * g.mc * g.mc;
-        CK3(cudaMalloc(&S->faces, (size_t)K * H * sizeof(float)));
+        const int P = g.hc * g.hc * g.hc, K = 6 * g.hc * g.hc, H = g.mc * g.mc * g.mc;
+        std::vector<float> img;
+        fill3_tc_gimage(G, P, K, &img);
+        CK3(cudaMalloc(&S->g3img, img.size() * sizeof(float)));
+        CK3(cudaMemcpy(S->g3img, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice));
+        const size_t an = fill3_tc_image_floats(H, K);
+        CK3(cudaMalloc(&S->a3img, an * sizeof(float)));
+        CK3(cudaMemset(S->a3img, 0, an * sizeof(float)));   // the padding stays zero
+        CK3(cudaMalloc(&S->tc3err, sizeof(int)));
+        CK3(cudaMemset(S->tc3err, 0, sizeof(int)));
     }
     return ASDSM_OK;
 }
@@ -1451,17 +1352,32 @@ int fill3(Solver3D* S, int pi, int mode, T* z, const double* s, double* u) {
     return ASDSM_OK;
 }
 
-// Algorithm 3 with zero source on all cube holes of the FP32 grid z: v = G f per hole.
+// Algorithm 3 with zero source on all cube holes of the FP32 grid z: v = G f per
+// hole, as one tcgen05 GEMM over all holes (fill3_tc.cu).
 int fill_g3(Solver3D* S, float* z) {
     const Geo3& g = S->g;
     const int P = g.hc * g.hc * g.hc, K = 6 * g.hc * g.hc, H = g.mc * g.mc * g.mc;
     const PMark3 pm = prof3_begin(S);
-    faces3_kernel<<<g1d((long long)K * H), T3, 0, S->st>>>(z, g, S->faces);
-    const dim3 grid((H + GB_N - 1) / GB_N, (P + GB_M - 1) / GB_M);
-    fill_g3_kernel<<<grid, GB_T, 0, S->st>>>(S->G3, S->G3_KP, S->faces, P, K, H, g, z);
-    note_launch(2);
-    CK3(cudaGetLastError());
+    Fill3TcArgs a{};
+    a.z = z; a.zout = z; a.gimg = S->g3img; a.aimg = S->a3img;
+    a.N = g.N; a.mc = g.mc; a.n = g.n; a.hc = g.hc;
+    a.P = P; a.K = K; a.H = H;
+    a.KC = (K + 31) / 32; a.PT = (P + 127) / 128; a.HT = (H + 127) / 128;
+    a.err = S->tc3err;
+    CK3(fill3_tc(a, S->st));
     prof3_end(S, pm, P3_FILL, 4.0 * ((double)K * H * 2.0 + (double)P * H + (double)P * K), 2.0 * P * (double)K * H);
+    return ASDSM_OK;
+}
+
+// The tensor-core Filler's timeout flag, read after the stream drained.
+int tc3_status(Solver3D* S) {
+    int f = 0;
+    CK3(cudaMemcpyAsync(&f, S->tc3err, sizeof(int), cudaMemcpyDeviceToHost, S->st));
+    CK3(cudaStreamSynchronize(S->st));
+    if (f) {
+        report_error("3D tensor-core Filler: a wait timed out");
+        return ASDSM_ERR_CUDA;
+    }
     return ASDSM_OK;
 }
 
@@ -1898,7 +1814,9 @@ int s3_set_opts(Solver3D* S, const asdsm_opts* o) {
 }
 
 int s3_solve(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
-    return S->opts.precision == ASDSM_FP64 ? solve3<double>(S, s, u, stats) : solve3<float>(S, s, u, stats);
+    const int rc = S->opts.precision == ASDSM_FP64 ? solve3<double>(S, s, u, stats) : solve3<float>(S, s, u, stats);
+    if (int tc = tc3_status(S)) return tc;
+    return rc;
 }
 
 int s3_initial_guess(Solver3D* S, const double* s, double* u) {
@@ -1981,8 +1899,10 @@ int submesh3(Solver3D* S, int pi, int mesh, const double* in, double* out) {
 
 int s3_submesh_solve(Solver3D* S, int mesh, const double* in, double* out) {
     if (mesh < 0 || mesh > 8) return ASDSM_ERR_INVALID;
-    return S->opts.precision == ASDSM_FP64 ? submesh3<double>(S, 0, mesh, in, out)
-                                           : submesh3<float>(S, 1, mesh, in, out);
+    const int rc = S->opts.precision == ASDSM_FP64 ? submesh3<double>(S, 0, mesh, in, out)
+                                                   : submesh3<float>(S, 1, mesh, in, out);
+    if (int tc = tc3_status(S)) return tc;
+    return rc;
 }
 
 int s3_profile(Solver3D* S, int enable) {
@@ -2034,8 +1954,9 @@ void s3_destroy(Solver3D* S) {
         if (e) cudaEventDestroy(e);
     for (cudaStream_t fs : {S->fork[0], S->fork[1], S->cap})
         if (fs) cudaStreamDestroy(fs);
-    if (S->G3) cudaFree(S->G3);
-    if (S->faces) cudaFree(S->faces);
+    if (S->g3img) cudaFree(S->g3img);
+    if (S->a3img) cudaFree(S->a3img);
+    if (S->tc3err) cudaFree(S->tc3err);
     for (cudaEvent_t e : S->evpool) cudaEventDestroy(e);
     for (cudaEvent_t ev : {S->ev0, S->ev1, S->ev2})
         if (ev) cudaEventDestroy(ev);

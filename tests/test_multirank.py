@@ -64,7 +64,7 @@ def test_single_rank_defaults(monkeypatch):
 def test_family_roofline_arithmetic():
     """bench.py's roofline entries: achieved = algorithmic work / summed event
     time, peaks from the measured figures (TF32 = bf16 x 1.1/2.25) or the
-    derived FP32 FMA peak."""
+    derived FP32 FMA peak; the tensor-core Filler against HBM."""
     import bench
     peaks = {"hbm_gbs": 6756.2, "bf16_tflops": 1914.9}
     r = bench.family_roofline("residual", {"launches": 2, "ms": 0.4, "bytes": 1.24e9, "flops": 0.0},
@@ -75,7 +75,9 @@ def test_family_roofline_arithmetic():
                               peaks, "measured", 152, 2070.0)
     fp32 = 152 * 128 * 2 * 2070e6 / 1e12
     assert r["bound"] == "alu" and abs(r["peak"] - fp32) < 1e-9 and abs(r["achieved"] - 20.0) < 1e-9
+    # The tensor-core Filler (~24 flop/byte, below the TF32 ridge) against HBM, its tensor rate beside.
     r = bench.family_roofline("fill_tc", {"launches": 1, "ms": 0.03, "bytes": 7.5e7, "flops": 1.77e9},
                               peaks, "measured", 152, 2070.0)
-    assert r["bound"] == "tensor" and abs(r["peak"] - 1914.9 * 1.1 / 2.25) < 1e-9
-    assert abs(r["achieved"] - 59.0) < 1e-9
+    assert r["bound"] == "hbm" and abs(r["achieved"] - 2500.0) < 1e-9 and abs(r["peak"] - 6756.2) < 1e-12
+    assert abs(r["tensor"]["peak_tflops"] - 1914.9 * 1.1 / 2.25) < 1e-9
+    assert abs(r["tensor"]["achieved_tflops"] - 59.0) < 1e-9
