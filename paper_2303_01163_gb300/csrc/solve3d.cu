@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(T3) convert3_kernel(const Ts* __restrict__ a, 
 //   planes:  the plane families' right-hand sides from the tracked residual;
 //   update:  u += sum_j c_j Z_j over the interior (FP64 accumulation).
 // ---------------------------------------------------------------------------
-constexpr int DK_CHUNKS = 64;      // skeleton chunks of the many-vector dots
+constexpr int DK_CHUNKS = 256;     // skeleton chunks of the many-vector dots
 constexpr int DK_VEC = 8;          // vectors per CTA
 
 template <typename T>
@@ -663,8 +663,10 @@ combine_many_kernel(const T* __restrict__ q, T* __restrict__ V, long long n, lon
     block_sum_pair(rr, 0.0, partials);
 }
 
+// rs (FP64) or, when rh is given, the float pairs rh + rl of the FP32 path.
 template <typename T>
-__global__ void __launch_bounds__(T3) planes_from_skel_kernel(const double* __restrict__ rs, Geo3 g, T* F0, T* F1,
+__global__ void __launch_bounds__(T3) planes_from_skel_kernel(const double* __restrict__ rs, const float* __restrict__ rh,
+                                                              const float* __restrict__ rl, Geo3 g, T* F0, T* F1,
                                                               T* F2) {
     const int Nf = g.Nf, n = g.n;
     const long long P = g.plane;
@@ -673,7 +675,8 @@ __global__ void __launch_bounds__(T3) planes_from_skel_kernel(const double* __re
         const bool row_coarse = j % n == 0 || l % n == 0;
         for (int i = 1 + threadIdx.x; i <= Nf; i += T3) {
             if (!row_coarse && i % n != 0) continue;
-            const T rt = (T)rs[skel3_index(i, j, l, g)];
+            const long long si = skel3_index(i, j, l, g);
+            const T rt = rh ? (T)(rh[si] + rl[si]) : (T)rs[si];
             if (i % n == 0) F0[(long long)(i / n - 1) * P + (long long)(l - 1) * Nf + (j - 1)] = rt;
             if (j % n == 0) F1[(long long)(j / n - 1) * P + (long long)(l - 1) * Nf + (i - 1)] = rt;
             if (l % n == 0) F2[(long long)(l / n - 1) * P + (long long)(j - 1) * Nf + (i - 1)] = rt;
@@ -724,25 +727,24 @@ __device__ __forceinline__ void acc_prod(F2& s, float a, float b) {
 __device__ __forceinline__ double f2_value(const F2& s) { return (double)s.h + (double)s.l; }
 
 __global__ void __launch_bounds__(T3)
-dots_many_f32_kernel(const float* __restrict__ q, const double* __restrict__ r, const float* __restrict__ V, long long n,
-                     long long vstride, int k, double* __restrict__ partials) {
+dots_many_f32_kernel(const float* __restrict__ q, const float* __restrict__ rhv, const float* __restrict__ rlv,
+                     const float* __restrict__ V, long long n, long long vstride, int k, double* __restrict__ partials) {
     __shared__ double red[T3 / 32][2 * DK_VEC + 3];
     const int chunk = blockIdx.x, j0 = blockIdx.y * DK_VEC;
     const long long len = (n + DK_CHUNKS - 1) / DK_CHUNKS, e0 = chunk * len, e1 = min(n, e0 + len);
     const int nv = min(DK_VEC, k - j0);
-    F2 aq[DK_VEC], ar[DK_VEC], a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
-    double a2 = 0.0;
+    F2 aq[DK_VEC], ar[DK_VEC], a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, a2 = {0.f, 0.f};
 #pragma unroll
     for (int t = 0; t < DK_VEC; ++t) { aq[t] = {0.f, 0.f}; ar[t] = {0.f, 0.f}; }
     for (long long e = e0 + threadIdx.x; e < e1; e += T3) {
         const float qv = q[e];
-        const double rd = r[e];
-        const float rh = (float)rd, rl = (float)(rd - (double)rh);
+        const float rh = rhv[e], rl = rlv[e];    // r's float pair (no FP64 work per element here)
         if (blockIdx.y == 0) {
             acc_prod(a0, qv, qv);
             acc_prod(a1, qv, rh);
             a1.l = fmaf(qv, rl, a1.l);
-            a2 = fma(rd, rd, a2);
+            acc_prod(a2, rh, rh);
+            a2.l = fmaf(2.0f * rh, rl, a2.l);
         }
 #pragma unroll
         for (int t = 0; t < DK_VEC; ++t)
@@ -753,16 +755,23 @@ dots_many_f32_kernel(const float* __restrict__ q, const double* __restrict__ r, 
                 ar[t].l = fmaf(rl, v, ar[t].l);
             }
     }
-    double acc[2 * DK_VEC + 3];
-    acc[0] = f2_value(a0); acc[1] = f2_value(a1); acc[2] = a2;
+    // Warp sums of the pairs with TwoSum (FP32 only), FP64 once per warp and value.
+    F2 acc[2 * DK_VEC + 3];
+    acc[0] = a0; acc[1] = a1; acc[2] = a2;
 #pragma unroll
-    for (int t = 0; t < DK_VEC; ++t) { acc[3 + t] = f2_value(aq[t]); acc[3 + DK_VEC + t] = f2_value(ar[t]); }
+    for (int t = 0; t < DK_VEC; ++t) { acc[3 + t] = aq[t]; acc[3 + DK_VEC + t] = ar[t]; }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int t = 0; t < 2 * DK_VEC + 3; ++t) {
-        double v = acc[t];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-        if (lane == 0) red[w][t] = v;
+        float hi = acc[t].h, lo = acc[t].l;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_down_sync(0xFFFFFFFFu, hi, o), l2 = __shfl_down_sync(0xFFFFFFFFu, lo, o);
+            const float sm = hi + h2, bp = sm - hi;
+            const float er = (hi - (sm - bp)) + (h2 - bp);
+            hi = sm;
+            lo = lo + l2 + er;
+        }
+        if (lane == 0) red[w][t] = (double)hi + (double)lo;
     }
     __syncthreads();
     if (threadIdx.x < 2 * DK_VEC + 3) {
@@ -777,10 +786,24 @@ dots_many_f32_kernel(const float* __restrict__ q, const double* __restrict__ r, 
     }
 }
 
-// V_k = (q - sum_j beta_j V_j) * inv_nu (beta as float pairs), r -= alpha V_k.
+// r as float pairs (hi, lo): rh = fl(r), rl = fl(r - rh); |r - rh - rl| <= 2^-48 |r|.
+__global__ void __launch_bounds__(T3) split_pairs_kernel(const double* __restrict__ r, long long n,
+                                                         float* __restrict__ rh, float* __restrict__ rl) {
+    for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < n; e += (long long)gridDim.x * T3) {
+        const double v = r[e];
+        const float h = (float)v;
+        rh[e] = h;
+        rl[e] = (float)(v - (double)h);
+    }
+}
+
+// V_k = (q - sum_j beta_j V_j) * inv_nu (beta as float pairs) and the tracked
+// residual, held as float pairs (rh, rl), r -= alpha V_k (alpha as a float pair):
+// FP32 operations only (TwoProd, TwoSum, then Fast2Sum to renormalise).
 __global__ void __launch_bounds__(T3)
 combine_many_f32_kernel(const float* __restrict__ q, float* __restrict__ V, long long n, long long vstride, int k,
-                        const float2* __restrict__ beta, double inv_nu, double alpha, double* __restrict__ r) {
+                        const float2* __restrict__ beta, float inv_nu, float ah, float al, float* __restrict__ rh,
+                        float* __restrict__ rl) {
     for (long long e = blockIdx.x * (long long)T3 + threadIdx.x; e < n; e += (long long)gridDim.x * T3) {
         F2 acc = {q[e], 0.f};
         for (int j = 0; j < k; ++j) {
@@ -789,9 +812,18 @@ combine_many_f32_kernel(const float* __restrict__ q, float* __restrict__ V, long
             acc_prod(acc, -b.x, v);
             acc.l = fmaf(-b.y, v, acc.l);
         }
-        const float vk = (float)(f2_value(acc) * inv_nu);
+        const float vk = fmaf(acc.h, inv_nu, acc.l * inv_nu);
         V[(long long)k * vstride + e] = vk;
-        r[e] = fma(-alpha, (double)vk, r[e]);
+        // (h, l) - (ah + al) vk
+        const float p = ah * vk;
+        const float pe = fmaf(ah, vk, -p);            // ah vk = p + pe exactly
+        const float h = rh[e], l = rl[e];
+        const float s = h - p, z = s - h;
+        const float t = (h - (s - z)) - (p + z);      // TwoSum error of h - p
+        const float lo = ((l + t) - pe) - al * vk;
+        const float sh = s + lo;                      // Fast2Sum (|s| >= |lo| in practice)
+        rl[e] = lo - (sh - s);
+        rh[e] = sh;
     }
 }
 
@@ -939,6 +971,8 @@ struct Solver3D {
         void* V = nullptr;               // their orthonormalised skeleton images, [m][skel]
         void* q = nullptr;               // the new image A e on the skeleton [skel]
         double* rs = nullptr;            // tracked residual on the skeleton [skel], FP64
+        float* rsh = nullptr;            // the same as float pairs (hi, lo), for the FP32 GCR products
+        float* rsl = nullptr;
         int m = 0;
     } w[2];
     double* dcoef = nullptr;             // [1024] step coefficients / Gram-Schmidt weights
@@ -1121,6 +1155,10 @@ int ensure_work3(Solver3D* S, int pi) {
     if ((rc = al(&w.uh, g.NN)) || (rc = al(&w.q, g.skel)) || (rc = al(&w.Z, m * g.NN)) || (rc = al(&w.V, m * g.skel)))
         return rc;
     CK3(cudaMalloc(&w.rs, (size_t)g.skel * sizeof(double)));
+    if (sizeof(T) == 4) {
+        CK3(cudaMalloc(&w.rsh, (size_t)g.skel * sizeof(float)));
+        CK3(cudaMalloc(&w.rsl, (size_t)g.skel * sizeof(float)));
+    }
     w.m = m;
     w.ready = true;
     return ASDSM_OK;
@@ -1138,6 +1176,9 @@ void free_work3(Solver3D* S, int pi) {
     fr(w.Xc); fr(w.Yc); fr(w.Xh); fr(w.Yh); fr(w.uh); fr(w.q); fr(w.Z); fr(w.V);
     if (w.rs) cudaFree(w.rs);
     w.rs = nullptr;
+    if (w.rsh) cudaFree(w.rsh);
+    if (w.rsl) cudaFree(w.rsl);
+    w.rsh = w.rsl = nullptr;
     w.ready = false;
 }
 
@@ -1566,6 +1607,11 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
             {
                 const PMark3 pm = prof3_begin(S);
                 if (int rc = residual3<T>(S, pi, s, u, true)) return rc;
+                if constexpr (sizeof(T) == 4) {
+                    split_pairs_kernel<<<g1d(g.skel), T3, 0, st>>>(w.rs, g.skel, w.rsh, w.rsl);
+                    note_launch();
+                    CK3(cudaGetLastError());
+                }
                 prof3_end(S, pm, P3_RESID, nf3 * 16.0 + 8.0 * g.skel + sizeof(T) * 3.0 * g.Nc * g.plane, 14.0 * nf3);
             }
             if (int rc = read3(S, S->dsmall, 2)) return rc;
@@ -1618,7 +1664,8 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
         skel_apply3_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(z, g, S->sten, (T*)w.q);
         const dim3 dgrid(DK_CHUNKS, std::max(1, (kc + DK_VEC - 1) / DK_VEC));
         if constexpr (sizeof(T) == 4)
-            dots_many_f32_kernel<<<dgrid, T3, 0, st>>>((const float*)w.q, w.rs, V, g.skel, g.skel, kc, S->dpart);
+            dots_many_f32_kernel<<<dgrid, T3, 0, st>>>((const float*)w.q, w.rsh, w.rsl, V, g.skel, g.skel, kc,
+                                                       S->dpart);
         else
             dots_many_kernel<T><<<dgrid, T3, 0, st>>>((const T*)w.q, w.rs, V, g.skel, g.skel, kc, S->dpart);
         const int ncol = 3 + 2 * kc;
@@ -1668,8 +1715,9 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
             if constexpr (sizeof(T) == 4) {
                 if (kc > 0)
                     if (int rc = upload_pairs(S, beta.data(), kc)) return rc;
+                const float ah = (float)alpha_, al = (float)(alpha_ - (double)ah);
                 combine_many_f32_kernel<<<g1d(g.skel), T3, 0, st>>>((const float*)w.q, V, g.skel, g.skel, kc, S->dcoef2,
-                                                                   1.0 / nu, alpha_, w.rs);
+                                                                   (float)(1.0 / nu), ah, al, w.rsh, w.rsl);
             } else {
                 if (kc > 0)
                     CK3(cudaMemcpyAsync(S->dcoef, beta.data(), (size_t)kc * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1695,8 +1743,10 @@ int solve3(Solver3D* S, const double* s, double* u, asdsm_stats* stats) {
             continue;
         }
         const PMark3 pm_pl = prof3_begin(S);
-        planes_from_skel_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(w.rs, g, (T*)w.F[0], (T*)w.F[1],
-                                                                                   (T*)w.F[2]);
+        // The FP32 path tracks the residual as float pairs between true residuals.
+        planes_from_skel_kernel<T><<<grid_rows((long long)g.Nf * g.Nf), T3, 0, st>>>(
+            w.rs, sizeof(T) == 4 ? w.rsh : nullptr, sizeof(T) == 4 ? w.rsl : nullptr, g, (T*)w.F[0], (T*)w.F[1],
+            (T*)w.F[2]);
         note_launch();
         CK3(cudaGetLastError());
         prof3_end(S, pm_pl, P3_GCR, 8.0 * g.skel + sizeof(T) * 3.0 * g.Nc * g.plane, 0.0);
