@@ -950,6 +950,8 @@ struct Solver3D {
     Sten3 sten{};
     Lift3 lift{};
     PlaneFam plane[3];
+    BcrTune ptune[2][2] = {};                // plane-block level shapes [precision][block size - 1]
+    bool ptuned[2] = {false, false};
     Fac line[2][3], coarse[2], hole[2];
     void* W[2] = {nullptr, nullptr};       // spline values [N_f][N_c]
     float* g3img = nullptr;                // hole extension operator G^T as the tensor-core operand image
@@ -1297,7 +1299,7 @@ int plane_solve3(Solver3D* S, int pi, int a, double* partials, int* nblocks, cud
         note_launch();
         CK3(cudaGetLastError());
         BcrSys<T> sys = sys3<T>(pf.fac[pi][b], w.Xb[a], bs == 1 ? (void*)(Y + (long long)k * P) : w.Yb[a]);
-        CK3(bcr_solve<T>(&sys, 1, st));
+        CK3(bcr_solve<T>(&sys, 1, st, S->ptuned[pi] ? &S->ptune[pi][bs - 1] : nullptr));
         if (bs == 2) {
             deinterleave_kernel<T><<<g1d(P), T3, 0, st>>>((const T*)w.Yb[a], P, Y + (long long)k * P,
                                                          Y + (long long)(k + 1) * P);
@@ -1333,11 +1335,62 @@ int planes3_enqueue(Solver3D* S, int pi, bool norms, cudaStream_t st) {
     return ASDSM_OK;
 }
 
+// Launch shapes of the plane blocks' BCR levels, timed once per precision
+// before the plane-solve graph is captured: per level and direction the
+// fastest of TM in {16, 64} rows per CTA and KS in {1, 2, 4, 8} CTAs splitting
+// the reduction, for the real (C = N_f) and the complex-pair (C = 2 N_f) blocks.
+template <typename T>
+int tune_planes3(Solver3D* S, int pi) {
+    if (S->ptuned[pi]) return ASDSM_OK;
+    auto& w = S->w[pi];
+    const PlaneFam& pf = S->plane[0];
+    cudaEvent_t e0, e1;
+    CK3(cudaEventCreate(&e0));
+    CK3(cudaEventCreate(&e1));
+    int rc = ASDSM_OK;
+    for (int bs = 1; bs <= 2 && rc == ASDSM_OK; ++bs) {
+        BcrTune& tu = S->ptune[pi][bs - 1];
+        tu = BcrTune{};
+        tu.num_sms = S->num_sms;
+        size_t b = 0;
+        while (b < pf.bs.size() && pf.bs[b] != bs) ++b;
+        if (b == pf.bs.size()) continue;                // no block of this size
+        const Fac& f = pf.fac[pi][b];
+        const BcrSys<T> sys = sys3<T>(f, w.Xb[0], w.Yb[0]);
+        const int nk = (f.C + 31) / 32;
+        for (int dir = 0; dir < 2 && rc == ASDSM_OK; ++dir)
+            for (int l = 0; l < (dir ? f.L : f.L - 1); ++l) {
+                float best = 1e30f;
+                int bestv = 0;
+                for (int tm : {16, 64})
+                    for (int ks : {1, 2, 4, 8}) {
+                        if (ks > (dir ? 2 : 1) * nk) continue;
+                        tu.cfg[dir][l] = (tm << 8) | ks;
+                        cudaError_t e = bcr_level<T>(&sys, 1, l, dir == 1, &tu, S->st);   // warm-up
+                        if (e == cudaSuccess) e = cudaEventRecord(e0, S->st);
+                        for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = bcr_level<T>(&sys, 1, l, dir == 1, &tu, S->st);
+                        if (e == cudaSuccess) e = cudaEventRecord(e1, S->st);
+                        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                        if (e != cudaSuccess) { rc = report_cuda_error(e); break; }
+                        if (ms < best) { best = ms; bestv = tu.cfg[dir][l]; }
+                    }
+                tu.cfg[dir][l] = bestv;
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == ASDSM_OK) S->ptuned[pi] = true;
+    return rc;
+}
+
 // The plane-family solves are the same launches every sweep (fixed buffers),
 // so after one plain run they are captured once as a CUDA graph and replayed
 // (not while profiling, whose event records would be captured too).
 template <typename T>
 int planes3(Solver3D* S, int pi, bool norms) {
+    if (int rc = tune_planes3<T>(S, pi)) return rc;
     const PMark3 pm = prof3_begin(S);
     double flops = 0.0;
     for (int a = 0; a < 3; ++a)
