@@ -421,6 +421,25 @@ def interior(grid3d):
     return np.asarray(grid3d)[1:-1, 1:-1, 1:-1].reshape(-1)
 
 
+def fine_system3d(N: int, alpha, beta, s_grid, g_grid):
+    """A_ff and b_ff of eq. (1.1) in 3D on the fine mesh alone (Section 2.3 in 3D).
+
+    The same operator and lifting as ``Discretisation3D`` builds for its fine
+    mesh, without the submesh operators and factorizations, so that a grid of
+    257^3 points fits in a few GB and seconds."""
+    M = N - 1
+    fine = np.arange(1, M)
+    A = operator_3d(M - 1, 1.0 / M, M - 1, 1.0 / M, M - 1, 1.0 / M, alpha, beta)
+    b = rhs_on_mesh(Meshes3D._product(fine, fine, fine), (1.0 / M,) * 3, alpha, beta, s_grid, g_grid, M)
+    return A, b
+
+
+def residual_grid3d(N: int, alpha, beta, s_grid, u_grid):
+    """r = b_ff - A_ff u on the interior, from the full grid u (its boundary is g)."""
+    A, b = fine_system3d(N, alpha, beta, s_grid, u_grid)
+    return b - A @ interior(u_grid), b
+
+
 def to_grid(u_ff, g_grid):
     out = np.array(g_grid, dtype=np.float64, copy=True)
     n = out.shape[0] - 2

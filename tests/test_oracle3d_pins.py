@@ -207,3 +207,32 @@ def test_filler_pass_in_3d_removes_the_hole_residual_and_keeps_the_skeleton():
     r1 = disc.residual(b[0], u1)
     assert np.linalg.norm(disc.P_holes @ r1) <= 1e-12 * np.linalg.norm(r0)
     np.testing.assert_array_equal(disc.P_skel @ u1, disc.P_skel @ u0)
+
+
+def test_fine_only_residual_matches_the_full_discretisation_and_vanishes_on_quadratics():
+    """residual_grid3d (the fine system alone, for grids too large for the
+    submesh factorizations) against Discretisation3D on a small grid, and
+    exactly zero on a quadratic field: centred second and first differences
+    are exact for quadratics, so the field solves the discrete system."""
+    N, mc = 17, 4
+    alpha, beta = (0.8, 1.7, 0.5), (2.5, -4.0, 1.5)
+    rng = np.random.default_rng(3)
+    s, u = rng.standard_normal((N, N, N)), rng.standard_normal((N, N, N))
+    disc = o3.Discretisation3D(N, mc, alpha, beta)
+    b_ff = disc.rhs(s, u)[0]
+    r, b = o3.residual_grid3d(N, alpha, beta, s, u)
+    assert np.allclose(b, b_ff, rtol=1e-14, atol=0)
+    assert np.allclose(r, disc.residual(b_ff, o3.interior(u)), rtol=1e-13, atol=1e-10)
+
+    N = 33
+    x = np.linspace(0.0, 1.0, N)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    w = 1.0 + X * X - 2.0 * Y * Z + 3.0 * Z * Z - X * Y
+    # -alpha . (w_xx, w_yy, w_zz) + beta . grad w
+    s = (-(alpha[0] * 2.0 + alpha[2] * 6.0)
+         + beta[0] * (2.0 * X - Y) + beta[1] * (-2.0 * Z - X) + beta[2] * (-2.0 * Y + 6.0 * Z))
+    r, b = o3.residual_grid3d(N, alpha, beta, s, w)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+    # a wrong sign of one first-difference term is visible
+    r_bad, _ = o3.residual_grid3d(N, alpha, (beta[0], -beta[1], beta[2]), s, w)
+    assert np.linalg.norm(r_bad) > 1e-3 * np.linalg.norm(b)
