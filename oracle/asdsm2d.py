@@ -67,6 +67,20 @@ R18 Hole residual.  In exact arithmetic the residual vanishes in the holes
     the hole systems with the hole part of the current residual and zeroes
     it (down to rounding).  The GCR cycle
     restarts afterwards.
+R27 Residual smoothing (Example 2 of Section 4, where the paper reports that
+    an unspecified artificial smoothing of the residual lowers the point where
+    plain ASDSM stagnates).  Two readings, both off by default: "knots"
+    replaces the projected residual at every cross point of a line by the
+    mean of its two fine-axis neighbours on that line (the irregularity the
+    paper shows sits at the coarse points); "lines" filters every projected
+    line with [1, 2, 1]/4 along its fine axis (zero beyond the boundary).
+R28 Extra anisotropic meshes for the extrapolation (the remark after
+    Algorithm 2, meshes Omega^{kh,H} and Omega^{H,kh}), with k = 2: the
+    samples f2, c2 of the solutions on Omega^{2h,H} and Omega^{H,2h} at the
+    coarse points remove each family's own fine-axis h^2 term,
+        u_hat = (4 fc - f2)/3 + (4 cf - c2)/3 - cc,
+    which extrapolates towards the continuous solution rather than towards
+    the fine discrete solution that ASDSM converges to.
 """
 from __future__ import annotations
 
@@ -273,7 +287,7 @@ class Discretisation2D:
         now agree at the cross points, and together they cover the skeleton
         Omega^{h,H} U Omega^{H,h}, holes left at zero (R11)."""
         at_cc = (self.P_fc_cc @ u_fc, self.P_cf_cc @ u_cf)
-        u_hat = at_cc[choice] if u_cc is None else at_cc[0] + at_cc[1] - u_cc
+        u_hat = at_cc[choice] if u_cc is None else extrapolate_knots(at_cc[0], at_cc[1], u_cc)
         fc = u_fc + self.spline_fc(u_hat - at_cc[0])
         cf = u_cf + self.spline_cf(u_hat - at_cc[1])
         # Cross points belong to both families; they are written once, from fc.
@@ -306,14 +320,50 @@ class Discretisation2D:
             u_t = self.skeleton(u_fc, u_cf, self.lu_cc.solve(b_cc))
         return self.filler(u_t, b_ff)
 
-    def correction(self, r, choice):
+    def correction(self, r, choice, smoothing=None):
         """The ASDSM correction of a sweep (Section 3.2): Algorithm 1 applied to
         the error equations, i.e. right-hand sides P_fc r and P_cf r on the two
-        anisotropic meshes, zero boundary data and zero source in the holes."""
-        return self.initial_guess(np.zeros_like(r), self.P_ff_fc @ r, self.P_ff_cf @ r, None, choice)
+        anisotropic meshes, zero boundary data and zero source in the holes;
+        with `smoothing` the projections are smoothed first (R27)."""
+        r_fc, r_cf = self.P_ff_fc @ r, self.P_ff_cf @ r
+        if smoothing is not None:
+            r_fc, r_cf = smooth_projections(self.m, r_fc, r_cf, smoothing)
+        return self.initial_guess(np.zeros_like(r), r_fc, r_cf, None, choice)
 
     def residual(self, b_ff, u):
         return b_ff - self.A_ff @ u
+
+
+def smooth_projections(m: Meshes2D, r_fc, r_cf, mode: str):
+    """R27: the projected residuals smoothed along each line's fine axis.
+
+    r_fc lists Omega^{h,H} x fastest (one row per coarse line y = jH), r_cf
+    lists Omega^{H,h} x fastest (one row per fine y), so the fine axis is the
+    second axis of the first and the first axis of the second."""
+    F = np.array(r_fc, dtype=np.float64).reshape(m.Nc, m.Nf)
+    C = np.array(r_cf, dtype=np.float64).reshape(m.Nf, m.Nc).T      # one row per coarse column x = iH
+    out = []
+    for V in (F, C):
+        P = np.pad(V, ((0, 0), (1, 1)))                              # zero beyond the boundary
+        if mode == "knots":
+            W = V.copy()
+            cross = np.arange(1, m.mc) * m.n - 1                     # positions of x = kH on the fine axis
+            W[:, cross] = 0.5 * (P[:, cross] + P[:, cross + 2])
+        elif mode == "lines":
+            W = 0.25 * P[:, :-2] + 0.5 * V + 0.25 * P[:, 2:]
+        else:
+            raise ValueError(f"unknown smoothing {mode!r}")
+        out.append(W)
+    return out[0].reshape(-1), out[1].T.reshape(-1)
+
+
+def extrapolate_knots(fc, cf, cc, f2=None, c2=None):
+    """u_hat at the coarse points: R7 from the samples of u_fc, u_cf and u_cc,
+    or R28 when the samples f2, c2 of the Omega^{2h,H}, Omega^{H,2h} solutions
+    are given too."""
+    if f2 is None:
+        return fc + cf - cc
+    return (4.0 * fc - f2) / 3.0 + (4.0 * cf - c2) / 3.0 - cc
 
 
 def normalised_families(u_fc, u_cf):
@@ -341,14 +391,15 @@ def stagnated(hist, window, factor):
 def asdsm(disc: Discretisation2D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, seed=0,
           hole_fix_ratio=0.25, hole_fix_growth=4.0, stagnation_window=10,
           stagnation_factor=1e-3,
-          u0=None, record_iterates=False):
+          u0=None, record_iterates=False, smoothing=None):
     """Algorithm 4 (ASDSM) with the readings R13-R15 and R18.
 
     The iterate starts from Algorithm 1 (or u0).  Each sweep takes the fine
     residual r = b_ff - A_ff u, builds the correction e from it (Section 3.2)
     and moves u along e by a least-squares step on the skeleton rows, where
     A e can be non-zero (Prop. 3.1): the clamped optimal scaling s_hat >= 0 of
-    Section 3.2 when accel_m = 1, restarted GCR(accel_m) otherwise (R15).
+    Section 3.2 when accel_m = 1, restarted GCR(accel_m) otherwise (R15);
+    `smoothing` selects a reading of R27 for the projected residuals.
 
     b = (b_ff, b_fc, b_cf, b_cc).  Returns (u, info); info holds the relative
     residual history (entry k is the residual of iterate k), the choice bits,
@@ -387,7 +438,7 @@ def asdsm(disc: Discretisation2D, b, *, tol=1e-10, max_sweeps=200, accel_m=1, se
             k += 1
             continue
         bit = choice_bit(seed, k)
-        e = disc.correction(r, bit)
+        e = disc.correction(r, bit, smoothing)
         q = sk @ (disc.A_ff @ e)     # A e on the skeleton rows
         rs = sk @ r
         if accel_m == 1:
