@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
-    res = subprocess.run([nvcc, "-shared", *ARCH, *objs, "-o", tmp], capture_output=True, text=True)
+    res = subprocess.run([nvcc, "-shared", *ARCH, *objs, "-lpthread", "-o", tmp], capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{res.stderr}")
     os.replace(tmp, LIB)

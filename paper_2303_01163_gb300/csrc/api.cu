@@ -19,7 +19,6 @@
 #include <cmath>
 #include <cstring>
 #include <cstdio>
-#include <cstdlib>
 #include <string>
 #include <vector>
 #include <algorithm>
@@ -41,6 +40,8 @@ struct DevBcr {
     void* Ti = nullptr;                          // FP32: tcgen05 level kernel image (BcrSys)
     int TKC = 0, TCB = 0;
     int* tc_err = nullptr;
+    void* Dt = nullptr;                          // FP32: the dense tail map (BcrSys::Dt)
+    int tail_rt = 0, tail_ld = 0;
     double wl[kMaxLevels] = {}, wr[kMaxLevels] = {};
     int R = 0, C = 0, L = 0;
     BcrCoefs k{};                                // the system itself (refinement residuals)
@@ -213,7 +214,31 @@ BcrSys<T> sys_of(const DevBcr& d, void* X, void* Y, int nsys = 1) {
     s.Mw = (const float*)d.Mw; s.Bw = (const float*)d.Bw;
     s.KW = d.KW; s.CW = d.CW;
     s.Ti = (const float*)d.Ti; s.TKC = d.TKC; s.TCB = d.TCB; s.tc_err = d.tc_err;
+    s.Dt = (const float*)d.Dt; s.tail_rt = d.tail_rt; s.tail_ld = d.tail_ld;
     return s;
+}
+
+// The last levels of the FP32 anisotropic solves as one dense map
+// (bcr_tail_map): kTailRows rows are left after the forward levels 0..L-4,
+// and levels L-3..L-1 of both directions become one product with a
+// (7 C) x (7 C) matrix (12.7 MB at C = 255) in place of five launches.
+// Systems with fewer than kTailMinC coarse lines keep every level: their
+// sweeps are short, and the changed rounding moved a slowly converging
+// 65 x 65 instance with mc = 2 from convergence to the stagnation test.
+constexpr int kTailRows = 7, kTailMinC = 31;
+int upload_tail(const BcrFactors& f, DevBcr* d) {
+    if (f.L < 4 || f.C < kTailMinC) return ASDSM_OK;
+    std::vector<double> D;
+    if (!bcr_tail_map(f, kTailRows, &D)) return ASDSM_OK;      // not finite in FP64: every level runs
+    const int n = kTailRows * f.C, ld = (n + 3) / 4 * 4;
+    std::vector<float> img((size_t)n * ld, 0.0f);
+    for (int r = 0; r < n; ++r)
+        for (int q = 0; q < n; ++q) img[(size_t)r * ld + q] = (float)D[(size_t)r * n + q];
+    CK(cudaMalloc(&d->Dt, img.size() * sizeof(float)));
+    CK(cudaMemcpy(d->Dt, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice));
+    d->tail_rt = kTailRows;
+    d->tail_ld = ld;
+    return ASDSM_OK;
 }
 
 // Hole factors (and the tuned CTA shape) into a FillArgs.
@@ -1621,7 +1646,8 @@ int asdsm_setup(const asdsm_desc* desc, const asdsm_opts* opts, void* stream, as
     if ((rc = upload_bcr<double>(ffc, &h->fc[0])) || (rc = upload_bcr<float>(ffc, &h->fc[1])) ||
         (rc = upload_bcr<double>(fcf, &h->cf[0])) || (rc = upload_bcr<float>(fcf, &h->cf[1])) ||
         (rc = upload_bcr<double>(fcc, &h->cc[0])) || (rc = upload_bcr<float>(fcc, &h->cc[1])) ||
-        (rc = upload_bcr<double>(fho, &h->hole[0])) || (rc = upload_bcr<float>(fho, &h->hole[1])))
+        (rc = upload_bcr<double>(fho, &h->hole[0])) || (rc = upload_bcr<float>(fho, &h->hole[1])) ||
+        (rc = upload_tail(ffc, &h->fc[1])) || (rc = upload_tail(fcf, &h->cf[1])))
         return fail(rc);
     // Spline moment operator, stored transposed ([knot][moment]) for the merge kernel.
     const std::vector<double> Sm = spline_moment_operator(g.mc);
@@ -2196,7 +2222,7 @@ void asdsm_destroy(asdsm_handle* h) {
     auto fr = [](void* p) { if (p) cudaFree(p); };
     for (int p = 0; p < 2; ++p) {
         DevBcr* ds[4] = {&h->fc[p], &h->cf[p], &h->cc[p], &h->hole[p]};
-        for (auto* d : ds) { fr(d->Mt); fr(d->Bt); fr(d->Mw); fr(d->Bw); fr(d->Ti); }
+        for (auto* d : ds) { fr(d->Mt); fr(d->Bt); fr(d->Mw); fr(d->Bw); fr(d->Ti); fr(d->Dt); }
         fr(h->Sm[p]);
         auto& w = h->w[p];
         void* bufs[] = {w.Xfc, w.Xcf, w.Yfc, w.Ycf, w.Xcc, w.Ycc, w.E1, w.E2, w.M1, w.M2, w.rskel, w.q, w.rfull, w.zv};

@@ -31,6 +31,14 @@ struct BcrFactors {
 };
 bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, double tu, BcrFactors* out);
 
+// The tail of the reduction as one dense map.  For rt = 2^t - 1 <= R, the
+// forward levels l0..L-2 and the back substitution L-1..l0 (l0 = L - t) touch
+// only the rt rows i = k 2^l0 (k = 1..rt) and map their reduced right-hand
+// sides to their solutions linearly; D is that map, (rt C) x (rt C)
+// row-major, entry ((k-1) C + c, (k'-1) C + c') from row k', column c' of the
+// input to row k, column c of the output.  False on a non-finite entry.
+bool bcr_tail_map(const BcrFactors& f, int rt, std::vector<double>* D);
+
 // The same with a dense C x C diagonal block:  a x_{i-1} + K x_i + c x_{i+1} = f_i
 // (K row-major; the 3D extension's submesh systems have Kronecker-sum blocks).
 bool make_bcr_dense(int R, double a, double c, int C, const std::vector<double>& K, BcrFactors* out);
@@ -77,6 +85,10 @@ struct BcrSys {
     const float* Ti;
     int TKC, TCB;
     int* tc_err;       // set to 1 when a tensor-core kernel's wait timed out
+    // FP32 only: bcr_tail_map for tail_rt rows, [tail_rt C][tail_ld] (rows
+    // padded with zeros to tail_ld, a multiple of 4); null: every level runs.
+    const float* Dt;
+    int tail_rt, tail_ld;
 };
 
 // Stencil coefficients of A_ff (5-point, Section 2.3): A u = cc u_c + cw u_w + ce u_e + cs u_s + cn u_n.

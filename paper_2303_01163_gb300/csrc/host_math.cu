@@ -8,11 +8,14 @@
 //   tridiagonal with blocks a I, (d I + T_col), c I.  With R = 2^L - 1 rows,
 //   cyclic reduction keeps the Toeplitz structure at every level, so one set
 //   of C x C factors per level serves every row (and every hole).
+// * The tail of that reduction as one dense map (the last levels, where only
+//   a few rows are left, as a single matrix-vector product on the device).
 // * The moment operator of the not-a-knot cubic spline used by "Spline" in
 //   Algorithm 2 (knot values zero at both ends).
 #include "asdsm_internal.h"
 #include <cmath>
 #include <algorithm>
+#include <thread>
 
 namespace asdsm {
 
@@ -251,6 +254,77 @@ bool make_bcr(int R, double a, double d, double c, int C, double tl, double td, 
     }
     for (double v : out->Mt) if (!std::isfinite(v)) return false;
     for (double v : out->Bt) if (!std::isfinite(v)) return false;
+    return true;
+}
+
+bool bcr_tail_map(const BcrFactors& f, int rt, std::vector<double>* D) {
+    int lt = 0;
+    while ((1 << lt) - 1 < rt) ++lt;
+    if (rt < 1 || (1 << lt) - 1 != rt || lt > f.L) return false;
+    const int C = f.C, L = f.L, l0 = L - lt, n = rt * C;
+    const size_t n2 = (size_t)C * C;
+    D->assign((size_t)n * n, 0.0);
+    // The map is linear and its columns are independent: apply the tail levels
+    // to the unit vectors, a contiguous range of columns per thread.
+    auto work = [&](int col0, int col1) {
+        const int w = col1 - col0;
+        if (w <= 0) return;
+        const size_t rowsz = (size_t)C * w;             // one tail row: [C][w]
+        std::vector<double> X((size_t)(rt + 2) * rowsz, 0.0), Y(X.size(), 0.0), v(rowsz);
+        auto row = [&](std::vector<double>& A, int k) { return A.data() + (size_t)k * rowsz; };
+        for (int col = col0; col < col1; ++col) row(X, col / C + 1)[(size_t)(col % C) * w + (col - col0)] = 1.0;
+        // out[c][j] += sum_k in[k][j] F[k][c]  (F: a transposed factor, [k][c] = M[c][k])
+        auto apply = [&](const double* F, const double* in, double* out) {
+            for (int k = 0; k < C; ++k) {
+                const double* ir = in + (size_t)k * w;
+                const double* fr = F + (size_t)k * C;
+                for (int c = 0; c < C; ++c) {
+                    const double fv = fr[c];
+                    if (fv == 0.0) continue;
+                    double* orow = out + (size_t)c * w;
+                    for (int j = 0; j < w; ++j) orow[j] += fv * ir[j];
+                }
+            }
+        };
+        auto neighbours = [&](std::vector<double>& A, int k, int step, int l) {
+            const double* a = row(A, k - step);
+            const double* b = row(A, k + step);
+            for (size_t e = 0; e < rowsz; ++e) v[e] = -(f.wl[l] * a[e] + f.wr[l] * b[e]);
+        };
+        // Forward levels l0..L-2: rows i = 2s(t+1), i.e. tail rows k = 2 step (t+1).
+        for (int l = l0; l + 1 < L; ++l) {
+            const int step = 1 << (l - l0);
+            for (int k = 2 * step; k <= rt + 1 - 2 * step; k += 2 * step) {
+                neighbours(X, k, step, l);
+                apply(f.Mt.data() + (size_t)l * n2, v.data(), row(X, k));
+            }
+        }
+        // Back substitution L-1..l0: rows i = s(2t+1); tail rows 0 and rt+1 stay zero.
+        for (int l = L - 1; l >= l0; --l) {
+            const int step = 1 << (l - l0);
+            for (int k = step; k <= rt + 1 - step; k += 2 * step) {
+                double* y = row(Y, k);
+                std::fill(y, y + rowsz, 0.0);
+                apply(f.Bt.data() + (size_t)l * n2, row(X, k), y);
+                neighbours(Y, k, step, l);
+                apply(f.Mt.data() + (size_t)l * n2, v.data(), y);
+            }
+        }
+        for (int k = 1; k <= rt; ++k)
+            for (int c = 0; c < C; ++c) {
+                const double* y = row(Y, k) + (size_t)c * w;
+                double* d = D->data() + ((size_t)(k - 1) * C + c) * n + col0;
+                for (int j = 0; j < w; ++j) d[j] = y[j];
+            }
+    };
+    const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int chunk = (n + nth - 1) / nth;
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work, std::min(n, t * chunk), std::min(n, (t + 1) * chunk));
+    work(0, std::min(n, chunk));
+    for (auto& th : pool) th.join();
+    for (double x : *D)
+        if (!std::isfinite(x)) return false;
     return true;
 }
 

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
 #include <cstdio>
+#include <algorithm>
 
 namespace cg = cooperative_groups;
 
@@ -537,6 +538,94 @@ cudaError_t launch_ks(int ks, dim3 grid, const BcrSys<T>& g0, const BcrSys<T>& g
     }
 }
 
+// The tail of the reduction (bcr_tail_map) as one dense matrix-vector
+// product per system: y = D x over the rt rows i = k 2^l0, one warp per
+// output row, x staged in shared memory, a fixed summation order per row.
+// Launched with programmatic dependent launch: the first TL_PF float4 of each
+// lane's share of its row of D (constant data) are loaded before the wait for
+// the forward level that produced x, the rest in batches of TL_PF afterwards.
+constexpr int TL_WARPS = 8, TL_PF = 8;
+
+__global__ void __launch_bounds__(32 * TL_WARPS) bcr_tail_kernel(BcrSys<float> g0, BcrSys<float> g1, int ngroups) {
+    extern __shared__ __align__(16) float xs[];
+    int z = blockIdx.y;
+    const BcrSys<float>* gp = &g0;
+    if (ngroups > 1 && z >= g0.nsys) { gp = &g1; z -= g0.nsys; }
+    const BcrSys<float>& g = *gp;
+    const bool sys_ok = z < g.nsys;
+    const int C = g.C, rt = g.tail_rt, ld = g.tail_ld, n = rt * C, n4 = ld >> 2;
+    const int s0 = (g.R + 1) / (rt + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * TL_WARPS + warp;
+    const bool ok = sys_ok && r < n;
+    const float4* Drow = reinterpret_cast<const float4*>(g.Dt) + (size_t)(ok ? r : 0) * n4;
+    asm volatile("griddepcontrol.launch_dependents;");
+    float4 pf[TL_PF];
+#pragma unroll
+    for (int u = 0; u < TL_PF; ++u) {
+        const int q = lane + 32 * u;
+        pf[u] = ok && q < n4 ? __ldg(Drow + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const float* X = g.X + (size_t)(sys_ok ? z : 0) * g.stride;
+    float* Y = g.Y + (size_t)(sys_ok ? z : 0) * g.stride;
+    for (int q = threadIdx.x; q < ld; q += blockDim.x) {
+        float v = 0.f;
+        if (sys_ok && q < n) v = X[(size_t)((q / C + 1) * s0 - 1) * C + q % C];
+        xs[q] = v;
+    }
+    __syncthreads();
+    if (!ok) return;
+    const float4* x4 = reinterpret_cast<const float4*>(xs);
+    float acc = 0.f;
+    auto dot4 = [&](const float4& d, int q) {
+        const float4 xv = x4[q];
+        acc = fmaf(d.x, xv.x, acc);
+        acc = fmaf(d.y, xv.y, acc);
+        acc = fmaf(d.z, xv.z, acc);
+        acc = fmaf(d.w, xv.w, acc);
+    };
+#pragma unroll
+    for (int u = 0; u < TL_PF; ++u)
+        if (lane + 32 * u < n4) dot4(pf[u], lane + 32 * u);
+    for (int base = 32 * TL_PF; base < n4; base += 32 * TL_PF) {
+#pragma unroll
+        for (int u = 0; u < TL_PF; ++u) {
+            const int q = base + lane + 32 * u;
+            pf[u] = q < n4 ? __ldg(Drow + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < TL_PF; ++u)
+            if (base + lane + 32 * u < n4) dot4(pf[u], base + lane + 32 * u);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) Y[(size_t)((r / C + 1) * s0 - 1) * C + r % C] = acc;
+}
+
+cudaError_t launch_tail(const BcrSys<float>* groups, int ngroups, cudaStream_t st) {
+    int maxn = 0, maxld = 0, nsys = 0;
+    for (int q = 0; q < ngroups; ++q) {
+        maxn = std::max(maxn, groups[q].tail_rt * groups[q].C);
+        maxld = std::max(maxld, groups[q].tail_ld);
+        nsys += groups[q].nsys;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((maxn + TL_WARPS - 1) / TL_WARPS, nsys, 1);
+    cfg.blockDim = dim3(32 * TL_WARPS);
+    cfg.dynamicSmemBytes = (size_t)maxld * sizeof(float);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const BcrSys<float>& g1 = ngroups > 1 ? groups[1] : groups[0];
+    cudaError_t e = cudaLaunchKernelEx(&cfg, bcr_tail_kernel, groups[0], g1, ngroups);
+    note_launch();
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <typename T, bool kBackward>
 cudaError_t launch_level(const BcrSys<T>* groups, int ngroups, int level, const BcrTune* tune, cudaStream_t st) {
     int maxC = 0, maxRows = 0, nsys = 0;
@@ -614,10 +703,27 @@ cudaError_t bcr_solve(const BcrSys<T>* groups, int ngroups, cudaStream_t st, con
     for (int q = 0; q < ngroups; ++q) L = groups[q].L > L ? groups[q].L : L;
     for (int q = 0; q < ngroups; ++q)
         if (groups[q].L != L) return cudaErrorInvalidValue;   // groups in one call share the level count
+    // Levels l0..L-1 of both directions become one dense product when every
+    // group carries the tail map (FP32 only).
+    int l0 = L;
+    if constexpr (sizeof(T) == 4) {
+        bool tail = true;
+        for (int q = 0; q < ngroups; ++q)
+            tail = tail && groups[q].Dt && groups[q].tail_rt == groups[0].tail_rt && groups[q].tail_rt > 0;
+        if (tail) {
+            int lt = 0;
+            while ((1 << lt) - 1 < groups[0].tail_rt) ++lt;
+            if (lt <= L) l0 = L - lt;
+        }
+    }
     cudaError_t e;
-    for (int l = 0; l + 1 < L; ++l)
+    for (int l = 0; l + 1 < L && l < l0; ++l)
         if ((e = launch_level<T, false>(groups, ngroups, l, tune, st)) != cudaSuccess) return e;
-    for (int l = L - 1; l >= 0; --l)
+    if constexpr (sizeof(T) == 4) {
+        if (l0 < L && (e = launch_tail(reinterpret_cast<const BcrSys<float>*>(groups), ngroups, st)) != cudaSuccess)
+            return e;
+    }
+    for (int l = (l0 < L ? l0 : L) - 1; l >= 0; --l)
         if ((e = launch_level<T, true>(groups, ngroups, l, tune, st)) != cudaSuccess) return e;
     return cudaSuccess;
 }
