@@ -1135,7 +1135,7 @@ int host_sweeps(asdsm_handle* h, SolveRun& r) {
             const double pred = bnorm > 0 ? std::sqrt(p2) / bnorm : std::sqrt(p2);
             if (rel > 2.0 * pred) { defer = false; stag_hold = win; }
         }
-        if (defer && rel < 100.0 * op.tol) defer = false;
+        if (defer && rel < kDeferStop * op.tol) defer = false;
         cycle_ended = false;
         rr_skel = r2 - rh2;
         rh2c = rh2;

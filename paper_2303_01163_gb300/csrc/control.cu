@@ -68,7 +68,7 @@ __global__ void ctl_after_residual_kernel(SweepCtl* c, const double* __restrict_
             const double pred = c->bnorm > 0 ? sqrt(p2) / c->bnorm : sqrt(p2);
             if (rel > 2.0 * pred) { c->defer = 0; c->stag_hold = c->window; }
         }
-        if (c->defer && rel < 100.0 * c->tol) c->defer = 0;
+        if (c->defer && rel < kDeferStop * c->tol) c->defer = 0;
         c->cycle_ended = 0;
         c->rr_skel = sums[0] - sums[1];
         c->rh2 = sums[1];

@@ -61,10 +61,13 @@ def test_batch_equals_single_solves_bitwise(lib, prec_name):
 
 
 def test_batch_instances_meet_the_parity_bars(lib):
+    # Holes of 31 x 31 (mc = 2, 4, 8): the 65^2 instance needs about 200 sweeps and
+    # its slow tail near 1e-9 can meet the 10-sweep stagnation test, depending on the
+    # rounding of its FP32 solves; the batch runs with the 30-sweep window for that.
     sizes = [65, 129, 257]
     probs, mcs = _problems(sizes, seed0=7)
     with lib.BatchSolver([(p.N, mc, p.alpha, p.beta) for p, mc in zip(probs, mcs)], precision=lib.MIXED,
-                         tol=1e-10, max_sweeps=2000) as bs:
+                         tol=1e-10, max_sweeps=2000, stagnation_window=30) as bs:
         us = [_dev(p.g) for p in probs]
         rc, stats = bs.solve([_dev(p.s) for p in probs], us)
     assert rc == lib.OK
