@@ -289,6 +289,24 @@ int asdsm_profile_read(asdsm_handle* h, asdsm_kprof* out, int cap);
  * for bad arguments or if the QR iteration does not converge. */
 int asdsm_real_schur(int n, const double* A, double* Q, double* T);
 
+/* The tail of the block cyclic reduction that solves the anisotropic
+ * systems of eq. (2.4) (host FP64, no device work, no handle), as the FP32
+ * solves apply it.  The system is
+ *   a x_{i-1} + (d I + T) x_i + c x_{i+1} = f_i,  i = 1..R,  x_0 = x_{R+1} = 0,
+ * with x_i, f_i vectors of C values and T = tridiag(tl, td, tu) (C x C);
+ * coef = {a, d, c, tl, td, tu}; R = 2^L - 1.  For rt = 2^t - 1 <= R the last
+ * t levels of the reduction involve only the rt rows i = k (R+1)/(rt+1),
+ * k = 1..rt, and map their reduced right-hand sides to their solutions
+ * linearly; D receives that map, (rt C) x (rt C) row-major, entry
+ * ((k-1) C + c, (k'-1) C + c') from row k', component c' of the input to
+ * row k, component c of the output.  For a right-hand side that vanishes
+ * off those rows the reduced right-hand sides are f itself, so D is then
+ * the restriction of the system's inverse to them.  D: host array of
+ * (rt C)^2 doubles.  Returns ASDSM_OK, or ASDSM_ERR_INVALID for sizes that
+ * break these rules (1 <= C <= 512, R <= 32767) or a system the reduction
+ * cannot factor. */
+int asdsm_bcr_tail_map(int R, int C, const double* coef, int rt, double* D);
+
 /* Failure-path self-test of the tensor-core kernels (no counterpart in the
  * paper): on the handle's stream, one CTA takes tensor memory as the
  * tcgen05 kernels do and waits on an mbarrier that nothing arrives at, with

@@ -95,6 +95,9 @@ def load() -> ctypes.CDLL:
     lib.asdsm_real_schur.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]
     lib.asdsm_real_schur.restype = ctypes.c_int
+    lib.asdsm_bcr_tail_map.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double)]
+    lib.asdsm_bcr_tail_map.restype = ctypes.c_int
     lib.asdsm_selftest_wait_timeout.argtypes = [P, ctypes.c_longlong]
     lib.asdsm_selftest_wait_timeout.restype = ctypes.c_int
     lib.asdsm_tune_check.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_int]

@@ -1992,6 +1992,16 @@ int asdsm_real_schur(int n, const double* A, double* Q, double* T) {
     return ASDSM_OK;
 }
 
+int asdsm_bcr_tail_map(int R, int C, const double* coef, int rt, double* D) {
+    if (R < 1 || R > 32767 || C < 1 || C > 512 || rt < 1 || rt > R || !coef || !D) return ASDSM_ERR_INVALID;
+    BcrFactors f;
+    if (!make_bcr(R, coef[0], coef[1], coef[2], C, coef[3], coef[4], coef[5], &f)) return ASDSM_ERR_INVALID;
+    std::vector<double> d;
+    if (!bcr_tail_map(f, rt, &d)) return ASDSM_ERR_INVALID;
+    std::memcpy(D, d.data(), d.size() * sizeof(double));
+    return ASDSM_OK;
+}
+
 int asdsm_selftest_wait_timeout(asdsm_handle* h, long long limit_ns) {
     if (!h || limit_ns <= 0 || limit_ns > 2000000000LL) return ASDSM_ERR_INVALID;
     if (h->s3) { g_last_error = "not available for the 3D extension"; return ASDSM_ERR_INVALID; }
