@@ -865,6 +865,8 @@ namespace {
 // BCR factors on the device in one precision.
 struct Fac {
     void* Mt = nullptr; void* Bt = nullptr;
+    void* Dt = nullptr;                 // FP32 plane blocks: the dense tail map (BcrSys::Dt)
+    int tail_rt = 0, tail_ld = 0;
     double wl[kMaxLevels] = {}, wr[kMaxLevels] = {};
     int R = 0, C = 0, L = 0;
 };
@@ -888,7 +890,8 @@ int upload_fac(const BcrFactors& f, Fac* d) {
 void free_fac(Fac& d) {
     if (d.Mt) cudaFree(d.Mt);
     if (d.Bt) cudaFree(d.Bt);
-    d.Mt = d.Bt = nullptr;
+    if (d.Dt) cudaFree(d.Dt);
+    d.Mt = d.Bt = d.Dt = nullptr;
 }
 
 template <typename T>
@@ -899,6 +902,7 @@ BcrSys<T> sys3(const Fac& d, void* X, void* Y, int nsys = 1) {
     for (int l = 0; l < d.L; ++l) { s.wl[l] = (T)d.wl[l]; s.wr[l] = (T)d.wr[l]; }
     s.R = d.R; s.C = d.C; s.L = d.L; s.nsys = nsys;
     s.stride = (long long)d.R * d.C;
+    s.Dt = (const float*)d.Dt; s.tail_rt = d.tail_rt; s.tail_ld = d.tail_ld;
     return s;
 }
 
@@ -1007,7 +1011,11 @@ int build_factors(Solver3D* S) {
     const double* be = S->desc.beta;
     Op1 fine[3], crs[3];
     for (int a = 0; a < 3; ++a) { fine[a] = op1(al[a], be[a], h); crs[a] = op1(al[a], be[a], H); }
-    struct Job { int kind, a, blk; BcrFactors f; bool ok = false; };
+    // Plane blocks with at least 31 columns and 15 rows also get the dense tail of
+    // their FP32 reduction (bcr_tail_map: the last three levels of both directions
+    // as one product with a (7 C) x (7 C) map, rows padded to a multiple of 4).
+    constexpr int kTailRows = 7;
+    struct Job { int kind, a, blk; BcrFactors f; bool ok = false; std::vector<float> timg; int tld = 0; };
     std::vector<Job> jobs;
     // Plane families: Schur form of the coarse-axis operator, then one system per block.
     for (int a = 0; a < 3; ++a) {
@@ -1062,6 +1070,14 @@ int build_factors(Solver3D* S) {
                     }
                 jb.ok = make_bcr_dense(Nf, fine[qa].lo, fine[qa].up, C, K, &jb.f);
             }
+            std::vector<double> D;
+            if (jb.ok && jb.f.L >= 4 && jb.f.C >= 31 && bcr_tail_map(jb.f, kTailRows, &D)) {
+                const int n = kTailRows * jb.f.C;
+                jb.tld = (n + 3) / 4 * 4;
+                jb.timg.assign((size_t)n * jb.tld, 0.0f);
+                for (int r = 0; r < n; ++r)
+                    for (int q = 0; q < n; ++q) jb.timg[(size_t)r * jb.tld + q] = (float)D[(size_t)r * n + q];
+            }
         } else if (jb.kind == 1) {
             // Line family: rows along the fine axis a, columns (cq, cp) coarse.
             jb.ok = make_bcr_dense(g.Nf, fine[jb.a].lo, fine[jb.a].up, g.Nc * g.Nc,
@@ -1104,7 +1120,14 @@ int build_factors(Solver3D* S) {
                    : jb.kind == 1 ? &S->line[pi][jb.a] : jb.kind == 2 ? &S->coarse[pi] : &S->hole[pi];
             const int rc = pi == 0 ? upload_fac<double>(jb.f, d) : upload_fac<float>(jb.f, d);
             if (rc) return rc;
+            if (pi == 1 && !jb.timg.empty()) {
+                CK3(cudaMalloc(&d->Dt, jb.timg.size() * sizeof(float)));
+                CK3(cudaMemcpy(d->Dt, jb.timg.data(), jb.timg.size() * sizeof(float), cudaMemcpyHostToDevice));
+                d->tail_rt = kTailRows;
+                d->tail_ld = jb.tld;
+            }
         }
+        std::vector<float>().swap(jb.timg);
     }
     for (int a = 0; a < 3; ++a) {
         if (int rc = upload_vec3<double>(S->plane[a].Q, &S->plane[a].Qd[0])) return rc;
