@@ -236,3 +236,28 @@ def test_fine_only_residual_matches_the_full_discretisation_and_vanishes_on_quad
     # a wrong sign of one first-difference term is visible
     r_bad, _ = o3.residual_grid3d(N, alpha, (beta[0], -beta[1], beta[2]), s, w)
     assert np.linalg.norm(r_bad) > 1e-3 * np.linalg.norm(b)
+
+
+def test_extrapolation_weights_per_axis_under_the_error_model():
+    """R21's weights axis by axis: when each mesh's solution carries its own
+    error a hx^2 + b hy^2 + c hz^2 (hx, hy, hz its spacings), the combination
+    at the knots and at the other line points is u + (a + b + c) h^2, the fine
+    mesh's value.  Exact fields (a = b = c = 0) only check that the weights sum
+    to one; here each axis's coefficient must come out h^2, so a wrong sign or
+    one line family in place of another fails."""
+    N, mc = 17, 4
+    disc = o3.Discretisation3D(N, mc, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0))
+    h, H = disc.m.h, disc.m.H
+    a, b, c = 0.7, -1.9, 2.6
+    x = np.linspace(0.0, 1.0, N)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    u = np.sin(X + 2.0 * Y) * np.cos(Z)
+    val = lambda sx, sy, sz: u + a * sx**2 + b * sy**2 + c * sz**2
+    U_plane = {"x": val(H, h, h), "y": val(h, H, h), "z": val(h, h, H)}     # P_a coarse in a
+    U_line = {"x": val(h, H, H), "y": val(H, h, H), "z": val(H, H, h)}      # L_a fine in a only
+    _, _, u_hat = disc.skeleton(U_plane, U_line, val(H, H, H))
+    msk = disc._masks()
+    inter = (msk["x"].astype(int) + msk["y"] + msk["z"]) >= 2
+    want = u + (a + b + c) * h**2
+    assert inter.sum() > 0
+    assert np.allclose(u_hat[inter], want[inter], rtol=0, atol=1e-13)
