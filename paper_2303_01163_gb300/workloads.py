@@ -21,6 +21,9 @@ Section 4; there is no dataset):
 * ``manufactured_sine_3d`` / ``random_fourier_3d`` - the 3D analogues.
 * ``polynomial_2d`` - u = p(x) q(y) with quadratic p, q: central differences
   are exact for it on every uniform mesh, which pins the whole initial guess.
+* ``manufactured_variable_2d`` - the second setting of Example 1: coefficients
+  that vary in space (alpha_1 = 1 + x^2, alpha_2 = 2 + x y, beta_1 = 2 - x,
+  beta_2 = 1 + y, given as functions of (x, y)) and u = sin(4 pi x + 4 pi y).
 """
 from __future__ import annotations
 
@@ -96,6 +99,26 @@ def manufactured_shifted_sine_2d(N: int, alpha=(1.0, 1.0), beta=(1.0, 1.0), k: f
     s = (ax + ay) * w**2 * u + (bx + by) * w * np.cos(w * X + w * Y)
     return Problem(2, N, tuple(alpha), tuple(beta), s, _boundary_only(u), u,
                    name=f"shiftsine2d_k{k}_N{N}")
+
+
+def variable_coefficients_example1():
+    """alpha_i(x, y), beta_i(x, y) of the second setting of Example 1 (Section 4)."""
+    alpha = (lambda x, y: 1.0 + x * x, lambda x, y: 2.0 + x * y)
+    beta = (lambda x, y: 2.0 - x, lambda x, y: 1.0 + y)
+    return alpha, beta
+
+
+def manufactured_variable_2d(N: int, k: float = 4.0) -> Problem:
+    """u = sin(k pi x + k pi y) with the coefficients of the second setting of
+    Example 1; s = -alpha_1 u_xx - alpha_2 u_yy + beta_1 u_x + beta_2 u_y."""
+    alpha, beta = variable_coefficients_example1()
+    X, Y = _grid2(N)
+    w = k * np.pi
+    u = np.sin(w * X + w * Y)
+    du = w * np.cos(w * X + w * Y)          # u_x = u_y
+    d2u = -w * w * u                        # u_xx = u_yy
+    s = (-alpha[0](X, Y) * d2u - alpha[1](X, Y) * d2u + beta[0](X, Y) * du + beta[1](X, Y) * du)
+    return Problem(2, N, alpha, beta, s, _boundary_only(u), u, name=f"variable2d_k{k}_N{N}")
 
 
 def polynomial_2d(N: int, alpha=(1.0, 1.0), beta=(1.0, 1.0),
