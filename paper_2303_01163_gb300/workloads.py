@@ -23,7 +23,8 @@ Section 4; there is no dataset):
   are exact for it on every uniform mesh, which pins the whole initial guess.
 * ``manufactured_variable_2d`` - the second setting of Example 1: coefficients
   that vary in space (alpha_1 = 1 + x^2, alpha_2 = 2 + x y, beta_1 = 2 - x,
-  beta_2 = 1 + y, given as functions of (x, y)) and u = sin(4 pi x + 4 pi y).
+  beta_2 = 1 + y, given as functions of (x, y)) and u = sin(4 pi x + 4 pi y);
+  ``manufactured_variable_3d`` - the same for the second setting of Example 4.
 """
 from __future__ import annotations
 
@@ -119,6 +120,26 @@ def manufactured_variable_2d(N: int, k: float = 4.0) -> Problem:
     d2u = -w * w * u                        # u_xx = u_yy
     s = (-alpha[0](X, Y) * d2u - alpha[1](X, Y) * d2u + beta[0](X, Y) * du + beta[1](X, Y) * du)
     return Problem(2, N, alpha, beta, s, _boundary_only(u), u, name=f"variable2d_k{k}_N{N}")
+
+
+def variable_coefficients_example4():
+    """alpha_i(x, y, z), beta_i(x, y, z) of the second setting of Example 4 (Section 4)."""
+    alpha = (lambda x, y, z: 1.0 + x * x, lambda x, y, z: 2.0 + x * y, lambda x, y, z: 3.0 - x * y * z)
+    beta = (lambda x, y, z: 2.0 - x, lambda x, y, z: 1.0 + y, lambda x, y, z: 2.0 - x + y * z)
+    return alpha, beta
+
+
+def manufactured_variable_3d(N: int, k: float = 4.0) -> Problem:
+    """u = sin(k pi (x + y + z)) with the coefficients of the second setting of
+    Example 4; s = sum_i (-alpha_i u_{x_i x_i} + beta_i u_{x_i}).  Grids [z, y, x]."""
+    alpha, beta = variable_coefficients_example4()
+    X, Y, Z = _grid3(N)
+    w = k * np.pi
+    u = np.sin(w * (X + Y + Z))
+    du = w * np.cos(w * (X + Y + Z))        # every first derivative
+    d2u = -w * w * u                        # every second derivative
+    s = sum(-alpha[a](X, Y, Z) * d2u + beta[a](X, Y, Z) * du for a in range(3))
+    return Problem(3, N, alpha, beta, s, _boundary_only(u), u, name=f"variable3d_k{k}_N{N}")
 
 
 def polynomial_2d(N: int, alpha=(1.0, 1.0), beta=(1.0, 1.0),
