@@ -17,6 +17,9 @@
 // reduction dimension among the 8 CTAs of a thread-block cluster, whose
 // partial tiles are summed in a fixed order through distributed shared
 // memory.  Used for the anisotropic families (R = N_f rows, C = N_c).
+// bcr_tail_kernel: the last three levels of both directions of an FP32 solve
+// as one dense product with the precomputed map of bcr_tail_map, where the
+// system carries it.
 // fill_holes_kernel: the Filler of Algorithm 3.  A warp segment of C+1 lanes
 // owns one hole (lane c = hole column c); 32/(C+1) holes share a warp.  The
 // factors of every level stay resident in shared memory for all holes a
