@@ -303,8 +303,8 @@ int asdsm_real_schur(int n, const double* A, double* Q, double* T);
  * off those rows the reduced right-hand sides are f itself, so D is then
  * the restriction of the system's inverse to them.  D: host array of
  * (rt C)^2 doubles.  Returns ASDSM_OK, or ASDSM_ERR_INVALID for sizes that
- * break these rules (1 <= C <= 512, R <= 32767) or a system the reduction
- * cannot factor. */
+ * break these rules (1 <= C <= 512, R <= 32767, rt C <= 8192) or a system the
+ * reduction cannot factor. */
 int asdsm_bcr_tail_map(int R, int C, const double* coef, int rt, double* D);
 
 /* Failure-path self-test of the tensor-core kernels (no counterpart in the

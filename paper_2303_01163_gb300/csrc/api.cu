@@ -1993,7 +1993,8 @@ int asdsm_real_schur(int n, const double* A, double* Q, double* T) {
 }
 
 int asdsm_bcr_tail_map(int R, int C, const double* coef, int rt, double* D) {
-    if (R < 1 || R > 32767 || C < 1 || C > 512 || rt < 1 || rt > R || !coef || !D) return ASDSM_ERR_INVALID;
+    if (R < 1 || R > 32767 || C < 1 || C > 512 || rt < 1 || rt > R || (long long)rt * C > 8192 || !coef || !D)
+        return ASDSM_ERR_INVALID;
     BcrFactors f;
     if (!make_bcr(R, coef[0], coef[1], coef[2], C, coef[3], coef[4], coef[5], &f)) return ASDSM_ERR_INVALID;
     std::vector<double> d;

@@ -71,6 +71,7 @@ def test_tail_map_rejects_bad_sizes(lib):
     coef = np.ascontiguousarray(_coef(1.0, 0.0, 1 / 16, 1.0, 0.0, 1 / 4), dtype=np.float64)
     D = np.zeros(100 * 100)                      # room for any map these sizes could describe
     p = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    # rt not of the form 2^t - 1; rt > R; R not 2^L - 1; no columns; no tail rows
-    for R, C, rt in [(15, 3, 5), (15, 3, 31), (14, 3, 7), (15, 0, 7), (15, 3, 0)]:
+    # rt not of the form 2^t - 1; rt > R; R not 2^L - 1; no columns; no tail rows; a map
+    # too large to hold (rt C > 8192)
+    for R, C, rt in [(15, 3, 5), (15, 3, 31), (14, 3, 7), (15, 0, 7), (15, 3, 0), (32767, 512, 31)]:
         assert lib.asdsm_bcr_tail_map(R, C, p(coef), rt, p(D)) != 0, (R, C, rt)
